@@ -1,0 +1,111 @@
+"""Seeded synthetic highway scenes and workload presets.
+
+This module holds the inputs of the batch trajectory optimizer and nothing of
+its arithmetic: random draws of the ego state, the obstacle vehicles and the
+goal tuples, plus the named workload presets.  Both the CUDA path's tests and
+benchmarks and the FP64 oracle read their inputs from here.
+
+The scenes stand in for the paper's IDM and NGSIM traffic (Sec. IV,
+"Implementation Details"), which are not available: a straight 4-lane highway
+in the road-attached frame (Sec. III assumption 1), lane width 3.5 m, lane
+centres y in {-5.25, -1.75, 1.75, 5.25} m (y positive to the left), obstacle
+vehicles moving parallel to the centre line at constant velocity (Sec. III
+assumption 3).
+
+Layouts (all float64 here; the CUDA binding casts to float32):
+  ego   [4]     y0, v0, psi0, acc0   (x0 = 0 by convention)
+  obst  [m, 4]  x0, y0, vx, vy at t = 0
+  goals [B, 3]  y_g, v_g, a_g at the end of the horizon
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LANE_WIDTH = 3.5
+LANES = np.array([-5.25, -1.75, 1.75, 5.25])
+
+# Physical and solver parameters shared by the workloads.  v_min, v_max,
+# a_max and rho are not given in the paper (Eq. v_bound; Sec. III-E); the
+# values here are this implementation's choices.
+BASE_PARAMS = dict(
+    T=8.0,           # horizon [s]
+    N=100,           # samples
+    n=12,            # Bernstein coefficients per axis (11th order)
+    rho=1.0,         # penalty rho_xy
+    a=5.6, b=2.5,    # ellipse semi-axes incl. inflation [m]
+    v_min=0.1, v_max=30.0, a_max=4.0,
+    iters=100,
+    tol=0.0,
+    check_every=10,
+)
+
+META_ABS = dict(kind=2, w1=1.0, w2=0.25, v_ref=20.0, y_ref=-5.25, psi_max_deg=13.0)
+
+
+@dataclass
+class Scene:
+    ego: np.ndarray
+    obst: np.ndarray
+    goals: np.ndarray
+    params: dict = field(default_factory=dict)
+    meta: dict = field(default_factory=dict)
+    name: str = ""
+    seed: int = 0
+
+
+def _spawn_obstacles(rng, m, x_lo, x_hi, v_lo, v_hi, ego_y, a, b, clearance=1.2):
+    """m obstacles on random lanes; an obstacle whose ellipse-normalised
+    distance to the ego at t = 0 is below `clearance` is drawn again."""
+    out = np.zeros((m, 4))
+    for j in range(m):
+        while True:
+            x0 = rng.uniform(x_lo, x_hi)
+            y0 = LANES[rng.integers(0, 4)]
+            if np.hypot(x0 / a, (y0 - ego_y) / b) >= clearance:
+                break
+        out[j] = (x0, y0, rng.uniform(v_lo, v_hi), 0.0)
+    return out
+
+
+def scene_small(seed: int = 0, m: int = 10, B: int = 11) -> Scene:
+    """One scene, 10 obstacles x ~ U(-30, 120) m, v ~ U(5, 20) m/s; ego on a
+    random lane centre with v ~ U(10, 20) m/s; B = 11 goals = the first 11 of
+    (lane right to left) x (speed 15, 20, 25 m/s), zero terminal acceleration."""
+    rng = np.random.default_rng(seed)
+    p = dict(BASE_PARAMS)
+    ego_y = LANES[rng.integers(0, 4)]
+    ego = np.array([ego_y, rng.uniform(10.0, 20.0), 0.0, 0.0])
+    obst = _spawn_obstacles(rng, m, -30.0, 120.0, 5.0, 20.0, ego_y, p["a"], p["b"])
+    goals = np.array([(y, v, 0.0) for y in LANES for v in (15.0, 20.0, 25.0)])[:B]
+    return Scene(ego, obst, goals, p, dict(META_ABS), f"highway_B{B}_m{m}", seed)
+
+
+def scene_large(seed: int = 0, m: int = 50, n_offsets: int = 8, n_speeds: int = 128) -> Scene:
+    """One scene, 50 obstacles x ~ U(-50, 250) m, v ~ U(5, 20) m/s; B = 1024
+    goals = 8 lateral offsets linspace(-5.25, 5.25, 8) x 128 speeds ~ U(5, 30)
+    m/s (offset-major), zero terminal acceleration."""
+    rng = np.random.default_rng(seed)
+    p = dict(BASE_PARAMS)
+    ego_y = LANES[rng.integers(0, 4)]
+    ego = np.array([ego_y, rng.uniform(10.0, 20.0), 0.0, 0.0])
+    obst = _spawn_obstacles(rng, m, -50.0, 250.0, 5.0, 20.0, ego_y, p["a"], p["b"])
+    offs = np.linspace(-5.25, 5.25, n_offsets)
+    speeds = rng.uniform(5.0, 30.0, size=n_speeds)
+    goals = np.array([(y, v, 0.0) for y in offs for v in speeds])
+    return Scene(ego, obst, goals, p, dict(META_ABS), f"highway_B{len(goals)}_m{m}", seed)
+
+
+def scene_custom(seed: int, B: int, m: int, N: int = 100, n: int = 12, x_range=(-50.0, 250.0)) -> Scene:
+    """A scene of the large-scene distribution with arbitrary B, m, N, n
+    (goals: random lateral offsets in [-5.25, 5.25] m and speeds U(5, 30))."""
+    rng = np.random.default_rng(seed)
+    p = dict(BASE_PARAMS)
+    p["N"] = N
+    p["n"] = n
+    ego_y = LANES[rng.integers(0, 4)]
+    ego = np.array([ego_y, rng.uniform(10.0, 20.0), 0.0, 0.0])
+    obst = _spawn_obstacles(rng, m, x_range[0], x_range[1], 5.0, 20.0, ego_y, p["a"], p["b"])
+    goals = np.stack([rng.uniform(-5.25, 5.25, B), rng.uniform(5.0, 30.0, B), np.zeros(B)], axis=1)
+    return Scene(ego, obst, goals, p, dict(META_ABS), f"highway_B{B}_m{m}_N{N}_n{n}", seed)
