@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the batch non-holonomic AM trajectory optimizer (arXiv
+2109.10392, Algorithm 1 + meta-cost argmin) on GB300.
+
+Workload: one synthetic highway scene per GPU with B = 1024 goals (8 lateral
+offsets x 128 speeds ~ U(5, 30) m/s), 50 constant-velocity obstacles, N = 100
+samples, 12 Bernstein coefficients per axis, at most 100 AM iterations with
+early exit once a trajectory's residual is <= 1e-2 m (checked every 10
+iterations), FP32.  A step is one mmpc_solve (cold start + Algorithm 1) and one
+mmpc_score (meta cost + argmin) over the batch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+One JSON line on stdout (rank 0).  `value`: trajectories per second, all
+ranks together, each trajectory iterated until its residual is <= 1e-2 m or
+the 100-iteration budget is spent (the stopping rule of the metric); the
+fraction that reached the residual target is reported beside it
+(detail.converged_fraction; in this dense 50-vehicle scene most goals are
+infeasible and end on the budget).  Each rank solves its own scene: weak
+scaling, no collective on the data path.  --impl reference times the FP64
+CPU oracle on the host cores instead (a bounded sample of the same scene per
+step, same stopping rule).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "trajectories/s to residual<=1e-2 m, warm-started vs plain GPU; % of roofline"
+UNIT = "trajectories/s"
+TOL = 1e-2
+CHECK_EVERY = 10
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SFU_PER_SM = 16
+SM_MAX_MHZ = 2070.0
+FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def workload(seed: int):
+    from paper_2109_10392_gb300 import scenes
+    sc = scenes.scene_large(seed)
+    params = dict(sc.params)
+    params.update(tol=TOL, check_every=CHECK_EVERY)
+    return sc, params
+
+
+def workload_name(params, B, m):
+    return f"highway_B{B}_m{m}_N{params['N']}_n{params['n']}_K{params['iters']}_tol{TOL:g}"
+
+
+def alu_ops_per_traj_iter(N, n, m):
+    """Algorithmic FP32 lane operations of one trajectory-iteration: per sample,
+    10 per obstacle (predicted position 2x2, normalised squared distance 2,
+    max(1/r - 1, 0) 2, accumulation 2; the reciprocal square root itself runs
+    on the SFU and is counted separately) plus 15 n for the basis contractions
+    (7 evaluations x, y, xdot, ydot, xddot, yddot, psi; 8 transposed products
+    F^T (F c - g) for x and y (3 each), P^T theta, P^T (psi - theta))."""
+    return N * (10 * m + 15 * n)
+
+
+def rank_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def combine_ranks(local: dict, world: int, dist=None) -> dict:
+    """Whole-job aggregate: units summed over ranks, time = max over ranks."""
+    if world == 1 or dist is None:
+        return dict(units=local["units"], ms=local["ms"], e2e_units=local["e2e_units"], e2e_ms=local["e2e_ms"])
+    import torch
+    t = torch.tensor([local["units"], local["e2e_units"]], dtype=torch.float64)
+    mx = torch.tensor([local["ms"], local["e2e_ms"]], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t, mx = t.cuda(), mx.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    t, mx = t.cpu(), mx.cpu()
+    return dict(units=float(t[0]), ms=float(mx[0]), e2e_units=float(t[1]), e2e_ms=float(mx[1]))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_mine(args):
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc
+
+    rank, world, local = rank_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    sc, params = workload(seed=rank)
+    B, m, n = len(sc.goals), sc.obst.shape[0], params["n"]
+    solver = mmpc.Solver(params, m)
+    meta = mmpc.make_meta(**sc.meta)
+    f32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).contiguous()  # noqa: E731
+    ego, obst, goals = f32(sc.ego), f32(sc.obst), f32(sc.goals)
+    coef = torch.empty((B, 3 * n), dtype=torch.float32, device=dev)
+    resid = torch.empty((B, 4), dtype=torch.float32, device=dev)
+    iters = torch.empty((B,), dtype=torch.int32, device=dev)
+    cost = torch.empty((B,), dtype=torch.float32, device=dev)
+    argmin = torch.empty((1,), dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve():
+        mmpc.mmpc_solve(solver.ctx, ego, obst, goals, coef, None, None, None, resid, iters, stream)
+
+    def score():
+        mmpc.mmpc_score(solver.ctx, meta, coef, cost, argmin, stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        solve()
+        score()
+    torch.cuda.synchronize(dev)
+    # the result of a step is deterministic: count converged trajectories once
+    conv = (resid[:, :3].max(dim=1).values <= TOL)
+    units_per_step = int(conv.sum().item())
+    iters_sum = int(iters.to(torch.int64).sum().item())
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()  # L2 flush between timed steps (outside the event brackets)
+        ev[i][0].record(stream)
+        solve()
+        ev[i][1].record(stream)
+        score()
+        ev[i][2].record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    solve_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    ms = sum(step_ms) / K
+    solve_avg = sum(solve_ms) / K
+
+    # end to end through the public API with host buffers: pinned inputs
+    # copied in, result (coefficients, residuals, costs, argmin) copied out
+    Ke = min(K, args.e2e_steps)
+    h_in = [torch.tensor(np.asarray(a, dtype=np.float32)).pin_memory() for a in (sc.ego, sc.obst, sc.goals)]
+    h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (coef, resid, cost, argmin)]
+    d_in = [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in h_in]
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = sum(t.numel() * t.element_size() for t in h_out)
+    e2e_units = 0
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter()
+    for _ in range(Ke):
+        for d, h in zip(d_in, h_in):
+            d.copy_(h, non_blocking=True)
+        mmpc.mmpc_solve(solver.ctx, d_in[0], d_in[1], d_in[2], coef, None, None, None, resid, iters, stream)
+        mmpc.mmpc_score(solver.ctx, meta, coef, cost, argmin, stream)
+        for h, d in zip(h_out, (coef, resid, cost, argmin)):
+            h.copy_(d, non_blocking=True)
+        stream.synchronize()
+        e2e_units += int((h_out[1][:, :3].max(dim=1).values <= TOL).sum())
+    e2e_ms = (time.perf_counter() - te) * 1e3 / Ke
+
+    e2e_conv = e2e_units / Ke
+    agg = combine_ranks(dict(units=B, ms=ms, e2e_units=B, e2e_ms=e2e_ms), world, dist)
+    conv_agg = combine_ranks(dict(units=units_per_step, ms=ms, e2e_units=e2e_conv, e2e_ms=e2e_ms), world, dist)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    N = params["N"]
+    ops = iters_sum * alu_ops_per_traj_iter(N, n, m)
+    achieved = ops / (solve_avg * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    sfu_ops = iters_sum * N * m
+    out = {
+        "metric": METRIC,
+        "value": agg["units"] / (agg["ms"] * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": agg["ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(params, B, m), "goals_per_scene": B, "obstacles": m,
+                   "samples": N, "coefficients": n, "max_iters": params["iters"], "tol_m": TOL,
+                   "check_every": CHECK_EVERY, "scenes_per_gpu": 1, "start": "cold",
+                   "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
+        "roofline": {"bound": "alu", "kernel": "am_solve_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz",
+                     "ops_per_launch": ops, "launch_ms": solve_avg,
+                     "sfu_frac": sfu_ops / (solve_avg * 1e-3) / (SM_COUNT * SFU_PER_SM * SM_MAX_MHZ * 1e6)},
+        "e2e": {"value": agg["e2e_units"] / (agg["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": agg["e2e_ms"], "steps": Ke},
+        "gpu_launches": 2 * K,
+        "clocks": clocks,
+        "detail": {"converged_per_step": conv_agg["units"], "trajectories_per_step": B * world,
+                   "converged_fraction": conv_agg["units"] / (B * world),
+                   "converged_per_s": conv_agg["units"] / (agg["ms"] * 1e-3),
+                   "mpc_solves_per_s": world / (agg["ms"] * 1e-3), "iterations_run": iters_sum,
+                   "solve_ms": solve_avg, "score_ms": ms - solve_avg, "wall_s": wall,
+                   "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, params, sample_stride=4)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def _oracle_run(sc, params, idx, threads):
+    import oracle
+    p = oracle.params(**params)
+    f = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)  # noqa: E731
+    t0 = time.perf_counter()
+    r = oracle.solve(p, f(sc.ego), f(sc.obst), f(sc.goals)[idx], nthreads=threads)
+    dt = time.perf_counter() - t0
+    conv = int((r["resid"][:, :3].max(axis=1) <= TOL).sum())
+    return dt, conv
+
+
+def cpu_baseline(sc, params, sample_stride=4):
+    """The FP64 oracle, as it stands, on the host cores, on every
+    `sample_stride`-th goal of the same scene."""
+    threads = os.cpu_count() or 1
+    idx = np.arange(0, len(sc.goals), sample_stride)
+    dt, conv = _oracle_run(sc, params, idx, threads)
+    return {"value": len(idx) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(idx)} of {len(sc.goals)} goals (every {sample_stride}th), same scene and stopping rule",
+            "converged_fraction": conv / len(idx), "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return None
+    sc, params = workload(seed=0)
+    threads = os.cpu_count() or 1
+    # size one step so that warmup + steps take about a minute in total
+    t1, _ = _oracle_run(sc, params, np.array([0]), 1)
+    per_step = 60.0 / max(1, args.steps + args.warmup)
+    ntraj = int(max(1, min(len(sc.goals), math.floor(per_step * threads / max(t1, 1e-6)))))
+    stride = max(1, len(sc.goals) // ntraj)
+    rng_off = 0
+    for _ in range(args.warmup):
+        _oracle_run(sc, params, np.arange(rng_off % stride, len(sc.goals), stride)[:ntraj], threads)
+    units, secs, conv_all = 0, 0.0, 0
+    for i in range(args.steps):
+        idx = np.arange(i % stride, len(sc.goals), stride)[:ntraj]
+        dt, conv = _oracle_run(sc, params, idx, threads)
+        units += len(idx)
+        conv_all += conv
+        secs += dt
+    value = units / secs
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(params, len(sc.goals), sc.obst.shape[0]),
+                   "trajectories_per_step": ntraj},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{ntraj} of {len(sc.goals)} goals per step (strided), same scene and stopping rule",
+                         "converged_fraction": conv_all / max(1, units)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    out = run_reference(args) if args.impl == "reference" else run_mine(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

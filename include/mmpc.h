@@ -1,0 +1,184 @@
+/*
+ * mmpc.h -- C ABI of the GB300 (sm_103a) batch non-holonomic trajectory
+ * optimizer of Adajania et al., "Multi-Modal Model Predictive Control through
+ * Batch Non-Holonomic Trajectory Optimization" (arXiv 2109.10392).
+ *
+ * One scene (ego state, m constant-velocity obstacles, Sec. III assumption 3)
+ * and a batch of B goals (end-of-horizon lateral position, speed,
+ * acceleration; Sec. I "Main Idea") define B trajectory optimisation problems
+ * that share every matrix (Remark 1).  mmpc_solve runs Algorithm 1 (Sec.
+ * III-E) for all of them on one stream; mmpc_score evaluates the meta cost
+ * of Sec. III-F and the batch argmin.
+ *
+ * Conventions
+ *   - Road-attached frame (Sec. III assumption 1): x along the road, y to the
+ *     left, heading psi from the centre line.  The ego starts at x = 0.
+ *   - Every array is row-major and densely packed.
+ *   - "device" pointers are CUDA device memory of the current device, owned
+ *     by the caller; "host" pointers are host memory owned by the caller.
+ *     The library owns only its mmpc_ctx (device constants and a few bytes
+ *     of device scratch, allocated in mmpc_setup, freed in mmpc_destroy).
+ *   - Calls taking a stream are asynchronous on that stream (a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream).  Argument errors are
+ *     detected on the host before anything is enqueued.
+ *   - Return codes: MMPC_OK or a negative MMPC_ERR_*.  mmpc_last_error()
+ *     gives a message for the last failing call on a context.  Non-convergence
+ *     is not an error: it is reported through the residual outputs.
+ *   - One context may be used from one host thread at a time, and its calls
+ *     must be ordered on the GPU (one stream, or streams joined by events):
+ *     mmpc_score uses the context's device scratch.
+ */
+#ifndef MMPC_H
+#define MMPC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MMPC_OK 0
+#define MMPC_ERR_INVALID_ARG (-1) /* bad pointer, NaN or out-of-range scalar */
+#define MMPC_ERR_SHAPE (-2)       /* size outside the supported range, or m != the m of setup */
+#define MMPC_ERR_CUDA (-3)        /* a CUDA runtime call failed (message in mmpc_last_error) */
+#define MMPC_ERR_TIMEOUT (-4)     /* reserved: a bounded device wait expired */
+#define MMPC_ERR_NOT_SETUP (-5)   /* NULL or destroyed context */
+
+/* Boundary rows per axis (the boundary set C_b,l of Eq. boundary):
+ *   x:   x(0), xdot(0), xddot(0), xdot(T), xddot(T)        (terminal x free)
+ *   y:   y(0), ydot(0), yddot(0), y(T), ydot(T), yddot(T)
+ *   psi: psi(0), psidot(0), psi(T), psidot(T)
+ * with values x(0) = 0, xdot(0) = v0 cos psi0, xddot(0) = acc0 cos psi0,
+ * xdot(T) = v_g, xddot(T) = a_g; y(0) = y0, ydot(0) = v0 sin psi0,
+ * yddot(0) = acc0 sin psi0, y(T) = y_g, ydot(T) = yddot(T) = 0;
+ * psi(0) = psi0 and zero heading rate at both ends and heading at T. */
+#define MMPC_NEQ_X 5
+#define MMPC_NEQ_Y 6
+#define MMPC_NEQ_PSI 4
+
+/* Supported sizes of this build. */
+#define MMPC_MIN_N 8
+#define MMPC_MAX_N 512      /* time samples (one GPU thread per sample) */
+#define MMPC_MIN_COEF 7     /* six y boundary rows need at least 7 coefficients */
+#define MMPC_MAX_COEF 16    /* coefficients per axis */
+#define MMPC_MAX_OBST 1024  /* obstacles per scene */
+
+/* Meta-cost kinds (Sec. III-F). */
+#define MMPC_META_CRUISE 0 /* Eq. cruise_cost: sum_t (v(t) - v_ref)^2 */
+#define MMPC_META_HSRL 1   /* Eq. hsrl_cost:  sum_t w1 (v(t) - v_ref)^2 + w2 (y(t) - y_ref)^2 */
+#define MMPC_META_ABS 2    /* sum_t w1 |v(t) - v_ref| + w2 |y(t) - y_ref| */
+
+typedef struct {
+    double T;        /* horizon [s] > 0 */
+    int N;           /* time samples t_i = i T / (N - 1), MMPC_MIN_N..MMPC_MAX_N */
+    int n;           /* basis functions per axis, MMPC_MIN_COEF..MMPC_MAX_COEF */
+    double rho;      /* penalty rho_xy of Eq. aug_cost, > 0 (one value for every block) */
+    double a, b;     /* obstacle ellipse semi-axes incl. inflation [m], Eq. coll_nonhol_standar */
+    double v_min;    /* speed bounds of Eq. v_bound, 0 < v_min <= v_max [m/s] */
+    double v_max;
+    double a_max;    /* acceleration bound of Eq. v_bound, > 0 [m/s^2] */
+    int iters;       /* maximum AM iterations of Algorithm 1, >= 0 */
+    float tol;       /* early exit: a trajectory stops once max(r_obs, r_acc, r_nh) <= tol
+                        (residual definitions at mmpc_solve); <= 0 disables */
+    int check_every; /* residuals are formed after iterations k with k % check_every == 0
+                        and after the last one; >= 1 */
+} mmpc_params;
+
+typedef struct mmpc_ctx mmpc_ctx;
+
+/* Number of doubles of the problem buffer for N samples and n coefficients:
+ *   N + 3 N n + n + 4 n^2 + 30 n.  Returns 0 for sizes out of range. */
+size_t mmpc_problem_size(int N, int n);
+
+/* Host FP64 builder of the shared matrices (Sec. III-C, Remark 1), written
+ * into `buf` (host, mmpc_problem_size(N, n) doubles), in this order:
+ *   t      [N]     sample times t_i = i T / (N - 1)
+ *   P      [N][n]  basis (Eq. param): Bernstein polynomials of degree n - 1 on t/T
+ *   Pd     [N][n]  first time derivative of the basis
+ *   Pdd    [N][n]  second time derivative
+ *   lin    [n]     coefficients of the function f(t) = t (P lin = t)
+ *   Q      [n][n]  Pdd^T Pdd (Eq. cost_reform)
+ *   K11_x  [n][n]  top-left block of Q_xy^-1 for the x axis (Eq. lin_solve_xy_1;
+ *                  Q_xy is block diagonal in x and y with blocks
+ *                  [[Q + rho (m P^T P + Pdd^T Pdd + Pd^T Pd), A_x^T], [A_x, 0]])
+ *   K11_y  [n][n]  same for y
+ *   K11_psi[n][n]  top-left block of Q_psi^-1 (Eq. lin_solve_psi_1)
+ *   K12_psi[n][4]  top-right block of Q_psi^-1
+ *   K12_x  [n][5]  top-right block of the x block of Q_xy^-1
+ *   K12_y  [n][6]  top-right block of the y block of Q_xy^-1
+ *   C0_x   [n][5]  top-right blocks of the boundary-only KKT inverses
+ *   C0_y   [n][6]  (rho = 0): the cold start c0 = C0 b solves
+ *   C0_psi [n][4]  min 1/2 c^T Q c s.t. A c = b
+ * for a scene with m obstacles (the xy blocks depend on m through F^T F).
+ * Returns MMPC_OK, MMPC_ERR_INVALID_ARG or MMPC_ERR_SHAPE; on a singular KKT
+ * matrix MMPC_ERR_INVALID_ARG. */
+int mmpc_build(const mmpc_params* p, int m, double* buf, size_t buf_len);
+
+/* Stages a problem buffer (layout of mmpc_build; a caller may supply its own
+ * basis and inverses in that layout) for scenes with exactly m obstacles:
+ * converts to FP32 (the K11_x and K11_y blocks as hi + lo FP32 pairs) and
+ * copies to device memory owned by the new context.  Synchronous.
+ * *out is NULL on failure. */
+int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t buf_len, mmpc_ctx** out);
+
+/* Algorithm 1 (Sec. III-E) for a batch of B goals in one scene, K iterations
+ * (p->iters) or fewer with early exit:
+ *   ego      device float[4]      y0, v0, psi0, acc0 (x0 = 0); v0 > 0
+ *   obst     device float[m][4]   x0, y0, vx, vy of each obstacle at t = 0;
+ *                                 predicted at constant velocity (m must equal
+ *                                 the m of mmpc_setup; may be NULL when m = 0)
+ *   goals    device float[B][3]   y_g, v_g, a_g at t = T
+ *   warm_coef device float[B][3n] or NULL: initial c_x, c_y, c_psi; NULL =
+ *                                 cold start (boundary-only QP, C0 above)
+ *   warm_lam device float[B][3n] or NULL: initial multipliers (NULL = 0)
+ *   coef_out device float[B][3n]  final c_x, c_y, c_psi
+ *   lam_out  device float[B][3n] or NULL: final lambda_x, lambda_y, lambda_psi
+ *   resid_out device float[B][4] or NULL: residual norms after the last
+ *                                 iteration, Euclidean norms of the blocks of
+ *                                 F c - g (Eq. nonconvex_reform):
+ *                                 [0] obstacle rows [m], [1] acceleration rows
+ *                                 [m/s^2], [2] non-holonomic rows [m/s], and
+ *                                 [3] the heading surrogate atan2(ydot, xdot) -
+ *                                 P c_psi [rad]
+ *   iters_out device int[B] or NULL: iterations run per trajectory
+ *   stream   cudaStream_t or NULL
+ * B = 0 enqueues nothing.  Output buffers must not alias inputs. */
+int mmpc_solve(mmpc_ctx* ctx, const float* ego, const float* obst, int m, const float* goals, int B,
+               const float* warm_coef, const float* warm_lam, float* coef_out, float* lam_out,
+               float* resid_out, int* iters_out, void* stream);
+
+typedef struct {
+    int kind;          /* MMPC_META_* */
+    float w1, w2;      /* weights >= 0 (w1 unused by MMPC_META_CRUISE) */
+    float v_ref;       /* cruise speed (CRUISE, ABS) or maximum speed (HSRL) [m/s] */
+    float y_ref;       /* lateral reference, e.g. the right lane centre [m] */
+    float psi_max;     /* heading restriction (Sec. III assumption 2) [rad]: a
+                          trajectory with |P c_psi| > psi_max at any sample gets
+                          cost +inf; <= 0 disables */
+} mmpc_meta;
+
+/* Meta cost of every trajectory (Sec. III-F) on the N samples, with
+ * v(t) = |(Pd c_x, Pd c_y)| and y(t) = P c_y, and the batch argmin:
+ *   meta       host mmpc_meta
+ *   coef       device float[B][3n] (as written by mmpc_solve)
+ *   cost_out   device float[B]; NaN costs are written as +inf
+ *   argmin_out device int[1]: lowest cost, lowest index on ties; -1 if every
+ *              cost is +inf or B = 0 */
+int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coef, int B, float* cost_out,
+               int* argmin_out, void* stream);
+
+/* Frees the context's device memory (synchronises the device first).  NULL is a no-op. */
+void mmpc_destroy(mmpc_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing mmpc_setup
+ * / mmpc_build when ctx is NULL).  Never NULL. */
+const char* mmpc_last_error(const mmpc_ctx* ctx);
+
+/* ABI version of this header (1). */
+int mmpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMPC_H */

@@ -1,0 +1,238 @@
+"""Thin Python binding of the mmpc C ABI (include/mmpc.h).
+
+Argument marshalling only: torch CUDA tensors are passed as raw device
+pointers together with the current CUDA stream; every step of the optimizer
+runs inside libmmpc.so.  There is no fallback: if the library is missing or
+fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+MMPC_OK = 0
+MMPC_ERR_INVALID_ARG = -1
+MMPC_ERR_SHAPE = -2
+MMPC_ERR_CUDA = -3
+MMPC_ERR_TIMEOUT = -4
+MMPC_ERR_NOT_SETUP = -5
+
+MMPC_META_CRUISE = 0
+MMPC_META_HSRL = 1
+MMPC_META_ABS = 2
+
+EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
+            "mmpc_last_error", "mmpc_version")
+
+
+class MmpcParams(ctypes.Structure):
+    _fields_ = [
+        ("T", ctypes.c_double),
+        ("N", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("rho", ctypes.c_double),
+        ("a", ctypes.c_double),
+        ("b", ctypes.c_double),
+        ("v_min", ctypes.c_double),
+        ("v_max", ctypes.c_double),
+        ("a_max", ctypes.c_double),
+        ("iters", ctypes.c_int),
+        ("tol", ctypes.c_float),
+        ("check_every", ctypes.c_int),
+    ]
+
+
+class MmpcMeta(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("w1", ctypes.c_float),
+        ("w2", ctypes.c_float),
+        ("v_ref", ctypes.c_float),
+        ("y_ref", ctypes.c_float),
+        ("psi_max", ctypes.c_float),
+    ]
+
+
+class MmpcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mmpc error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libmmpc.so (building it in-tree first when it is missing or
+    older than its sources)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmmpc.so not found at {path}; run paper_2109_10392_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    vp, dp, fp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p
+    L.mmpc_problem_size.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.mmpc_problem_size.restype = ctypes.c_size_t
+    L.mmpc_build.argtypes = [ctypes.POINTER(MmpcParams), ctypes.c_int, dp, ctypes.c_size_t]
+    L.mmpc_build.restype = ctypes.c_int
+    L.mmpc_setup.argtypes = [ctypes.POINTER(MmpcParams), ctypes.c_int, dp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.mmpc_setup.restype = ctypes.c_int
+    L.mmpc_solve.argtypes = [vp, fp, fp, ctypes.c_int, fp, ctypes.c_int, fp, fp, fp, fp, fp, ip, vp]
+    L.mmpc_solve.restype = ctypes.c_int
+    L.mmpc_score.argtypes = [vp, ctypes.POINTER(MmpcMeta), fp, ctypes.c_int, fp, ip, vp]
+    L.mmpc_score.restype = ctypes.c_int
+    L.mmpc_destroy.argtypes = [vp]
+    L.mmpc_destroy.restype = None
+    L.mmpc_last_error.argtypes = [vp]
+    L.mmpc_last_error.restype = ctypes.c_char_p
+    L.mmpc_version.argtypes = []
+    L.mmpc_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def make_params(T, N, n, rho, a, b, v_min, v_max, a_max, iters=100, tol=0.0, check_every=10, **_ignored) -> MmpcParams:
+    return MmpcParams(float(T), int(N), int(n), float(rho), float(a), float(b), float(v_min), float(v_max),
+                      float(a_max), int(iters), float(tol), int(check_every))
+
+
+def make_meta(kind=MMPC_META_ABS, w1=1.0, w2=0.25, v_ref=20.0, y_ref=-5.25, psi_max_deg=13.0, psi_max=None,
+              **_ignored) -> MmpcMeta:
+    pm = float(psi_max) if psi_max is not None else math.radians(float(psi_max_deg))
+    return MmpcMeta(int(kind), float(w1), float(w2), float(v_ref), float(y_ref), pm)
+
+
+def _err(ctx, code):
+    msg = lib().mmpc_last_error(ctx)
+    raise MmpcError(code, msg.decode() if msg else "")
+
+
+def mmpc_problem_size(N: int, n: int) -> int:
+    return int(lib().mmpc_problem_size(int(N), int(n)))
+
+
+def mmpc_build(params: MmpcParams, m: int) -> np.ndarray:
+    """Host FP64 builder (basis, KKT inverse blocks); returns the packed buffer."""
+    size = mmpc_problem_size(params.N, params.n)
+    buf = np.zeros(max(size, 1), dtype=np.float64)
+    rc = lib().mmpc_build(ctypes.byref(params), int(m), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), size)
+    if rc != MMPC_OK:
+        _err(None, rc)
+    return buf[:size]
+
+
+def mmpc_setup(params: MmpcParams, m: int, buf: np.ndarray) -> ctypes.c_void_p:
+    buf = np.ascontiguousarray(buf, dtype=np.float64)
+    ctx = ctypes.c_void_p()
+    rc = lib().mmpc_setup(ctypes.byref(params), int(m), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          buf.size, ctypes.byref(ctx))
+    if rc != MMPC_OK:
+        _err(None, rc)
+    return ctx
+
+
+def _ptr(t, dtype_name="float32"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def mmpc_solve(ctx, ego, obst, goals, coef_out, warm_coef=None, warm_lam=None, lam_out=None, resid_out=None,
+               iters_out=None, stream=None) -> None:
+    """Enqueue Algorithm 1 for the batch on `stream` (default: torch's current
+    stream).  All tensors are CUDA, contiguous, float32 (iters_out int32)."""
+    m = 0 if obst is None else int(obst.shape[0])
+    B = int(goals.shape[0])
+    rc = lib().mmpc_solve(ctx, _ptr(ego), _ptr(obst) if m else None, m, _ptr(goals), B, _ptr(warm_coef),
+                          _ptr(warm_lam), _ptr(coef_out), _ptr(lam_out), _ptr(resid_out),
+                          _ptr(iters_out, "int32"), _stream(stream))
+    if rc != MMPC_OK:
+        _err(ctx, rc)
+
+
+def mmpc_score(ctx, meta: MmpcMeta, coef, cost_out, argmin_out, stream=None) -> None:
+    B = int(coef.shape[0])
+    rc = lib().mmpc_score(ctx, ctypes.byref(meta), _ptr(coef), B, _ptr(cost_out), _ptr(argmin_out, "int32"),
+                          _stream(stream))
+    if rc != MMPC_OK:
+        _err(ctx, rc)
+
+
+def mmpc_destroy(ctx) -> None:
+    if ctx:
+        lib().mmpc_destroy(ctx)
+
+
+def mmpc_last_error(ctx=None) -> str:
+    return lib().mmpc_last_error(ctx).decode()
+
+
+@dataclass
+class SolveResult:
+    coef: "object"
+    lam: "object"
+    resid: "object"
+    iters: "object"
+
+
+class Solver:
+    """Owns one mmpc context (one scene size: N, n and m obstacles)."""
+
+    def __init__(self, params: dict, m: int, problem: np.ndarray | None = None):
+        self.params = make_params(**params)
+        self.m = int(m)
+        self.n = self.params.n
+        self.problem = mmpc_build(self.params, self.m) if problem is None else problem
+        self.ctx = mmpc_setup(self.params, self.m, self.problem)
+
+    def close(self):
+        if self.ctx:
+            mmpc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, ego, obst, goals, warm_coef=None, warm_lam=None, stream=None, want_lam=True) -> SolveResult:
+        import torch
+        B = int(goals.shape[0])
+        dev = goals.device
+        coef = torch.empty((B, 3 * self.n), dtype=torch.float32, device=dev)
+        lam = torch.empty((B, 3 * self.n), dtype=torch.float32, device=dev) if want_lam else None
+        resid = torch.empty((B, 4), dtype=torch.float32, device=dev)
+        iters = torch.empty((B,), dtype=torch.int32, device=dev)
+        mmpc_solve(self.ctx, ego, obst, goals, coef, warm_coef, warm_lam, lam, resid, iters, stream)
+        return SolveResult(coef, lam, resid, iters)
+
+    def score(self, meta: dict | MmpcMeta, coef, stream=None):
+        import torch
+        mt = meta if isinstance(meta, MmpcMeta) else make_meta(**meta)
+        B = int(coef.shape[0])
+        cost = torch.empty((B,), dtype=torch.float32, device=coef.device)
+        am = torch.empty((1,), dtype=torch.int32, device=coef.device)
+        mmpc_score(self.ctx, mt, coef, cost, am, stream)
+        return cost, am

@@ -1,0 +1,119 @@
+"""Helpers of the GPU-vs-oracle parity tests.
+
+Both sides get the same inputs: the seeded scene rounded to float32 (the CUDA
+path's input precision), passed to the oracle as float64.  Positions are
+compared as x(t), y(t) on the N samples, evaluated in FP64 from each side's
+coefficients with the oracle's basis.
+
+Conditioning.  Algorithm 1 is an iteration on a non-convex problem; for
+trajectories that do not converge (an infeasible goal in dense traffic
+leaves a colliding compromise), the iterate after K steps can depend
+violently on rounding: perturbing the oracle's own inputs by 1e-12 moves
+some of them by decimetres.  No FP32 (or re-ordered FP64) implementation can
+match those to 1e-3 m.  `sensitivity` measures, per trajectory, how far the
+oracle's own result moves when every input is perturbed by a random relative
+1e-6; a trajectory is in the parity set when that motion is below 1e-4 m,
+i.e. the problem amplifies input rounding less than 100x per unit.  Between
+that and 1e-2 m of motion the bar scales with the conditioning (10x the
+measured motion); above it the trajectory is chaotic under rounding and is
+checked for validity only (finite, on the boundary rows).
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import oracle
+
+POS_TOL = 1e-3        # [m] positions, from the stated parity target
+COST_RTOL = 1e-4      # meta cost, relative
+SENS_EPS = 1e-6       # relative input perturbation of the conditioning probe
+SENS_TOL = 1e-4       # [m] oracle motion under that perturbation for the parity set
+CHAOS_TOL = 1e-2      # [m] above this motion a trajectory is checked for validity only
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def ncores():
+    return max(1, os.cpu_count() or 1)
+
+
+def oracle_solve(params: dict, ego, obst, goals, **kw):
+    return oracle.solve(oracle.params(**params), ego, obst, goals, nthreads=ncores(), **kw)
+
+
+def gpu_solve(params: dict, ego, obst, goals, warm_coef=None, warm_lam=None, solver=None):
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc
+    m = obst.shape[0]
+    s = solver or mmpc.Solver(params, m)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).contiguous()  # noqa: E731
+    res = s.solve(t(ego), t(obst).reshape(m, 4) if m else None, t(goals).reshape(-1, 3),
+                  None if warm_coef is None else t(warm_coef), None if warm_lam is None else t(warm_lam))
+    torch.cuda.synchronize()
+    out = dict(coef=res.coef.double().cpu().numpy(), lam=res.lam.double().cpu().numpy(),
+               resid=res.resid.double().cpu().numpy(), iters=res.iters.cpu().numpy())
+    if solver is None:
+        s.close()
+    return out
+
+
+def positions(params: dict, coef):
+    x, y, _ = oracle.positions(oracle.params(**params), coef)
+    return x, y
+
+
+def pos_err(params: dict, coef_a, coef_b):
+    xa, ya = positions(params, coef_a)
+    xb, yb = positions(params, coef_b)
+    return np.max(np.hypot(xa - xb, ya - yb), axis=1)
+
+
+def sensitivity(params: dict, ego, obst, goals, ref_coef, trials=2, seed=1234, init=None, init_lam=None):
+    """Per trajectory: the largest position motion of the oracle's result when
+    every input (and the warm start, if any) is perturbed by a random relative
+    SENS_EPS."""
+    rng = np.random.default_rng(seed)
+    worst = np.zeros(len(goals))
+    for _ in range(trials):
+        pe = lambda a: None if a is None else a * (1.0 + SENS_EPS * rng.uniform(-1, 1, size=np.shape(a)))  # noqa: E731
+        r = oracle_solve(params, pe(ego), pe(obst), pe(goals), init=pe(init), init_lam=pe(init_lam))
+        worst = np.maximum(worst, pos_err(params, r["coef"], ref_coef))
+    return worst
+
+
+def boundary_error(params: dict, ego, goals, coef):
+    """max |A c - b| over the boundary rows, per trajectory (oracle matrices)."""
+    p = oracle.params(**params)
+    M = oracle.matrices(p, 0)
+    n = p.n
+    out = np.zeros(len(goals))
+    for l in range(len(goals)):
+        bxy, bpsi = oracle.boundary(ego, goals[l])
+        c = coef[l]
+        out[l] = max(np.max(np.abs(M["Axy"] @ c[:2 * n] - bxy)), np.max(np.abs(M["Apsi"] @ c[2 * n:] - bpsi)))
+    return out
+
+
+def meta_oracle(params: dict, coef, meta: dict):
+    return oracle.meta_cost(oracle.params(**params), coef, kind=meta["kind"], w1=meta["w1"], w2=meta["w2"],
+                            v_ref=meta["v_ref"], y_ref=meta["y_ref"], psi_max=np.deg2rad(meta["psi_max_deg"]))
+
+
+def gpu_score(params: dict, m: int, coef, meta: dict, solver=None):
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc
+    s = solver or mmpc.Solver(params, m)
+    c = torch.tensor(np.asarray(coef, dtype=np.float32), device="cuda:0").contiguous()
+    cost, am = s.score(meta, c)
+    torch.cuda.synchronize()
+    out = cost.double().cpu().numpy(), int(am.item())
+    if solver is None:
+        s.close()
+    return out

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs (rounded to float32 for both).
+
+Bars, from the parity target of this path: positions within 1e-3 m after the
+fixed iteration count, meta costs within 1e-4 relative, the same argmin --
+on the trajectories whose result is determined by the inputs to better than
+the FP32 rounding (parity set, see parity_utils); the others are checked for
+validity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import parity_utils as U
+from paper_2109_10392_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _scene_arrays(sc):
+    return U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
+
+
+def _check_parity(params, ego, obst, goals, gpu, orc, min_frac=0.3, sens=None, init=None, init_lam=None):
+    """Positions within 1e-3 m on the parity set; on the moderately
+    conditioned rest, within 10x the oracle's own response to a 1e-6 relative
+    input perturbation (i.e. what a 1e-5 perturbation moves, linearly); the
+    chaotic rest (that response above 1 cm) only for validity."""
+    err = U.pos_err(params, gpu["coef"], orc["coef"])
+    if sens is None:
+        sens = U.sensitivity(params, ego, obst, goals, orc["coef"], init=init, init_lam=init_lam)
+    good = sens < U.SENS_TOL
+    mid = ~good & (sens < U.CHAOS_TOL)
+    info = f"err {np.array2string(err, precision=2)} sens {np.array2string(sens, precision=2)}"
+    assert good.mean() >= min_frac, f"parity set {good.mean():.3f} below {min_frac}; {info}"
+    assert np.all(err[good] <= U.POS_TOL), info
+    assert np.all(err[mid] <= np.maximum(U.POS_TOL, 10 * sens[mid])), info
+    assert np.all(np.isfinite(gpu["coef"]))
+    # validity of the rest: the boundary rows hold
+    be = U.boundary_error(params, ego, goals, gpu["coef"])
+    assert np.all(be < 1e-2), be.max()
+    return err, good
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_highway_11_goals_10_obstacles(seed):
+    sc = scenes.scene_small(seed)
+    ego, obst, goals = _scene_arrays(sc)
+    orc = U.oracle_solve(sc.params, ego, obst, goals)
+    gpu = U.gpu_solve(sc.params, ego, obst, goals)
+    err, good = _check_parity(sc.params, ego, obst, goals, gpu, orc)
+    # residual outputs follow the oracle's definitions
+    assert np.allclose(gpu["resid"][good], orc["resid"][good], rtol=1e-2, atol=2e-3)
+    assert np.all(gpu["iters"] == sc.params["iters"])
+    # meta cost and argmin
+    cg, ag = U.gpu_score(sc.params, obst.shape[0], gpu["coef"], sc.meta)
+    co, ao = U.meta_oracle(sc.params, orc["coef"], sc.meta)
+    fin = np.isfinite(co) & good
+    assert np.all(np.abs(cg[fin] - co[fin]) <= U.COST_RTOL * np.abs(co[fin]) + 1e-3)
+    if ao >= 0 and good[ao]:
+        second = np.sort(co[np.isfinite(co)])[1] if np.isfinite(co).sum() > 1 else np.inf
+        if second - co[ao] > 2 * U.COST_RTOL * co[ao] + 2e-3:
+            assert ag == ao
+        else:
+            assert abs(co[ag] - co[ao]) <= 2 * U.COST_RTOL * co[ao] + 2e-3
+
+
+# (N, n, m, B, iters): several warps of samples with ragged tails, both
+# coefficient paddings (12, 16), and every launch-bound variant (<=128, <=256,
+# <=512 threads).
+SHAPES = [
+    (16, 7, 0, 3, 30),
+    (37, 10, 3, 5, 25),
+    (100, 12, 1, 4, 40),
+    (130, 12, 5, 3, 20),
+    (200, 16, 8, 4, 20),
+    (64, 13, 2, 3, 15),
+    (300, 12, 4, 2, 10),
+    (512, 16, 2, 2, 6),
+]
+
+
+@pytest.mark.parametrize("N,n,m,B,iters", SHAPES)
+def test_shapes(N, n, m, B, iters):
+    sc = scenes.scene_custom(seed=N + n + m, B=B, m=m, N=N, n=n, x_range=(10.0, 150.0))
+    params = dict(sc.params)
+    params["iters"] = iters
+    ego, obst, goals = _scene_arrays(sc)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    gpu = U.gpu_solve(params, ego, obst, goals)
+    _check_parity(params, ego, obst, goals, gpu, orc)
+
+
+def test_full_size_sampled():
+    """The 1024-goal, 50-obstacle scene in the launch configuration the
+    benchmark times; the oracle runs on every trajectory, the conditioning
+    probe on every 8th."""
+    sc = scenes.scene_large(0)
+    ego, obst, goals = _scene_arrays(sc)
+    gpu = U.gpu_solve(sc.params, ego, obst, goals)
+    sel = np.arange(0, len(goals), 8)
+    orc = U.oracle_solve(sc.params, ego, obst, goals[sel])
+    sens = U.sensitivity(sc.params, ego, obst, goals[sel], orc["coef"])
+    gs = {k: v[sel] for k, v in gpu.items()}
+    _check_parity(sc.params, ego, obst, goals[sel], gs, orc, sens=sens)
+
+
+def test_cold_start_only():
+    sc = scenes.scene_small(5)
+    params = dict(sc.params)
+    params["iters"] = 0
+    ego, obst, goals = _scene_arrays(sc)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    gpu = U.gpu_solve(params, ego, obst, goals)
+    assert np.all(U.pos_err(params, gpu["coef"], orc["coef"]) < 1e-4)
+    assert np.allclose(gpu["resid"], orc["resid"], rtol=1e-3, atol=1e-3)
+    assert np.all(gpu["iters"] == 0)
+    assert np.allclose(gpu["lam"], 0.0)
+
+
+def test_warm_start_continues_the_iteration():
+    sc = scenes.scene_small(6)
+    ego, obst, goals = _scene_arrays(sc)
+    p10 = dict(sc.params); p10["iters"] = 10
+    p5 = dict(sc.params); p5["iters"] = 5
+    r10 = U.oracle_solve(p10, ego, obst, goals)
+    c10, l10 = U.f32(r10["coef"]), U.f32(r10["lam"])
+    orc = U.oracle_solve(p5, ego, obst, goals, init=c10, init_lam=l10)
+    gpu = U.gpu_solve(p5, ego, obst, goals, warm_coef=c10, warm_lam=l10)
+    _check_parity(p5, ego, obst, goals, gpu, orc, init=c10, init_lam=l10)
+
+
+def test_warm_start_off_the_boundary_rows():
+    """A warm start that violates A c = b is put back on the boundary rows by
+    the first step, as Eq. lin_solve_xy_2 does from any iterate."""
+    sc = scenes.scene_small(7)
+    ego, obst, goals = _scene_arrays(sc)
+    params = dict(sc.params); params["iters"] = 8
+    rng = np.random.default_rng(0)
+    warm = U.f32(U.oracle_solve(dict(params, iters=0), ego, obst, goals)["coef"] + rng.normal(scale=0.5, size=(len(goals), 36)))
+    orc = U.oracle_solve(params, ego, obst, goals, init=warm)
+    gpu = U.gpu_solve(params, ego, obst, goals, warm_coef=warm)
+    _check_parity(params, ego, obst, goals, gpu, orc, init=warm)
+    assert np.all(U.boundary_error(params, ego, goals, gpu["coef"]) < 1e-3)
+
+
+def test_early_exit_matches_fixed_count():
+    sc = scenes.scene_small(8)
+    params = dict(sc.params); params.update(tol=1e-2, check_every=5)
+    ego, obst, goals = _scene_arrays(sc)
+    gpu = U.gpu_solve(params, ego, obst, goals)
+    it = gpu["iters"]
+    assert np.all((it % 5 == 0) | (it == params["iters"]))
+    conv = np.max(gpu["resid"][:, :3], axis=1)
+    early = it < params["iters"]
+    assert np.all(conv[early] <= 1e-2)
+    for K in np.unique(it):
+        idx = np.where(it == K)[0]
+        pk = dict(sc.params); pk["iters"] = int(K)
+        orc = U.oracle_solve(pk, ego, obst, goals[idx])
+        err = U.pos_err(pk, gpu["coef"][idx], orc["coef"])
+        assert np.all(err <= U.POS_TOL), (K, err.max())
+
+
+def test_colocated_obstacle_degenerate_projection():
+    """Ego and an obstacle at the same place with the same velocity: every
+    sample has w = 0, where alpha = atan2(0, 0) = 0 and d = 1, so each sample
+    contributes a to the obstacle residual: r_obs = a sqrt(N) at the start."""
+    params = dict(scenes.BASE_PARAMS); params["iters"] = 0
+    ego = np.array([0.0, 15.0, 0.0, 0.0])
+    obst = np.array([[0.0, 0.0, 15.0, 0.0]])
+    goals = np.array([[0.0, 15.0, 0.0]])
+    gpu = U.gpu_solve(params, ego, obst, goals)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    expect = params["a"] * np.sqrt(params["N"])
+    assert np.isclose(gpu["resid"][0, 0], expect, rtol=1e-5)
+    assert np.isclose(orc["resid"][0, 0], expect, rtol=1e-9)
+    params["iters"] = 20
+    gpu = U.gpu_solve(params, ego, obst, goals)
+    assert np.all(np.isfinite(gpu["coef"])) and np.all(np.isfinite(gpu["resid"]))
+    assert np.all(U.boundary_error(params, ego, goals, gpu["coef"]) < 1e-3)
+
+
+def test_batch_independence_and_determinism():
+    sc = scenes.scene_small(9)
+    ego, obst, goals = _scene_arrays(sc)
+    a = U.gpu_solve(sc.params, ego, obst, goals)
+    b = U.gpu_solve(sc.params, ego, obst, goals)
+    assert np.array_equal(a["coef"], b["coef"])
+    perm = np.random.default_rng(3).permutation(len(goals))
+    c = U.gpu_solve(sc.params, ego, obst, goals[perm])
+    assert np.array_equal(a["coef"][perm], c["coef"])
+    d = U.gpu_solve(sc.params, ego, obst, goals[:3])
+    assert np.array_equal(a["coef"][:3], d["coef"])
+
+
+def test_nan_goal_never_wins():
+    sc = scenes.scene_small(10)
+    ego, obst, goals = _scene_arrays(sc)
+    goals = goals.copy()
+    goals[2, 1] = np.nan
+    gpu = U.gpu_solve(sc.params, ego, obst, goals)
+    cost, am = U.gpu_score(sc.params, obst.shape[0], gpu["coef"], sc.meta)
+    assert np.isinf(cost[2]) and am != 2
+    ok = U.gpu_solve(sc.params, ego, obst, np.delete(goals, 2, axis=0))
+    assert np.array_equal(np.delete(gpu["coef"], 2, axis=0), ok["coef"])
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_score_kinds_and_heading_filter(kind):
+    sc = scenes.scene_small(11)
+    ego, obst, goals = _scene_arrays(sc)
+    gpu = U.gpu_solve(sc.params, ego, obst, goals)
+    meta = dict(sc.meta); meta["kind"] = kind; meta["w1"] = 1.5; meta["psi_max_deg"] = 4.0
+    cg, ag = U.gpu_score(sc.params, obst.shape[0], gpu["coef"], meta)
+    co, ao = U.meta_oracle(sc.params, U.f32(gpu["coef"]), meta)
+    # same coefficients on both sides: only the FP32 sum differs; the heading
+    # decision is compared where |psi| is not within 1e-5 rad of the limit
+    _, _, psi = oracle.positions(oracle.params(**sc.params), U.f32(gpu["coef"]))
+    near = np.any(np.abs(np.abs(psi) - np.deg2rad(4.0)) < 1e-5, axis=1)
+    fin = np.isfinite(co) & ~near
+    assert np.array_equal(np.isinf(cg[~near]), np.isinf(co[~near]))
+    assert np.all(np.abs(cg[fin] - co[fin]) <= 1e-5 * np.abs(co[fin]) + 1e-4)
+    if ao >= 0:
+        assert np.isfinite(cg[ag]) and abs(co[ag] - co[ao]) <= 1e-5 * co[ao] + 1e-4
+    else:
+        assert ag == -1
+
+
+def test_empty_batch_and_errors():
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc
+    params = dict(scenes.BASE_PARAMS)
+    s = mmpc.Solver(params, 2)
+    dev = "cuda:0"
+    ego = torch.zeros(4, device=dev); ego[1] = 15
+    obst = torch.zeros((2, 4), device=dev)
+    goals = torch.zeros((0, 3), device=dev)
+    res = s.solve(ego, obst, goals)
+    assert res.coef.shape == (0, 36)
+    cost, am = s.score(scenes.META_ABS, res.coef)
+    torch.cuda.synchronize()
+    assert am.item() == -1
+    with pytest.raises(mmpc.MmpcError) as ei:
+        s.solve(ego, torch.zeros((3, 4), device=dev), torch.zeros((1, 3), device=dev))
+    assert ei.value.code == mmpc.MMPC_ERR_SHAPE
+    with pytest.raises(mmpc.MmpcError) as ei:
+        s.score(dict(scenes.META_ABS, w1=-1.0), torch.zeros((1, 36), device=dev))
+    assert ei.value.code == mmpc.MMPC_ERR_INVALID_ARG
+    s.close()
