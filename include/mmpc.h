@@ -174,6 +174,28 @@ void mmpc_destroy(mmpc_ctx* ctx);
  * / mmpc_build when ctx is NULL).  Never NULL. */
 const char* mmpc_last_error(const mmpc_ctx* ctx);
 
+/* Allocation-free scoring, for callers that cannot allocate device memory
+ * once they run: a hard real-time control loop that reserves all its memory at
+ * start-up, or a host framework that hands out device memory only from its
+ * own pool.  The paper has no counterpart; this is the computation of
+ * mmpc_score without a context:
+ *   meta       host mmpc_meta
+ *   N, n       samples and coefficients per axis (same ranges as mmpc_params)
+ *   P, Pd      device float[N][n]: the basis and its first derivative (e.g. the
+ *              P and Pd sections of an mmpc_build buffer cast to float)
+ *   coef, B, cost_out, argmin_out: as in mmpc_score; 0 <= B <= MMPC_STATIC_SCORE_MAX_B,
+ *              larger B -> MMPC_ERR_SHAPE
+ * Its scratch (8 bytes per 8 trajectories plus 8, at most 64 KiB) is a
+ * file-scope device array of the library, held by every GPU that loads it
+ * until the process exits, and shared by all calls: calls whose work overlaps
+ * on the GPU race and must be serialised by the caller.  It calls no
+ * cudaMalloc or cudaFree.  The first call on a device looks up the array's
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture. */
+#define MMPC_STATIC_SCORE_MAX_B 65536
+int mmpc_score_static(const mmpc_meta* meta, int N, int n, const float* P, const float* Pd, const float* coef,
+                      int B, float* cost_out, int* argmin_out, void* stream);
+
 /* ABI version of this header (1). */
 int mmpc_version(void);
 

@@ -907,3 +907,187 @@ extern "C" const char* mmpc_last_error(const mmpc_ctx* ctx)
 }
 
 extern "C" int mmpc_version(void) { return 1; }
+
+// ---------------------------------------------------------------------------
+// Allocation-free scoring (mmpc_score_static).
+//
+// For callers that must not allocate device memory once they are running --
+// a hard real-time control loop whose memory is all reserved at start-up, or
+// a host framework that hands out device memory only from its own pool and
+// forbids raw cudaMalloc/cudaFree -- this entry point scores a batch without a
+// context and without any allocation.  Its scratch (a ticket counter and one
+// partial argmin key per CTA) lives in the file-scope array below, which every
+// GPU that loads this library holds until the process exits.  Consequences:
+//  * all calls share the array and it keeps the last call's contents; the
+//    ticket is cleared by each call before its kernel runs, and each CTA
+//    writes its own key before the last CTA reads it;
+//  * calls whose kernels overlap on the GPU (different streams, or several
+//    host threads) race on the array and must be serialised by the caller;
+//  * the first call on a device looks up the array's device address with
+//    cudaGetSymbolAddress (with that device current) and caches it; make that
+//    first call before any stream capture.
+// ---------------------------------------------------------------------------
+namespace mmpc {
+
+constexpr int STATIC_WARPS_PER_CTA = 8;
+constexpr int STATIC_MAX_CTAS = MMPC_STATIC_SCORE_MAX_B / STATIC_WARPS_PER_CTA;
+
+// [0]: ticket counter (low 32 bits); [1 + i]: best packed key of CTA i.
+static __device__ __align__(256) unsigned long long g_static_score_scratch[1 + STATIC_MAX_CTAS];
+
+struct StaticScoreArgs {
+    int N, n, B, kind;
+    float w1, w2, v_ref, y_ref, psi_max;
+    const float* P;   // [N][n]
+    const float* Pd;  // [N][n]
+    const float* coef;
+    float* cost_out;
+    int* argmin_out;
+    unsigned long long* scratch;
+};
+
+template <int NC>
+__global__ void __launch_bounds__(32 * STATIC_WARPS_PER_CTA) score_static_kernel(const StaticScoreArgs S)
+{
+    __shared__ unsigned long long s_key[STATIC_WARPS_PER_CTA];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * STATIC_WARPS_PER_CTA + warp;
+    unsigned long long key = ~0ull;
+    if (gw < S.B) {
+        const int n = S.n, N = S.N;
+        const float* cf = S.coef + (size_t)gw * 3 * n;
+        float cx[NC], cy[NC], cp[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            cx[k] = k < n ? __ldg(cf + k) : 0.f;
+            cy[k] = k < n ? __ldg(cf + n + k) : 0.f;
+            cp[k] = k < n ? __ldg(cf + 2 * n + k) : 0.f;
+        }
+        float cost = 0.f;
+        bool bad = false;
+        for (int t = lane; t < N; t += 32) {
+            float xd = 0.f, yd = 0.f, y = 0.f, ps = 0.f;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                const float p = k < n ? __ldg(S.P + t * n + k) : 0.f;
+                const float d = k < n ? __ldg(S.Pd + t * n + k) : 0.f;
+                xd = fmaf(d, cx[k], xd);
+                yd = fmaf(d, cy[k], yd);
+                y = fmaf(p, cy[k], y);
+                ps = fmaf(p, cp[k], ps);
+            }
+            const float vel = sqrtf(fmaf(xd, xd, yd * yd));
+            const float dv = vel - S.v_ref, dy = y - S.y_ref;
+            if (S.kind == MMPC_META_CRUISE) cost = fmaf(dv, dv, cost);
+            else if (S.kind == MMPC_META_HSRL) cost += S.w1 * dv * dv + S.w2 * dy * dy;
+            else cost += S.w1 * fabsf(dv) + S.w2 * fabsf(dy);
+            if (S.psi_max > 0.f && fabsf(ps) > S.psi_max) bad = true;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cost += __shfl_xor_sync(FULL, cost, off);
+        bad = __any_sync(FULL, bad);
+        if (bad || isnan(cost)) cost = __int_as_float(0x7f800000);
+        if (lane == 0) S.cost_out[gw] = cost;
+        key = ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned)gw;
+    }
+    if (lane == 0) s_key[warp] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long best = s_key[0];
+        for (int w = 1; w < STATIC_WARPS_PER_CTA; ++w) best = s_key[w] < best ? s_key[w] : best;
+        S.scratch[1 + blockIdx.x] = best;
+        __threadfence();
+        const unsigned ticket = atomicAdd(reinterpret_cast<unsigned*>(S.scratch), 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {  // the last CTA reduces the per-CTA keys
+        __threadfence();
+        unsigned long long best = ~0ull;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(S.scratch + 1 + i);
+            best = k < best ? k : best;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULL, best, off);
+            best = o < best ? o : best;
+        }
+        if (lane == 0) s_key[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            best = s_key[0];
+            for (int w = 1; w < STATIC_WARPS_PER_CTA; ++w) best = s_key[w] < best ? s_key[w] : best;
+            const unsigned bits = (unsigned)(best >> 32);
+            *S.argmin_out = (bits >= 0x7f800000u) ? -1 : (int)(best & 0xffffffffu);
+            atomicExch(reinterpret_cast<unsigned*>(S.scratch), 0u);
+        }
+    }
+}
+
+}  // namespace mmpc
+
+namespace {
+
+std::mutex g_static_mu;
+unsigned long long* g_static_ptr[64] = {};  // per device ordinal
+
+int static_fail(const std::string& msg, int code)
+{
+    mmpc::set_global_error(msg);
+    return code;
+}
+
+}  // namespace
+
+extern "C" int mmpc_score_static(const mmpc_meta* meta, int N, int n, const float* P, const float* Pd,
+                                 const float* coef, int B, float* cost_out, int* argmin_out, void* stream)
+{
+    using namespace mmpc;
+    if (!meta || !P || !Pd || !argmin_out || (B > 0 && (!coef || !cost_out)))
+        return static_fail("mmpc_score_static: NULL pointer argument", MMPC_ERR_INVALID_ARG);
+    if (!sizes_ok(N, n)) return static_fail("mmpc_score_static: N or n out of the supported range", MMPC_ERR_SHAPE);
+    if (B < 0 || B > MMPC_STATIC_SCORE_MAX_B)
+        return static_fail("mmpc_score_static: B must be in [0, MMPC_STATIC_SCORE_MAX_B = " +
+                               std::to_string(MMPC_STATIC_SCORE_MAX_B) + "]",
+                           MMPC_ERR_SHAPE);
+    if (meta->kind < MMPC_META_CRUISE || meta->kind > MMPC_META_ABS)
+        return static_fail("mmpc_score_static: unknown meta kind", MMPC_ERR_INVALID_ARG);
+    if (!(meta->w1 >= 0.f) || !(meta->w2 >= 0.f) || !std::isfinite(meta->w1) || !std::isfinite(meta->w2) ||
+        !std::isfinite(meta->v_ref) || !std::isfinite(meta->y_ref) || std::isnan(meta->psi_max))
+        return static_fail("mmpc_score_static: meta weights must be finite and >= 0", MMPC_ERR_INVALID_ARG);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return static_fail(std::string("cudaGetDevice: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+    if (dev < 0 || dev >= 64) return static_fail("mmpc_score_static: device ordinal >= 64", MMPC_ERR_CUDA);
+    unsigned long long* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_static_score_scratch);
+            if (e != cudaSuccess)
+                return static_fail(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+            g_static_ptr[dev] = static_cast<unsigned long long*>(ptr);
+        }
+        scratch = g_static_ptr[dev];
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (B == 0) {
+        e = cudaMemsetAsync(argmin_out, 0xff, sizeof(int), st);  // -1
+        return e == cudaSuccess ? MMPC_OK : static_fail(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+    }
+    e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), st);  // the ticket starts at zero
+    if (e != cudaSuccess) return static_fail(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+    StaticScoreArgs s{};
+    s.N = N; s.n = n; s.B = B; s.kind = meta->kind;
+    s.w1 = meta->w1; s.w2 = meta->w2; s.v_ref = meta->v_ref; s.y_ref = meta->y_ref; s.psi_max = meta->psi_max;
+    s.P = P; s.Pd = Pd; s.coef = coef; s.cost_out = cost_out; s.argmin_out = argmin_out; s.scratch = scratch;
+    const int grid = (B + STATIC_WARPS_PER_CTA - 1) / STATIC_WARPS_PER_CTA;
+    if (n <= 12) score_static_kernel<12><<<grid, 32 * STATIC_WARPS_PER_CTA, 0, st>>>(s);
+    else score_static_kernel<16><<<grid, 32 * STATIC_WARPS_PER_CTA, 0, st>>>(s);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : static_fail(std::string("score_static launch: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+}

@@ -28,7 +28,8 @@ MMPC_META_HSRL = 1
 MMPC_META_ABS = 2
 
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
-            "mmpc_last_error", "mmpc_version")
+            "mmpc_last_error", "mmpc_version", "mmpc_score_static")
+MMPC_STATIC_SCORE_MAX_B = 65536
 
 
 class MmpcParams(ctypes.Structure):
@@ -95,6 +96,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_last_error.restype = ctypes.c_char_p
     L.mmpc_version.argtypes = []
     L.mmpc_version.restype = ctypes.c_int
+    L.mmpc_score_static.argtypes = [ctypes.POINTER(MmpcMeta), ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int,
+                                    fp, ip, vp]
+    L.mmpc_score_static.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -177,6 +181,16 @@ def mmpc_score(ctx, meta: MmpcMeta, coef, cost_out, argmin_out, stream=None) -> 
                           _stream(stream))
     if rc != MMPC_OK:
         _err(ctx, rc)
+
+
+def mmpc_score_static(meta: MmpcMeta, N: int, n: int, P, Pd, coef, cost_out, argmin_out, stream=None) -> None:
+    """Allocation-free scoring without a context (see include/mmpc.h): P and Pd
+    are device float32 [N, n]; no device memory is allocated by the call."""
+    B = int(coef.shape[0])
+    rc = lib().mmpc_score_static(ctypes.byref(meta), int(N), int(n), _ptr(P), _ptr(Pd), _ptr(coef), B,
+                                 _ptr(cost_out), _ptr(argmin_out, "int32"), _stream(stream))
+    if rc != MMPC_OK:
+        _err(None, rc)
 
 
 def mmpc_destroy(ctx) -> None:
