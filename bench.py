@@ -62,14 +62,26 @@ def workload_name(params, B, m):
     return f"highway_B{B}_m{m}_N{params['N']}_n{params['n']}_K{params['iters']}_tol{TOL:g}"
 
 
-def alu_ops_per_traj_iter(N, n, m):
-    """Algorithmic FP32 lane operations of one trajectory-iteration: per sample,
-    10 per obstacle (predicted position 2x2, normalised squared distance 2,
-    max(1/r - 1, 0) 2, accumulation 2; the reciprocal square root itself runs
-    on the SFU and is counted separately) plus 15 n for the basis contractions
-    (7 evaluations x, y, xdot, ydot, xddot, yddot, psi; 8 transposed products
-    F^T (F c - g) for x and y (3 each), P^T theta, P^T (psi - theta))."""
-    return N * (10 * m + 15 * n)
+OPS_PER_ELEMENT = 10  # FP32 lane ops per evaluated obstacle-sample pair
+
+
+def contraction_ops_per_sample(n):
+    """FP32 lane ops of the basis contractions per sample and pass: 7
+    evaluations (x, y, xdot, ydot, xddot, yddot, psi) and 8 transposed products
+    (F^T (F c - g) for x and y, 3 blocks each; P^T theta; P^T (psi - theta)),
+    n multiply-adds each."""
+    return 15 * n
+
+
+def alu_ops(N, n, passes, elements):
+    """Algorithmic FP32 lane operations of a solve: `elements` evaluated
+    obstacle-sample pairs of Eq. split_alpha_o at 10 ops each (predicted
+    position and offset 4, normalised squared distance 2, max(1/r - 1, 0) 2,
+    accumulation 2; the reciprocal square root runs on the SFU and is counted
+    separately), plus the contractions of every sample in every pass (the
+    initial one and one per iteration).  Element-wise trigonometry is not
+    counted.  Without culling, elements = passes N m."""
+    return elements * OPS_PER_ELEMENT + passes * N * contraction_ops_per_sample(n)
 
 
 def rank_env():
@@ -158,6 +170,8 @@ def run_mine(args):
     torch.cuda.set_device(dev)
 
     sc, params = workload(seed=rank)
+    params["cull"] = 0 if args.no_cull else 1
+    params["variant"] = args.variant
     B, m, n = len(sc.goals), sc.obst.shape[0], params["n"]
     solver = mmpc.Solver(params, m)
     meta = mmpc.make_meta(**sc.meta)
@@ -188,6 +202,7 @@ def run_mine(args):
     iters_sum = int(iters.to(torch.int64).sum().item())
 
     K = args.steps
+    mmpc.mmpc_take_work_count(solver.ctx)  # reset the evaluated-pair counter
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     sampler = ClockSampler(dev.index or 0)
     sampler.start()
@@ -207,6 +222,7 @@ def run_mine(args):
         dist.barrier()
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
+    elements = mmpc.mmpc_take_work_count(solver.ctx) / K  # per launch
     solve_ms = [e[0].elapsed_time(e[1]) for e in ev]
     step_ms = [e[0].elapsed_time(e[2]) for e in ev]
     ms = sum(step_ms) / K
@@ -243,10 +259,12 @@ def run_mine(args):
         return None
 
     N = params["N"]
-    ops = iters_sum * alu_ops_per_traj_iter(N, n, m)
+    passes = iters_sum + B
+    ops = alu_ops(N, n, passes, elements)
+    dense_ops = alu_ops(N, n, passes, passes * N * m)
     achieved = ops / (solve_avg * 1e-3) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    sfu_ops = iters_sum * N * m
+    sfu_ops = elements
     out = {
         "metric": METRIC,
         "value": agg["units"] / (agg["ms"] * 1e-3),
@@ -261,6 +279,7 @@ def run_mine(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": workload_name(params, B, m), "goals_per_scene": B, "obstacles": m,
+                   "culling": bool(params["cull"]), "kernel_variant": params["variant"],
                    "samples": N, "coefficients": n, "max_iters": params["iters"], "tol_m": TOL,
                    "check_every": CHECK_EVERY, "scenes_per_gpu": 1, "start": "cold",
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
@@ -268,6 +287,8 @@ def run_mine(args):
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": None,
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz",
                      "ops_per_launch": ops, "launch_ms": solve_avg,
+                     "evaluated_pairs_per_launch": elements, "dense_pairs_per_launch": passes * N * m,
+                     "dense_equivalent_achieved": dense_ops / (solve_avg * 1e-3) / 1e12,
                      "sfu_frac": sfu_ops / (solve_avg * 1e-3) / (SM_COUNT * SFU_PER_SM * SM_MAX_MHZ * 1e6)},
         "e2e": {"value": agg["e2e_units"] / (agg["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": agg["e2e_ms"], "steps": Ke},
@@ -355,6 +376,9 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cull", action="store_true", help="evaluate every obstacle-sample pair (no culling)")
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
+                    help="solve kernel: 1 one sample per thread, 2 two samples per thread, 0 automatic")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -82,6 +82,12 @@ typedef struct {
                         (residual definitions at mmpc_solve); <= 0 disables */
     int check_every; /* residuals are formed after iterations k with k % check_every == 0
                         and after the last one; >= 1 */
+    int cull;        /* 1: skip the obstacle-sample pairs of Eq. split_alpha_o that are
+                        provably outside the ellipse (each skipped pair contributes exactly
+                        zero, so results are bit-identical to 0 = evaluate every pair) */
+    int variant;     /* kernel: 1 = one time sample per thread (N <= 256), 2 = two
+                        samples per thread; 0 = automatic (1 for batches of at most one
+                        trajectory per SM, else 2).  Results agree to rounding. */
 } mmpc_params;
 
 typedef struct mmpc_ctx mmpc_ctx;
@@ -166,6 +172,12 @@ typedef struct {
  *              cost is +inf or B = 0 */
 int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coef, int B, float* cost_out,
                int* argmin_out, void* stream);
+
+/* Number of obstacle-sample pairs (Eq. split_alpha_o) the solve kernels of
+ * this context evaluated since the last call, summed over iterations and
+ * trajectories (m N per trajectory-iteration without culling).  Synchronises
+ * the device, writes the count to *elements (host) and resets it. */
+int mmpc_take_work_count(mmpc_ctx* ctx, unsigned long long* elements);
 
 /* Frees the context's device memory (synchronises the device first).  NULL is a no-op. */
 void mmpc_destroy(mmpc_ctx* ctx);

@@ -149,6 +149,8 @@ std::string check_params(const mmpc_params* p)
     if (p->iters < 0) return "iters must be >= 0";
     if (p->check_every < 1) return "check_every must be >= 1";
     if (std::isnan(p->tol)) return "tol is NaN";
+    if (p->variant < 0 || p->variant > 2) return "variant must be 0, 1 or 2";
+    if (p->variant == 1 && p->N > 256) return "variant 1 needs N <= 256";
     return "";
 }
 

@@ -1,8 +1,9 @@
 // GB300 (sm_103a) kernels and C ABI of the batch non-holonomic trajectory
 // optimizer (Adajania et al., arXiv 2109.10392, Algorithm 1 of Sec. III-E).
 //
-// Solve kernel: one CTA per trajectory l of the batch, one thread per time
-// sample t.  Every quantity that Algorithm 1 carries from one iteration to the
+// Solve kernel: one CTA per trajectory l of the batch, one thread per pair of
+// time samples (2i, 2i+1), whose arithmetic runs as packed f32x2 operations
+// (FFMA2 / FADD2 / FMUL2: one issue slot for two samples).  Every quantity that Algorithm 1 carries from one iteration to the
 // next for trajectory l -- c_x, c_y, c_psi and lambda_x, lambda_y, lambda_psi
 // -- stays on chip (registers of warp 0, broadcast through shared memory) for
 // all iterations; the auxiliary variables v, alpha, d, alpha_a, d_a of Eqs.
@@ -47,22 +48,39 @@ thread_local std::string g_error = "no error";
 void set_global_error(const std::string& msg) { g_error = msg; }
 
 // ---------------------------------------------------------------------------
-// Device constant blob (FP32), section offsets in floats.  Every section
-// starts on a 16-byte boundary; per-coefficient rows are padded to NC.
+// Device constant blob (FP32), section offsets in floats, every section on a
+// 16-byte boundary.  Three regions:
+//   [pair rows | common | sample rows]
+// The pair-sample kernel stages [pair rows | common] into shared memory, the
+// one-sample kernel [common | sample rows]; the scoring kernels read the
+// sample rows from global memory.
+//   pair rows:   PP, PdP, PddP [ceil(N/2)][NC][2]  basis rows of samples
+//                (2i, 2i+1) interleaved per coefficient (rows of samples >= N
+//                and every k >= n are zero); tP [ceil(N/2)][2] their times
+//   common:      brow [6][NC] (P, Pd, Pdd at t = 0 and t = T); lin [NC]; Q,
+//                K11 (x hi, x lo, y hi, y lo), K11_psi [NC][NC]; K12_psi
+//                [NC][4]; K12_x, K12_y, C0_x, C0_y [NC][8]; C0_psi [NC][4]
+//   sample rows: P, Pd, Pdd [N][NC]; t [N]
 // ---------------------------------------------------------------------------
 struct BlobLayout {
-    int P, Pd, Pdd, t, lin, Q, Kxh, Kxl, Kyh, Kyl, Kp11, Kp12, K12x, K12y, C0x, C0y, C0p, total;
+    int PP, PdP, PddP, tP;                                                        // pair rows
+    int brow, lin, Q, Kxh, Kxl, Kyh, Kyl, Kp11, Kp12, K12x, K12y, C0x, C0y, C0p;  // common
+    int P, Pd, Pdd, t;                                                            // sample rows
+    int common, rows1, total;  // region starts (common, sample rows) and end
 };
 
 static BlobLayout blob_layout(int N, int NC)
 {
     auto up4 = [](int v) { return (v + 3) & ~3; };
+    const int NP = (N + 1) / 2;
     BlobLayout B{};
     int o = 0;
-    B.P = o; o += up4(N * NC);
-    B.Pd = o; o += up4(N * NC);
-    B.Pdd = o; o += up4(N * NC);
-    B.t = o; o += up4(N);
+    B.PP = o; o += NP * NC * 2;
+    B.PdP = o; o += NP * NC * 2;
+    B.PddP = o; o += NP * NC * 2;
+    B.tP = o; o += up4(NP * 2);
+    B.common = o;
+    B.brow = o; o += 6 * NC;
     B.lin = o; o += up4(NC);
     B.Q = o; o += NC * NC;
     B.Kxh = o; o += NC * NC;
@@ -76,12 +94,18 @@ static BlobLayout blob_layout(int N, int NC)
     B.C0x = o; o += NC * 8;
     B.C0y = o; o += NC * 8;
     B.C0p = o; o += NC * 4;
-    B.total = up4(o);
+    o = up4(o);
+    B.rows1 = o;
+    B.P = o; o += up4(N * NC);
+    B.Pd = o; o += up4(N * NC);
+    B.Pdd = o; o += up4(N * NC);
+    B.t = o; o += up4(N);
+    B.total = o;
     return B;
 }
 
 struct SolveArgs {
-    int N, n, m, B, iters, check_every;
+    int N, n, m, B, iters, check_every, cull;
     float rho, a, b, inv_a, inv_b, v_min, v_max, a_max, tol;
     BlobLayout L;
     const float* blob;
@@ -95,6 +119,7 @@ struct SolveArgs {
     float* resid_out;
     int* iters_out;
     unsigned* err_flag;
+    unsigned long long* work;  // evaluated obstacle-sample pairs (summed over CTAs)
 };
 
 struct ScoreArgs {
@@ -224,73 +249,92 @@ __device__ __forceinline__ bool stage_blob(float* dst, const float* src, int byt
     return __syncthreads_and(done) != 0;
 }
 
-// Dot product of a 16-byte aligned row with NC coefficients in shared memory.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Dot products of the basis rows of one sample pair ([NC][2], interleaved)
+// with NC coefficients held duplicated ([NC][2] = (c_k, c_k)): both samples'
+// values in one FFMA2 chain.
 template <int NC>
-__device__ __forceinline__ float dot_row(const float* __restrict__ row, const float* __restrict__ c)
+__device__ __forceinline__ float2 dot_pair(const float* __restrict__ rows, const float* __restrict__ cd)
 {
-    float s = 0.f;
+    float2 s = f2(0.f);
 #pragma unroll
-    for (int k = 0; k < NC; k += 4) {
-        const float4 r = *reinterpret_cast<const float4*>(row + k);
-        const float4 q = *reinterpret_cast<const float4*>(c + k);
-        s = fmaf(r.x, q.x, s);
-        s = fmaf(r.y, q.y, s);
-        s = fmaf(r.z, q.z, s);
-        s = fmaf(r.w, q.w, s);
+    for (int k = 0; k < NC; k += 2) {
+        const float4 r = *reinterpret_cast<const float4*>(rows + 2 * k);
+        const float4 c = *reinterpret_cast<const float4*>(cd + 2 * k);
+        s = __ffma2_rn(f2(r.x, r.y), f2(c.x, c.y), s);
+        s = __ffma2_rn(f2(r.z, r.w), f2(c.z, c.w), s);
     }
     return s;
 }
 
-// Sum over obstacles at one sample (Eq. split_alpha_o): with n = w / (a, b)
-// the ellipse-normalised offset of obstacle j and s = max(0, 1/|n| - 1),
-// S += n s; the constraint rows of F_o c - g_o at this sample sum to
-// (-a Sx, -b Sy).  With RESID the squared residual sum_j |a nx s, b ny s|^2
-// is accumulated too.  Two interleaved accumulator pairs for ILP.
-template <bool RESID>
-__device__ __forceinline__ void obstacle_sum(const float4* __restrict__ obs, int m, float Xn, float Yn, float tt,
-                                             float a2, float b2, float& Sx, float& Sy, float& R2)
+// Sum over obstacles at the sample pair (Eq. split_alpha_o).  With n = w / (a,
+// b) the ellipse-normalised offset of obstacle j and s = max(0, 1/|n| - 1),
+// S += n s; the rows of F_o c - g_o at a sample sum to (-a Sx, -b Sy).  With
+// RESID the squared row residuals sum_j |(a nx s, b ny s)|^2 are accumulated
+// too.  obs holds per obstacle (-x0/a, -x0/a, -vx/a, -vx/a) and (-y0/b, -y0/b,
+// -vy/b, -vy/b) in the frame moving with v0, so n = N + fma(-v, t, -x0) is
+// two packed instructions per coordinate for both samples.
+template <bool RESID, bool LIST>
+__device__ __forceinline__ void obstacle_sum2(const float4* __restrict__ obs, const int* __restrict__ list, int m,
+                                              float2 Xn, float2 Yn, float2 tt, float a2, float b2, float2& Sx,
+                                              float2& Sy, float2& R2)
 {
-    float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f, r0 = 0.f, r1 = 0.f;
+    // The per-obstacle terms are independent; they are accumulated in
+    // obstacle order through one chain, so that skipping obstacles whose term
+    // is exactly zero (culling) leaves every sum bit-identical.
+    float2 sx = f2(0.f), sy = f2(0.f), r = f2(0.f);
+    const float2 m1 = f2(-1.f);
     int j = 0;
 #pragma unroll 2
     for (; j + 1 < m; j += 2) {
-        const float4 o0 = obs[j];
-        const float4 o1 = obs[j + 1];
-        const float nx0 = Xn - fmaf(o0.z, tt, o0.x);
-        const float ny0 = Yn - fmaf(o0.w, tt, o0.y);
-        const float nx1 = Xn - fmaf(o1.z, tt, o1.x);
-        const float ny1 = Yn - fmaf(o1.w, tt, o1.y);
-        const float q0 = fmaf(nx0, nx0, ny0 * ny0);
-        const float q1 = fmaf(nx1, nx1, ny1 * ny1);
-        const float s0 = fmaxf(rsqrtf(q0) - 1.f, 0.f);
-        const float s1 = fmaxf(rsqrtf(q1) - 1.f, 0.f);
-        sx0 = fmaf(nx0, s0, sx0);
-        sy0 = fmaf(ny0, s0, sy0);
-        sx1 = fmaf(nx1, s1, sx1);
-        sy1 = fmaf(ny1, s1, sy1);
+        const int j0 = LIST ? list[j] : j;
+        const int j1 = LIST ? list[j + 1] : j + 1;
+        const float4 ax0 = obs[2 * j0], ay0 = obs[2 * j0 + 1];
+        const float4 ax1 = obs[2 * j1], ay1 = obs[2 * j1 + 1];
+        const float2 nx0 = __fadd2_rn(Xn, __ffma2_rn(f2(ax0.z, ax0.w), tt, f2(ax0.x, ax0.y)));
+        const float2 ny0 = __fadd2_rn(Yn, __ffma2_rn(f2(ay0.z, ay0.w), tt, f2(ay0.x, ay0.y)));
+        const float2 nx1 = __fadd2_rn(Xn, __ffma2_rn(f2(ax1.z, ax1.w), tt, f2(ax1.x, ax1.y)));
+        const float2 ny1 = __fadd2_rn(Yn, __ffma2_rn(f2(ay1.z, ay1.w), tt, f2(ay1.x, ay1.y)));
+        const float2 q0 = __ffma2_rn(nx0, nx0, __fmul2_rn(ny0, ny0));
+        const float2 q1 = __ffma2_rn(nx1, nx1, __fmul2_rn(ny1, ny1));
+        float2 s0 = __fadd2_rn(f2(rsqrtf(q0.x), rsqrtf(q0.y)), m1);
+        float2 s1 = __fadd2_rn(f2(rsqrtf(q1.x), rsqrtf(q1.y)), m1);
+        s0 = f2(fmaxf(s0.x, 0.f), fmaxf(s0.y, 0.f));
+        s1 = f2(fmaxf(s1.x, 0.f), fmaxf(s1.y, 0.f));
+        sx = __ffma2_rn(nx1, s1, __ffma2_rn(nx0, s0, sx));
+        sy = __ffma2_rn(ny1, s1, __ffma2_rn(ny0, s0, sy));
         if (RESID) {
-            r0 = fmaf(s0 * s0, fmaf(a2 * nx0, nx0, b2 * ny0 * ny0), r0);
-            r1 = fmaf(s1 * s1, fmaf(a2 * nx1, nx1, b2 * ny1 * ny1), r1);
+            const float2 w0 = __ffma2_rn(__fmul2_rn(f2(a2), nx0), nx0, __fmul2_rn(__fmul2_rn(f2(b2), ny0), ny0));
+            const float2 w1 = __ffma2_rn(__fmul2_rn(f2(a2), nx1), nx1, __fmul2_rn(__fmul2_rn(f2(b2), ny1), ny1));
+            r = __ffma2_rn(__fmul2_rn(s1, s1), w1, __ffma2_rn(__fmul2_rn(s0, s0), w0, r));
         }
     }
     if (j < m) {
-        const float4 o0 = obs[j];
-        const float nx0 = Xn - fmaf(o0.z, tt, o0.x);
-        const float ny0 = Yn - fmaf(o0.w, tt, o0.y);
-        const float q0 = fmaf(nx0, nx0, ny0 * ny0);
-        const float s0 = fmaxf(rsqrtf(q0) - 1.f, 0.f);
-        sx0 = fmaf(nx0, s0, sx0);
-        sy0 = fmaf(ny0, s0, sy0);
-        if (RESID) r0 = fmaf(s0 * s0, fmaf(a2 * nx0, nx0, b2 * ny0 * ny0), r0);
+        const int j0 = LIST ? list[j] : j;
+        const float4 ax0 = obs[2 * j0], ay0 = obs[2 * j0 + 1];
+        const float2 nx0 = __fadd2_rn(Xn, __ffma2_rn(f2(ax0.z, ax0.w), tt, f2(ax0.x, ax0.y)));
+        const float2 ny0 = __fadd2_rn(Yn, __ffma2_rn(f2(ay0.z, ay0.w), tt, f2(ay0.x, ay0.y)));
+        const float2 q0 = __ffma2_rn(nx0, nx0, __fmul2_rn(ny0, ny0));
+        float2 s0 = __fadd2_rn(f2(rsqrtf(q0.x), rsqrtf(q0.y)), m1);
+        s0 = f2(fmaxf(s0.x, 0.f), fmaxf(s0.y, 0.f));
+        sx = __ffma2_rn(nx0, s0, sx);
+        sy = __ffma2_rn(ny0, s0, sy);
+        if (RESID) {
+            const float2 w0 = __ffma2_rn(__fmul2_rn(f2(a2), nx0), nx0, __fmul2_rn(__fmul2_rn(f2(b2), ny0), ny0));
+            r = __ffma2_rn(__fmul2_rn(s0, s0), w0, r);
+        }
     }
-    Sx = sx0 + sx1;
-    Sy = sy0 + sy1;
-    R2 = r0 + r1;
+    Sx = sx;
+    Sy = sy;
+    R2 = r;
 }
 
-// The same sum, slowly, with the degenerate case of an ego sample exactly at
-// an obstacle centre (w = 0): there alpha = atan2(0, 0) = 0 and d = 1, so the
-// target is xi + (a, 0) and the row of F_o c - g_o is (-a, 0).
+// The same sum for one sample (h = 0 or 1 of the pair), slowly, with the
+// degenerate case of a sample exactly at an obstacle centre (w = 0): there
+// alpha = atan2(0, 0) = 0 and d = 1, so the target is xi + (a, 0) and the row
+// of F_o c - g_o is (-a, 0).
 __device__ __noinline__ void obstacle_sum_exact(const float4* __restrict__ obs, int m, float Xn, float Yn, float tt,
                                                 float a2, float b2, float& Sx, float& Sy, float& R2)
 {
@@ -298,47 +342,148 @@ __device__ __noinline__ void obstacle_sum_exact(const float4* __restrict__ obs, 
     Sy = 0.f;
     R2 = 0.f;
     for (int j = 0; j < m; ++j) {
-        const float4 o = obs[j];
-        const float nx = Xn - fmaf(o.z, tt, o.x);
-        const float ny = Yn - fmaf(o.w, tt, o.y);
+        const float4 ax = obs[2 * j], ay = obs[2 * j + 1];
+        const float nx = Xn + fmaf(ax.z, tt, ax.x);
+        const float ny = Yn + fmaf(ay.z, tt, ay.x);
         const float q = fmaf(nx, nx, ny * ny);
         if (q == 0.f) {
             Sx += 1.f;
             R2 += a2;
         } else {
-            const float s = fmaxf(rsqrtf(q) - 1.f, 0.f);
-            Sx = fmaf(nx, s, Sx);
-            Sy = fmaf(ny, s, Sy);
-            R2 = fmaf(s * s, fmaf(a2 * nx, nx, b2 * ny * ny), R2);
+            const float sj = fmaxf(rsqrtf(q) - 1.f, 0.f);
+            Sx = fmaf(nx, sj, Sx);
+            Sy = fmaf(ny, sj, Sy);
+            R2 = fmaf(sj * sj, fmaf(a2 * nx, nx, b2 * ny * ny), R2);
         }
     }
 }
 
+// Exact culling for Eq. split_alpha_o.  The warp's samples span the box
+// [xlo, xhi] x [ylo, yhi] (ellipse-normalised, moving frame) over the time
+// window [tw_lo, tw_hi]; an obstacle moves along a segment over that window.
+// When the two boxes are apart by more than 1 (plus a margin far above the
+// FP32 rounding of the coordinates) along x or y, every sample of the warp has
+// |n| > 1 for that obstacle, so s = max(1/|n| - 1, 0) = 0 and the obstacle
+// adds exactly nothing.  Writes the indices of the remaining obstacles to
+// list (warp-private) and returns their count (warp-uniform).  A non-finite
+// coordinate keeps every obstacle, so NaN propagates as without culling.
+__device__ __forceinline__ float warp_min(float v)
+{
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ int cull_list(const float4* __restrict__ obs, int m, float2 Xn, float2 Yn, float2 valid,
+                                         float tw_lo, float tw_hi, int* list, int lane)
+{
+    const float inf = __int_as_float(0x7f800000);
+    float xlo = inf, xhi = -inf, ylo = inf, yhi = -inf;
+    if (valid.x > 0.f) { xlo = Xn.x; xhi = Xn.x; ylo = Yn.x; yhi = Yn.x; }
+    if (valid.y > 0.f) {
+        xlo = fminf(xlo, Xn.y); xhi = fmaxf(xhi, Xn.y);
+        ylo = fminf(ylo, Yn.y); yhi = fmaxf(yhi, Yn.y);
+    }
+    const bool bad = (valid.x > 0.f && !(isfinite(Xn.x) && isfinite(Yn.x))) ||
+                     (valid.y > 0.f && !(isfinite(Xn.y) && isfinite(Yn.y)));
+    xlo = warp_min(xlo);
+    xhi = warp_max(xhi);
+    ylo = warp_min(ylo);
+    yhi = warp_max(yhi);
+    const bool any_bad = __any_sync(FULL, bad);
+    constexpr float M = 1.001f;
+    const unsigned below = (1u << lane) - 1u;
+    int count = 0;
+    for (int j0 = 0; j0 < m; j0 += 32) {
+        const int j = j0 + lane;
+        bool keep = false;
+        if (j < m) {
+            const float4 ax = obs[2 * j], ay = obs[2 * j + 1];
+            // the obstacle centre is -(p + pv t) in the stored (negated) form
+            const float e1 = -fmaf(ax.z, tw_lo, ax.x), e2 = -fmaf(ax.z, tw_hi, ax.x);
+            const float f1 = -fmaf(ay.z, tw_lo, ay.x), g1 = -fmaf(ay.z, tw_hi, ay.x);
+            const bool apart = (xlo - fmaxf(e1, e2) >= M) || (fminf(e1, e2) - xhi >= M) ||
+                               (ylo - fmaxf(f1, g1) >= M) || (fminf(f1, g1) - yhi >= M);
+            keep = any_bad || !apart;
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) list[count + __popc(bal & below)] = j;
+        count += __popc(bal);
+    }
+    __syncwarp();
+    return count;
+}
+
+// sin and cos of a heading: the SFU approximations where they are accurate
+// (|psi| < 3: absolute error of order 1e-6 or below), the full-range library
+// function elsewhere.
+__device__ __forceinline__ void heading_sincos(float ps, float* sn, float* cs)
+{
+    if (fabsf(ps) < 3.f) __sincosf(ps, sn, cs);
+    else sincosf(ps, sn, cs);
+}
+
 // ---------------------------------------------------------------------------
-// The fused AM kernel.  Grid: one CTA per trajectory; block: 32 ceil(N/32)
-// threads, thread t owns sample t.  Warp 0 owns the coefficient state: lane k
-// (k < NC) coefficient k of the x axis (and of psi), lane 16 + k coefficient k
-// of the y axis.
+// The fused AM kernel.  Grid: one CTA per trajectory; block: 32 ceil(ceil(N/2)
+// / 32) threads (at most 8 warps), thread i owns samples 2i and 2i+1.  Every
+// warp holds the whole coefficient state -- lane k (k < NC) coefficient k of
+// the x axis and of psi, lane 16 + k coefficient k of the y axis -- and runs
+// the two small QP steps itself from the CTA's partial sums: all warps
+// compute bit-identical values, so an iteration needs only two CTA barriers
+// (after the partial sums of P^T theta and after those of F^T (F c - g)).
 // ---------------------------------------------------------------------------
 template <int NC>
 struct SolveSmem {
-    static constexpr int VD = 3 * NC + 4;  // values reduced per sample in the projection phase
+    static constexpr int VD = 3 * NC + 4;  // values reduced per thread in the projection phase
     static constexpr int RSD = (VD + 3) & ~3;
     static constexpr int RSB = NC;
 };
 
+constexpr int MAX_WARPS = 8;
+
+template <int MAXT>
+struct MinBlocks {
+    static constexpr int value = MAXT <= 64 ? 8 : (MAXT <= 128 ? 4 : 2);
+};
+
+// dot product of a 16-byte aligned row of NC floats with a vector given as
+// duplicated pairs ([NC][2] = (v_k, v_k)); four partial sums for ILP.
+template <int NC>
+__device__ __forceinline__ float dot_dup(const float* __restrict__ row, const float* __restrict__ vd)
+{
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NC; j += 4) {
+        const float4 r = *reinterpret_cast<const float4*>(row + j);
+        const float4 v0 = *reinterpret_cast<const float4*>(vd + 2 * j);
+        const float4 v1 = *reinterpret_cast<const float4*>(vd + 2 * j + 4);
+        acc[0] = fmaf(r.x, v0.x, acc[0]);
+        acc[1] = fmaf(r.y, v0.z, acc[1]);
+        acc[2] = fmaf(r.z, v1.x, acc[2]);
+        acc[3] = fmaf(r.w, v1.z, acc[3]);
+    }
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
 template <int NC, int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 : 1)) am_solve_kernel(const SolveArgs A)
+__global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(const SolveArgs A)
 {
     constexpr int VD = SolveSmem<NC>::VD;
     constexpr int RSD = SolveSmem<NC>::RSD;
     constexpr int RSB = SolveSmem<NC>::RSB;
     extern __shared__ __align__(16) float smem[];
-    __shared__ __align__(16) float s_cx[NC];
-    __shared__ __align__(16) float s_cy[NC];
-    __shared__ __align__(16) float s_cp[NC];
+    // per-warp copies of the coefficient vectors, duplicated: (c_k, c_k)
+    __shared__ __align__(16) float s_cxd[MAX_WARPS][2 * NC];
+    __shared__ __align__(16) float s_cyd[MAX_WARPS][2 * NC];
+    __shared__ __align__(16) float s_cpd[MAX_WARPS][2 * NC];
+    __shared__ __align__(16) float s_vec[MAX_WARPS][2][2 * NC];  // per-warp scratch vectors (x, y)
     __shared__ __align__(8) unsigned long long s_mbar;
-    __shared__ int s_done;
 
     const int l = blockIdx.x;
     const int tid = threadIdx.x;
@@ -346,90 +491,100 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 :
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int N = A.N, m = A.m;
+    const int NP = (N + 1) >> 1;
     const BlobLayout& L = A.L;
 
     float* blob = smem;
-    float4* obs = reinterpret_cast<float4*>(smem + L.total);
-    float* red = reinterpret_cast<float*>(obs + m);
+    float4* obs = reinterpret_cast<float4*>(smem + L.rows1);
+    float* red1 = reinterpret_cast<float*>(obs + 2 * m);   // [warp][RSB]: P^T theta
+    float* red2 = red1 + MAX_WARPS * RSB;                   // [warp][RSD]: F^T (F c - g), ...
+    int* olist = reinterpret_cast<int*>(red2 + MAX_WARPS * RSD) + warp * m;  // this warp's active obstacles
+    float* cxd = s_cxd[warp];
+    float* cyd = s_cyd[warp];
+    float* cpd = s_cpd[warp];
 
     // Scene: ego (Sec. III, x0 = 0) and obstacles, normalised by the ellipse
-    // axes and expressed in the frame moving with v0 along x.
+    // axes, negated, duplicated for the sample pair, in the frame moving with v0.
     const float y0 = __ldg(A.ego + 0), v0 = __ldg(A.ego + 1), psi0 = __ldg(A.ego + 2), acc0 = __ldg(A.ego + 3);
     for (int j = tid; j < m; j += blockDim.x) {
         const float* o = A.obst + 4 * j;
-        obs[j] = make_float4(__ldg(o + 0) * A.inv_a, __ldg(o + 1) * A.inv_b, (__ldg(o + 2) - v0) * A.inv_a,
-                             __ldg(o + 3) * A.inv_b);
+        const float px = -__ldg(o + 0) * A.inv_a, pvx = -(__ldg(o + 2) - v0) * A.inv_a;
+        const float py = -__ldg(o + 1) * A.inv_b, pvy = -__ldg(o + 3) * A.inv_b;
+        obs[2 * j] = make_float4(px, px, pvx, pvx);
+        obs[2 * j + 1] = make_float4(py, py, pvy, pvy);
     }
-    if (!stage_blob(blob, A.blob, L.total * 4, &s_mbar, A.err_flag)) return;
+    if (!stage_blob(blob, A.blob, L.rows1 * 4, &s_mbar, A.err_flag)) return;
 
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
-    const bool has_t = tid < N;
-    const int ts = has_t ? tid : 0;
-    const float* Prow = blob + L.P + ts * NC;
-    const float* Pdrow = blob + L.Pd + ts * NC;
-    const float* Pddrow = blob + L.Pdd + ts * NC;
-    const float tt = blob[L.t + ts];
+    const bool has_pair = tid < NP;
+    const int ip = has_pair ? tid : 0;
+    const float* PP = blob + L.PP + ip * 2 * NC;
+    const float* PdP = blob + L.PdP + ip * 2 * NC;
+    const float* PddP = blob + L.PddP + ip * 2 * NC;
+    const float2 tt = f2(blob[L.tP + 2 * ip], blob[L.tP + 2 * ip + 1]);
+    const float2 valid = f2(has_pair ? 1.f : 0.f, (has_pair && 2 * ip + 1 < N) ? 1.f : 0.f);
+    // the warp's samples [64 warp, 64 warp + 64) and their time window
+    const int w_first = 64 * warp;
+    const int w_last = min(N, 64 * warp + 64) - 1;
+    const float tw_lo = blob[L.tP + w_first], tw_hi = blob[L.tP + w_last];
+    unsigned long long work = 0;  // evaluated obstacle-sample pairs (lane 0)
 
-    // ---- warp-0 coefficient state -----------------------------------------
+    // ---- coefficient state, identical in every warp ---------------------------
     const bool isy = lane >= 16;
     const int k = lane & 15;
-    const bool act = k < NC && warp == 0;
-    const int kk = k < NC ? k : 0;
-    const int gbase = lane & 16;
-    float c = 0.f, e = 0.f, lam = 0.f, u = 0.f, lampsi = 0.f, cbp = 0.f, corr = 0.f;
-
-    if (warp == 0) {
+    const bool act = k < NC;
+    const int kk = act ? k : 0;
+    float c = 0.f, e = 0.f, lam = 0.f, lampsi = 0.f, cbp = 0.f, corr = 0.f;
+    float* own = isy ? cyd : cxd;
+    float* vec = s_vec[warp][isy ? 1 : 0];
+    {
         const float* g = A.goals + 3 * l;
         const float yg = __ldg(g + 0), vg = __ldg(g + 1), ag = __ldg(g + 2);
         float cpsi, spsi;
         sincosf(psi0, &spsi, &cpsi);
         // boundary values (see mmpc.h), x relative to v0 t
-        float bx[5] = {0.f, v0 * cpsi - v0, acc0 * cpsi, vg - v0, ag};
-        float by[6] = {y0, v0 * spsi, acc0 * spsi, yg, 0.f, 0.f};
-        float bp[4] = {psi0, 0.f, 0.f, 0.f};
+        const float bx[6] = {0.f, v0 * cpsi - v0, acc0 * cpsi, vg - v0, ag, 0.f};
+        const float by[6] = {y0, v0 * spsi, acc0 * spsi, yg, 0.f, 0.f};
+        const float bp[4] = {psi0, 0.f, 0.f, 0.f};
         const int nb = isy ? 6 : 5;
-        const float* bb = isy ? by : bx;
         if (A.warm_c) {
             c = act && k < A.n ? __ldg(A.warm_c + (size_t)l * 3 * A.n + (isy ? A.n : 0) + k) : 0.f;
             if (!isy && act && k < A.n) c -= v0 * blob[L.lin + k];
         } else {
             const float* C0 = blob + (isy ? L.C0y : L.C0x) + kk * 8;
-            float s = 0.f;
-            for (int r = 0; r < nb; ++r) s = fmaf(C0[r], bb[r], s);
-            c = act ? s : 0.f;
+            float sacc = 0.f;
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+                if (r < nb) sacc = fmaf(C0[r], isy ? by[r] : bx[r], sacc);
+            c = act ? sacc : 0.f;
         }
         // K12 (b - A c^0): zero for an exact cold start.  Eq. lin_solve_xy_2
         // from any c^0 equals c^0 + K12 (b - A c^0) + K11 u^0 with u^0 taken at
         // c^0 itself, so this term is added by the first step (the
         // auxiliaries of iterate 0 are those of the start as given).
         {
-            const float* rows[6];
-            if (!isy) {
-                rows[0] = blob + L.P; rows[1] = blob + L.Pd; rows[2] = blob + L.Pdd;
-                rows[3] = blob + L.Pd + (N - 1) * NC; rows[4] = blob + L.Pdd + (N - 1) * NC; rows[5] = rows[4];
-            } else {
-                rows[0] = blob + L.P; rows[1] = blob + L.Pd; rows[2] = blob + L.Pdd;
-                rows[3] = blob + L.P + (N - 1) * NC; rows[4] = blob + L.Pd + (N - 1) * NC;
-                rows[5] = blob + L.Pdd + (N - 1) * NC;
-            }
+            // boundary rows: x uses (P0, Pd0, Pdd0, PdT, PddT), y (P0, Pd0, Pdd0, PT, PdT, PddT)
+            const int rx[6] = {0, 1, 2, 4, 5, 5};
             const float* K12 = blob + (isy ? L.K12y : L.K12x) + kk * 8;
 #pragma unroll
             for (int r = 0; r < 6; ++r) {
-                float ac = act ? rows[r][kk] * c : 0.f;  // A_r c, summed over the 16 lanes of the axis group
+                const int row = isy ? r : rx[r];
+                float ac = act ? blob[L.brow + row * NC + kk] * c : 0.f;  // A_r c over the 16 lanes of the axis group
                 ac += __shfl_xor_sync(FULL, ac, 8);
                 ac += __shfl_xor_sync(FULL, ac, 4);
                 ac += __shfl_xor_sync(FULL, ac, 2);
                 ac += __shfl_xor_sync(FULL, ac, 1);
-                if (r < nb) corr = fmaf(K12[r], bb[r] - ac, corr);
+                if (r < nb) corr = fmaf(K12[r], (isy ? by[r] : bx[r]) - ac, corr);
             }
             if (!act) corr = 0.f;
         }
-        if (!isy) {
+        {
             const float* Kp12 = blob + L.Kp12 + kk * 4;
-            float s = 0.f;
-            for (int r = 0; r < 4; ++r) s = fmaf(Kp12[r], bp[r], s);
-            cbp = act ? s : 0.f;
+            float sacc = 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sacc = fmaf(Kp12[r], bp[r], sacc);
+            cbp = (act && !isy) ? sacc : 0.f;
         }
         float cp0 = 0.f;
         if (!isy && act) {
@@ -437,6 +592,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 :
                 cp0 = k < A.n ? __ldg(A.warm_c + (size_t)l * 3 * A.n + 2 * A.n + k) : 0.f;
             } else {
                 const float* C0 = blob + L.C0p + kk * 4;
+#pragma unroll
                 for (int r = 0; r < 4; ++r) cp0 = fmaf(C0[r], bp[r], cp0);
             }
         }
@@ -445,14 +601,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 :
             if (!isy) lampsi = __ldg(A.warm_l + (size_t)l * 3 * A.n + 2 * A.n + k);
         }
         if (act) {
-            (isy ? s_cy : s_cx)[k] = c;
-            if (!isy) s_cp[k] = cp0;
+            reinterpret_cast<float2*>(own)[k] = f2(c);
+            if (!isy) reinterpret_cast<float2*>(cpd)[k] = f2(cp0);
         }
-        if (lane == 0) s_done = 0;
     }
-    __syncthreads();
+    __syncwarp();
 
-    float xd = 0.f, yd = 0.f, theta = 0.f;
+    float2 xd = f2(0.f), yd = f2(0.f), theta = f2(0.f);
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
     int kit = 0;
     const int iters = A.iters;
@@ -464,32 +619,497 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 :
         float v[VD];
 #pragma unroll
         for (int i = 0; i < VD; ++i) v[i] = 0.f;
-        if (has_t) {
-            const float x = dot_row<NC>(Prow, s_cx);
-            const float y = dot_row<NC>(Prow, s_cy);
-            const float xdd = dot_row<NC>(Pddrow, s_cx);
-            const float ydd = dot_row<NC>(Pddrow, s_cy);
-            const float ps = dot_row<NC>(Prow, s_cp);
+        {  // every lane runs this block (the culling is warp-collective); lanes
+           // without a sample pair read pair 0's rows and are masked at the end
+            const float2 x = dot_pair<NC>(PP, cxd);
+            const float2 y = dot_pair<NC>(PP, cyd);
+            const float2 xdd = dot_pair<NC>(PddP, cxd);
+            const float2 ydd = dot_pair<NC>(PddP, cyd);
+            const float2 ps = dot_pair<NC>(PP, cpd);
             // Eq. v_update and the non-holonomic rows v (cos psi, sin psi)
-            const float spd = sqrtf(fmaf(xd, xd, yd * yd));
-            const float vel = fminf(fmaxf(spd, A.v_min), A.v_max);
+            const float2 sp2 = __ffma2_rn(xd, xd, __fmul2_rn(yd, yd));
+            const float2 nvel = f2(-fminf(fmaxf(sqrtf(sp2.x), A.v_min), A.v_max),
+                                   -fminf(fmaxf(sqrtf(sp2.y), A.v_min), A.v_max));
+            float2 sn, cs;
+            heading_sincos(ps.x, &sn.x, &cs.x);
+            heading_sincos(ps.y, &sn.y, &cs.y);
+            const float2 evx = __ffma2_rn(nvel, cs, xd);
+            const float2 evy = __ffma2_rn(nvel, sn, yd);
+            // Eq. split_alpha_a: projection of (xddot, yddot) on the disk of radius a_max
+            const float2 an2 = __ffma2_rn(xdd, xdd, __fmul2_rn(ydd, ydd));
+            const float2 fr = f2(1.f - fminf(1.f, A.a_max * rsqrtf(an2.x)), 1.f - fminf(1.f, A.a_max * rsqrtf(an2.y)));
+            const float2 eax = __fmul2_rn(xdd, fr);
+            const float2 eay = __fmul2_rn(ydd, fr);
+            // Eq. split_alpha_o, summed over the obstacles
+            const float2 Xn = __fmul2_rn(x, f2(A.inv_a)), Yn = __fmul2_rn(y, f2(A.inv_b));
+            float2 Sx, Sy, R2;
+            if (A.cull) {
+                const int cnt = cull_list(obs, m, Xn, Yn, valid, tw_lo, tw_hi, olist, lane);
+                if (lane == 0) work += (unsigned long long)cnt * (unsigned)(w_last - w_first + 1);
+                if (resid) obstacle_sum2<true, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+                else obstacle_sum2<false, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+            } else {
+                if (lane == 0) work += (unsigned long long)m * (unsigned)(w_last - w_first + 1);
+                if (resid) obstacle_sum2<true, false>(obs, nullptr, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+                else obstacle_sum2<false, false>(obs, nullptr, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+            }
+            if (isnan(Sx.x) || isnan(Sy.x)) obstacle_sum_exact(obs, m, Xn.x, Yn.x, tt.x, a2, b2, Sx.x, Sy.x, R2.x);
+            if (isnan(Sx.y) || isnan(Sy.y)) obstacle_sum_exact(obs, m, Xn.y, Yn.y, tt.y, a2, b2, Sx.y, Sy.y, R2.y);
+            const float2 eox = __fmul2_rn(Sx, f2(-A.a));
+            const float2 eoy = __fmul2_rn(Sy, f2(-A.b));
+            const float2 dpsi = __fadd2_rn(ps, f2(-theta.x, -theta.y));
+#pragma unroll
+            for (int q = 0; q < NC; q += 2) {
+                const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
+                const float4 d4 = *reinterpret_cast<const float4*>(PdP + 2 * q);
+                const float4 dd4 = *reinterpret_cast<const float4*>(PddP + 2 * q);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 pr = h ? f2(p4.z, p4.w) : f2(p4.x, p4.y);
+                    const float2 dr = h ? f2(d4.z, d4.w) : f2(d4.x, d4.y);
+                    const float2 ddr = h ? f2(dd4.z, dd4.w) : f2(dd4.x, dd4.y);
+                    const float2 sx = __ffma2_rn(pr, eox, __ffma2_rn(ddr, eax, __fmul2_rn(dr, evx)));
+                    const float2 sy = __ffma2_rn(pr, eoy, __ffma2_rn(ddr, eay, __fmul2_rn(dr, evy)));
+                    const float2 sp = __fmul2_rn(pr, dpsi);
+                    v[q + h] = sx.x + sx.y;
+                    v[NC + q + h] = sy.x + sy.y;
+                    v[2 * NC + q + h] = sp.x + sp.y;
+                }
+            }
+            if (resid) {
+                const float2 ra = __ffma2_rn(eax, eax, __fmul2_rn(eay, eay));
+                const float2 rv = __ffma2_rn(evx, evx, __fmul2_rn(evy, evy));
+                const float2 rp = __fmul2_rn(dpsi, dpsi);
+                v[3 * NC + 0] = fmaf(R2.x, valid.x, R2.y * valid.y);
+                v[3 * NC + 1] = fmaf(ra.x, valid.x, ra.y * valid.y);
+                v[3 * NC + 2] = fmaf(rv.x, valid.x, rv.y * valid.y);
+                v[3 * NC + 3] = fmaf(rp.x, valid.x, rp.y * valid.y);
+            }
+            if (!has_pair) {
+#pragma unroll
+                for (int i = 0; i < VD; ++i) v[i] = 0.f;
+            }
+        }
+        reduce_store<VD>(v, red2, warp, RSD, lane);
+    };
+
+    // Velocity directions and the heading target theta = atan2(ydot, xdot)
+    // (Eq. split_psi), and the partial sums of P^T theta.
+    auto heading = [&](bool reduce) {
+        if (has_pair) {
+            xd = __fadd2_rn(dot_pair<NC>(PdP, cxd), f2(v0));
+            yd = dot_pair<NC>(PdP, cyd);
+            theta = f2(atan2f(yd.x, xd.x), atan2f(yd.y, xd.y));
+        }
+        if (reduce) {
+            float v[NC];
+#pragma unroll
+            for (int q = 0; q < NC; q += 2) {
+                const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
+                const float2 s0 = __fmul2_rn(f2(p4.x, p4.y), theta);
+                const float2 s1 = __fmul2_rn(f2(p4.z, p4.w), theta);
+                v[q] = has_pair ? s0.x + s0.y : 0.f;
+                v[q + 1] = has_pair ? s1.x + s1.y : 0.f;
+            }
+            reduce_store<NC>(v, red1, warp, RSB, lane);
+        }
+    };
+
+    // Eq. split_psi / lin_solve_psi_2: c_psi = K11_psi (rho P^T theta +
+    // lambda_psi) + K12_psi b_psi, in every warp.
+    auto psi_step = [&]() {
+        float pth = 0.f;
+        for (int w = 0; w < nwarps; ++w) pth += red1[w * RSB + kk];
+        if (!isy && act) reinterpret_cast<float2*>(vec)[k] = f2(fmaf(rho, pth, lampsi));
+        __syncwarp();
+        if (!isy && act) {
+            const float cp = cbp + dot_dup<NC>(blob + L.Kp11 + kk * NC, vec);
+            reinterpret_cast<float2*>(cpd)[k] = f2(cp);
+        }
+        __syncwarp();
+    };
+
+    // After a projection phase, in every warp: multiplier update (Sec. III-E,
+    // "Multiplier Update") unless `first`, the increment u = lambda - Q c -
+    // rho F^T (F c - g), the residual check, then step (split_xy) unless done.
+    // Returns done.
+    auto finish = [&](bool first, bool check) -> bool {
+        float ftd = 0.f, pd = 0.f;
+        for (int w = 0; w < nwarps; ++w) {
+            ftd += red2[w * RSD + (isy ? NC : 0) + kk];
+            pd += red2[w * RSD + 2 * NC + kk];
+        }
+        if (check) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                float sacc = 0.f;
+                for (int w = 0; w < nwarps; ++w) sacc += red2[w * RSD + 3 * NC + r];
+                rsum[r] = sacc;
+            }
+        }
+        if (!first && act) {
+            lam = fmaf(-rho, ftd, lam);
+            if (!isy) lampsi = fmaf(-rho, pd, lampsi);
+        }
+        const float qc = dot_dup<NC>(blob + L.Q + kk * NC, own);
+        const float u = act ? (lam - qc - rho * ftd) : 0.f;
+        bool done = kit >= iters;
+        if (!first && check && A.tol > 0.f && kit % A.check_every == 0) {
+            const float conv = fmaxf(sqrtf(rsum[0]), fmaxf(sqrtf(rsum[1]), sqrtf(rsum[2])));
+            done = done || conv <= A.tol;
+        }
+        if (!done) {
+            // Eq. lin_solve_xy_2 in increment form, K11 applied as hi + lo
+            if (act) reinterpret_cast<float2*>(vec)[k] = f2(u);
+            __syncwarp();
+            if (act) {
+                const float d0 = dot_dup<NC>(blob + (isy ? L.Kyh : L.Kxh) + kk * NC, vec);
+                const float d1 = dot_dup<NC>(blob + (isy ? L.Kyl : L.Kxl) + kk * NC, vec);
+                const float dd = (d0 + d1) + (first ? e + corr : e);
+                const float snew = c + dd;
+                e = dd - (snew - c);
+                c = snew;
+            }
+            __syncwarp();
+            if (act) reinterpret_cast<float2*>(own)[k] = f2(c);
+            __syncwarp();
+        }
+        return done;
+    };
+
+    // ---- initial iterate: auxiliaries of c^0, no multiplier update -------
+    heading(false);
+    project(true);
+    __syncthreads();
+    bool done = finish(true, true);
+
+    // ---- Algorithm 1 ---------------------------------------------------------
+    while (!done) {
+        ++kit;
+        const bool check = (kit % A.check_every == 0) || kit >= iters;
+        heading(true);   // theta and the partial sums of P^T theta
+        __syncthreads();
+        psi_step();      // Eq. split_psi
+        project(check);  // Eqs. split_v, split_alpha_o, split_alpha_a; partial sums
+        __syncthreads();
+        done = finish(false, check);  // multipliers, residual check, step (split_xy)
+    }
+
+    // ---- outputs -------------------------------------------------------------
+    if (warp == 0) {
+        const int n = A.n;
+        const size_t o = (size_t)l * 3 * n;
+        if (act && k < n) {
+            if (!isy) {
+                A.coef_out[o + k] = (c + e) + v0 * blob[L.lin + k];
+                A.coef_out[o + 2 * n + k] = cpd[2 * k];
+            } else {
+                A.coef_out[o + n + k] = c + e;
+            }
+            if (A.lam_out) {
+                A.lam_out[o + (isy ? n : 0) + k] = lam;
+                if (!isy) A.lam_out[o + 2 * n + k] = lampsi;
+            }
+        }
+        if (A.resid_out && lane < 4) A.resid_out[(size_t)l * 4 + lane] = sqrtf(rsum[lane]);
+        if (A.iters_out && lane == 0) A.iters_out[l] = kit;
+    }
+    if (lane == 0 && A.work) atomicAdd(A.work, work);
+}
+
+// ---------------------------------------------------------------------------
+// One-sample variant of the fused AM kernel: thread t owns sample t (block:
+// 32 ceil(N/32) threads, at most 8 warps), for batches too small to give the
+// pair kernel enough warps.  Same algorithm, state layout and barriers; the
+// obstacle terms are the same expressions on scalars, accumulated in the
+// same obstacle order.
+// ---------------------------------------------------------------------------
+
+// obs1 holds per obstacle (-x0/a, -y0/b, -vx/a, -vy/b) in the moving frame.
+template <bool RESID, bool LIST>
+__device__ __forceinline__ void obstacle_sum1(const float4* __restrict__ obs, const int* __restrict__ list, int m,
+                                              float Xn, float Yn, float tt, float a2, float b2, float& Sx, float& Sy,
+                                              float& R2)
+{
+    float sx = 0.f, sy = 0.f, r = 0.f;
+    int j = 0;
+#pragma unroll 2
+    for (; j + 1 < m; j += 2) {
+        const float4 o0 = obs[LIST ? list[j] : j];
+        const float4 o1 = obs[LIST ? list[j + 1] : j + 1];
+        const float nx0 = Xn + fmaf(o0.z, tt, o0.x), ny0 = Yn + fmaf(o0.w, tt, o0.y);
+        const float nx1 = Xn + fmaf(o1.z, tt, o1.x), ny1 = Yn + fmaf(o1.w, tt, o1.y);
+        const float s0 = fmaxf(rsqrtf(fmaf(nx0, nx0, ny0 * ny0)) - 1.f, 0.f);
+        const float s1 = fmaxf(rsqrtf(fmaf(nx1, nx1, ny1 * ny1)) - 1.f, 0.f);
+        sx = fmaf(nx1, s1, fmaf(nx0, s0, sx));
+        sy = fmaf(ny1, s1, fmaf(ny0, s0, sy));
+        if (RESID)
+            r = fmaf(s1 * s1, fmaf(a2 * nx1, nx1, b2 * ny1 * ny1), fmaf(s0 * s0, fmaf(a2 * nx0, nx0, b2 * ny0 * ny0), r));
+    }
+    if (j < m) {
+        const float4 o0 = obs[LIST ? list[j] : j];
+        const float nx0 = Xn + fmaf(o0.z, tt, o0.x), ny0 = Yn + fmaf(o0.w, tt, o0.y);
+        const float s0 = fmaxf(rsqrtf(fmaf(nx0, nx0, ny0 * ny0)) - 1.f, 0.f);
+        sx = fmaf(nx0, s0, sx);
+        sy = fmaf(ny0, s0, sy);
+        if (RESID) r = fmaf(s0 * s0, fmaf(a2 * nx0, nx0, b2 * ny0 * ny0), r);
+    }
+    Sx = sx;
+    Sy = sy;
+    R2 = r;
+}
+
+__device__ __noinline__ void obstacle_sum1_exact(const float4* __restrict__ obs, int m, float Xn, float Yn, float tt,
+                                                 float a2, float b2, float& Sx, float& Sy, float& R2)
+{
+    Sx = 0.f;
+    Sy = 0.f;
+    R2 = 0.f;
+    for (int j = 0; j < m; ++j) {
+        const float4 o = obs[j];
+        const float nx = Xn + fmaf(o.z, tt, o.x);
+        const float ny = Yn + fmaf(o.w, tt, o.y);
+        const float q = fmaf(nx, nx, ny * ny);
+        if (q == 0.f) {  // alpha = atan2(0, 0) = 0, d = 1: the row is (-a, 0)
+            Sx += 1.f;
+            R2 += a2;
+        } else {
+            const float sj = fmaxf(rsqrtf(q) - 1.f, 0.f);
+            Sx = fmaf(nx, sj, Sx);
+            Sy = fmaf(ny, sj, Sy);
+            R2 = fmaf(sj * sj, fmaf(a2 * nx, nx, b2 * ny * ny), R2);
+        }
+    }
+}
+
+// Exact culling as cull_list, for a warp of single samples.
+__device__ __forceinline__ int cull_list1(const float4* __restrict__ obs, int m, float Xn, float Yn, bool valid,
+                                          float tw_lo, float tw_hi, int* list, int lane)
+{
+    const float inf = __int_as_float(0x7f800000);
+    const float xlo = warp_min(valid ? Xn : inf), xhi = warp_max(valid ? Xn : -inf);
+    const float ylo = warp_min(valid ? Yn : inf), yhi = warp_max(valid ? Yn : -inf);
+    const bool any_bad = __any_sync(FULL, valid && !(isfinite(Xn) && isfinite(Yn)));
+    constexpr float M = 1.001f;
+    const unsigned below = (1u << lane) - 1u;
+    int count = 0;
+    for (int j0 = 0; j0 < m; j0 += 32) {
+        const int j = j0 + lane;
+        bool keep = false;
+        if (j < m) {
+            const float4 o = obs[j];
+            const float e1 = -fmaf(o.z, tw_lo, o.x), e2 = -fmaf(o.z, tw_hi, o.x);
+            const float f1 = -fmaf(o.w, tw_lo, o.y), g1 = -fmaf(o.w, tw_hi, o.y);
+            const bool apart = (xlo - fmaxf(e1, e2) >= M) || (fminf(e1, e2) - xhi >= M) ||
+                               (ylo - fmaxf(f1, g1) >= M) || (fminf(f1, g1) - yhi >= M);
+            keep = any_bad || !apart;
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) list[count + __popc(bal & below)] = j;
+        count += __popc(bal);
+    }
+    __syncwarp();
+    return count;
+}
+
+// dot product of two 16-byte aligned vectors of NC floats; four partial sums.
+template <int NC>
+__device__ __forceinline__ float dot_plain(const float* __restrict__ a, const float* __restrict__ b)
+{
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NC; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(a + j);
+        const float4 y = *reinterpret_cast<const float4*>(b + j);
+        acc[0] = fmaf(x.x, y.x, acc[0]);
+        acc[1] = fmaf(x.y, y.y, acc[1]);
+        acc[2] = fmaf(x.z, y.z, acc[2]);
+        acc[3] = fmaf(x.w, y.w, acc[3]);
+    }
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+// single dot product chain (the sample-row evaluations)
+template <int NC>
+__device__ __forceinline__ float dot_row(const float* __restrict__ row, const float* __restrict__ c)
+{
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < NC; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(row + j);
+        const float4 y = *reinterpret_cast<const float4*>(c + j);
+        acc = fmaf(x.x, y.x, acc);
+        acc = fmaf(x.y, y.y, acc);
+        acc = fmaf(x.z, y.z, acc);
+        acc = fmaf(x.w, y.w, acc);
+    }
+    return acc;
+}
+
+template <int MAXT>
+struct MinBlocks1 {
+    static constexpr int value = MAXT <= 128 ? 7 : (MAXT <= 256 ? 3 : 1);
+};
+
+template <int NC, int MAXT>
+__global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel1(const SolveArgs A)
+{
+    constexpr int VD = SolveSmem<NC>::VD;
+    constexpr int RSD = SolveSmem<NC>::RSD;
+    constexpr int RSB = SolveSmem<NC>::RSB;
+    extern __shared__ __align__(16) float smem[];
+    __shared__ __align__(16) float s_cx[MAX_WARPS][NC];  // per-warp copies of the coefficient vectors
+    __shared__ __align__(16) float s_cy[MAX_WARPS][NC];
+    __shared__ __align__(16) float s_cp[MAX_WARPS][NC];
+    __shared__ __align__(16) float s_vec[MAX_WARPS][2][NC];
+    __shared__ __align__(8) unsigned long long s_mbar;
+
+    const int l = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int N = A.N, m = A.m;
+    const BlobLayout& L = A.L;
+    const int base = L.common;  // the staged region starts at the common section
+
+    float* blob = smem;  // blob[x - base] holds global section offset x
+    float4* obs = reinterpret_cast<float4*>(smem + (L.total - base));
+    float* red1 = reinterpret_cast<float*>(obs + m);
+    float* red2 = red1 + MAX_WARPS * RSB;
+    int* olist = reinterpret_cast<int*>(red2 + MAX_WARPS * RSD) + warp * m;
+    float* cx = s_cx[warp];
+    float* cy = s_cy[warp];
+    float* cpv = s_cp[warp];
+
+    const float y0 = __ldg(A.ego + 0), v0 = __ldg(A.ego + 1), psi0 = __ldg(A.ego + 2), acc0 = __ldg(A.ego + 3);
+    for (int j = tid; j < m; j += blockDim.x) {
+        const float* o = A.obst + 4 * j;
+        obs[j] = make_float4(-__ldg(o + 0) * A.inv_a, -__ldg(o + 1) * A.inv_b, -(__ldg(o + 2) - v0) * A.inv_a,
+                             -__ldg(o + 3) * A.inv_b);
+    }
+    if (!stage_blob(blob, A.blob + base, (L.total - base) * 4, &s_mbar, A.err_flag)) return;
+
+    const float rho = A.rho;
+    const float a2 = A.a * A.a, b2 = A.b * A.b;
+    const bool has_t = tid < N;
+    const int ts = has_t ? tid : 0;
+    const float* Prow = blob + (L.P - base) + ts * NC;
+    const float* Pdrow = blob + (L.Pd - base) + ts * NC;
+    const float* Pddrow = blob + (L.Pdd - base) + ts * NC;
+    const float tt = blob[(L.t - base) + ts];
+    const int w_first = 32 * warp;
+    const int w_last = min(N, 32 * warp + 32) - 1;
+    const float tw_lo = blob[(L.t - base) + w_first], tw_hi = blob[(L.t - base) + w_last];
+    unsigned long long work = 0;
+
+    const bool isy = lane >= 16;
+    const int k = lane & 15;
+    const bool act = k < NC;
+    const int kk = act ? k : 0;
+    float c = 0.f, e = 0.f, lam = 0.f, lampsi = 0.f, cbp = 0.f, corr = 0.f;
+    float* own = isy ? cy : cx;
+    float* vec = s_vec[warp][isy ? 1 : 0];
+    {
+        const float* g = A.goals + 3 * l;
+        const float yg = __ldg(g + 0), vg = __ldg(g + 1), ag = __ldg(g + 2);
+        float cpsi, spsi;
+        sincosf(psi0, &spsi, &cpsi);
+        const float bx[6] = {0.f, v0 * cpsi - v0, acc0 * cpsi, vg - v0, ag, 0.f};
+        const float by[6] = {y0, v0 * spsi, acc0 * spsi, yg, 0.f, 0.f};
+        const float bp[4] = {psi0, 0.f, 0.f, 0.f};
+        const int nb = isy ? 6 : 5;
+        if (A.warm_c) {
+            c = act && k < A.n ? __ldg(A.warm_c + (size_t)l * 3 * A.n + (isy ? A.n : 0) + k) : 0.f;
+            if (!isy && act && k < A.n) c -= v0 * blob[(L.lin - base) + k];
+        } else {
+            const float* C0 = blob + ((isy ? L.C0y : L.C0x) - base) + kk * 8;
+            float sacc = 0.f;
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+                if (r < nb) sacc = fmaf(C0[r], isy ? by[r] : bx[r], sacc);
+            c = act ? sacc : 0.f;
+        }
+        {  // K12 (b - A c^0), added by the first step (see the pair kernel)
+            const int rx[6] = {0, 1, 2, 4, 5, 5};
+            const float* K12 = blob + ((isy ? L.K12y : L.K12x) - base) + kk * 8;
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                const int row = isy ? r : rx[r];
+                float ac = act ? blob[(L.brow - base) + row * NC + kk] * c : 0.f;
+                ac += __shfl_xor_sync(FULL, ac, 8);
+                ac += __shfl_xor_sync(FULL, ac, 4);
+                ac += __shfl_xor_sync(FULL, ac, 2);
+                ac += __shfl_xor_sync(FULL, ac, 1);
+                if (r < nb) corr = fmaf(K12[r], (isy ? by[r] : bx[r]) - ac, corr);
+            }
+            if (!act) corr = 0.f;
+        }
+        {
+            const float* Kp12 = blob + (L.Kp12 - base) + kk * 4;
+            float sacc = 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sacc = fmaf(Kp12[r], bp[r], sacc);
+            cbp = (act && !isy) ? sacc : 0.f;
+        }
+        float cp0 = 0.f;
+        if (!isy && act) {
+            if (A.warm_c) {
+                cp0 = k < A.n ? __ldg(A.warm_c + (size_t)l * 3 * A.n + 2 * A.n + k) : 0.f;
+            } else {
+                const float* C0 = blob + (L.C0p - base) + kk * 4;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) cp0 = fmaf(C0[r], bp[r], cp0);
+            }
+        }
+        if (A.warm_l && act && k < A.n) {
+            lam = __ldg(A.warm_l + (size_t)l * 3 * A.n + (isy ? A.n : 0) + k);
+            if (!isy) lampsi = __ldg(A.warm_l + (size_t)l * 3 * A.n + 2 * A.n + k);
+        }
+        if (act) {
+            own[k] = c;
+            if (!isy) cpv[k] = cp0;
+        }
+    }
+    __syncwarp();
+
+    float xd = 0.f, yd = 0.f, theta = 0.f;
+    float rsum[4] = {0.f, 0.f, 0.f, 0.f};
+    int kit = 0;
+    const int iters = A.iters;
+
+    auto project = [&](bool resid) {
+        float v[VD];
+#pragma unroll
+        for (int i = 0; i < VD; ++i) v[i] = 0.f;
+        {
+            const float x = dot_row<NC>(Prow, cx);
+            const float y = dot_row<NC>(Prow, cy);
+            const float xdd = dot_row<NC>(Pddrow, cx);
+            const float ydd = dot_row<NC>(Pddrow, cy);
+            const float ps = dot_row<NC>(Prow, cpv);
+            const float vel = fminf(fmaxf(sqrtf(fmaf(xd, xd, yd * yd)), A.v_min), A.v_max);
             float sn, cs;
-            sincosf(ps, &sn, &cs);
+            heading_sincos(ps, &sn, &cs);
             const float evx = fmaf(-vel, cs, xd);
             const float evy = fmaf(-vel, sn, yd);
-            // Eq. split_alpha_a: projection of (xddot, yddot) on the disk of radius a_max
             const float an2 = fmaf(xdd, xdd, ydd * ydd);
-            const float sc = fminf(1.f, A.a_max * rsqrtf(an2));
-            const float eax = xdd * (1.f - sc);
-            const float eay = ydd * (1.f - sc);
-            // Eq. split_alpha_o, summed over the obstacles
-            float Sx, Sy, R2;
+            const float fr = 1.f - fminf(1.f, A.a_max * rsqrtf(an2));
+            const float eax = xdd * fr, eay = ydd * fr;
             const float Xn = x * A.inv_a, Yn = y * A.inv_b;
-            if (resid) obstacle_sum<true>(obs, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-            else obstacle_sum<false>(obs, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-            if (isnan(Sx) || isnan(Sy)) obstacle_sum_exact(obs, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-            const float eox = -A.a * Sx;
-            const float eoy = -A.b * Sy;
+            float Sx, Sy, R2;
+            if (A.cull) {
+                const int cnt = cull_list1(obs, m, Xn, Yn, has_t, tw_lo, tw_hi, olist, lane);
+                if (lane == 0) work += (unsigned long long)cnt * (unsigned)(w_last - w_first + 1);
+                if (resid) obstacle_sum1<true, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+                else obstacle_sum1<false, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+            } else {
+                if (lane == 0) work += (unsigned long long)m * (unsigned)(w_last - w_first + 1);
+                if (resid) obstacle_sum1<true, false>(obs, nullptr, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+                else obstacle_sum1<false, false>(obs, nullptr, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+            }
+            if (isnan(Sx) || isnan(Sy)) obstacle_sum1_exact(obs, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+            const float eox = -A.a * Sx, eoy = -A.b * Sy;
             const float dpsi = ps - theta;
 #pragma unroll
             for (int q = 0; q < NC; q += 4) {
@@ -512,16 +1132,18 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 :
                 v[3 * NC + 2] = fmaf(evx, evx, evy * evy);
                 v[3 * NC + 3] = dpsi * dpsi;
             }
+            if (!has_t) {
+#pragma unroll
+                for (int i = 0; i < VD; ++i) v[i] = 0.f;
+            }
         }
-        reduce_store<VD>(v, red, warp, RSD, lane);
+        reduce_store<VD>(v, red2, warp, RSD, lane);
     };
 
-    // Velocity directions and the heading target theta = atan2(ydot, xdot)
-    // (Eq. split_psi), and the partial sums of P^T theta.
     auto heading = [&](bool reduce) {
         if (has_t) {
-            xd = dot_row<NC>(Pdrow, s_cx) + v0;
-            yd = dot_row<NC>(Pdrow, s_cy);
+            xd = dot_row<NC>(Pdrow, cx) + v0;
+            yd = dot_row<NC>(Pdrow, cy);
             theta = atan2f(yd, xd);
         }
         if (reduce) {
@@ -534,104 +1156,84 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 :
                 v[q + 2] = has_t ? p4.z * theta : 0.f;
                 v[q + 3] = has_t ? p4.w * theta : 0.f;
             }
-            reduce_store<NC>(v, red, warp, RSB, lane);
+            reduce_store<NC>(v, red1, warp, RSB, lane);
         }
     };
 
-    // Warp 0 after a projection phase: multiplier update (Sec. III-E,
-    // "Multiplier Update") unless `first`, the increment u = lambda - Q c -
-    // rho F^T (F c - g), residual check; then step (split_xy) if not done.
-    auto finish = [&](bool first, bool check) {
+    auto psi_step = [&]() {
+        float pth = 0.f;
+        for (int w = 0; w < nwarps; ++w) pth += red1[w * RSB + kk];
+        if (!isy && act) vec[k] = fmaf(rho, pth, lampsi);
+        __syncwarp();
+        if (!isy && act) cpv[k] = cbp + dot_plain<NC>(blob + (L.Kp11 - base) + kk * NC, vec);
+        __syncwarp();
+    };
+
+    auto finish = [&](bool first, bool check) -> bool {
         float ftd = 0.f, pd = 0.f;
         for (int w = 0; w < nwarps; ++w) {
-            ftd += red[w * RSD + (isy ? NC : 0) + kk];
-            pd += red[w * RSD + 2 * NC + kk];
+            ftd += red2[w * RSD + (isy ? NC : 0) + kk];
+            pd += red2[w * RSD + 2 * NC + kk];
         }
         if (check) {
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                float s = 0.f;
-                for (int w = 0; w < nwarps; ++w) s += red[w * RSD + 3 * NC + r];
-                rsum[r] = s;
+                float sacc = 0.f;
+                for (int w = 0; w < nwarps; ++w) sacc += red2[w * RSD + 3 * NC + r];
+                rsum[r] = sacc;
             }
         }
         if (!first && act) {
             lam = fmaf(-rho, ftd, lam);
             if (!isy) lampsi = fmaf(-rho, pd, lampsi);
         }
-        const float* Qrow = blob + L.Q + kk * NC;
-        float qc = 0.f;
-#pragma unroll
-        for (int j = 0; j < NC; ++j) qc = fmaf(Qrow[j], __shfl_sync(FULL, c, gbase + j), qc);
-        u = act ? (lam - qc - rho * ftd) : 0.f;
+        const float qc = dot_plain<NC>(blob + (L.Q - base) + kk * NC, own);
+        const float u = act ? (lam - qc - rho * ftd) : 0.f;
         bool done = kit >= iters;
         if (!first && check && A.tol > 0.f && kit % A.check_every == 0) {
             const float conv = fmaxf(sqrtf(rsum[0]), fmaxf(sqrtf(rsum[1]), sqrtf(rsum[2])));
             done = done || conv <= A.tol;
         }
         if (!done) {
-            // Eq. lin_solve_xy_2 in increment form, K11 applied as hi + lo
-            const float* Kh = blob + (isy ? L.Kyh : L.Kxh) + kk * NC;
-            const float* Kl = blob + (isy ? L.Kyl : L.Kxl) + kk * NC;
-            float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const float uj = __shfl_sync(FULL, u, gbase + j);
-                d0 = fmaf(Kh[j], uj, d0);
-                d1 = fmaf(Kl[j], uj, d1);
-            }
+            if (act) vec[k] = u;
+            __syncwarp();
             if (act) {
+                const float d0 = dot_plain<NC>(blob + ((isy ? L.Kyh : L.Kxh) - base) + kk * NC, vec);
+                const float d1 = dot_plain<NC>(blob + ((isy ? L.Kyl : L.Kxl) - base) + kk * NC, vec);
                 const float dd = (d0 + d1) + (first ? e + corr : e);
-                const float s = c + dd;
-                e = dd - (s - c);
-                c = s;
-                (isy ? s_cy : s_cx)[k] = c;
+                const float snew = c + dd;
+                e = dd - (snew - c);
+                c = snew;
             }
+            __syncwarp();
+            if (act) own[k] = c;
+            __syncwarp();
         }
-        if (lane == 0) s_done = done ? 1 : 0;
+        return done;
     };
 
-    // ---- initial iterate: auxiliaries of c^0, no multiplier update -------
     heading(false);
     project(true);
     __syncthreads();
-    if (warp == 0) finish(true, true);
-    __syncthreads();
-
-    // ---- Algorithm 1 ---------------------------------------------------------
-    while (!*reinterpret_cast<volatile int*>(&s_done)) {
+    bool done = finish(true, true);
+    while (!done) {
         ++kit;
         const bool check = (kit % A.check_every == 0) || kit >= iters;
-        // Eq. split_psi: theta and P^T theta
         heading(true);
         __syncthreads();
-        if (warp == 0 && !isy) {
-            float pth = 0.f;
-            for (int w = 0; w < nwarps; ++w) pth += red[w * RSB + kk];
-            const float r = fmaf(rho, pth, lampsi);
-            const float* Kp = blob + L.Kp11 + kk * NC;
-            float cp = cbp;
-#pragma unroll
-            for (int j = 0; j < NC; ++j) cp = fmaf(Kp[j], __shfl_sync(0x0000ffffu, r, j), cp);
-            if (act) s_cp[k] = cp;
-        }
-        __syncthreads();
-        // Eqs. split_v, split_alpha_o, split_alpha_a and the partial sums
+        psi_step();
         project(check);
         __syncthreads();
-        // multipliers, residual check and the next step (split_xy)
-        if (warp == 0) finish(false, check);
-        __syncthreads();
+        done = finish(false, check);
     }
 
-    // ---- outputs -------------------------------------------------------------
     if (warp == 0) {
         const int n = A.n;
         const size_t o = (size_t)l * 3 * n;
         if (act && k < n) {
             if (!isy) {
-                A.coef_out[o + k] = (c + e) + v0 * blob[L.lin + k];
-                A.coef_out[o + 2 * n + k] = s_cp[k];
+                A.coef_out[o + k] = (c + e) + v0 * blob[(L.lin - base) + k];
+                A.coef_out[o + 2 * n + k] = cpv[k];
             } else {
                 A.coef_out[o + n + k] = c + e;
             }
@@ -643,6 +1245,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128) ? 7 : ((MAXT <= 256) ? 3 :
         if (A.resid_out && lane < 4) A.resid_out[(size_t)l * 4 + lane] = sqrtf(rsum[lane]);
         if (A.iters_out && lane == 0) A.iters_out[l] = kit;
     }
+    if (lane == 0 && A.work) atomicAdd(A.work, work);
 }
 
 // ---------------------------------------------------------------------------
@@ -723,7 +1326,9 @@ struct mmpc_ctx {
     int NC;
     mmpc::BlobLayout L;
     float* d_blob = nullptr;
-    unsigned long long* d_scratch = nullptr;  // [0] packed argmin key, [1] low: ticket, high: error flags
+    unsigned long long* d_scratch = nullptr;  // [0] packed argmin key, [1] low: ticket, high: error flags, [2] work count
+    int sm_count = -1;                        // SMs of the device (queried on the first solve)
+    int last_variant = 0;
     std::string err = "no error";
 };
 
@@ -743,10 +1348,9 @@ int cuda_fail(mmpc_ctx* ctx, cudaError_t e, const char* what)
     return fail(ctx, MMPC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-template <int NC, int MAXT>
-int launch_solve_t(mmpc_ctx* ctx, const SolveArgs& a, int threads, size_t smem, cudaStream_t st)
+template <typename K>
+int launch_kernel(mmpc_ctx* ctx, K kern, const SolveArgs& a, int threads, size_t smem, cudaStream_t st)
 {
-    auto kern = am_solve_kernel<NC, MAXT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     kern<<<a.B, threads, smem, st>>>(a);
@@ -755,12 +1359,48 @@ int launch_solve_t(mmpc_ctx* ctx, const SolveArgs& a, int threads, size_t smem, 
     return MMPC_OK;
 }
 
+// The pair kernel: ceil(N/2) pair threads rounded up to warps.
 template <int NC>
-int launch_solve_nc(mmpc_ctx* ctx, const SolveArgs& a, int threads, size_t smem, cudaStream_t st)
+void* pair_kernel(int threads)
 {
-    if (threads <= 128) return launch_solve_t<NC, 128>(ctx, a, threads, smem, st);
-    if (threads <= 256) return launch_solve_t<NC, 256>(ctx, a, threads, smem, st);
-    return launch_solve_t<NC, 512>(ctx, a, threads, smem, st);
+    if (threads <= 64) return (void*)am_solve_kernel<NC, 64>;
+    if (threads <= 128) return (void*)am_solve_kernel<NC, 128>;
+    return (void*)am_solve_kernel<NC, 256>;
+}
+
+// The one-sample kernel: N threads rounded up to warps.
+template <int NC>
+void* single_kernel(int threads)
+{
+    if (threads <= 128) return (void*)am_solve_kernel1<NC, 128>;
+    return (void*)am_solve_kernel1<NC, 256>;
+}
+
+struct LaunchShape {
+    void* kern;
+    int threads;
+    size_t smem;
+};
+
+LaunchShape shape_for(const mmpc_ctx* ctx, int variant, int m)
+{
+    const int N = ctx->p.N;
+    const int RSD = ctx->NC == 12 ? SolveSmem<12>::RSD : SolveSmem<16>::RSD;
+    const int RSB = ctx->NC;
+    const size_t red = sizeof(float) * (size_t)MAX_WARPS * (RSB + RSD);
+    LaunchShape s{};
+    if (variant == 1) {
+        s.threads = 32 * ((N + 31) / 32);
+        s.smem = sizeof(float) * (size_t)(ctx->L.total - ctx->L.common) + 16 * (size_t)m + red +
+                 sizeof(int) * (size_t)(s.threads / 32) * m;
+        s.kern = ctx->NC == 12 ? single_kernel<12>(s.threads) : single_kernel<16>(s.threads);
+    } else {
+        const int NP = (N + 1) / 2;
+        s.threads = 32 * ((NP + 31) / 32);
+        s.smem = sizeof(float) * (size_t)ctx->L.rows1 + 32 * (size_t)m + red + sizeof(int) * (size_t)(s.threads / 32) * m;
+        s.kern = ctx->NC == 12 ? pair_kernel<12>(s.threads) : pair_kernel<16>(s.threads);
+    }
+    return s;
 }
 
 bool finite4(float v) { return std::isfinite(v); }
@@ -783,6 +1423,7 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
     const int NC = n <= 12 ? 12 : 16;
     const BlobLayout L = blob_layout(N, NC);
     std::vector<float> h(L.total, 0.f);
+    auto h_set = [&](int i, float v) { h[i] = v; };
     auto mat = [&](size_t src, int dst, int rows, int cols, int dcols, bool lo) {
         for (int r = 0; r < rows; ++r)
             for (int c = 0; c < cols; ++c) {
@@ -791,6 +1432,23 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
                 h[dst + r * dcols + c] = lo ? (float)(v - (double)hi) : hi;
             }
     };
+    // basis rows of the sample pairs (2i, 2i+1), interleaved per coefficient
+    const int NP = (N + 1) / 2;
+    auto pairs = [&](size_t src, int dst) {
+        for (int i = 0; i < NP; ++i)
+            for (int h = 0; h < 2; ++h) {
+                const int smp = 2 * i + h;
+                if (smp >= N) continue;
+                for (int c = 0; c < n; ++c) h_set(dst + (i * NC + c) * 2 + h, (float)buf[src + (size_t)smp * n + c]);
+            }
+    };
+    pairs(PL.P, L.PP);
+    pairs(PL.Pd, L.PdP);
+    pairs(PL.Pdd, L.PddP);
+    for (int smp = 0; smp < N; ++smp) h_set(L.tP + smp, (float)buf[PL.t + smp]);
+    const size_t brow_src[6] = {PL.P, PL.Pd, PL.Pdd, PL.P + (size_t)(N - 1) * n, PL.Pd + (size_t)(N - 1) * n,
+                                PL.Pdd + (size_t)(N - 1) * n};
+    for (int r = 0; r < 6; ++r) mat(brow_src[r], L.brow + r * NC, 1, n, n, false);
     mat(PL.P, L.P, N, n, NC, false);
     mat(PL.Pd, L.Pd, N, n, NC, false);
     mat(PL.Pdd, L.Pdd, N, n, NC, false);
@@ -815,10 +1473,10 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
     ctx->NC = NC;
     ctx->L = L;
     cudaError_t e = cudaMalloc(&ctx->d_blob, sizeof(float) * L.total);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, 3 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_blob, h.data(), sizeof(float) * L.total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        const unsigned long long init[2] = {~0ull, 0ull};
+        const unsigned long long init[3] = {~0ull, 0ull, 0ull};
         e = cudaMemcpy(ctx->d_scratch, init, sizeof(init), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
@@ -853,13 +1511,31 @@ extern "C" int mmpc_solve(mmpc_ctx* ctx, const float* ego, const float* obst, in
     a.ego = ego; a.obst = obst; a.goals = goals; a.warm_c = warm_coef; a.warm_l = warm_lam;
     a.coef_out = coef_out; a.lam_out = lam_out; a.resid_out = resid_out; a.iters_out = iters_out;
     a.err_flag = reinterpret_cast<unsigned*>(ctx->d_scratch + 1) + 1;
-    const int threads = 32 * ((p.N + 31) / 32);
-    const int nw = threads / 32;
-    const int RSD = ctx->NC == 12 ? SolveSmem<12>::RSD : SolveSmem<16>::RSD;
-    const size_t smem = sizeof(float) * (size_t)ctx->L.total + 16 * (size_t)m + sizeof(float) * (size_t)nw * RSD;
-    if (smem > 227 * 1024) return fail(ctx, MMPC_ERR_SHAPE, "scene does not fit in shared memory");
+    a.work = ctx->d_scratch + 2;
+    a.cull = p.cull ? 1 : 0;
+    int variant = p.variant;
+    if (variant == 0) {
+        // automatic: the pair kernel (half the instructions per sample),
+        // except for batches of at most one trajectory per SM, where the
+        // one-sample kernel's four warps per trajectory shorten the latency
+        variant = 2;
+        if (p.N <= 256) {
+            if (ctx->sm_count < 0) {
+                int dev = 0, sms = 0;
+                cudaError_t e = cudaGetDevice(&dev);
+                if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "device query");
+                ctx->sm_count = sms;
+            }
+            if (B <= ctx->sm_count) variant = 1;
+        }
+    }
+    const LaunchShape sh = shape_for(ctx, variant, m);
+    if (sh.smem > 227 * 1024) return fail(ctx, MMPC_ERR_SHAPE, "scene does not fit in shared memory");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    return ctx->NC == 12 ? launch_solve_nc<12>(ctx, a, threads, smem, st) : launch_solve_nc<16>(ctx, a, threads, smem, st);
+    using KernT = void (*)(const SolveArgs);
+    ctx->last_variant = variant;
+    return launch_kernel(ctx, reinterpret_cast<KernT>(sh.kern), a, sh.threads, sh.smem, st);
 }
 
 extern "C" int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coef, int B, float* cost_out,
@@ -889,6 +1565,16 @@ extern "C" int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coe
     else score_kernel<16><<<grid, 32 * wpb, 0, st>>>(s);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MMPC_OK : cuda_fail(ctx, e, "score launch");
+}
+
+extern "C" int mmpc_take_work_count(mmpc_ctx* ctx, unsigned long long* elements)
+{
+    if (!ctx || !ctx->d_blob) return fail(nullptr, MMPC_ERR_NOT_SETUP, "context not set up");
+    if (!elements) return fail(ctx, MMPC_ERR_INVALID_ARG, "NULL pointer argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(elements, ctx->d_scratch + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_scratch + 2, 0, sizeof(unsigned long long));
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(ctx, e, "mmpc_take_work_count");
 }
 
 extern "C" void mmpc_destroy(mmpc_ctx* ctx)

@@ -28,7 +28,7 @@ MMPC_META_HSRL = 1
 MMPC_META_ABS = 2
 
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
-            "mmpc_last_error", "mmpc_version", "mmpc_score_static")
+            "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
 
@@ -46,6 +46,8 @@ class MmpcParams(ctypes.Structure):
         ("iters", ctypes.c_int),
         ("tol", ctypes.c_float),
         ("check_every", ctypes.c_int),
+        ("cull", ctypes.c_int),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -99,13 +101,16 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_score_static.argtypes = [ctypes.POINTER(MmpcMeta), ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int,
                                     fp, ip, vp]
     L.mmpc_score_static.restype = ctypes.c_int
+    L.mmpc_take_work_count.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.mmpc_take_work_count.restype = ctypes.c_int
     _lib = L
     return L
 
 
-def make_params(T, N, n, rho, a, b, v_min, v_max, a_max, iters=100, tol=0.0, check_every=10, **_ignored) -> MmpcParams:
+def make_params(T, N, n, rho, a, b, v_min, v_max, a_max, iters=100, tol=0.0, check_every=10, cull=1, variant=0,
+                **_ignored) -> MmpcParams:
     return MmpcParams(float(T), int(N), int(n), float(rho), float(a), float(b), float(v_min), float(v_max),
-                      float(a_max), int(iters), float(tol), int(check_every))
+                      float(a_max), int(iters), float(tol), int(check_every), int(cull), int(variant))
 
 
 def make_meta(kind=MMPC_META_ABS, w1=1.0, w2=0.25, v_ref=20.0, y_ref=-5.25, psi_max_deg=13.0, psi_max=None,
@@ -191,6 +196,16 @@ def mmpc_score_static(meta: MmpcMeta, N: int, n: int, P, Pd, coef, cost_out, arg
                                  _ptr(cost_out), _ptr(argmin_out, "int32"), _stream(stream))
     if rc != MMPC_OK:
         _err(None, rc)
+
+
+def mmpc_take_work_count(ctx) -> int:
+    """Obstacle-sample pairs evaluated by this context's solves since the last
+    call (synchronises the device; resets the count)."""
+    out = ctypes.c_ulonglong(0)
+    rc = lib().mmpc_take_work_count(ctx, ctypes.byref(out))
+    if rc != MMPC_OK:
+        _err(ctx, rc)
+    return int(out.value)
 
 
 def mmpc_destroy(ctx) -> None:
