@@ -54,13 +54,15 @@ void set_global_error(const std::string& msg) { g_error = msg; }
 // The pair-sample kernel stages [pair rows | common] into shared memory, the
 // one-sample kernel [common | sample rows]; the scoring kernels read the
 // sample rows from global memory.
-//   pair rows:   PP, PdP, PddP [ceil(N/2)][NC][2]  basis rows of samples
-//                (2i, 2i+1) interleaved per coefficient (rows of samples >= N
-//                and every k >= n are zero); tP [ceil(N/2)][2] their times
+//   pair rows:   PP, PdP, PddP [NPT][NC][2]  basis rows of samples (2i, 2i+1)
+//                interleaved per coefficient, NPT = ceil(N/2) rounded up to
+//                whole warps (rows of samples >= N and every k >= n are zero,
+//                so padded lanes contribute exact zeros); tP [NPT][2] times
 //   common:      brow [6][NC] (P, Pd, Pdd at t = 0 and t = T); lin [NC]; Q,
 //                K11 (x hi, x lo, y hi, y lo), K11_psi [NC][NC]; K12_psi
 //                [NC][4]; K12_x, K12_y, C0_x, C0_y [NC][8]; C0_psi [NC][4]
-//   sample rows: P, Pd, Pdd [N][NC]; t [N]
+//   sample rows: P, Pd, Pdd [NST][NC]; t [NST], NST = N rounded up to whole
+//                warps (zero rows beyond N)
 // ---------------------------------------------------------------------------
 struct BlobLayout {
     int PP, PdP, PddP, tP;                                                        // pair rows
@@ -72,7 +74,10 @@ struct BlobLayout {
 static BlobLayout blob_layout(int N, int NC)
 {
     auto up4 = [](int v) { return (v + 3) & ~3; };
-    const int NP = (N + 1) / 2;
+    // pair rows cover 32 ceil(ceil(N/2) / 32) pairs and sample rows 32
+    // ceil(N/32) samples: one per thread of the launch, zero beyond N
+    const int NP = 32 * (((N + 1) / 2 + 31) / 32);
+    const int NS = 32 * ((N + 31) / 32);
     BlobLayout B{};
     int o = 0;
     B.PP = o; o += NP * NC * 2;
@@ -96,10 +101,10 @@ static BlobLayout blob_layout(int N, int NC)
     B.C0p = o; o += NC * 4;
     o = up4(o);
     B.rows1 = o;
-    B.P = o; o += up4(N * NC);
-    B.Pd = o; o += up4(N * NC);
-    B.Pdd = o; o += up4(N * NC);
-    B.t = o; o += up4(N);
+    B.P = o; o += NS * NC;
+    B.Pd = o; o += NS * NC;
+    B.Pdd = o; o += NS * NC;
+    B.t = o; o += NS;
     B.total = o;
     return B;
 }
@@ -194,16 +199,24 @@ __device__ __forceinline__ void warp_rs(float (&v)[VM], int lane)
 
 // Reduce-scatter the C values of every warp and store the per-warp sums at
 // red[warp * stride + index].
+// dst = this lane's store address for C values (see rs_dst), or nullptr for
+// lanes that hold duplicates.
 template <int C>
-__device__ __forceinline__ void reduce_store(float (&v)[C], float* red, int warp, int stride, int lane)
+__device__ __forceinline__ void reduce_store(float (&v)[C], float* dst, int lane)
 {
     warp_rs<C, 16, C>(v, lane);
     constexpr int K = rs_count(C);
-    if (rs_writer(C, lane)) {
-        const int base = rs_base(C, lane);
+    if (dst) {
 #pragma unroll
-        for (int i = 0; i < K; ++i) red[warp * stride + base + i] = v[i];
+        for (int i = 0; i < K; ++i) dst[i] = v[i];
     }
+}
+
+// Where this lane stores its share of a reduce-scatter of C values into
+// red[warp * stride + index]; nullptr if it holds a duplicate.
+__device__ __forceinline__ float* rs_dst(int c, float* red, int warp, int stride, int lane)
+{
+    return rs_writer(c, lane) ? red + warp * stride + rs_base(c, lane) : nullptr;
 }
 
 // ---------------------------------------------------------------------------
@@ -358,15 +371,15 @@ __device__ __noinline__ void obstacle_sum_exact(const float4* __restrict__ obs, 
     }
 }
 
-// Exact culling for Eq. split_alpha_o.  The warp's samples span the box
-// [xlo, xhi] x [ylo, yhi] (ellipse-normalised, moving frame) over the time
-// window [tw_lo, tw_hi]; an obstacle moves along a segment over that window.
-// When the two boxes are apart by more than 1 (plus a margin far above the
-// FP32 rounding of the coordinates) along x or y, every sample of the warp has
-// |n| > 1 for that obstacle, so s = max(1/|n| - 1, 0) = 0 and the obstacle
-// adds exactly nothing.  Writes the indices of the remaining obstacles to
-// list (warp-private) and returns their count (warp-uniform).  A non-finite
-// coordinate keeps every obstacle, so NaN propagates as without culling.
+// Exact culling for Eq. split_alpha_o.  The warp's samples span a box
+// (ellipse-normalised, moving frame) over the time window [tw_lo, tw_hi]; an
+// obstacle moves along a segment over that window.  When the two boxes are
+// apart by more than 1 (plus a margin far above the FP32 rounding of the
+// coordinates) along x or y, every sample of the warp has |n| > 1 for that
+// obstacle, so s = max(1/|n| - 1, 0) = 0 and the obstacle adds exactly
+// nothing.  The remaining obstacles' indices go to a warp-private list, in
+// increasing order.  A non-finite coordinate keeps every obstacle, so NaN
+// propagates as without culling.
 __device__ __forceinline__ float warp_min(float v)
 {
     float r;
@@ -380,36 +393,62 @@ __device__ __forceinline__ float warp_max(float v)
     return r;
 }
 
-__device__ __forceinline__ int cull_list(const float4* __restrict__ obs, int m, float2 Xn, float2 Yn, float2 valid,
-                                         float tw_lo, float tw_hi, int* list, int lane)
+// Warp-private culling list with reuse.  The list is built for an
+// enlarged box (the warp's sample box grown by LIST_MARGIN) and kept while
+// the sample box stays inside it, so the obstacle tests run only when the
+// trajectory has moved noticeably.  Every obstacle that is not provably apart
+// from the list box is in the list, so a reused list is still exact.
+struct CullState {
+    float xlo, xhi, ylo, yhi;  // list box (empty at the start)
+    int count;
+};
+
+constexpr float CULL_MARGIN = 1.001f;  // normalised distance beyond which a term is exactly zero
+constexpr float LIST_MARGIN = 0.25f;   // growth of the list box
+
+__device__ __forceinline__ void cull_init(CullState& cs)
 {
     const float inf = __int_as_float(0x7f800000);
-    float xlo = inf, xhi = -inf, ylo = inf, yhi = -inf;
-    if (valid.x > 0.f) { xlo = Xn.x; xhi = Xn.x; ylo = Yn.x; yhi = Yn.x; }
-    if (valid.y > 0.f) {
-        xlo = fminf(xlo, Xn.y); xhi = fmaxf(xhi, Xn.y);
-        ylo = fminf(ylo, Yn.y); yhi = fmaxf(yhi, Yn.y);
+    cs.xlo = inf; cs.xhi = -inf; cs.ylo = inf; cs.yhi = -inf;
+    cs.count = 0;
+}
+
+// PAIRED: obstacles stored as two duplicated float4 (pair kernel), else one
+// float4 (p_x, p_y, pv_x, pv_y) (one-sample kernel); p and pv are negated.
+template <bool PAIRED>
+__device__ __forceinline__ int cull_update(CullState& cs, int m, float xlo, float xhi, float ylo, float yhi,
+                                           bool any_bad, float tw_lo, float tw_hi, int* list, int lane,
+                                           const float4* __restrict__ obs)
+{
+    const float inf = __int_as_float(0x7f800000);
+    if (!any_bad && xlo >= cs.xlo && xhi <= cs.xhi && ylo >= cs.ylo && yhi <= cs.yhi) return cs.count;
+    if (any_bad) {  // a non-finite coordinate: keep every obstacle from now on
+        cs.xlo = -inf; cs.xhi = inf; cs.ylo = -inf; cs.yhi = inf;
+    } else {
+        cs.xlo = xlo - LIST_MARGIN; cs.xhi = xhi + LIST_MARGIN;
+        cs.ylo = ylo - LIST_MARGIN; cs.yhi = yhi + LIST_MARGIN;
     }
-    const bool bad = (valid.x > 0.f && !(isfinite(Xn.x) && isfinite(Yn.x))) ||
-                     (valid.y > 0.f && !(isfinite(Xn.y) && isfinite(Yn.y)));
-    xlo = warp_min(xlo);
-    xhi = warp_max(xhi);
-    ylo = warp_min(ylo);
-    yhi = warp_max(yhi);
-    const bool any_bad = __any_sync(FULL, bad);
-    constexpr float M = 1.001f;
     const unsigned below = (1u << lane) - 1u;
     int count = 0;
     for (int j0 = 0; j0 < m; j0 += 32) {
         const int j = j0 + lane;
         bool keep = false;
         if (j < m) {
-            const float4 ax = obs[2 * j], ay = obs[2 * j + 1];
+            float2 ox, oy;  // (p, pv) along x and y
+            if (PAIRED) {
+                const float4 a = obs[2 * j], b = obs[2 * j + 1];
+                ox = f2(a.x, a.z);
+                oy = f2(b.x, b.z);
+            } else {
+                const float4 a = obs[j];
+                ox = f2(a.x, a.z);
+                oy = f2(a.y, a.w);
+            }
             // the obstacle centre is -(p + pv t) in the stored (negated) form
-            const float e1 = -fmaf(ax.z, tw_lo, ax.x), e2 = -fmaf(ax.z, tw_hi, ax.x);
-            const float f1 = -fmaf(ay.z, tw_lo, ay.x), g1 = -fmaf(ay.z, tw_hi, ay.x);
-            const bool apart = (xlo - fmaxf(e1, e2) >= M) || (fminf(e1, e2) - xhi >= M) ||
-                               (ylo - fmaxf(f1, g1) >= M) || (fminf(f1, g1) - yhi >= M);
+            const float e1 = -fmaf(ox.y, tw_lo, ox.x), e2 = -fmaf(ox.y, tw_hi, ox.x);
+            const float f1 = -fmaf(oy.y, tw_lo, oy.x), g1 = -fmaf(oy.y, tw_hi, oy.x);
+            const bool apart = (cs.xlo - fmaxf(e1, e2) >= CULL_MARGIN) || (fminf(e1, e2) - cs.xhi >= CULL_MARGIN) ||
+                               (cs.ylo - fmaxf(f1, g1) >= CULL_MARGIN) || (fminf(f1, g1) - cs.yhi >= CULL_MARGIN);
             keep = any_bad || !apart;
         }
         const unsigned bal = __ballot_sync(FULL, keep);
@@ -417,7 +456,59 @@ __device__ __forceinline__ int cull_list(const float4* __restrict__ obs, int m, 
         count += __popc(bal);
     }
     __syncwarp();
+    cs.count = count;
     return count;
+}
+
+// The warp's sample box for the pair kernel; returns whether a valid sample
+// has a non-finite coordinate.
+__device__ __forceinline__ bool box_pair(float2 Xn, float2 Yn, float2 valid, float& xlo, float& xhi, float& ylo,
+                                         float& yhi)
+{
+    const float inf = __int_as_float(0x7f800000);
+    float a = inf, b = -inf, c = inf, d = -inf;
+    if (valid.x > 0.f) { a = Xn.x; b = Xn.x; c = Yn.x; d = Yn.x; }
+    if (valid.y > 0.f) { a = fminf(a, Xn.y); b = fmaxf(b, Xn.y); c = fminf(c, Yn.y); d = fmaxf(d, Yn.y); }
+    const bool bad = (valid.x > 0.f && !(isfinite(Xn.x) && isfinite(Yn.x))) ||
+                     (valid.y > 0.f && !(isfinite(Xn.y) && isfinite(Yn.y)));
+    xlo = warp_min(a);
+    xhi = warp_max(b);
+    ylo = warp_min(c);
+    yhi = warp_max(d);
+    return __any_sync(FULL, bad);
+}
+
+// atan2 for two samples at once: octant reduction to a = min(|x|, |y|) /
+// max(|x|, |y|) in [0, 1], atan(a) = a p(a^2) with the degree-7 polynomial
+// fitted by csrc/fit_atan.py (maximum error 1.6e-7 rad in FP32 evaluation),
+// then the octant fix-ups atan2 = pi/2 - r (|y| > |x|), pi - r (x < 0, the
+// sign bit deciding, so -0 counts as negative as in IEEE atan2) and the sign
+// of y.  atan2(0, 0) = 0.
+__device__ __forceinline__ float2 atan2_pair(float2 y, float2 x)
+{
+    const float ax0 = fabsf(x.x), ax1 = fabsf(x.y), ay0 = fabsf(y.x), ay1 = fabsf(y.y);
+    const float hi0 = fmaxf(fmaxf(ax0, ay0), 1e-30f), hi1 = fmaxf(fmaxf(ax1, ay1), 1e-30f);
+    const float2 a = f2(__fdividef(fminf(ax0, ay0), hi0), __fdividef(fminf(ax1, ay1), hi1));
+    const float2 z = __fmul2_rn(a, a);
+    float2 p = f2(-4.062573425e-03f);
+    p = __ffma2_rn(p, z, f2(2.189946361e-02f));
+    p = __ffma2_rn(p, z, f2(-5.597937107e-02f));
+    p = __ffma2_rn(p, z, f2(9.648545831e-02f));
+    p = __ffma2_rn(p, z, f2(-1.391191483e-01f));
+    p = __ffma2_rn(p, z, f2(1.994746774e-01f));
+    p = __ffma2_rn(p, z, f2(-3.332997561e-01f));
+    p = __ffma2_rn(p, z, f2(9.999994040e-01f));
+    float2 r = __fmul2_rn(a, p);
+    const float2 c1 = __fadd2_rn(f2(1.5707963268f), f2(-r.x, -r.y));
+    r = f2(ay0 > ax0 ? c1.x : r.x, ay1 > ax1 ? c1.y : r.y);
+    const float2 c2 = __fadd2_rn(f2(3.1415926536f), f2(-r.x, -r.y));
+    r = f2(__float_as_int(x.x) < 0 ? c2.x : r.x, __float_as_int(x.y) < 0 ? c2.y : r.y);
+    return f2(copysignf(r.x, y.x), copysignf(r.y, y.y));
+}
+
+__device__ __forceinline__ float atan2_own(float y, float x)
+{
+    return atan2_pair(f2(y, 0.f), f2(x, 1.f)).x;
 }
 
 // sin and cos of a heading: the SFU approximations where they are accurate
@@ -518,7 +609,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
     const bool has_pair = tid < NP;
-    const int ip = has_pair ? tid : 0;
+    (void)has_pair;
+    const int ip = tid;  // rows are padded to the thread count (zero rows beyond N)
     const float* PP = blob + L.PP + ip * 2 * NC;
     const float* PdP = blob + L.PdP + ip * 2 * NC;
     const float* PddP = blob + L.PddP + ip * 2 * NC;
@@ -529,6 +621,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
     const int w_last = min(N, 64 * warp + 64) - 1;
     const float tw_lo = blob[L.tP + w_first], tw_hi = blob[L.tP + w_last];
     unsigned long long work = 0;  // evaluated obstacle-sample pairs (lane 0)
+    CullState cull;
+    cull_init(cull);
 
     // ---- coefficient state, identical in every warp ---------------------------
     const bool isy = lane >= 16;
@@ -609,6 +703,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
 
     float2 xd = f2(0.f), yd = f2(0.f), theta = f2(0.f);
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
+    float* const dstB = rs_dst(RSB, red1, warp, RSB, lane);  // this lane's reduce-scatter outputs
+    float* const dstD = rs_dst(VD, red2, warp, RSD, lane);
     int kit = 0;
     const int iters = A.iters;
 
@@ -619,8 +715,7 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
         float v[VD];
 #pragma unroll
         for (int i = 0; i < VD; ++i) v[i] = 0.f;
-        {  // every lane runs this block (the culling is warp-collective); lanes
-           // without a sample pair read pair 0's rows and are masked at the end
+        {  // lanes without a sample pair read zero rows: their terms vanish
             const float2 x = dot_pair<NC>(PP, cxd);
             const float2 y = dot_pair<NC>(PP, cyd);
             const float2 xdd = dot_pair<NC>(PddP, cxd);
@@ -644,7 +739,10 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
             const float2 Xn = __fmul2_rn(x, f2(A.inv_a)), Yn = __fmul2_rn(y, f2(A.inv_b));
             float2 Sx, Sy, R2;
             if (A.cull) {
-                const int cnt = cull_list(obs, m, Xn, Yn, valid, tw_lo, tw_hi, olist, lane);
+                float bxlo, bxhi, bylo, byhi;
+                const bool bad = box_pair(Xn, Yn, valid, bxlo, bxhi, bylo, byhi);
+                const int cnt =
+                    cull_update<true>(cull, m, bxlo, bxhi, bylo, byhi, bad, tw_lo, tw_hi, olist, lane, obs);
                 if (lane == 0) work += (unsigned long long)cnt * (unsigned)(w_last - w_first + 1);
                 if (resid) obstacle_sum2<true, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
                 else obstacle_sum2<false, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
@@ -685,22 +783,16 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
                 v[3 * NC + 2] = fmaf(rv.x, valid.x, rv.y * valid.y);
                 v[3 * NC + 3] = fmaf(rp.x, valid.x, rp.y * valid.y);
             }
-            if (!has_pair) {
-#pragma unroll
-                for (int i = 0; i < VD; ++i) v[i] = 0.f;
-            }
         }
-        reduce_store<VD>(v, red2, warp, RSD, lane);
+        reduce_store<VD>(v, dstD, lane);
     };
 
     // Velocity directions and the heading target theta = atan2(ydot, xdot)
     // (Eq. split_psi), and the partial sums of P^T theta.
     auto heading = [&](bool reduce) {
-        if (has_pair) {
-            xd = __fadd2_rn(dot_pair<NC>(PdP, cxd), f2(v0));
-            yd = dot_pair<NC>(PdP, cyd);
-            theta = f2(atan2f(yd.x, xd.x), atan2f(yd.y, xd.y));
-        }
+        xd = __fadd2_rn(dot_pair<NC>(PdP, cxd), f2(v0));
+        yd = dot_pair<NC>(PdP, cyd);
+        theta = atan2_pair(yd, xd);
         if (reduce) {
             float v[NC];
 #pragma unroll
@@ -708,10 +800,10 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
                 const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
                 const float2 s0 = __fmul2_rn(f2(p4.x, p4.y), theta);
                 const float2 s1 = __fmul2_rn(f2(p4.z, p4.w), theta);
-                v[q] = has_pair ? s0.x + s0.y : 0.f;
-                v[q + 1] = has_pair ? s1.x + s1.y : 0.f;
+                v[q] = s0.x + s0.y;
+                v[q + 1] = s1.x + s1.y;
             }
-            reduce_store<NC>(v, red1, warp, RSB, lane);
+            reduce_store<NC>(v, dstB, lane);
         }
     };
 
@@ -882,36 +974,6 @@ __device__ __noinline__ void obstacle_sum1_exact(const float4* __restrict__ obs,
     }
 }
 
-// Exact culling as cull_list, for a warp of single samples.
-__device__ __forceinline__ int cull_list1(const float4* __restrict__ obs, int m, float Xn, float Yn, bool valid,
-                                          float tw_lo, float tw_hi, int* list, int lane)
-{
-    const float inf = __int_as_float(0x7f800000);
-    const float xlo = warp_min(valid ? Xn : inf), xhi = warp_max(valid ? Xn : -inf);
-    const float ylo = warp_min(valid ? Yn : inf), yhi = warp_max(valid ? Yn : -inf);
-    const bool any_bad = __any_sync(FULL, valid && !(isfinite(Xn) && isfinite(Yn)));
-    constexpr float M = 1.001f;
-    const unsigned below = (1u << lane) - 1u;
-    int count = 0;
-    for (int j0 = 0; j0 < m; j0 += 32) {
-        const int j = j0 + lane;
-        bool keep = false;
-        if (j < m) {
-            const float4 o = obs[j];
-            const float e1 = -fmaf(o.z, tw_lo, o.x), e2 = -fmaf(o.z, tw_hi, o.x);
-            const float f1 = -fmaf(o.w, tw_lo, o.y), g1 = -fmaf(o.w, tw_hi, o.y);
-            const bool apart = (xlo - fmaxf(e1, e2) >= M) || (fminf(e1, e2) - xhi >= M) ||
-                               (ylo - fmaxf(f1, g1) >= M) || (fminf(f1, g1) - yhi >= M);
-            keep = any_bad || !apart;
-        }
-        const unsigned bal = __ballot_sync(FULL, keep);
-        if (keep) list[count + __popc(bal & below)] = j;
-        count += __popc(bal);
-    }
-    __syncwarp();
-    return count;
-}
-
 // dot product of two 16-byte aligned vectors of NC floats; four partial sums.
 template <int NC>
 __device__ __forceinline__ float dot_plain(const float* __restrict__ a, const float* __restrict__ b)
@@ -993,7 +1055,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
     const bool has_t = tid < N;
-    const int ts = has_t ? tid : 0;
+    const int ts = tid;  // rows are padded to the thread count (zero rows beyond N)
+    const float valid = has_t ? 1.f : 0.f;
     const float* Prow = blob + (L.P - base) + ts * NC;
     const float* Pdrow = blob + (L.Pd - base) + ts * NC;
     const float* Pddrow = blob + (L.Pdd - base) + ts * NC;
@@ -1002,6 +1065,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
     const int w_last = min(N, 32 * warp + 32) - 1;
     const float tw_lo = blob[(L.t - base) + w_first], tw_hi = blob[(L.t - base) + w_last];
     unsigned long long work = 0;
+    CullState cull;
+    cull_init(cull);
 
     const bool isy = lane >= 16;
     const int k = lane & 15;
@@ -1075,6 +1140,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
 
     float xd = 0.f, yd = 0.f, theta = 0.f;
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
+    float* const dstB = rs_dst(RSB, red1, warp, RSB, lane);
+    float* const dstD = rs_dst(VD, red2, warp, RSD, lane);
     int kit = 0;
     const int iters = A.iters;
 
@@ -1099,7 +1166,12 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
             const float Xn = x * A.inv_a, Yn = y * A.inv_b;
             float Sx, Sy, R2;
             if (A.cull) {
-                const int cnt = cull_list1(obs, m, Xn, Yn, has_t, tw_lo, tw_hi, olist, lane);
+                const float inf = __int_as_float(0x7f800000);
+                const float bxlo = warp_min(has_t ? Xn : inf), bxhi = warp_max(has_t ? Xn : -inf);
+                const float bylo = warp_min(has_t ? Yn : inf), byhi = warp_max(has_t ? Yn : -inf);
+                const bool bad = __any_sync(FULL, has_t && !(isfinite(Xn) && isfinite(Yn)));
+                const int cnt =
+                    cull_update<false>(cull, m, bxlo, bxhi, bylo, byhi, bad, tw_lo, tw_hi, olist, lane, obs);
                 if (lane == 0) work += (unsigned long long)cnt * (unsigned)(w_last - w_first + 1);
                 if (resid) obstacle_sum1<true, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
                 else obstacle_sum1<false, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
@@ -1127,36 +1199,30 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
                 }
             }
             if (resid) {
-                v[3 * NC + 0] = R2;
-                v[3 * NC + 1] = fmaf(eax, eax, eay * eay);
-                v[3 * NC + 2] = fmaf(evx, evx, evy * evy);
-                v[3 * NC + 3] = dpsi * dpsi;
-            }
-            if (!has_t) {
-#pragma unroll
-                for (int i = 0; i < VD; ++i) v[i] = 0.f;
+                v[3 * NC + 0] = R2 * valid;
+                v[3 * NC + 1] = fmaf(eax, eax, eay * eay) * valid;
+                v[3 * NC + 2] = fmaf(evx, evx, evy * evy) * valid;
+                v[3 * NC + 3] = dpsi * dpsi * valid;
             }
         }
-        reduce_store<VD>(v, red2, warp, RSD, lane);
+        reduce_store<VD>(v, dstD, lane);
     };
 
     auto heading = [&](bool reduce) {
-        if (has_t) {
-            xd = dot_row<NC>(Pdrow, cx) + v0;
-            yd = dot_row<NC>(Pdrow, cy);
-            theta = atan2f(yd, xd);
-        }
+        xd = dot_row<NC>(Pdrow, cx) + v0;
+        yd = dot_row<NC>(Pdrow, cy);
+        theta = atan2_own(yd, xd);
         if (reduce) {
             float v[NC];
 #pragma unroll
             for (int q = 0; q < NC; q += 4) {
                 const float4 p4 = *reinterpret_cast<const float4*>(Prow + q);
-                v[q + 0] = has_t ? p4.x * theta : 0.f;
-                v[q + 1] = has_t ? p4.y * theta : 0.f;
-                v[q + 2] = has_t ? p4.z * theta : 0.f;
-                v[q + 3] = has_t ? p4.w * theta : 0.f;
+                v[q + 0] = p4.x * theta;
+                v[q + 1] = p4.y * theta;
+                v[q + 2] = p4.z * theta;
+                v[q + 3] = p4.w * theta;
             }
-            reduce_store<NC>(v, red1, warp, RSB, lane);
+            reduce_store<NC>(v, dstB, lane);
         }
     };
 
