@@ -173,6 +173,56 @@ typedef struct {
 int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coef, int B, float* cost_out,
                int* argmin_out, void* stream);
 
+/* ---- Batches of scenes ---------------------------------------------------
+ * Many independent scenes (MPC problems of different vehicles, or of one
+ * vehicle at different times) solved and scored together: one persistent
+ * launch of the solve kernel over all (scene, trajectory) items, one scoring
+ * launch and a per-scene argmin.  Each scene has its own context, so scenes
+ * may differ in N and m (and in the other parameters); all contexts must have
+ * n <= 12, or all n > 12. */
+typedef struct {
+    mmpc_ctx* ctx;       /* the scene's problem; ctx->m obstacles */
+    const float* ego;    /* device float[4], as for mmpc_solve */
+    const float* obst;   /* device float[m][4] */
+    const float* goals;  /* device float[B][3] */
+    int B;               /* goals of this scene, >= 0 */
+    float* coef_out;     /* device float[B][3n] */
+    float* lam_out;      /* device float[B][3n] or NULL */
+    float* resid_out;    /* device float[B][4] or NULL */
+    int* iters_out;      /* device int[B] or NULL */
+    float* cost_out;     /* device float[B]: meta costs */
+    int* argmin_out;     /* device int[1]: argmin as mmpc_score */
+} mmpc_scene;
+
+typedef struct mmpc_batch mmpc_batch;
+
+/* Creates a batch over S scene descriptors (copied; the device buffers they
+ * point to must stay valid) scored with one meta cost.  Allocates the
+ * batch's device tables once; mmpc_batch_run then allocates nothing and can
+ * be captured in a CUDA graph.  Synchronous. */
+int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_meta* meta, mmpc_batch** out);
+
+/* Order in which the persistent CTAs take (scene, trajectory) items:
+ * 1 scene by scene as given, 2 scenes by decreasing work per trajectory
+ * (N (m + 32)), 3 round-robin over the scenes of 2, one trajectory of each
+ * at a time.  Synchronous. */
+int mmpc_batch_set_schedule(mmpc_batch* b, int schedule);
+
+/* Times the three schedules (a warm-up and two timed runs each, on `stream`),
+ * keeps the fastest and writes it to *chosen (may be NULL).  Synchronous. */
+int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen);
+
+/* Solves and scores every scene of the batch on `stream` (asynchronous). */
+int mmpc_batch_run(mmpc_batch* b, void* stream);
+
+/* After a run (synchronises the device): each scene's completion time in ms
+ * since the run's first CTA started (host float[S], may be NULL), and the
+ * largest of them. */
+int mmpc_batch_times(mmpc_batch* b, float* scene_ms, float* makespan_ms);
+
+/* Frees the batch (synchronises the device first).  NULL is a no-op. */
+void mmpc_batch_destroy(mmpc_batch* b);
+
 /* Number of obstacle-sample pairs (Eq. split_alpha_o) the solve kernels of
  * this context evaluated since the last call, summed over iterations and
  * trajectories (m N per trajectory-iteration without culling).  Synchronises

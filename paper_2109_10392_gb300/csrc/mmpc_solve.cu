@@ -30,6 +30,7 @@
 //    the carried coefficients small; outputs are in the road frame.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -259,7 +260,11 @@ __device__ __forceinline__ bool stage_blob(float* dst, const float* src, int byt
         }
         if (!done && pass == 0 && threadIdx.x == 0) atomicOr(err_flag, ERR_TMA_TIMEOUT);
     }
-    return __syncthreads_and(done) != 0;
+    const bool ok = __syncthreads_and(done) != 0;
+    // every thread has seen the phase complete: retire the barrier so that a
+    // CTA that stages again (one item after another) initialises a fresh one
+    if (ok && threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+    return ok;
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -511,13 +516,49 @@ __device__ __forceinline__ float atan2_own(float y, float x)
     return atan2_pair(f2(y, 0.f), f2(x, 1.f)).x;
 }
 
-// sin and cos of a heading: the SFU approximations where they are accurate
-// (|psi| < 3: absolute error of order 1e-6 or below), the full-range library
-// function elsewhere.
+// sin and cos of two headings.  Cody-Waite reduction r = psi - q pi/2 with
+// q = rint(psi 2/pi) and pi/2 split into a float32 head and tail (two FMAs),
+// then sin r = r + r^3 S(r^2) and cos r = 1 - r^2/2 + r^4 C(r^2) on
+// [-pi/4, pi/4] with the polynomials fitted by csrc/fit_sincos.py (maximum
+// error 6.6e-8 in float32 evaluation for |psi| <= 20), and the quadrant
+// q mod 4 swapping and negating them.  The accuracy matters: the multiplier
+// update integrates any bias of the non-holonomic targets v (cos psi,
+// sin psi) over the iterations, so an approximation with errors of a few
+// 1e-7 drifts the iterate by millimetres within 100 iterations.  Headings of
+// magnitude 1e5 or more (never a real heading) take the library sincosf.
+__device__ __forceinline__ void sincos_pair(const float2 ps, float2& sn, float2& cs)
+{
+    const float2 qs = __fmul2_rn(ps, f2(6.366197723675814e-01f));
+    const float2 q = f2(rintf(qs.x), rintf(qs.y));
+    const float2 nq = f2(-q.x, -q.y);
+    float2 r = __ffma2_rn(nq, f2(1.570796371e+00f), ps);
+    r = __ffma2_rn(nq, f2(-4.371138829e-08f), r);
+    const float2 z = __fmul2_rn(r, r);
+    float2 ps_ = __ffma2_rn(f2(-1.949599100e-04f), z, f2(8.331981488e-03f));
+    ps_ = __ffma2_rn(ps_, z, f2(-1.666665077e-01f));
+    float2 pc = __ffma2_rn(f2(2.443822632e-05f), z, f2(-1.388736535e-03f));
+    pc = __ffma2_rn(pc, z, f2(4.166664556e-02f));
+    const float2 s = __ffma2_rn(__fmul2_rn(z, r), ps_, r);
+    const float2 c = __ffma2_rn(z, __ffma2_rn(z, pc, f2(-0.5f)), f2(1.f));
+    const int j0 = (int)q.x, j1 = (int)q.y;
+    sn.x = (j0 & 1) ? c.x : s.x;
+    sn.y = (j1 & 1) ? c.y : s.y;
+    cs.x = (j0 & 1) ? s.x : c.x;
+    cs.y = (j1 & 1) ? s.y : c.y;
+    if (j0 & 2) sn.x = -sn.x;
+    if (j1 & 2) sn.y = -sn.y;
+    if ((j0 + 1) & 2) cs.x = -cs.x;
+    if ((j1 + 1) & 2) cs.y = -cs.y;
+    if (fabsf(ps.x) >= 1e5f) sincosf(ps.x, &sn.x, &cs.x);
+    if (fabsf(ps.y) >= 1e5f) sincosf(ps.y, &sn.y, &cs.y);
+}
+
 __device__ __forceinline__ void heading_sincos(float ps, float* sn, float* cs)
 {
-    if (fabsf(ps) < 3.f) __sincosf(ps, sn, cs);
-    else sincosf(ps, sn, cs);
+    float2 s, c;
+    sincos_pair(f2(ps, 0.f), s, c);
+    *sn = s.x;
+    *cs = c.x;
 }
 
 // ---------------------------------------------------------------------------
@@ -562,8 +603,12 @@ __device__ __forceinline__ float dot_dup(const float* __restrict__ row, const fl
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
+// The pair kernel's work for trajectory l of the problem A, by the whole CTA.
+// Warps beyond ceil(ceil(N/2) / 32) (a CTA sized for a longer horizon, in a
+// batch of scenes) hold no samples: they only follow the coefficient state
+// through the barriers.
 template <int NC, int MAXT>
-__global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(const SolveArgs A)
+__device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
 {
     constexpr int VD = SolveSmem<NC>::VD;
     constexpr int RSD = SolveSmem<NC>::RSD;
@@ -576,13 +621,13 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
     __shared__ __align__(16) float s_vec[MAX_WARPS][2][2 * NC];  // per-warp scratch vectors (x, y)
     __shared__ __align__(8) unsigned long long s_mbar;
 
-    const int l = blockIdx.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const int nwarps = blockDim.x >> 5;
     const int N = A.N, m = A.m;
     const int NP = (N + 1) >> 1;
+    const int nwarps = (NP + 31) >> 5;  // warps that hold samples
+    const bool idle = warp >= nwarps;
     const BlobLayout& L = A.L;
 
     float* blob = smem;
@@ -604,21 +649,20 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
         obs[2 * j] = make_float4(px, px, pvx, pvx);
         obs[2 * j + 1] = make_float4(py, py, pvy, pvy);
     }
-    if (!stage_blob(blob, A.blob, L.rows1 * 4, &s_mbar, A.err_flag)) return;
+    if (!stage_blob(blob, A.blob, L.rows1 * 4, &s_mbar, A.err_flag)) return false;
 
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
-    const bool has_pair = tid < NP;
-    (void)has_pair;
-    const int ip = tid;  // rows are padded to the thread count (zero rows beyond N)
+    const int ip = idle ? 0 : tid;  // rows are padded to whole warps (zero rows beyond N)
     const float* PP = blob + L.PP + ip * 2 * NC;
     const float* PdP = blob + L.PdP + ip * 2 * NC;
     const float* PddP = blob + L.PddP + ip * 2 * NC;
     const float2 tt = f2(blob[L.tP + 2 * ip], blob[L.tP + 2 * ip + 1]);
+    const bool has_pair = !idle && tid < NP;
     const float2 valid = f2(has_pair ? 1.f : 0.f, (has_pair && 2 * ip + 1 < N) ? 1.f : 0.f);
     // the warp's samples [64 warp, 64 warp + 64) and their time window
-    const int w_first = 64 * warp;
-    const int w_last = min(N, 64 * warp + 64) - 1;
+    const int w_first = idle ? 0 : 64 * warp;
+    const int w_last = idle ? 0 : min(N, 64 * warp + 64) - 1;
     const float tw_lo = blob[L.tP + w_first], tw_hi = blob[L.tP + w_last];
     unsigned long long work = 0;  // evaluated obstacle-sample pairs (lane 0)
     CullState cull;
@@ -726,8 +770,7 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
             const float2 nvel = f2(-fminf(fmaxf(sqrtf(sp2.x), A.v_min), A.v_max),
                                    -fminf(fmaxf(sqrtf(sp2.y), A.v_min), A.v_max));
             float2 sn, cs;
-            heading_sincos(ps.x, &sn.x, &cs.x);
-            heading_sincos(ps.y, &sn.y, &cs.y);
+            sincos_pair(ps, sn, cs);
             const float2 evx = __ffma2_rn(nvel, cs, xd);
             const float2 evy = __ffma2_rn(nvel, sn, yd);
             // Eq. split_alpha_a: projection of (xddot, yddot) on the disk of radius a_max
@@ -870,8 +913,10 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
     };
 
     // ---- initial iterate: auxiliaries of c^0, no multiplier update -------
-    heading(false);
-    project(true);
+    if (!idle) {
+        heading(false);
+        project(true);
+    }
     __syncthreads();
     bool done = finish(true, true);
 
@@ -879,10 +924,10 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
     while (!done) {
         ++kit;
         const bool check = (kit % A.check_every == 0) || kit >= iters;
-        heading(true);   // theta and the partial sums of P^T theta
+        if (!idle) heading(true);   // theta and the partial sums of P^T theta
         __syncthreads();
-        psi_step();      // Eq. split_psi
-        project(check);  // Eqs. split_v, split_alpha_o, split_alpha_a; partial sums
+        psi_step();                 // Eq. split_psi
+        if (!idle) project(check);  // Eqs. split_v, split_alpha_o, split_alpha_a; partial sums
         __syncthreads();
         done = finish(false, check);  // multipliers, residual check, step (split_xy)
     }
@@ -906,7 +951,14 @@ __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(
         if (A.resid_out && lane < 4) A.resid_out[(size_t)l * 4 + lane] = sqrtf(rsum[lane]);
         if (A.iters_out && lane == 0) A.iters_out[l] = kit;
     }
-    if (lane == 0 && A.work) atomicAdd(A.work, work);
+    if (lane == 0 && A.work && !idle) atomicAdd(A.work, work);
+    return true;
+}
+
+template <int NC, int MAXT>
+__global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(const __grid_constant__ SolveArgs A)
+{
+    pair_body<NC, MAXT>(A, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1320,50 +1372,67 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
 // index) -- costs are non-negative, so their bit patterns order like the
 // values -- finished by the last CTA, which also resets the scratch words.
 // ---------------------------------------------------------------------------
+// Meta cost of trajectory l (warp-collective; every lane returns it).
+template <int NC>
+__device__ __forceinline__ float traj_cost(const ScoreArgs& S, int l, int lane)
+{
+    const int n = S.n, N = S.N;
+    const float* cf = S.coef + (size_t)l * 3 * n;
+    float cx[NC], cy[NC], cp[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        cx[k] = k < n ? __ldg(cf + k) : 0.f;
+        cy[k] = k < n ? __ldg(cf + n + k) : 0.f;
+        cp[k] = k < n ? __ldg(cf + 2 * n + k) : 0.f;
+    }
+    float cost = 0.f;
+    bool bad = false;
+    for (int t = lane; t < N; t += 32) {
+        const float* P = S.blob + S.L.P + t * NC;
+        const float* Pd = S.blob + S.L.Pd + t * NC;
+        float xd = 0.f, yd = 0.f, y = 0.f, ps = 0.f;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const float p = __ldg(P + k), d = __ldg(Pd + k);
+            xd = fmaf(d, cx[k], xd);
+            yd = fmaf(d, cy[k], yd);
+            y = fmaf(p, cy[k], y);
+            ps = fmaf(p, cp[k], ps);
+        }
+        const float vel = sqrtf(fmaf(xd, xd, yd * yd));
+        const float dv = vel - S.v_ref, dy = y - S.y_ref;
+        if (S.kind == MMPC_META_CRUISE) cost = fmaf(dv, dv, cost);
+        else if (S.kind == MMPC_META_HSRL) cost += S.w1 * dv * dv + S.w2 * dy * dy;
+        else cost += S.w1 * fabsf(dv) + S.w2 * fabsf(dy);
+        if (S.psi_max > 0.f && fabsf(ps) > S.psi_max) bad = true;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cost += __shfl_xor_sync(FULL, cost, off);
+    bad = __any_sync(FULL, bad);
+    if (bad || isnan(cost)) cost = __int_as_float(0x7f800000);
+    return cost;
+}
+
+__device__ __forceinline__ unsigned long long cost_key(float cost, int l)
+{
+    return ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned)l;
+}
+
+__device__ __forceinline__ int key_argmin(unsigned long long key)
+{
+    return ((unsigned)(key >> 32) >= 0x7f800000u) ? -1 : (int)(key & 0xffffffffu);
+}
+
 template <int NC>
 __global__ void __launch_bounds__(256) score_kernel(const ScoreArgs S)
 {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw < S.B) {
-        const int n = S.n, N = S.N;
-        const float* cf = S.coef + (size_t)gw * 3 * n;
-        float cx[NC], cy[NC], cp[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            cx[k] = k < n ? __ldg(cf + k) : 0.f;
-            cy[k] = k < n ? __ldg(cf + n + k) : 0.f;
-            cp[k] = k < n ? __ldg(cf + 2 * n + k) : 0.f;
-        }
-        float cost = 0.f;
-        bool bad = false;
-        for (int t = lane; t < N; t += 32) {
-            const float* P = S.blob + S.L.P + t * NC;
-            const float* Pd = S.blob + S.L.Pd + t * NC;
-            float xd = 0.f, yd = 0.f, y = 0.f, ps = 0.f;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                const float p = __ldg(P + k), d = __ldg(Pd + k);
-                xd = fmaf(d, cx[k], xd);
-                yd = fmaf(d, cy[k], yd);
-                y = fmaf(p, cy[k], y);
-                ps = fmaf(p, cp[k], ps);
-            }
-            const float vel = sqrtf(fmaf(xd, xd, yd * yd));
-            const float dv = vel - S.v_ref, dy = y - S.y_ref;
-            if (S.kind == MMPC_META_CRUISE) cost = fmaf(dv, dv, cost);
-            else if (S.kind == MMPC_META_HSRL) cost += S.w1 * dv * dv + S.w2 * dy * dy;
-            else cost += S.w1 * fabsf(dv) + S.w2 * fabsf(dy);
-            if (S.psi_max > 0.f && fabsf(ps) > S.psi_max) bad = true;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) cost += __shfl_xor_sync(FULL, cost, off);
-        bad = __any_sync(FULL, bad);
-        if (bad || isnan(cost)) cost = __int_as_float(0x7f800000);
+        const float cost = traj_cost<NC>(S, gw, lane);
         if (lane == 0) {
             S.cost_out[gw] = cost;
-            const unsigned long long key = ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned)gw;
-            atomicMin(S.best, key);
+            atomicMin(S.best, cost_key(cost, gw));
         }
     }
     __syncthreads();
@@ -1373,12 +1442,81 @@ __global__ void __launch_bounds__(256) score_kernel(const ScoreArgs S)
         if (ticket == gridDim.x - 1) {
             __threadfence();
             const unsigned long long key = atomicAdd(S.best, 0ull);
-            const unsigned bits = (unsigned)(key >> 32);
-            *S.argmin_out = (bits >= 0x7f800000u) ? -1 : (int)(key & 0xffffffffu);
+            *S.argmin_out = key_argmin(key);
             atomicExch(S.best, ~0ull);
             atomicExch(S.ticket, 0u);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batches of scenes.  One persistent launch of the pair kernel body: each CTA
+// takes (scene, trajectory) items from a queue (an atomic counter over the
+// item list, whose order the schedule sets) until the list is exhausted, and
+// stamps each scene's completion time (%globaltimer) when it finishes one of
+// its trajectories.  Scoring is one launch over all items with a packed
+// 64-bit atomicMin key per scene, and a finalising launch.
+// Scratch words: [0] queue counter, [1] earliest CTA start, [2, 2 + S) scene
+// completion times, [2 + S, 2 + 2S) scene argmin keys.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int NC, int MAXT>
+__global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value)
+    am_solve_batch_kernel(const SolveArgs* __restrict__ scenes, const int2* __restrict__ items, int total,
+                          unsigned long long* scratch)
+{
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();  // the previous item is finished by every thread
+        if (threadIdx.x == 0) {
+            s_item = (int)atomicAdd(reinterpret_cast<unsigned*>(scratch), 1u);
+            atomicMin(scratch + 1, global_ns());
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= total) break;
+        const int2 sl = items[it];
+        // a staging copy that never landed (flagged in the scene's error word)
+        // stops this CTA: nothing may be staged over a copy still in flight
+        if (!pair_body<NC, MAXT>(scenes[sl.x], sl.y)) break;
+        __syncthreads();
+        if (threadIdx.x == 0) atomicMax(scratch + 2 + sl.x, global_ns());
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) score_batch_kernel(const ScoreArgs* __restrict__ sc,
+                                                          const int2* __restrict__ items, int total,
+                                                          unsigned long long* keys)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= total) return;
+    const int2 sl = items[gw];
+    const ScoreArgs& S = sc[sl.x];
+    const float cost = traj_cost<NC>(S, sl.y, lane);
+    if (lane == 0) {
+        S.cost_out[sl.y] = cost;
+        atomicMin(keys + sl.x, cost_key(cost, sl.y));
+    }
+}
+
+__global__ void batch_reset_kernel(unsigned long long* scratch, int S)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 + 2 * S; i += gridDim.x * blockDim.x)
+        scratch[i] = (i == 1 || i >= 2 + S) ? ~0ull : 0ull;
+}
+
+__global__ void batch_finish_kernel(const ScoreArgs* __restrict__ sc, int S, const unsigned long long* keys)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x)
+        *sc[s].argmin_out = key_argmin(keys[s]);
 }
 
 }  // namespace mmpc
@@ -1842,4 +1980,254 @@ extern "C" int mmpc_score_static(const mmpc_meta* meta, int N, int n, const floa
     else score_static_kernel<16><<<grid, 32 * STATIC_WARPS_PER_CTA, 0, st>>>(s);
     e = cudaGetLastError();
     return e == cudaSuccess ? MMPC_OK : static_fail(std::string("score_static launch: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of scenes (host side)
+// ---------------------------------------------------------------------------
+struct mmpc_batch {
+    int S = 0, NC = 12, total = 0, threads = 0, grid = 0, schedule = 0;
+    size_t smem = 0;
+    void* kern = nullptr;
+    std::vector<mmpc_scene> scenes;
+    std::vector<mmpc::SolveArgs> args;
+    std::vector<mmpc::ScoreArgs> sargs;
+    mmpc::SolveArgs* d_args = nullptr;
+    mmpc::ScoreArgs* d_sargs = nullptr;
+    int2* d_items = nullptr;
+    unsigned long long* d_scratch = nullptr;  // [2 + 2S], laid out as the batch kernels describe
+};
+
+namespace {
+
+int batch_fail(const std::string& msg, int code)
+{
+    mmpc::set_global_error(msg);
+    return code;
+}
+
+void batch_free(mmpc_batch* b)
+{
+    if (!b) return;
+    cudaFree(b->d_args);
+    cudaFree(b->d_sargs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_scratch);
+    delete b;
+}
+
+// Item order for a schedule: 1 scene by scene in the given order, 2 scenes by
+// decreasing work per trajectory (N (m + 32): obstacle-sample pairs plus the
+// per-sample work), 3 trajectories of all scenes by decreasing work.
+std::vector<int2> batch_items(const mmpc_batch* b, int schedule)
+{
+    std::vector<int> order(b->S);
+    for (int s = 0; s < b->S; ++s) order[s] = s;
+    auto cost = [&](int s) {
+        const mmpc_ctx* c = b->scenes[s].ctx;
+        return (double)c->p.N * (double)(c->m + 32);
+    };
+    if (schedule >= 2)
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<int2> items;
+    items.reserve(b->total);
+    if (schedule == 3) {
+        // round-robin over the scenes in decreasing-work order: the longest
+        // trajectories start first and every scene progresses from the start
+        int maxB = 0;
+        for (int s : order) maxB = std::max(maxB, b->scenes[s].B);
+        for (int l = 0; l < maxB; ++l)
+            for (int s : order)
+                if (l < b->scenes[s].B) items.push_back(make_int2(s, l));
+    } else {
+        for (int s : order)
+            for (int l = 0; l < b->scenes[s].B; ++l) items.push_back(make_int2(s, l));
+    }
+    return items;
+}
+
+}  // namespace
+
+extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_meta* meta, mmpc_batch** out)
+{
+    using namespace mmpc;
+    if (out) *out = nullptr;
+    if (!out || !scenes || !meta || S < 1) return batch_fail("mmpc_batch_create: bad arguments", MMPC_ERR_INVALID_ARG);
+    if (meta->kind < MMPC_META_CRUISE || meta->kind > MMPC_META_ABS || !(meta->w1 >= 0.f) || !(meta->w2 >= 0.f) ||
+        !std::isfinite(meta->w1) || !std::isfinite(meta->w2) || !std::isfinite(meta->v_ref) ||
+        !std::isfinite(meta->y_ref) || std::isnan(meta->psi_max))
+        return batch_fail("mmpc_batch_create: invalid meta cost", MMPC_ERR_INVALID_ARG);
+    mmpc_batch* b = new mmpc_batch();
+    b->S = S;
+    b->scenes.assign(scenes, scenes + S);
+    int max_m = 0, maxN = 0, maxRows = 0;
+    for (int s = 0; s < S; ++s) {
+        const mmpc_scene& sc = scenes[s];
+        const mmpc_ctx* c = sc.ctx;
+        if (!c || !c->d_blob) { batch_free(b); return batch_fail("mmpc_batch_create: scene without a set-up context", MMPC_ERR_NOT_SETUP); }
+        if (s == 0) b->NC = c->NC;
+        if (c->NC != b->NC) { batch_free(b); return batch_fail("mmpc_batch_create: scenes mix n <= 12 and n > 12", MMPC_ERR_SHAPE); }
+        if (sc.B < 0 || !sc.ego || (c->m > 0 && !sc.obst) || (sc.B > 0 && (!sc.goals || !sc.coef_out || !sc.cost_out)) || !sc.argmin_out) {
+            batch_free(b);
+            return batch_fail("mmpc_batch_create: NULL pointer in scene " + std::to_string(s), MMPC_ERR_INVALID_ARG);
+        }
+        b->total += sc.B;
+        max_m = std::max(max_m, c->m);
+        maxN = std::max(maxN, c->p.N);
+        maxRows = std::max(maxRows, c->L.rows1);
+    }
+    const int NP = (maxN + 1) / 2;
+    b->threads = 32 * ((NP + 31) / 32);
+    const int RSD = b->NC == 12 ? SolveSmem<12>::RSD : SolveSmem<16>::RSD;
+    b->smem = sizeof(float) * (size_t)maxRows + 32 * (size_t)max_m + sizeof(float) * (size_t)MAX_WARPS * (b->NC + RSD) +
+              sizeof(int) * (size_t)(b->threads / 32) * max_m;
+    if (b->smem > 227 * 1024) { batch_free(b); return batch_fail("mmpc_batch_create: scenes do not fit in shared memory", MMPC_ERR_SHAPE); }
+    if (b->NC == 12) {
+        b->kern = b->threads <= 64 ? (void*)am_solve_batch_kernel<12, 64>
+                : b->threads <= 128 ? (void*)am_solve_batch_kernel<12, 128> : (void*)am_solve_batch_kernel<12, 256>;
+    } else {
+        b->kern = b->threads <= 64 ? (void*)am_solve_batch_kernel<16, 64>
+                : b->threads <= 128 ? (void*)am_solve_batch_kernel<16, 128> : (void*)am_solve_batch_kernel<16, 256>;
+    }
+    cudaError_t e = cudaFuncSetAttribute(b->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kern, b->threads, b->smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        batch_free(b);
+        return batch_fail(std::string("mmpc_batch_create: occupancy query: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+    }
+    b->grid = std::max(1, std::min(b->total, sms * per_sm));
+
+    b->args.resize(S);
+    b->sargs.resize(S);
+    for (int s = 0; s < S; ++s) {
+        const mmpc_scene& sc = scenes[s];
+        const mmpc_ctx* c = sc.ctx;
+        const mmpc_params& p = c->p;
+        SolveArgs& a = b->args[s];
+        a = SolveArgs{};
+        a.N = p.N; a.n = p.n; a.m = c->m; a.B = sc.B; a.iters = p.iters; a.check_every = p.check_every;
+        a.cull = p.cull ? 1 : 0;
+        a.rho = (float)p.rho; a.a = (float)p.a; a.b = (float)p.b;
+        a.inv_a = (float)(1.0 / p.a); a.inv_b = (float)(1.0 / p.b);
+        a.v_min = (float)p.v_min; a.v_max = (float)p.v_max; a.a_max = (float)p.a_max; a.tol = p.tol;
+        a.L = c->L;
+        a.blob = c->d_blob;
+        a.ego = sc.ego; a.obst = sc.obst; a.goals = sc.goals; a.warm_c = nullptr; a.warm_l = nullptr;
+        a.coef_out = sc.coef_out; a.lam_out = sc.lam_out; a.resid_out = sc.resid_out; a.iters_out = sc.iters_out;
+        a.err_flag = reinterpret_cast<unsigned*>(c->d_scratch + 1) + 1;
+        a.work = c->d_scratch + 2;  // counted per scene, read with mmpc_take_work_count
+        ScoreArgs& g = b->sargs[s];
+        g = ScoreArgs{};
+        g.N = p.N; g.n = p.n; g.B = sc.B; g.kind = meta->kind;
+        g.w1 = meta->w1; g.w2 = meta->w2; g.v_ref = meta->v_ref; g.y_ref = meta->y_ref; g.psi_max = meta->psi_max;
+        g.L = c->L; g.blob = c->d_blob; g.coef = sc.coef_out; g.cost_out = sc.cost_out; g.argmin_out = sc.argmin_out;
+    }
+    const size_t nscratch = 2 + 2 * (size_t)S;
+    e = cudaMalloc(&b->d_args, sizeof(SolveArgs) * S);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sargs, sizeof(ScoreArgs) * S);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * std::max(1, b->total));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_scratch, sizeof(unsigned long long) * nscratch);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_args, b->args.data(), sizeof(SolveArgs) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_sargs, b->sargs.data(), sizeof(ScoreArgs) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_scratch, 0, sizeof(unsigned long long) * nscratch);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return batch_fail(std::string("mmpc_batch_create: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+    }
+    *out = b;
+    return mmpc_batch_set_schedule(b, 1);
+}
+
+extern "C" int mmpc_batch_set_schedule(mmpc_batch* b, int schedule)
+{
+    if (!b) return batch_fail("mmpc_batch_set_schedule: NULL batch", MMPC_ERR_NOT_SETUP);
+    if (schedule < 1 || schedule > 3) return batch_fail("mmpc_batch_set_schedule: schedule must be 1, 2 or 3", MMPC_ERR_INVALID_ARG);
+    const std::vector<int2> items = batch_items(b, schedule);
+    if (b->total > 0) {
+        cudaError_t e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return batch_fail(std::string("mmpc_batch_set_schedule: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+    }
+    b->schedule = schedule;
+    return MMPC_OK;
+}
+
+extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
+{
+    using namespace mmpc;
+    if (!b) return batch_fail("mmpc_batch_run: NULL batch", MMPC_ERR_NOT_SETUP);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    batch_reset_kernel<<<1, 256, 0, st>>>(b->d_scratch, b->S);
+    if (b->total > 0) {
+        using KernT = void (*)(const SolveArgs*, const int2*, int, unsigned long long*);
+        reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args, b->d_items, b->total,
+                                                                            b->d_scratch);
+        const int wpb = 8;
+        const int sgrid = (b->total + wpb - 1) / wpb;
+        if (b->NC == 12) score_batch_kernel<12><<<sgrid, 32 * wpb, 0, st>>>(b->d_sargs, b->d_items, b->total, b->d_scratch + 2 + b->S);
+        else score_batch_kernel<16><<<sgrid, 32 * wpb, 0, st>>>(b->d_sargs, b->d_items, b->total, b->d_scratch + 2 + b->S);
+    }
+    batch_finish_kernel<<<(b->S + 255) / 256, 256, 0, st>>>(b->d_sargs, b->S, b->d_scratch + 2 + b->S);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : batch_fail(std::string("mmpc_batch_run: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+}
+
+extern "C" int mmpc_batch_times(mmpc_batch* b, float* scene_ms, float* makespan_ms)
+{
+    if (!b) return batch_fail("mmpc_batch_times: NULL batch", MMPC_ERR_NOT_SETUP);
+    std::vector<unsigned long long> h(1 + (size_t)b->S);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), b->d_scratch + 1, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return batch_fail(std::string("mmpc_batch_times: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+    const unsigned long long t0 = h[0];
+    float mk = 0.f;
+    for (int s = 0; s < b->S; ++s) {
+        const float ms = (h[1 + s] >= t0 && h[1 + s] != 0ull) ? (float)((h[1 + s] - t0) * 1e-6) : 0.f;
+        if (scene_ms) scene_ms[s] = ms;
+        mk = std::max(mk, ms);
+    }
+    if (makespan_ms) *makespan_ms = mk;
+    return MMPC_OK;
+}
+
+extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
+{
+    if (!b) return batch_fail("mmpc_batch_autotune: NULL batch", MMPC_ERR_NOT_SETUP);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return batch_fail("mmpc_batch_autotune: cudaEventCreate failed", MMPC_ERR_CUDA);
+    int best = 1;
+    float best_ms = 1e30f;
+    int rc = MMPC_OK;
+    for (int sch = 1; sch <= 3 && rc == MMPC_OK; ++sch) {
+        rc = mmpc_batch_set_schedule(b, sch);
+        if (rc == MMPC_OK) rc = mmpc_batch_run(b, stream);  // warm-up
+        float total = 0.f;
+        for (int r = 0; r < 2 && rc == MMPC_OK; ++r) {
+            cudaEventRecord(e0, st);
+            rc = mmpc_batch_run(b, stream);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            total += ms;
+        }
+        if (rc == MMPC_OK && total < best_ms) { best_ms = total; best = sch; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MMPC_OK) return rc;
+    rc = mmpc_batch_set_schedule(b, best);
+    if (chosen) *chosen = best;
+    return rc;
+}
+
+extern "C" void mmpc_batch_destroy(mmpc_batch* b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
 }

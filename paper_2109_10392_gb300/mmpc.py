@@ -28,7 +28,9 @@ MMPC_META_HSRL = 1
 MMPC_META_ABS = 2
 
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
-            "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count")
+            "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
+            "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
+            "mmpc_batch_destroy")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
 
@@ -59,6 +61,22 @@ class MmpcMeta(ctypes.Structure):
         ("v_ref", ctypes.c_float),
         ("y_ref", ctypes.c_float),
         ("psi_max", ctypes.c_float),
+    ]
+
+
+class MmpcScene(ctypes.Structure):
+    _fields_ = [
+        ("ctx", ctypes.c_void_p),
+        ("ego", ctypes.c_void_p),
+        ("obst", ctypes.c_void_p),
+        ("goals", ctypes.c_void_p),
+        ("B", ctypes.c_int),
+        ("coef_out", ctypes.c_void_p),
+        ("lam_out", ctypes.c_void_p),
+        ("resid_out", ctypes.c_void_p),
+        ("iters_out", ctypes.c_void_p),
+        ("cost_out", ctypes.c_void_p),
+        ("argmin_out", ctypes.c_void_p),
     ]
 
 
@@ -103,6 +121,19 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_score_static.restype = ctypes.c_int
     L.mmpc_take_work_count.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
     L.mmpc_take_work_count.restype = ctypes.c_int
+    L.mmpc_batch_create.argtypes = [ctypes.POINTER(MmpcScene), ctypes.c_int, ctypes.POINTER(MmpcMeta),
+                                    ctypes.POINTER(vp)]
+    L.mmpc_batch_create.restype = ctypes.c_int
+    L.mmpc_batch_set_schedule.argtypes = [vp, ctypes.c_int]
+    L.mmpc_batch_set_schedule.restype = ctypes.c_int
+    L.mmpc_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
+    L.mmpc_batch_autotune.restype = ctypes.c_int
+    L.mmpc_batch_run.argtypes = [vp, vp]
+    L.mmpc_batch_run.restype = ctypes.c_int
+    L.mmpc_batch_times.argtypes = [vp, fp, ctypes.POINTER(ctypes.c_float)]
+    L.mmpc_batch_times.restype = ctypes.c_int
+    L.mmpc_batch_destroy.argtypes = [vp]
+    L.mmpc_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -265,3 +296,101 @@ class Solver:
         am = torch.empty((1,), dtype=torch.int32, device=coef.device)
         mmpc_score(self.ctx, mt, coef, cost, am, stream)
         return cost, am
+
+
+class Batch:
+    """Many scenes solved and scored together (mmpc_batch_*): one persistent
+    solve launch over all (scene, trajectory) items, one scoring launch, a
+    per-scene argmin.  `scenes` is a list of dicts with keys params (dict),
+    ego, obst (CUDA float32 tensors, obst [m, 4] or None) and goals ([B, 3]).
+    The outputs are allocated here once, as flat tensors over all scenes
+    (`flat`) with per-scene views (`out`); `run` only enqueues kernels, so it
+    can be captured in a CUDA graph.  All scenes must have n <= 12, or all
+    n > 12."""
+
+    def __init__(self, scenes: list, meta: dict | MmpcMeta, want_lam: bool = False):
+        import torch
+        self.meta = meta if isinstance(meta, MmpcMeta) else make_meta(**meta)
+        self.solvers, self.inputs, self.out = [], [], []
+        self.S = len(scenes)
+        self.handle = None
+        dev = scenes[0]["goals"].device if scenes else torch.device("cuda:0")
+        Bs = [int(sc["goals"].shape[0]) for sc in scenes]
+        ns = [int(sc["params"]["n"]) for sc in scenes]
+        tot_c = sum(3 * b * n for b, n in zip(Bs, ns))
+        tot_b = sum(Bs)
+        z = lambda k, dt=torch.float32: torch.zeros((k,), dtype=dt, device=dev)  # noqa: E731
+        self.flat = dict(coef=z(tot_c), lam=z(tot_c) if want_lam else None, resid=z(4 * tot_b),
+                         iters=z(tot_b, torch.int32), cost=z(tot_b), argmin=z(max(1, self.S), torch.int32))
+        self.offsets = []
+        desc = (MmpcScene * max(1, self.S))()
+        oc = ob = 0
+        for i, sc in enumerate(scenes):
+            obst = sc["obst"]
+            m = 0 if obst is None else int(obst.shape[0])
+            sv = Solver(sc["params"], m)
+            self.solvers.append(sv)
+            B, n = Bs[i], ns[i]
+            F = self.flat
+            o = dict(coef=F["coef"][oc:oc + 3 * n * B].view(B, 3 * n),
+                     lam=None if F["lam"] is None else F["lam"][oc:oc + 3 * n * B].view(B, 3 * n),
+                     resid=F["resid"][4 * ob:4 * (ob + B)].view(B, 4), iters=F["iters"][ob:ob + B],
+                     cost=F["cost"][ob:ob + B], argmin=F["argmin"][i:i + 1])
+            self.offsets.append((oc, ob))
+            oc += 3 * n * B
+            ob += B
+            desc[i] = MmpcScene(sv.ctx, _ptr(sc["ego"]), _ptr(obst) if m else None, _ptr(sc["goals"]), B,
+                                _ptr(o["coef"]), _ptr(o["lam"]), _ptr(o["resid"]), _ptr(o["iters"], "int32"),
+                                _ptr(o["cost"]), _ptr(o["argmin"], "int32"))
+            self.inputs.append(sc)
+            self.out.append(o)
+        self.handle = ctypes.c_void_p()
+        rc = lib().mmpc_batch_create(desc, self.S, ctypes.byref(self.meta), ctypes.byref(self.handle))
+        if rc != MMPC_OK:
+            self.handle = None
+            self.close()
+            _err(None, rc)
+
+    def set_schedule(self, schedule: int) -> None:
+        rc = lib().mmpc_batch_set_schedule(self.handle, int(schedule))
+        if rc != MMPC_OK:
+            _err(None, rc)
+
+    def autotune(self, stream=None) -> int:
+        chosen = ctypes.c_int(0)
+        rc = lib().mmpc_batch_autotune(self.handle, _stream(stream), ctypes.byref(chosen))
+        if rc != MMPC_OK:
+            _err(None, rc)
+        return int(chosen.value)
+
+    def run(self, stream=None) -> None:
+        rc = lib().mmpc_batch_run(self.handle, _stream(stream))
+        if rc != MMPC_OK:
+            _err(None, rc)
+
+    def times(self):
+        """(per-scene completion times in ms since the first CTA started, makespan)."""
+        ms = np.zeros(max(1, self.S), dtype=np.float32)
+        mk = ctypes.c_float(0.0)
+        rc = lib().mmpc_batch_times(self.handle, ctypes.c_void_p(ms.ctypes.data), ctypes.byref(mk))
+        if rc != MMPC_OK:
+            _err(None, rc)
+        return ms[:self.S], float(mk.value)
+
+    def take_work_count(self) -> int:
+        """Obstacle-sample pairs evaluated by the batch's runs (summed over scenes)."""
+        return sum(mmpc_take_work_count(s.ctx) for s in self.solvers)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mmpc_batch_destroy(self.handle)
+            self.handle = None
+        for s in getattr(self, "solvers", []):
+            s.close()
+        self.solvers = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

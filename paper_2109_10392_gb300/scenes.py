@@ -109,3 +109,19 @@ def scene_custom(seed: int, B: int, m: int, N: int = 100, n: int = 12, x_range=(
     obst = _spawn_obstacles(rng, m, x_range[0], x_range[1], 5.0, 20.0, ego_y, p["a"], p["b"])
     goals = np.stack([rng.uniform(-5.25, 5.25, B), rng.uniform(5.0, 30.0, B), np.zeros(B)], axis=1)
     return Scene(ego, obst, goals, p, dict(META_ABS), f"highway_B{B}_m{m}_N{N}_n{n}", seed)
+
+
+def scene_batch(seed: int, S: int = 256, B_range=(16, 512), m_range=(5, 40), N_choices=(50, 100, 150),
+                n: int = 12) -> list:
+    """S independent scenes of the large-scene distribution with uneven goal
+    counts B ~ U{B_range}, obstacle counts m ~ U{m_range} and horizons sampled
+    at N in N_choices (the batching workload); scene i has seed (seed, i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(S):
+        B = int(rng.integers(B_range[0], B_range[1] + 1))
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        N = int(rng.choice(N_choices))
+        sub = int(rng.integers(0, 2**31 - 1))
+        out.append(scene_custom(sub, B, m, N=N, n=n))
+    return out

@@ -117,3 +117,24 @@ def gpu_score(params: dict, m: int, coef, meta: dict, solver=None):
     if solver is None:
         s.close()
     return out
+
+
+def check_parity(params, ego, obst, goals, gpu, orc, min_frac=0.3, sens=None, init=None, init_lam=None):
+    """Positions within 1e-3 m on the parity set; on the moderately
+    conditioned rest, within 10x the oracle's own response to a 1e-6 relative
+    input perturbation (i.e. what a 1e-5 perturbation moves, linearly); the
+    chaotic rest (that response above 1 cm) only for validity."""
+    err = pos_err(params, gpu["coef"], orc["coef"])
+    if sens is None:
+        sens = sensitivity(params, ego, obst, goals, orc["coef"], init=init, init_lam=init_lam)
+    good = sens < SENS_TOL
+    mid = ~good & (sens < CHAOS_TOL)
+    info = f"err {np.array2string(err, precision=2)} sens {np.array2string(sens, precision=2)}"
+    assert good.mean() >= min_frac, f"parity set {good.mean():.3f} below {min_frac}; {info}"
+    assert np.all(err[good] <= POS_TOL), info
+    assert np.all(err[mid] <= np.maximum(POS_TOL, 10 * sens[mid])), info
+    assert np.all(np.isfinite(gpu["coef"]))
+    # validity of the rest: the boundary rows hold
+    be = boundary_error(params, ego, goals, gpu["coef"])
+    assert np.all(be < 1e-2), be.max()
+    return err, good

@@ -97,6 +97,19 @@ def test_calls_without_context_fail_cleanly():
     assert L.mmpc_score(None, ctypes.byref(meta), None, 0, None, None, None) == mmpc.MMPC_ERR_NOT_SETUP
     assert L.mmpc_last_error(None)
     L.mmpc_destroy(None)
+    # batches: argument and context checks come before any CUDA call
+    out = ctypes.c_void_p()
+    assert L.mmpc_batch_create(None, 1, ctypes.byref(meta), ctypes.byref(out)) == mmpc.MMPC_ERR_INVALID_ARG
+    desc = (mmpc.MmpcScene * 2)()
+    assert L.mmpc_batch_create(desc, 0, ctypes.byref(meta), ctypes.byref(out)) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_batch_create(desc, 2, ctypes.byref(meta), ctypes.byref(out)) == mmpc.MMPC_ERR_NOT_SETUP
+    assert not out.value
+    bad = mmpc.make_meta(kind=9)
+    assert L.mmpc_batch_create(desc, 2, ctypes.byref(bad), ctypes.byref(out)) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_batch_run(None, None) == mmpc.MMPC_ERR_NOT_SETUP
+    assert L.mmpc_batch_set_schedule(None, 1) == mmpc.MMPC_ERR_NOT_SETUP
+    assert L.mmpc_batch_times(None, None, None) == mmpc.MMPC_ERR_NOT_SETUP
+    L.mmpc_batch_destroy(None)
 
 
 def test_setup_rejects_bad_buffers():

@@ -21,25 +21,7 @@ def _scene_arrays(sc):
     return U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
 
 
-def _check_parity(params, ego, obst, goals, gpu, orc, min_frac=0.3, sens=None, init=None, init_lam=None):
-    """Positions within 1e-3 m on the parity set; on the moderately
-    conditioned rest, within 10x the oracle's own response to a 1e-6 relative
-    input perturbation (i.e. what a 1e-5 perturbation moves, linearly); the
-    chaotic rest (that response above 1 cm) only for validity."""
-    err = U.pos_err(params, gpu["coef"], orc["coef"])
-    if sens is None:
-        sens = U.sensitivity(params, ego, obst, goals, orc["coef"], init=init, init_lam=init_lam)
-    good = sens < U.SENS_TOL
-    mid = ~good & (sens < U.CHAOS_TOL)
-    info = f"err {np.array2string(err, precision=2)} sens {np.array2string(sens, precision=2)}"
-    assert good.mean() >= min_frac, f"parity set {good.mean():.3f} below {min_frac}; {info}"
-    assert np.all(err[good] <= U.POS_TOL), info
-    assert np.all(err[mid] <= np.maximum(U.POS_TOL, 10 * sens[mid])), info
-    assert np.all(np.isfinite(gpu["coef"]))
-    # validity of the rest: the boundary rows hold
-    be = U.boundary_error(params, ego, goals, gpu["coef"])
-    assert np.all(be < 1e-2), be.max()
-    return err, good
+_check_parity = U.check_parity
 
 
 @pytest.mark.parametrize("variant", [1, 2])
@@ -297,3 +279,22 @@ def test_variants_agree():
     sens = U.sensitivity(sc.params, ego, obst, goals, orc["coef"])
     good = sens < U.SENS_TOL
     assert np.all(U.pos_err(sc.params, a["coef"], b["coef"])[good] <= U.POS_TOL)
+
+
+@pytest.mark.parametrize("iters", [100, 300])
+def test_no_drift_over_long_runs(iters):
+    """The multiplier update integrates any bias of the per-sample targets, so
+    a biased heading sin/cos (or another systematic FP32 error) makes the
+    iterate drift away from the oracle linearly in the iteration count.  An
+    obstacle-free scene, whose slow heading mode shows such a drift most
+    clearly, must stay within the position bar after 300 iterations."""
+    sc = scenes.scene_custom(12, 9, 0, N=60, x_range=(-30.0, 120.0))
+    params = dict(sc.params)
+    params.update(iters=iters, tol=0.0)
+    ego, obst, goals = U.f32(sc.ego), U.f32(sc.obst).reshape(-1, 4), U.f32(sc.goals)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    for variant in (1, 2):
+        params["variant"] = variant
+        gpu = U.gpu_solve(params, ego, obst, goals)
+        err = U.pos_err(params, gpu["coef"], orc["coef"])
+        assert err.max() <= U.POS_TOL, (variant, err)
