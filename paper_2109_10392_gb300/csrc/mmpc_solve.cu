@@ -3,10 +3,11 @@
 //
 // Solve kernel: one CTA per trajectory l of the batch, one thread per pair of
 // time samples (2i, 2i+1), whose arithmetic runs as packed f32x2 operations
-// (FFMA2 / FADD2 / FMUL2: one issue slot for two samples).  Every quantity that Algorithm 1 carries from one iteration to the
-// next for trajectory l -- c_x, c_y, c_psi and lambda_x, lambda_y, lambda_psi
-// -- stays on chip (registers of warp 0, broadcast through shared memory) for
-// all iterations; the auxiliary variables v, alpha, d, alpha_a, d_a of Eqs.
+// (FFMA2 / FADD2 / FMUL2: one issue slot for two samples).  Every quantity
+// that Algorithm 1 carries from one iteration to the next for trajectory l --
+// c_x, c_y, c_psi and lambda_x, lambda_y, lambda_psi -- stays on chip for all
+// iterations (registers of every warp, which all run the small QP steps on
+// the same partial sums); the auxiliary variables v, alpha, d, alpha_a, d_a of Eqs.
 // split_v, split_alpha_o and split_alpha_a are closed-form functions of the
 // coefficients and are recomputed in registers where they are used.  The
 // shared matrices (basis rows, KKT inverse blocks) are staged once per CTA
@@ -2018,7 +2019,8 @@ void batch_free(mmpc_batch* b)
 
 // Item order for a schedule: 1 scene by scene in the given order, 2 scenes by
 // decreasing work per trajectory (N (m + 32): obstacle-sample pairs plus the
-// per-sample work), 3 trajectories of all scenes by decreasing work.
+// per-sample work), 3 round-robin over the scenes in the order of 2, one
+// trajectory of each at a time.
 std::vector<int2> batch_items(const mmpc_batch* b, int schedule)
 {
     std::vector<int> order(b->S);
