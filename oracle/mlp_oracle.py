@@ -58,7 +58,11 @@ def bf16_round(x):
 
 
 def lane_index(y):
-    return np.clip(np.floor((np.asarray(y, dtype=np.float64) + ROAD_LEFT) / LANE_WIDTH), 0, 3)
+    """clip(floor((y + 7) / 3.5), 0, 3), formed in float32 with one rounding
+    per operation: an integer decision, taken in the GPU's precision."""
+    f = np.float32
+    q = ((np.asarray(y, dtype=np.float32) + f(ROAD_LEFT)).astype(f) / f(LANE_WIDTH)).astype(f)
+    return np.clip(np.floor(q), 0, 3).astype(np.float64)
 
 
 def nearest_order(ego, obst, a, b):

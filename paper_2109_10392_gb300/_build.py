@@ -14,8 +14,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libmmpc.so")
-SOURCES = ["mmpc_solve.cu", "mmpc_build.cpp"]
-HEADERS = ["mmpc_internal.h", os.path.join("..", "..", "include", "mmpc.h")]
+SOURCES = ["mmpc_solve.cu", "mmpc_build.cpp", "mmpc_mlp.cu"]
+HEADERS = ["mmpc_internal.h", os.path.join("..", "..", "include", "mmpc.h"),
+           os.path.join("..", "..", "include", "mmpc_mlp.h")]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,7 +36,7 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the two translation units in parallel and link libmmpc.so next
+    """Compile the translation units in parallel and link libmmpc.so next
     to this file.  Returns the library path."""
     if not force and not _stale():
         return LIB

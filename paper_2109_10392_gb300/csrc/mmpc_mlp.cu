@@ -1,0 +1,683 @@
+// GB300 (sm_103a) kernels of the learned warm start (include/mmpc_mlp.h):
+// scene features, the MLP forward / backward / AdamW kernels, and the
+// encoding between solutions of Algorithm 1 (Sec. III-E) and network outputs.
+//
+// The network is small (64 -> 256 -> 256 -> 256 -> 6n) and its cost is
+// negligible next to the solves it warm-starts, so its products run as a
+// tiled FP32 SIMT GEMM (64 x 64 tiles, 4 x 4 outputs per thread, operands
+// staged through shared memory) with the bfloat16 weights widened on load
+// and every epilogue fused: bias + GELU (keeping the pre-activation for the
+// backward pass), the GELU derivative on the backward product, split-K
+// partial sums for the weight gradients reduced in a fixed order (so training
+// is deterministic).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mmpc_mlp.h"
+
+namespace {
+
+thread_local std::string g_mlp_error = "no error";
+
+int fail(int code, const std::string& msg)
+{
+    g_mlp_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(MMPC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// Features, encoding, statistics
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool key_less(float ki, int i, float kj, int j)
+{
+    const bool ni = isnan(ki), nj = isnan(kj);
+    if (ni || nj) return (!ni && nj) || (ni && nj && i < j);
+    return ki < kj || (ki == kj && i < j);
+}
+
+__device__ __forceinline__ float lane_of(float y)
+{
+    const float q = floorf(__fdiv_rn(__fadd_rn(y, 7.f), 3.5f));
+    return fminf(fmaxf(q, 0.f), 3.f);
+}
+
+// One CTA per scene: ranking keys of the obstacles, the scene part of the
+// feature row in shared memory, then every goal's row.
+__global__ void __launch_bounds__(128) features_kernel(const mmpc_warm_scene* __restrict__ sc, int S, float a,
+                                                       float b)
+{
+    const int s = blockIdx.x;
+    if (s >= S) return;
+    const mmpc_warm_scene d = sc[s];
+    __shared__ float key[MMPC_MAX_OBST];
+    __shared__ int slot[MMPC_MLP_NEAREST];
+    __shared__ float row[MMPC_MLP_FEATURES];
+    const int tid = threadIdx.x;
+    const float y0 = d.ego[0], v0 = d.ego[1];
+    const int m = min(max(d.m, 0), MMPC_MAX_OBST);
+    for (int j = tid; j < m; j += blockDim.x) {
+        const float ux = __fdiv_rn(d.obst[4 * j], a);
+        const float uy = __fdiv_rn(__fsub_rn(d.obst[4 * j + 1], y0), b);
+        key[j] = __fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy));
+    }
+    if (tid < MMPC_MLP_NEAREST) slot[tid] = -1;
+    __syncthreads();
+    for (int j = tid; j < m; j += blockDim.x) {
+        const float kj = key[j];
+        int rank = 0;
+        for (int i = 0; i < m && rank < MMPC_MLP_NEAREST; ++i) rank += key_less(key[i], i, kj, j) ? 1 : 0;
+        if (rank < MMPC_MLP_NEAREST) slot[rank] = j;
+    }
+    __syncthreads();
+    if (tid < MMPC_MLP_FEATURES) {
+        float v = 0.f;
+        if (tid == 0) v = y0 / 3.5f;
+        else if (tid == 1) v = v0 / 20.f;
+        else if (tid == 2) v = d.ego[2];
+        else if (tid == 3) v = d.ego[3] / 4.f;
+        else if (tid < 4 + 5 * MMPC_MLP_NEAREST) {
+            const int sl = (tid - 4) / 5, f = (tid - 4) % 5;
+            const int j = slot[sl];
+            if (j < 0) {
+                v = f == 0 ? 10.f : 0.f;
+            } else {
+                const float* o = d.obst + 4 * j;
+                v = f == 0 ? o[0] / 100.f
+                  : f == 1 ? (o[1] - y0) / 3.5f
+                  : f == 2 ? (o[2] - v0) / 20.f
+                  : f == 3 ? o[3] / 20.f
+                           : lane_of(o[1]) - lane_of(y0);
+            }
+        } else if (tid == 57) {
+            v = 1.f;
+        }
+        row[tid] = v;
+    }
+    __syncthreads();
+    const int B = max(d.B, 0);
+    for (int e = tid; e < B * MMPC_MLP_FEATURES; e += blockDim.x) {
+        const int r = e / MMPC_MLP_FEATURES, c = e % MMPC_MLP_FEATURES;
+        float v = row[c];
+        if (c == 54) v = (d.goals[3 * r] - y0) / 3.5f;
+        else if (c == 55) v = d.goals[3 * r + 1] / 20.f;
+        else if (c == 56) v = d.goals[3 * r + 2] / 4.f;
+        d.X[(size_t)r * MMPC_MLP_FEATURES + c] = v;
+    }
+}
+
+// shift of column k of the encoding: v0 lin_k for c_x, y0 for c_y, 0 else
+__device__ __forceinline__ float enc_shift(int k, int n, float T, float y0, float v0)
+{
+    if (k < n) return v0 * (T * (float)k / (float)(n - 1));
+    if (k < 2 * n) return y0;
+    return 0.f;
+}
+
+__global__ void decode_kernel(const mmpc_warm_scene* __restrict__ sc, int S, int n, float T,
+                              const float* __restrict__ mu, const float* __restrict__ sigma)
+{
+    const int s = blockIdx.x;
+    if (s >= S) return;
+    const mmpc_warm_scene d = sc[s];
+    const float y0 = d.ego[0], v0 = d.ego[1];
+    const int W = 6 * n, B = max(d.B, 0);
+    for (int e = threadIdx.x; e < B * W; e += blockDim.x) {
+        const int r = e / W, k = e % W;
+        const float t = fmaf(d.Y[e], sigma[k], mu[k]);
+        if (k < 3 * n) d.coef[(size_t)r * 3 * n + k] = t + enc_shift(k, n, T, y0, v0);
+        else d.lam[(size_t)r * 3 * n + (k - 3 * n)] = t;
+    }
+}
+
+__global__ void encode_kernel(const mmpc_warm_scene* __restrict__ sc, int S, int n, float T,
+                              const float* __restrict__ mu, const float* __restrict__ sigma)
+{
+    const int s = blockIdx.x;
+    if (s >= S) return;
+    const mmpc_warm_scene d = sc[s];
+    const float y0 = d.ego[0], v0 = d.ego[1];
+    const int W = 6 * n, B = max(d.B, 0);
+    for (int e = threadIdx.x; e < B * W; e += blockDim.x) {
+        const int r = e / W, k = e % W;
+        const float t = k < 3 * n ? d.coef[(size_t)r * 3 * n + k] - enc_shift(k, n, T, y0, v0)
+                                  : d.lam[(size_t)r * 3 * n + (k - 3 * n)];
+        d.Z[e] = (t - mu[k]) / sigma[k];
+    }
+}
+
+// One CTA per column, float64 sums, two passes (mean, then squared deviations).
+__global__ void __launch_bounds__(256) column_stats_kernel(const float* __restrict__ X, int rows, int cols,
+                                                           float* __restrict__ mean_out, float* __restrict__ std_out)
+{
+    const int c = blockIdx.x;
+    __shared__ double part[256];
+    __shared__ double s_mean;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) acc += X[(size_t)r * cols + c];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_mean = part[0] / rows;
+    __syncthreads();
+    const double mean = s_mean;
+    acc = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double dv = X[(size_t)r * cols + c] - mean;
+        acc += dv * dv;
+    }
+    __syncthreads();
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sd = sqrt(part[0] / rows);
+        mean_out[c] = (float)mean;
+        std_out[c] = sd > 0.0 ? (float)sd : 1.f;
+    }
+}
+
+__global__ void gather_kernel(const float* __restrict__ src, int src_rows, int cols, const int* __restrict__ idx,
+                              int rows, float* __restrict__ out)
+{
+    const size_t total = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), c = (int)(e % cols);
+        const int i = idx[r];
+        out[e] = (i >= 0 && i < src_rows) ? src[(size_t)i * cols + c] : __int_as_float(0x7fc00000);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM with fused epilogues
+//   C[i][j] = sum_{k in chunk z} A(i, k) B(k, j)
+//   A(i, k) = TA ? A[k lda + i] : A[i lda + k]     (float)
+//   B(k, j) = TBT ? B[j ldb + k] : B[k ldb + j]    (float or bfloat16)
+// ---------------------------------------------------------------------------
+constexpr int BM = 64, BN = 64, BK = 16;
+
+enum Epi { EPI_BIAS = 0, EPI_BIAS_GELU = 1, EPI_GELU_GRAD = 2, EPI_PARTIAL = 3 };
+
+__device__ __forceinline__ float ld(const float* p) { return *p; }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad(float x)
+{
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+template <typename TBt, bool TA, bool TBT, int EPI>
+__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, int kchunk, const float* __restrict__ A,
+                                                   int lda, const TBt* __restrict__ B, int ldb, float* __restrict__ C,
+                                                   int ldc, const float* __restrict__ bias, float* __restrict__ pre,
+                                                   const float* __restrict__ aux)
+{
+    __shared__ __align__(16) float As[BK][BM + 4];
+    __shared__ __align__(16) float Bs[BK][BN + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            int ii, kk;
+            if (TA) { ii = e % BM; kk = e / BM; }
+            else { kk = e % BK; ii = e / BK; }
+            const int gi = i0 + ii, gk = k0 + kk;
+            float v = 0.f;
+            if (gi < M && gk < ke) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+            As[kk][ii] = v;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += 256) {
+            int kk, jj;
+            if (TBT) { kk = e % BK; jj = e / BK; }
+            else { jj = e % BN; kk = e / BN; }
+            const int gk = k0 + kk, gj = j0 + jj;
+            float v = 0.f;
+            if (gk < ke && gj < N) v = ld(TBT ? B + (size_t)gj * ldb + gk : B + (size_t)gk * ldb + gj);
+            Bs[kk][jj] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 bb = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    float* Cz = C + (EPI == EPI_PARTIAL ? (size_t)blockIdx.z * M * ldc : 0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gi = i0 + ty * 4 + r;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int gj = j0 + tx * 4 + c;
+            if (gj >= N) continue;
+            const size_t o = (size_t)gi * ldc + gj;
+            float v = acc[r][c];
+            if (EPI == EPI_BIAS) {
+                Cz[o] = v + bias[gj];
+            } else if (EPI == EPI_BIAS_GELU) {
+                v += bias[gj];
+                if (pre) pre[o] = v;
+                Cz[o] = gelu(v);
+            } else if (EPI == EPI_GELU_GRAD) {
+                Cz[o] = v * gelu_grad(aux[o]);
+            } else {
+                Cz[o] = v;
+            }
+        }
+    }
+}
+
+// out[e] = sum_{z < Z} part[z][e], z in increasing order (deterministic).
+__global__ void reduce_partials_kernel(const float* __restrict__ part, int Z, size_t count, float* __restrict__ out)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < Z; ++z) s += part[(size_t)z * count + e];
+        out[e] = s;
+    }
+}
+
+// db[j] = sum_r D[r][j]: one warp per column, lanes over rows, fixed order.
+__global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ D, int rows, int cols,
+                                                     float* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= cols) return;
+    float s = 0.f;
+    for (int r = lane; r < rows; r += 32) s += D[(size_t)r * cols + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[j] = s;
+}
+
+// D = 2 (y - z) / count; loss += sum (y - z)^2 / count.
+__global__ void __launch_bounds__(256) mse_kernel(const float* __restrict__ Y, const float* __restrict__ Z,
+                                                  size_t count, float* __restrict__ D, float* __restrict__ loss)
+{
+    const float inv = 1.f / (float)count;
+    float acc = 0.f;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const float r = Y[e] - Z[e];
+        D[e] = 2.f * r * inv;
+        acc = fmaf(r * inv, r, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// AdamW on one parameter array (wd = 0 for biases); refreshes the bfloat16 copy.
+__global__ void adamw_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                             float* __restrict__ v, __nv_bfloat16* __restrict__ w16, size_t count, float lr,
+                             float beta1, float beta2, float eps, float wd, float c1, float c2)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const float ge = g[e];
+        const float me = fmaf(beta1, m[e], (1.f - beta1) * ge);
+        const float ve = fmaf(beta2, v[e], (1.f - beta2) * ge * ge);
+        m[e] = me;
+        v[e] = ve;
+        const float mh = me * c1, vh = ve * c2;
+        const float we = w[e] - lr * (mh / (sqrtf(vh) + eps) + wd * w[e]);
+        w[e] = we;
+        if (w16) w16[e] = __float2bfloat16_rn(we);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ w16, size_t count)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        w16[e] = __float2bfloat16_rn(w[e]);
+}
+
+int grid_for(size_t count, int threads = 256)
+{
+    return (int)std::max<size_t>(1, std::min<size_t>((count + threads - 1) / threads, 152 * 16));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The network object
+// ---------------------------------------------------------------------------
+struct mmpc_mlp {
+    mmpc_mlp_config cfg{};
+    int L = 0, maxw = 0, inf_rows = 0, ksplit_rows = 512;
+    std::vector<float*> W, b, gW, gb, mW, vW, mb, vb;
+    std::vector<__nv_bfloat16*> W16;
+    std::vector<float*> H;    // H[i]: input of layer i (i >= 1), [max_batch][width[i]]
+    std::vector<float*> P;    // P[i]: pre-activation of layer i (hidden), [max_batch][width[i+1]]
+    float* Yb = nullptr;      // [max_batch][width[L]]
+    float* D0 = nullptr;      // backward ping-pong [max_batch][maxw]
+    float* D1 = nullptr;
+    float* part = nullptr;    // split-K partials of a weight gradient
+    size_t part_count = 0;
+    float* I0 = nullptr;      // inference ping-pong [inf_rows][maxw]
+    float* I1 = nullptr;
+    long long step = 0;
+};
+
+namespace {
+
+size_t wcount(const mmpc_mlp* n, int i) { return (size_t)n->cfg.width[i] * n->cfg.width[i + 1]; }
+
+void mlp_free(mmpc_mlp* n)
+{
+    if (!n) return;
+    auto f = [](void* p) { if (p) cudaFree(p); };
+    for (auto* v : {&n->W, &n->b, &n->gW, &n->gb, &n->mW, &n->vW, &n->mb, &n->vb, &n->H, &n->P})
+        for (float* p : *v) f(p);
+    for (auto* p : n->W16) f(p);
+    f(n->Yb); f(n->D0); f(n->D1); f(n->part); f(n->I0); f(n->I1);
+    delete n;
+}
+
+template <typename TBt, bool TA, bool TBT, int EPI>
+void gemm(int M, int N, int K, int splits, const float* A, int lda, const TBt* B, int ldb, float* C, int ldc,
+          const float* bias, float* pre, const float* aux, cudaStream_t st)
+{
+    const int kchunk = splits > 1 ? ((K + splits - 1) / splits + BK - 1) / BK * BK : K;
+    const int z = splits > 1 ? (K + kchunk - 1) / kchunk : 1;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, z);
+    gemm_kernel<TBt, TA, TBT, EPI><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, bias, pre, aux);
+}
+
+int splits_for(const mmpc_mlp* n, int rows) { return std::max(1, (rows + n->ksplit_rows - 1) / n->ksplit_rows); }
+
+// Forward over M <= rows of the buffers; keep = store pre-activations and
+// layer inputs for the backward pass.
+void forward_rows(mmpc_mlp* n, const float* X, int M, float* Y, bool keep, float* b0, float* b1, cudaStream_t st)
+{
+    const int L = n->L;
+    const float* in = X;
+    for (int i = 0; i < L; ++i) {
+        const int K = n->cfg.width[i], N = n->cfg.width[i + 1];
+        const bool last = i == L - 1;
+        float* out = last ? Y : (keep ? n->H[i + 1] : (i % 2 == 0 ? b0 : b1));
+        if (last)
+            gemm<__nv_bfloat16, false, false, EPI_BIAS>(M, N, K, 1, in, K, n->W16[i], N, out, N, n->b[i], nullptr,
+                                                        nullptr, st);
+        else
+            gemm<__nv_bfloat16, false, false, EPI_BIAS_GELU>(M, N, K, 1, in, K, n->W16[i], N, out, N, n->b[i],
+                                                             keep ? n->P[i] : nullptr, nullptr, st);
+        in = out;
+    }
+}
+
+bool valid_cfg(const mmpc_mlp_config* c)
+{
+    if (!c || c->layers < 1 || c->layers > MMPC_MLP_MAX_LAYERS || c->max_batch < 1) return false;
+    for (int i = 0; i <= c->layers; ++i)
+        if (c->width[i] < 1 || c->width[i] > MMPC_MLP_MAX_WIDTH) return false;
+    return std::isfinite(c->beta1) && std::isfinite(c->beta2) && std::isfinite(c->eps) && std::isfinite(c->weight_decay) &&
+           c->beta1 >= 0.f && c->beta1 < 1.f && c->beta2 >= 0.f && c->beta2 < 1.f && c->eps > 0.f && c->weight_decay >= 0.f;
+}
+
+int check_scenes(const mmpc_warm_scene* sc, int S)
+{
+    if (S < 0 || (S > 0 && !sc)) return fail(MMPC_ERR_INVALID_ARG, "scene table is NULL or S < 0");
+    return MMPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mmpc_mlp_last_error(void) { return g_mlp_error.c_str(); }
+
+int mmpc_features(const mmpc_warm_scene* scenes, int S, float a, float b, void* stream)
+{
+    int rc = check_scenes(scenes, S);
+    if (rc) return rc;
+    if (!(a > 0.f) || !(b > 0.f)) return fail(MMPC_ERR_INVALID_ARG, "ellipse semi-axes must be positive");
+    if (S == 0) return MMPC_OK;
+    features_kernel<<<S, 128, 0, (cudaStream_t)stream>>>(scenes, S, a, b);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "features_kernel");
+}
+
+int mmpc_warm_decode(const mmpc_warm_scene* scenes, int S, int n, float T, const float* mu, const float* sigma,
+                     void* stream)
+{
+    int rc = check_scenes(scenes, S);
+    if (rc) return rc;
+    if (n < MMPC_MIN_COEF || n > MMPC_MAX_COEF || !(T > 0.f) || !mu || !sigma)
+        return fail(MMPC_ERR_INVALID_ARG, "bad n, T or NULL mu / sigma");
+    if (S == 0) return MMPC_OK;
+    decode_kernel<<<S, 256, 0, (cudaStream_t)stream>>>(scenes, S, n, T, mu, sigma);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "decode_kernel");
+}
+
+int mmpc_warm_encode(const mmpc_warm_scene* scenes, int S, int n, float T, const float* mu, const float* sigma,
+                     void* stream)
+{
+    int rc = check_scenes(scenes, S);
+    if (rc) return rc;
+    if (n < MMPC_MIN_COEF || n > MMPC_MAX_COEF || !(T > 0.f) || !mu || !sigma)
+        return fail(MMPC_ERR_INVALID_ARG, "bad n, T or NULL mu / sigma");
+    if (S == 0) return MMPC_OK;
+    encode_kernel<<<S, 256, 0, (cudaStream_t)stream>>>(scenes, S, n, T, mu, sigma);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "encode_kernel");
+}
+
+int mmpc_column_stats(const float* X, int rows, int cols, float* mean_out, float* std_out, void* stream)
+{
+    if (!X || !mean_out || !std_out || rows < 1 || cols < 1) return fail(MMPC_ERR_INVALID_ARG, "bad column_stats arguments");
+    column_stats_kernel<<<cols, 256, 0, (cudaStream_t)stream>>>(X, rows, cols, mean_out, std_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "column_stats_kernel");
+}
+
+int mmpc_gather_rows(const float* src, int src_rows, int cols, const int* idx, int rows, float* out, void* stream)
+{
+    if (!src || !idx || !out || src_rows < 0 || cols < 1 || rows < 0) return fail(MMPC_ERR_INVALID_ARG, "bad gather arguments");
+    if (rows == 0) return MMPC_OK;
+    gather_kernel<<<grid_for((size_t)rows * cols), 256, 0, (cudaStream_t)stream>>>(src, src_rows, cols, idx, rows, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "gather_kernel");
+}
+
+int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const float* const* b, mmpc_mlp** out)
+{
+    if (out) *out = nullptr;
+    if (!out || !W || !b) return fail(MMPC_ERR_INVALID_ARG, "NULL argument");
+    if (!valid_cfg(cfg)) return fail(MMPC_ERR_INVALID_ARG, "invalid network configuration");
+    for (int i = 0; i < cfg->layers; ++i)
+        if (!W[i] || !b[i]) return fail(MMPC_ERR_INVALID_ARG, "NULL weight or bias array");
+    mmpc_mlp* n = new mmpc_mlp();
+    n->cfg = *cfg;
+    n->L = cfg->layers;
+    n->maxw = *std::max_element(cfg->width, cfg->width + cfg->layers + 1);
+    n->inf_rows = std::max(cfg->max_batch, 65536);
+    const size_t mb = (size_t)cfg->max_batch;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](float** p, size_t cnt) {
+        if (e == cudaSuccess) e = cudaMalloc(p, sizeof(float) * std::max<size_t>(cnt, 1));
+    };
+    const int L = n->L;
+    n->W.assign(L, nullptr); n->b.assign(L, nullptr); n->gW.assign(L, nullptr); n->gb.assign(L, nullptr);
+    n->mW.assign(L, nullptr); n->vW.assign(L, nullptr); n->mb.assign(L, nullptr); n->vb.assign(L, nullptr);
+    n->W16.assign(L, nullptr); n->H.assign(L, nullptr); n->P.assign(L, nullptr);
+    size_t maxw_count = 0;
+    for (int i = 0; i < L; ++i) {
+        const size_t wc = wcount(n, i), bc = cfg->width[i + 1];
+        maxw_count = std::max(maxw_count, wc);
+        alloc(&n->W[i], wc); alloc(&n->gW[i], wc); alloc(&n->mW[i], wc); alloc(&n->vW[i], wc);
+        alloc(&n->b[i], bc); alloc(&n->gb[i], bc); alloc(&n->mb[i], bc); alloc(&n->vb[i], bc);
+        if (e == cudaSuccess) e = cudaMalloc(&n->W16[i], sizeof(__nv_bfloat16) * wc);
+        if (i >= 1) alloc(&n->H[i], mb * cfg->width[i]);
+        if (i < L - 1) alloc(&n->P[i], mb * cfg->width[i + 1]);
+    }
+    alloc(&n->Yb, mb * cfg->width[L]);
+    alloc(&n->D0, mb * n->maxw);
+    alloc(&n->D1, mb * n->maxw);
+    const int zmax = splits_for(n, cfg->max_batch);
+    n->part_count = maxw_count * zmax;
+    alloc(&n->part, n->part_count);
+    alloc(&n->I0, (size_t)n->inf_rows * n->maxw);
+    alloc(&n->I1, (size_t)n->inf_rows * n->maxw);
+    for (int i = 0; i < L && e == cudaSuccess; ++i) {
+        const size_t wc = wcount(n, i), bc = cfg->width[i + 1];
+        e = cudaMemcpy(n->W[i], W[i], sizeof(float) * wc, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(n->b[i], b[i], sizeof(float) * bc, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(n->mW[i], 0, sizeof(float) * wc);
+        if (e == cudaSuccess) e = cudaMemset(n->vW[i], 0, sizeof(float) * wc);
+        if (e == cudaSuccess) e = cudaMemset(n->mb[i], 0, sizeof(float) * bc);
+        if (e == cudaSuccess) e = cudaMemset(n->vb[i], 0, sizeof(float) * bc);
+        if (e == cudaSuccess) e = cudaMemset(n->gW[i], 0, sizeof(float) * wc);
+        if (e == cudaSuccess) e = cudaMemset(n->gb[i], 0, sizeof(float) * bc);
+        if (e == cudaSuccess) {
+            to_bf16_kernel<<<grid_for(wc), 256>>>(n->W[i], n->W16[i], wc);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        mlp_free(n);
+        return cuda_fail(e, "mmpc_mlp_create");
+    }
+    *out = n;
+    return MMPC_OK;
+}
+
+int mmpc_mlp_forward(mmpc_mlp* n, const float* X, int M, float* Y, void* stream)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    if (M < 0 || (M > 0 && (!X || !Y))) return fail(MMPC_ERR_INVALID_ARG, "bad forward arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int in = n->cfg.width[0], outw = n->cfg.width[n->L];
+    for (int r0 = 0; r0 < M; r0 += n->inf_rows) {
+        const int rows = std::min(n->inf_rows, M - r0);
+        forward_rows(n, X + (size_t)r0 * in, rows, Y + (size_t)r0 * outw, false, n->I0, n->I1, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_forward");
+}
+
+int mmpc_mlp_loss_grad(mmpc_mlp* n, const float* X, const float* Z, int M, float* loss_out, void* stream)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    if (!X || !Z || M < 1 || M > n->cfg.max_batch) return fail(MMPC_ERR_INVALID_ARG, "bad loss_grad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int L = n->L;
+    forward_rows(n, X, M, n->Yb, true, nullptr, nullptr, st);
+    const size_t cnt = (size_t)M * n->cfg.width[L];
+    if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(float), st);
+    mse_kernel<<<grid_for(cnt), 256, 0, st>>>(n->Yb, Z, cnt, n->D0, loss_out);
+    float* D = n->D0;
+    float* Dn = n->D1;
+    const int splits = splits_for(n, M);
+    for (int i = L - 1; i >= 0; --i) {
+        const int K = n->cfg.width[i], N = n->cfg.width[i + 1];
+        const float* Hin = i == 0 ? X : n->H[i];
+        // dW[i] = H^T D: (K x M) (M x N), split over the M rows, reduced in order
+        gemm<float, true, false, EPI_PARTIAL>(K, N, M, splits, Hin, K, D, N, n->part, N, nullptr, nullptr, nullptr, st);
+        const int kchunk = ((M + splits - 1) / splits + BK - 1) / BK * BK;
+        const int z = (M + kchunk - 1) / kchunk;
+        reduce_partials_kernel<<<grid_for((size_t)K * N), 256, 0, st>>>(n->part, z, (size_t)K * N, n->gW[i]);
+        colsum_kernel<<<(N + 7) / 8, 256, 0, st>>>(D, M, N, n->gb[i]);
+        if (i > 0) {
+            // D_prev = (D W^T) * gelu'(P[i-1])
+            gemm<__nv_bfloat16, false, true, EPI_GELU_GRAD>(M, K, N, 1, D, N, n->W16[i], N, Dn, K, nullptr, nullptr,
+                                                            n->P[i - 1], st);
+            std::swap(D, Dn);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_loss_grad");
+}
+
+int mmpc_mlp_adamw(mmpc_mlp* n, float lr, void* stream)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    if (!std::isfinite(lr) || lr < 0.f) return fail(MMPC_ERR_INVALID_ARG, "bad learning rate");
+    cudaStream_t st = (cudaStream_t)stream;
+    n->step += 1;
+    const mmpc_mlp_config& c = n->cfg;
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)c.beta1, (double)n->step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)c.beta2, (double)n->step)));
+    for (int i = 0; i < n->L; ++i) {
+        const size_t wc = wcount(n, i), bc = c.width[i + 1];
+        adamw_kernel<<<grid_for(wc), 256, 0, st>>>(n->W[i], n->gW[i], n->mW[i], n->vW[i], n->W16[i], wc, lr, c.beta1,
+                                                   c.beta2, c.eps, c.weight_decay, c1, c2);
+        adamw_kernel<<<grid_for(bc), 256, 0, st>>>(n->b[i], n->gb[i], n->mb[i], n->vb[i], nullptr, bc, lr, c.beta1,
+                                                   c.beta2, c.eps, 0.f, c1, c2);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_adamw");
+}
+
+int mmpc_mlp_read(mmpc_mlp* n, int what, int layer, float* host, size_t count)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    if (layer < 0 || layer >= n->L || !host || what < 0 || what > 7) return fail(MMPC_ERR_INVALID_ARG, "bad read arguments");
+    const bool isw = what == 0 || what == 2 || what == 4 || what == 5;
+    const size_t want = isw ? wcount(n, layer) : (size_t)n->cfg.width[layer + 1];
+    if (count != want) return fail(MMPC_ERR_SHAPE, "count does not match the array size");
+    const float* src = what == 0 ? n->W[layer] : what == 1 ? n->b[layer] : what == 2 ? n->gW[layer]
+                     : what == 3 ? n->gb[layer] : what == 4 ? n->mW[layer] : what == 5 ? n->vW[layer]
+                     : what == 6 ? n->mb[layer] : n->vb[layer];
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, src, sizeof(float) * count, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_read");
+}
+
+int mmpc_mlp_write(mmpc_mlp* n, int what, int layer, const float* host, size_t count)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    if (layer < 0 || layer >= n->L || !host || (what != 0 && what != 1)) return fail(MMPC_ERR_INVALID_ARG, "bad write arguments");
+    const size_t want = what == 0 ? wcount(n, layer) : (size_t)n->cfg.width[layer + 1];
+    if (count != want) return fail(MMPC_ERR_SHAPE, "count does not match the array size");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(what == 0 ? n->W[layer] : n->b[layer], host, sizeof(float) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && what == 0) {
+        to_bf16_kernel<<<grid_for(count), 256>>>(n->W[layer], n->W16[layer], count);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_write");
+}
+
+void mmpc_mlp_destroy(mmpc_mlp* n)
+{
+    if (!n) return;
+    cudaDeviceSynchronize();
+    mlp_free(n);
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+"""Thin Python binding of the warm-start C ABI (include/mmpc_mlp.h).
+
+Argument marshalling only: torch CUDA tensors go to libmmpc.so as raw device
+pointers with the current CUDA stream; the features, the network's forward,
+backward and AdamW steps, and the encoding all run in the library's kernels.
+No fallback: a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import mmpc
+
+FEATURES = 64
+MAX_LAYERS = 8
+EXPORTED = ("mmpc_features", "mmpc_warm_decode", "mmpc_warm_encode", "mmpc_column_stats", "mmpc_gather_rows",
+            "mmpc_mlp_create", "mmpc_mlp_forward", "mmpc_mlp_loss_grad", "mmpc_mlp_adamw", "mmpc_mlp_read",
+            "mmpc_mlp_write", "mmpc_mlp_destroy", "mmpc_mlp_last_error")
+READ_W, READ_B, READ_DW, READ_DB, READ_MW, READ_VW, READ_MB, READ_VB = range(8)
+
+
+class WarmScene(ctypes.Structure):
+    _fields_ = [
+        ("ego", ctypes.c_void_p),
+        ("obst", ctypes.c_void_p),
+        ("m", ctypes.c_int),
+        ("goals", ctypes.c_void_p),
+        ("B", ctypes.c_int),
+        ("X", ctypes.c_void_p),
+        ("Y", ctypes.c_void_p),
+        ("coef", ctypes.c_void_p),
+        ("lam", ctypes.c_void_p),
+        ("Z", ctypes.c_void_p),
+    ]
+
+
+class MlpConfig(ctypes.Structure):
+    _fields_ = [
+        ("layers", ctypes.c_int),
+        ("width", ctypes.c_int * (MAX_LAYERS + 1)),
+        ("max_batch", ctypes.c_int),
+        ("beta1", ctypes.c_float),
+        ("beta2", ctypes.c_float),
+        ("eps", ctypes.c_float),
+        ("weight_decay", ctypes.c_float),
+    ]
+
+
+_bound = False
+
+
+def lib():
+    global _bound
+    L = mmpc.lib()
+    if _bound:
+        return L
+    vp, ip, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    L.mmpc_features.argtypes = [vp, ip, fp, fp, vp]
+    L.mmpc_warm_decode.argtypes = [vp, ip, ip, fp, vp, vp, vp]
+    L.mmpc_warm_encode.argtypes = [vp, ip, ip, fp, vp, vp, vp]
+    L.mmpc_column_stats.argtypes = [vp, ip, ip, vp, vp, vp]
+    L.mmpc_gather_rows.argtypes = [vp, ip, ip, vp, ip, vp, vp]
+    L.mmpc_mlp_create.argtypes = [ctypes.POINTER(MlpConfig), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.mmpc_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
+    L.mmpc_mlp_loss_grad.argtypes = [vp, vp, vp, ip, vp, vp]
+    L.mmpc_mlp_adamw.argtypes = [vp, fp, vp]
+    L.mmpc_mlp_read.argtypes = [vp, ip, ip, vp, ctypes.c_size_t]
+    L.mmpc_mlp_write.argtypes = [vp, ip, ip, vp, ctypes.c_size_t]
+    L.mmpc_mlp_destroy.argtypes = [vp]
+    L.mmpc_mlp_destroy.restype = None
+    L.mmpc_mlp_last_error.argtypes = []
+    L.mmpc_mlp_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("mmpc_mlp_destroy", "mmpc_mlp_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _bound = True
+    return L
+
+
+def _check(rc):
+    if rc != mmpc.MMPC_OK:
+        raise mmpc.MmpcError(rc, lib().mmpc_mlp_last_error().decode())
+
+
+_ptr = mmpc._ptr
+_stream = mmpc._stream
+
+
+class SceneTable:
+    """A device array of mmpc_warm_scene descriptors (kept alive with the
+    tensors it points to)."""
+
+    def __init__(self, rows: list, device):
+        import torch
+        self.rows = rows
+        arr = (WarmScene * max(1, len(rows)))(*[WarmScene(**r) for r in rows])
+        raw = np.frombuffer(bytes(arr), dtype=np.uint8)
+        self.dev = torch.from_numpy(raw.copy()).to(device)
+        self.S = len(rows)
+
+    @property
+    def ptr(self):
+        return ctypes.c_void_p(self.dev.data_ptr())
+
+
+def scene_row(ego=None, obst=None, goals=None, X=None, Y=None, coef=None, lam=None, Z=None):
+    """Descriptor fields from CUDA tensors (None -> NULL)."""
+    m = 0 if obst is None else int(obst.shape[0])
+    B = 0 if goals is None else int(goals.shape[0])
+    if goals is None:
+        for t in (X, Y, coef, lam, Z):
+            if t is not None:
+                B = int(t.shape[0])
+                break
+    p = lambda t: None if t is None else _ptr(t).value  # noqa: E731
+    return dict(ego=p(ego), obst=p(obst) if m else None, m=m, goals=p(goals), B=B, X=p(X), Y=p(Y), coef=p(coef),
+                lam=p(lam), Z=p(Z))
+
+
+def features(table: SceneTable, a: float, b: float, stream=None):
+    _check(lib().mmpc_features(table.ptr, table.S, float(a), float(b), _stream(stream)))
+
+
+def warm_decode(table: SceneTable, n: int, T: float, mu, sigma, stream=None):
+    _check(lib().mmpc_warm_decode(table.ptr, table.S, int(n), float(T), _ptr(mu), _ptr(sigma), _stream(stream)))
+
+
+def warm_encode(table: SceneTable, n: int, T: float, mu, sigma, stream=None):
+    _check(lib().mmpc_warm_encode(table.ptr, table.S, int(n), float(T), _ptr(mu), _ptr(sigma), _stream(stream)))
+
+
+def column_stats(X, mean_out, std_out, stream=None):
+    rows, cols = int(X.shape[0]), int(X.shape[1])
+    _check(lib().mmpc_column_stats(_ptr(X), rows, cols, _ptr(mean_out), _ptr(std_out), _stream(stream)))
+
+
+def gather_rows(src, idx, out, stream=None):
+    _check(lib().mmpc_gather_rows(_ptr(src), int(src.shape[0]), int(src.shape[1]), _ptr(idx, "int32"),
+                                  int(idx.shape[0]), _ptr(out), _stream(stream)))
+
+
+class Mlp:
+    """Owns one mmpc_mlp (weights, gradients, AdamW moments, activations)."""
+
+    def __init__(self, widths, Ws, bs, max_batch=4096, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4):
+        L = len(widths) - 1
+        cfg = MlpConfig()
+        cfg.layers = L
+        for i, w in enumerate(widths):
+            cfg.width[i] = int(w)
+        cfg.max_batch = int(max_batch)
+        cfg.beta1, cfg.beta2, cfg.eps, cfg.weight_decay = beta1, beta2, eps, weight_decay
+        self.widths = [int(w) for w in widths]
+        self._W = [np.ascontiguousarray(W, dtype=np.float32) for W in Ws]
+        self._b = [np.ascontiguousarray(b, dtype=np.float32) for b in bs]
+        for i, (W, b) in enumerate(zip(self._W, self._b)):
+            assert W.shape == (widths[i], widths[i + 1]) and b.shape == (widths[i + 1],)
+        Wp = (ctypes.c_void_p * L)(*[W.ctypes.data for W in self._W])
+        bp = (ctypes.c_void_p * L)(*[b.ctypes.data for b in self._b])
+        self.handle = ctypes.c_void_p()
+        _check(lib().mmpc_mlp_create(ctypes.byref(cfg), Wp, bp, ctypes.byref(self.handle)))
+        self.max_batch = int(max_batch)
+
+    def forward(self, X, Y, stream=None):
+        _check(lib().mmpc_mlp_forward(self.handle, _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)))
+
+    def loss_grad(self, X, Z, loss=None, stream=None):
+        _check(lib().mmpc_mlp_loss_grad(self.handle, _ptr(X), _ptr(Z), int(X.shape[0]), _ptr(loss), _stream(stream)))
+
+    def adamw(self, lr, stream=None):
+        _check(lib().mmpc_mlp_adamw(self.handle, float(lr), _stream(stream)))
+
+    def read(self, what, layer):
+        i, o = self.widths[layer], self.widths[layer + 1]
+        shape = (i, o) if what in (READ_W, READ_DW, READ_MW, READ_VW) else (o,)
+        out = np.zeros(shape, dtype=np.float32)
+        _check(lib().mmpc_mlp_read(self.handle, int(what), int(layer), ctypes.c_void_p(out.ctypes.data), out.size))
+        return out
+
+    def write(self, what, layer, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float32)
+        _check(lib().mmpc_mlp_write(self.handle, int(what), int(layer), ctypes.c_void_p(a.ctypes.data), a.size))
+
+    def weights(self):
+        L = len(self.widths) - 1
+        return [self.read(READ_W, i) for i in range(L)], [self.read(READ_B, i) for i in range(L)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mmpc_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

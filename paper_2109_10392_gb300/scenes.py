@@ -125,3 +125,19 @@ def scene_batch(seed: int, S: int = 256, B_range=(16, 512), m_range=(5, 40), N_c
         sub = int(rng.integers(0, 2**31 - 1))
         out.append(scene_custom(sub, B, m, N=N, n=n))
     return out
+
+
+WARM_WIDTHS = (64, 256, 256, 256, 72)  # warm-start network: features -> 3 x 256 -> 6n (n = 12)
+
+
+def mlp_init(seed: int, widths=WARM_WIDTHS):
+    """Seeded initial weights of an MLP (Glorot-uniform matrices [in, out],
+    zero biases), float32.  Random draws only; the network itself is in the
+    library."""
+    rng = np.random.default_rng(seed)
+    Ws, bs = [], []
+    for i, o in zip(widths[:-1], widths[1:]):
+        lim = np.sqrt(6.0 / (i + o))
+        Ws.append(rng.uniform(-lim, lim, (i, o)).astype(np.float32))
+        bs.append(np.zeros(o, dtype=np.float32))
+    return Ws, bs

@@ -16,15 +16,20 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "mmpc.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mmpc_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mmpc_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol():
+    from paper_2109_10392_gb300 import mlp
     L = mmpc.lib()
     names = _declared()
-    assert set(names) == set(mmpc.EXPORTED)
+    assert set(names) == set(mmpc.EXPORTED) | set(mlp.EXPORTED)
     for name in names:
         assert hasattr(L, name), name
     assert L.mmpc_version() == 1
@@ -123,3 +128,24 @@ def test_setup_rejects_bad_buffers():
     with pytest.raises(mmpc.MmpcError) as ei:
         mmpc.mmpc_setup(p, 5, bad)
     assert ei.value.code == mmpc.MMPC_ERR_INVALID_ARG
+
+
+def test_warm_start_calls_check_arguments_first():
+    from paper_2109_10392_gb300 import mlp
+    L = mlp.lib()
+    assert L.mmpc_features(None, -1, 5.6, 2.5, None) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_features(None, 0, 0.0, 2.5, None) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_warm_decode(None, 0, 3, 8.0, None, None, None) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_column_stats(None, 0, 1, None, None, None) == mmpc.MMPC_ERR_INVALID_ARG
+    cfg = mlp.MlpConfig()
+    cfg.layers = 0
+    out = ctypes.c_void_p()
+    W = (ctypes.c_void_p * 1)()
+    assert L.mmpc_mlp_create(ctypes.byref(cfg), W, W, ctypes.byref(out)) == mmpc.MMPC_ERR_INVALID_ARG
+    cfg.layers, cfg.width[0], cfg.width[1], cfg.max_batch = 1, 4, 2000, 8   # width above the limit
+    cfg.beta1, cfg.beta2, cfg.eps = 0.9, 0.999, 1e-8
+    assert L.mmpc_mlp_create(ctypes.byref(cfg), W, W, ctypes.byref(out)) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_mlp_forward(None, None, 0, None, None) == mmpc.MMPC_ERR_NOT_SETUP
+    assert L.mmpc_mlp_adamw(None, 1e-3, None) == mmpc.MMPC_ERR_NOT_SETUP
+    assert L.mmpc_mlp_last_error()
+    L.mmpc_mlp_destroy(None)

@@ -1,0 +1,231 @@
+"""The warm-start kernels (include/mmpc_mlp.h) against the FP64 oracle
+(oracle/mlp_oracle.py) on the same seeded inputs: feature rows (the nearest-
+obstacle order exactly, values to float32 rounding), encoding and decoding,
+the network's outputs, loss and gradients with the same bfloat16-rounded
+weights, and the AdamW update.  Tolerances follow from float32 accumulation
+over at most 256 terms (relative 1e-5 - 1e-4 of each array's scale)."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from paper_2109_10392_gb300 import mlp, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a, dtype=np.float32):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=dtype), device="cuda:0").contiguous()
+
+
+def _host(t):
+    return t.double().cpu().numpy()
+
+
+def _scene_rows(scs):
+    import torch
+    out, keep = [], []
+    for sc in scs:
+        ego, goals = _dev(sc.ego), _dev(sc.goals).reshape(-1, 3)
+        obst = _dev(sc.obst).reshape(-1, 4) if sc.obst.shape[0] else None
+        X = torch.zeros((goals.shape[0], 64), device="cuda:0")
+        out.append(mlp.scene_row(ego=ego, obst=obst, goals=goals, X=X))
+        keep.append((ego, obst, goals, X))
+    return out, keep
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def test_features_match_oracle():
+    import torch
+    scs = [scenes.scene_custom(1, 37, 50), scenes.scene_custom(2, 5, 3), scenes.scene_custom(3, 1, 0),
+           scenes.scene_custom(4, 0, 12), scenes.scene_custom(5, 9, 1024, x_range=(-500.0, 500.0))]
+    # a scene with exact ties and a duplicated obstacle
+    tie = scenes.scene_custom(6, 4, 6)
+    tie.obst[1] = tie.obst[0]
+    tie.obst[3, 0] = -tie.obst[2, 0]
+    tie.obst[3, 1] = tie.obst[2, 1]
+    scs.append(tie)
+    rows, keep = _scene_rows(scs)
+    table = mlp.SceneTable(rows, "cuda:0")
+    mlp.features(table, 5.6, 2.5)
+    torch.cuda.synchronize()
+    for sc, (_, _, _, X) in zip(scs, keep):
+        want = M.features(_f32(sc.ego), _f32(sc.obst), _f32(sc.goals), 5.6, 2.5)
+        got = _host(X)
+        assert got.shape == want.shape
+        if want.size:
+            # the slot order is an exact decision: x0 / 100 of every slot matches to rounding
+            assert np.allclose(got[:, 4:54:5], want[:, 4:54:5], rtol=1e-6, atol=1e-7)
+            assert np.allclose(got, want, rtol=1e-6, atol=1e-6)
+
+
+def test_encode_decode_match_oracle():
+    import torch
+    n, T = 12, 8.0
+    rng = np.random.default_rng(0)
+    egos = [np.array([1.75, 14.0, 0.0, 0.0]), np.array([-5.25, 19.5, 0.02, 0.3])]
+    Bs = [7, 3]
+    coefs = [rng.normal(size=(B, 3 * n)) * 10 for B in Bs]
+    lams = [rng.normal(size=(B, 3 * n)) for B in Bs]
+    mu = rng.normal(size=6 * n)
+    sigma = rng.uniform(0.5, 3.0, 6 * n)
+    rows, keep = [], []
+    for ego, c, l in zip(egos, coefs, lams):
+        t = dict(ego=_dev(ego), coef=_dev(c), lam=_dev(l), Z=torch.zeros((c.shape[0], 6 * n), device="cuda:0"))
+        keep.append(t)
+        rows.append(mlp.scene_row(**t))
+    table = mlp.SceneTable(rows, "cuda:0")
+    mlp.warm_encode(table, n, T, _dev(mu), _dev(sigma))
+    torch.cuda.synchronize()
+    for ego, c, l, t in zip(egos, coefs, lams, keep):
+        want = (M.encode(_f32(c), _f32(l), ego, T, n) - _f32(mu)) / _f32(sigma)
+        assert np.allclose(_host(t["Z"]), want, rtol=1e-5, atol=1e-5)
+    # decode the encoded rows back
+    rows2, keep2 = [], []
+    for ego, t in zip(egos, keep):
+        B = t["Z"].shape[0]
+        d = dict(ego=t["ego"], Y=t["Z"], coef=torch.zeros((B, 3 * n), device="cuda:0"),
+                 lam=torch.zeros((B, 3 * n), device="cuda:0"))
+        keep2.append(d)
+        rows2.append(mlp.scene_row(**d))
+    table2 = mlp.SceneTable(rows2, "cuda:0")
+    mlp.warm_decode(table2, n, T, _dev(mu), _dev(sigma))
+    torch.cuda.synchronize()
+    for ego, c, l, d, t in zip(egos, coefs, lams, keep2, keep):
+        wc, wl = M.decode(_host(t["Z"]) * _f32(sigma) + _f32(mu), ego, T, n)
+        assert np.allclose(_host(d["coef"]), wc, rtol=1e-5, atol=1e-4)
+        assert np.allclose(_host(d["lam"]), wl, rtol=1e-5, atol=1e-5)
+        assert np.allclose(_host(d["coef"]), c, rtol=1e-4, atol=1e-3)
+
+
+def _net(seed=0, max_batch=512):
+    Ws, bs = scenes.mlp_init(seed)
+    rng = np.random.default_rng(seed + 100)
+    bs = [rng.normal(0, 0.1, b.shape).astype(np.float32) for b in bs]
+    return Ws, bs, mlp.Mlp(scenes.WARM_WIDTHS, Ws, bs, max_batch=max_batch, weight_decay=1e-2)
+
+
+def test_forward_matches_oracle():
+    import torch
+    Ws, bs, net = _net(1)
+    rng = np.random.default_rng(2)
+    for M_rows in (1, 65, 300):
+        X = rng.normal(size=(M_rows, 64)).astype(np.float32)
+        Y = torch.zeros((M_rows, 72), device="cuda:0")
+        net.forward(_dev(X), Y)
+        torch.cuda.synchronize()
+        want, _ = M.forward(Ws, bs, X.astype(np.float64), bf16=True)
+        got = _host(Y)
+        scale = np.abs(want).max()
+        assert np.max(np.abs(got - want)) <= 2e-5 * scale, (M_rows, np.max(np.abs(got - want)), scale)
+    net.close()
+
+
+def test_gradients_match_oracle():
+    import torch
+    Ws, bs, net = _net(3)
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(203, 64)).astype(np.float32)
+    Z = rng.normal(size=(203, 72)).astype(np.float32)
+    loss = torch.zeros((1,), device="cuda:0")
+    net.loss_grad(_dev(X), _dev(Z), loss)
+    torch.cuda.synchronize()
+    L, gW, gb = M.loss_and_grads(Ws, bs, X.astype(np.float64), Z.astype(np.float64), bf16=True)
+    assert abs(float(loss.item()) - L) <= 1e-5 * L
+    for i in range(4):
+        dW, db = net.read(mlp.READ_DW, i), net.read(mlp.READ_DB, i)
+        sW, sb = np.abs(gW[i]).max(), np.abs(gb[i]).max()
+        assert np.max(np.abs(dW - gW[i])) <= 1e-4 * sW, (i, np.max(np.abs(dW - gW[i])), sW)
+        assert np.max(np.abs(db - gb[i])) <= 1e-4 * sb, (i, np.max(np.abs(db - gb[i])), sb)
+    net.close()
+
+
+def test_gradients_are_deterministic():
+    import torch
+    _, _, net = _net(5, max_batch=2048)
+    rng = np.random.default_rng(6)
+    X, Z = _dev(rng.normal(size=(2048, 64))), _dev(rng.normal(size=(2048, 72)))
+    net.loss_grad(X, Z)
+    a = [net.read(mlp.READ_DW, i) for i in range(4)]
+    net.loss_grad(X, Z)
+    torch.cuda.synchronize()
+    b = [net.read(mlp.READ_DW, i) for i in range(4)]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    net.close()
+
+
+def test_adamw_matches_oracle():
+    import torch
+    Ws, bs, net = _net(7)
+    rng = np.random.default_rng(8)
+    X, Z = _dev(rng.normal(size=(128, 64))), _dev(rng.normal(size=(128, 72)))
+    state = [(np.zeros_like(W, dtype=np.float64), np.zeros_like(W, dtype=np.float64),
+              np.zeros_like(b, dtype=np.float64), np.zeros_like(b, dtype=np.float64)) for W, b in zip(Ws, bs)]
+    w = [W.astype(np.float64) for W in Ws]
+    bb = [b.astype(np.float64) for b in bs]
+    lr, b1, b2, eps, wd = 1e-3, 0.9, 0.999, 1e-8, 1e-2
+    for step in (1, 2, 3):
+        net.loss_grad(X, Z)
+        gW = [net.read(mlp.READ_DW, i).astype(np.float64) for i in range(4)]
+        gB = [net.read(mlp.READ_DB, i).astype(np.float64) for i in range(4)]
+        net.adamw(lr)
+        torch.cuda.synchronize()
+        for i in range(4):
+            mW, vW, mb, vb = state[i]
+            w[i], mW, vW = M.adamw(w[i], gW[i], mW, vW, step, lr, b1, b2, eps, wd)
+            bb[i], mb, vb = M.adamw(bb[i], gB[i], mb, vb, step, lr, b1, b2, eps, 0.0)
+            state[i] = (mW, vW, mb, vb)
+            gotW, gotb = net.read(mlp.READ_W, i), net.read(mlp.READ_B, i)
+            assert np.max(np.abs(gotW - w[i])) <= 1e-6 + 1e-5 * lr, (step, i, np.max(np.abs(gotW - w[i])))
+            assert np.max(np.abs(gotb - bb[i])) <= 1e-6 + 1e-5 * lr
+            assert np.allclose(net.read(mlp.READ_MW, i), mW, rtol=1e-4, atol=1e-9)
+            assert np.allclose(net.read(mlp.READ_VW, i), vW, rtol=1e-4, atol=1e-12)
+    net.close()
+
+
+def test_training_fits_a_smooth_map():
+    """Behaviour: the kernels' training loop fits a smooth synthetic map."""
+    import torch
+    Ws, bs = scenes.mlp_init(9, (64, 128, 128, 8))
+    net = mlp.Mlp((64, 128, 128, 8), Ws, bs, max_batch=1024, weight_decay=0.0)
+    rng = np.random.default_rng(10)
+    A = rng.normal(size=(64, 8)) / 8
+    X = rng.normal(size=(1024, 64))
+    Z = np.tanh(X @ A) + 0.1 * (X[:, :8] ** 2)
+    Xd, Zd = _dev(X), _dev(Z)
+    loss = torch.zeros((1,), device="cuda:0")
+    first = None
+    for it in range(400):
+        net.loss_grad(Xd, Zd, loss)
+        if it == 0:
+            first = float(loss.item())
+        net.adamw(3e-3)
+    net.loss_grad(Xd, Zd, loss)
+    last = float(loss.item())
+    assert last < 0.05 * first, (first, last)
+    net.close()
+
+
+def test_column_stats_and_gather():
+    import torch
+    rng = np.random.default_rng(11)
+    X = rng.normal(3.0, 2.0, size=(1000, 7)).astype(np.float32)
+    X[:, 3] = 5.0  # constant column: deviation replaced by 1
+    mean, sd = torch.zeros(7, device="cuda:0"), torch.zeros(7, device="cuda:0")
+    mlp.column_stats(_dev(X), mean, sd)
+    idx = np.array([5, 0, 999, 5, -1, 1000], dtype=np.int32)
+    out = torch.zeros((6, 7), device="cuda:0")
+    mlp.gather_rows(_dev(X), _dev(idx, np.int32), out)
+    torch.cuda.synchronize()
+    X64 = X.astype(np.float64)
+    assert np.allclose(_host(mean), X64.mean(0), rtol=1e-6, atol=1e-6)
+    want_sd = X64.std(0)
+    want_sd[3] = 1.0
+    assert np.allclose(_host(sd), want_sd, rtol=1e-5)
+    got = _host(out)
+    assert np.array_equal(got[:4], X64[[5, 0, 999, 5]])
+    assert np.all(np.isnan(got[4:]))
