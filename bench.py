@@ -492,6 +492,78 @@ def run_batch(args):
     return out
 
 
+def run_warm(args):
+    """Learned warm start (trained here, on the GPU, by the library's kernels)
+    against the cold start on fresh scenes; one step = one CUDA graph replay
+    over all evaluation scenes (warm: features, network, decode, solve,
+    cold fallback of the misses, score)."""
+    import torch
+
+    from paper_2109_10392_gb300 import warmstart
+
+    rank, world, local = rank_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    cfg = warmstart.WarmConfig(train_scenes=args.warm_train_scenes, steps=args.warm_steps, seed=rank)
+    t0 = time.perf_counter()
+    X, T = warmstart.build_dataset(cfg, dev)
+    t1 = time.perf_counter()
+    ws, losses = warmstart.train(cfg, X, T, dev)
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    Xv, Tv = warmstart.build_dataset(cfg, dev, seed_offset=7_777_777, S=max(256, cfg.train_scenes // 50))
+    val = warmstart.validation_loss(ws, Xv, Tv)
+    train_rows = int(X.shape[0])
+    del X, T, Xv, Tv
+    S, B = args.warm_eval_scenes, 256
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    dense = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=args.steps, seed=10**6 + rank, plain=True)
+    clocks = sampler.stop()
+    sparse = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=max(3, args.steps // 2), seed=2 * 10**6 + rank,
+                                obstacles=10, x_range=(-30.0, 120.0))
+    ws.close()
+    wf = dense["warm_fallback"]
+    agg = combine_ranks(dict(units=S * B, ms=wf["ms"], e2e_units=S * B, e2e_ms=wf["ms"]), world, dist)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    p = cfg.params
+    N, n, m = p["N"], p["n"], cfg.obstacles
+    ops = alu_ops(N, n, wf["passes"], wf["passes"] * N * m)
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = ops / (wf["ms"] * 1e-3) / 1e12
+    out = {
+        "metric": METRIC, "value": agg["units"] / (agg["ms"] * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"highway_warm_S{S}_B{B}_m{m}_N{N}_n{n}_K100_tol{TOL:g}", "start": "learned warm start "
+                   "(lambda0 = Q c0) with cold fallback of the misses", "train_scenes": cfg.train_scenes,
+                   "train_rows": train_rows, "train_steps": cfg.steps, "network": list(cfg.widths),
+                   "graph": "one CUDA graph replay per step",
+                   "l2": "inputs and per-step outputs (1M trajectories) exceed L2"},
+        "roofline": {"bound": "alu", "kernel": "am_solve_batch_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": None,
+                     "ops_basis": "dense algorithmic ops of every AM pass run (warm passes + cold passes of the "
+                                  "fallback), over the whole graph step",
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz"},
+        "e2e": None,
+        "gpu_launches": 12 * args.steps,
+        "clocks": clocks,
+        "detail": {"dense_50_obstacles": dense, "sparse_10_obstacles": sparse, "val_loss": val,
+                   "loss_first_last": [losses[0][1], losses[-1][1]], "dataset_s": t1 - t0, "train_s": t2 - t1},
+    }
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
 def _oracle_run(sc, params, idx, threads):
     import oracle
     p = oracle.params(**params)
@@ -562,8 +634,12 @@ def main():
     ap.add_argument("--no-cull", action="store_true", help="evaluate every obstacle-sample pair (no culling)")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                     help="solve kernel: 1 one sample per thread, 2 two samples per thread, 0 automatic")
-    ap.add_argument("--workload", default="scene", choices=["scene", "batch"],
-                    help="scene: one 1024-goal scene per GPU; batch: 256 uneven scenes per GPU in one graph")
+    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "warm"],
+                    help="scene: one 1024-goal scene per GPU; batch: 256 uneven scenes per GPU in one graph; "
+                         "warm: learned warm start (trained in the run) against the cold start")
+    ap.add_argument("--warm-train-scenes", type=int, default=200_000)
+    ap.add_argument("--warm-steps", type=int, default=4000)
+    ap.add_argument("--warm-eval-scenes", type=int, default=4096)
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2, 3],
                     help="batch item order (0: autotuned)")
     args = ap.parse_args()
@@ -572,7 +648,7 @@ def main():
     if args.impl == "reference":
         out = run_reference(args)
     else:
-        out = run_batch(args) if args.workload == "batch" else run_mine(args)
+        out = {"batch": run_batch, "warm": run_warm}.get(args.workload, run_mine)(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

@@ -192,6 +192,8 @@ typedef struct {
     int* iters_out;      /* device int[B] or NULL */
     float* cost_out;     /* device float[B]: meta costs */
     int* argmin_out;     /* device int[1]: argmin as mmpc_score */
+    const float* warm_coef;  /* device float[B][3n] initial c, or NULL (cold start), as mmpc_solve */
+    const float* warm_lam;   /* device float[B][3n] initial lambda, or NULL (zero) */
 } mmpc_scene;
 
 typedef struct mmpc_batch mmpc_batch;
@@ -212,8 +214,21 @@ int mmpc_batch_set_schedule(mmpc_batch* b, int schedule);
  * keeps the fastest and writes it to *chosen (may be NULL).  Synchronous. */
 int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen);
 
-/* Solves and scores every scene of the batch on `stream` (asynchronous). */
+/* Solves and scores every scene of the batch on `stream` (asynchronous).
+ * With the fallback on, the trajectories of warm-started scenes whose
+ * convergence residual (largest of resid_out[0..2]) missed the scene's
+ * tol > 0 are solved again from the cold start, in a second persistent
+ * launch over a list built on the device, before scoring; their outputs
+ * (coef, lam, resid, iters) are those of the cold solve. */
 int mmpc_batch_run(mmpc_batch* b, void* stream);
+
+/* Fallback to the cold start (see mmpc_batch_run) on (on != 0) or off
+ * (the default).  Needs resid_out of the warm-started scenes. */
+int mmpc_batch_set_fallback(mmpc_batch* b, int on);
+
+/* After a run (synchronises the device): the number of trajectories the
+ * last run solved again from the cold start. */
+int mmpc_batch_fallbacks(mmpc_batch* b, int* count);
 
 /* After a run (synchronises the device): each scene's completion time in ms
  * since the run's first CTA started (host float[S], may be NULL), and the

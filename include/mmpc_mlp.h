@@ -59,23 +59,33 @@ typedef struct {
  * Errors: MMPC_ERR_INVALID_ARG (NULL, S < 0, a or b <= 0), MMPC_ERR_CUDA. */
 int mmpc_features(const mmpc_warm_scene* scenes, int S, float a, float b, void* stream);
 
-/* Network outputs -> warm start (uses ego, B, Y, coef, lam): with
- * t = Y sigma + mu per column (mu, sigma: device float[6n]),
+/* Network outputs -> warm start (uses ego, B, Y, coef, lam).  The outputs
+ * are 3n (coefficients only) or 6n (coefficients and multipliers) per row;
+ * with t = Y sigma + mu per column (mu, sigma: device float[outputs]),
  *   c_x = t[0:n] + v0 lin,  c_y = t[n:2n] + y0,  c_psi = t[2n:3n],
- *   lambda = t[3n:6n],  lin_k = T k / (n - 1)  (the coefficients of f(t) = t).
- * n in [MMPC_MIN_COEF, MMPC_MAX_COEF].  Errors as mmpc_features. */
-int mmpc_warm_decode(const mmpc_warm_scene* scenes, int S, int n, float T, const float* mu,
-                     const float* sigma, void* stream);
+ *   lin_k = T k / (n - 1)  (the coefficients of f(t) = t),
+ * and lambda = t[3n:6n] (6n outputs), else per axis lambda = Q c when Q
+ * (device float[n][n], the Q = Pdd^T Pdd of mmpc_build) is given, else 0.
+ * lambda = Q c are the multipliers of a fixed point of Algorithm 1: there
+ * F c = g, and the step (split_xy) leaves c unchanged iff K11 (lambda - Q c)
+ * = 0.  lam may be NULL.  n in [MMPC_MIN_COEF, MMPC_MAX_COEF].  Errors as
+ * mmpc_features. */
+int mmpc_warm_decode(const mmpc_warm_scene* scenes, int S, int n, float T, int outputs, const float* mu,
+                     const float* sigma, const float* Q, void* stream);
 
 /* The inverse (uses ego, B, coef, lam, Z): Z = (t - mu) / sigma with t the
- * encoding above.  With mu = 0 and sigma = 1 it writes the raw t. */
-int mmpc_warm_encode(const mmpc_warm_scene* scenes, int S, int n, float T, const float* mu,
+ * encoding above (3n or 6n columns).  With mu = 0 and sigma = 1 it writes
+ * the raw t. */
+int mmpc_warm_encode(const mmpc_warm_scene* scenes, int S, int n, float T, int outputs, const float* mu,
                      const float* sigma, void* stream);
 
 /* Column means and standard deviations (population) of a device matrix
  * X [rows][cols], in two passes in float64: mean_out, std_out device
  * float[cols]; a zero deviation is replaced by 1.  rows >= 1. */
 int mmpc_column_stats(const float* X, int rows, int cols, float* mean_out, float* std_out, void* stream);
+
+/* out[r][c] = (X[r][c] - mean[c]) / sd[c] (device arrays; out may be X). */
+int mmpc_standardize(const float* X, int rows, int cols, const float* mean, const float* sd, float* out, void* stream);
 
 /* out[r] = src[idx[r]] for rows of `cols` floats (device idx int[rows]).
  * Indices are checked against src_rows on the device; a bad index writes a

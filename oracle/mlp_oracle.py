@@ -117,23 +117,37 @@ def lin(T, n):
     return T * np.arange(n) / (n - 1)
 
 
-def encode(coef, lam, ego, T, n):
-    """Targets [B, 6n] from a solution: (c_x - v0 lin, c_y - y0, c_psi,
-    lambda_x, lambda_y, lambda_psi)."""
+def encode(coef, lam, ego, T, n, outputs=None):
+    """Targets [B, outputs] from a solution: (c_x - v0 lin, c_y - y0, c_psi)
+    and, for outputs = 6n, (lambda_x, lambda_y, lambda_psi)."""
+    outputs = 6 * n if outputs is None else outputs
     coef = np.asarray(coef, dtype=np.float64).reshape(-1, 3 * n)
-    lam = np.asarray(lam, dtype=np.float64).reshape(-1, 3 * n)
-    t = np.concatenate([coef, lam], axis=1).copy()
+    t = coef.copy()
+    if outputs == 6 * n:
+        t = np.concatenate([t, np.asarray(lam, dtype=np.float64).reshape(-1, 3 * n)], axis=1)
     t[:, :n] -= ego[1] * lin(T, n)
     t[:, n:2 * n] -= ego[0]
     return t
 
 
-def decode(t, ego, T, n):
-    """Inverse of `encode`: (coef [B, 3n], lam [B, 3n])."""
-    t = np.asarray(t, dtype=np.float64).reshape(-1, 6 * n).copy()
+def decode(t, ego, T, n, Q=None):
+    """Inverse of `encode`: (coef [B, 3n], lam [B, 3n]).  With 3n outputs
+    the multipliers are not predicted: lambda = Q c per axis when Q is given
+    (the multipliers of a fixed point of the iteration, whose constraint
+    residual F c - g vanishes, up to components in the row space of the
+    boundary rows), else 0."""
+    t = np.asarray(t, dtype=np.float64)
+    t = t.reshape(t.shape[0] if t.ndim > 1 else 1, -1).copy()
     t[:, :n] += ego[1] * lin(T, n)
     t[:, n:2 * n] += ego[0]
-    return t[:, :3 * n], t[:, 3 * n:]
+    coef = t[:, :3 * n]
+    if t.shape[1] == 6 * n:
+        return coef, t[:, 3 * n:]
+    if Q is None:
+        return coef, np.zeros_like(coef)
+    Q = np.asarray(Q, dtype=np.float64)
+    lam = np.concatenate([coef[:, a * n:(a + 1) * n] @ Q.T for a in range(3)], axis=1)
+    return coef, lam
 
 
 # ---------------------------------------------------------------------------

@@ -124,30 +124,53 @@ __device__ __forceinline__ float enc_shift(int k, int n, float T, float y0, floa
     return 0.f;
 }
 
-__global__ void decode_kernel(const mmpc_warm_scene* __restrict__ sc, int S, int n, float T,
-                              const float* __restrict__ mu, const float* __restrict__ sigma)
+// Thread per (row, axis): the axis' n coefficients from the outputs, then its
+// multipliers -- predicted (6n outputs), Q c (3n outputs and Q given), or 0.
+__global__ void decode_kernel(const mmpc_warm_scene* __restrict__ sc, int S, int n, float T, int outputs,
+                              const float* __restrict__ mu, const float* __restrict__ sigma,
+                              const float* __restrict__ Q)
 {
     const int s = blockIdx.x;
     if (s >= S) return;
+    __shared__ float q[MMPC_MAX_COEF * MMPC_MAX_COEF];
+    if (Q)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) q[e] = Q[e];
+    __syncthreads();
     const mmpc_warm_scene d = sc[s];
     const float y0 = d.ego[0], v0 = d.ego[1];
-    const int W = 6 * n, B = max(d.B, 0);
-    for (int e = threadIdx.x; e < B * W; e += blockDim.x) {
-        const int r = e / W, k = e % W;
-        const float t = fmaf(d.Y[e], sigma[k], mu[k]);
-        if (k < 3 * n) d.coef[(size_t)r * 3 * n + k] = t + enc_shift(k, n, T, y0, v0);
-        else d.lam[(size_t)r * 3 * n + (k - 3 * n)] = t;
+    const int W = outputs, B = max(d.B, 0);
+    for (int u = threadIdx.x; u < 3 * B; u += blockDim.x) {
+        const int r = u / 3, ax = u % 3;
+        const float* y = d.Y + (size_t)r * W;
+        float c[MMPC_MAX_COEF];
+        for (int k = 0; k < n; ++k) {
+            const int col = ax * n + k;
+            c[k] = fmaf(y[col], sigma[col], mu[col]) + enc_shift(col, n, T, y0, v0);
+            d.coef[(size_t)r * 3 * n + col] = c[k];
+        }
+        if (!d.lam) continue;
+        float* lo = d.lam + (size_t)r * 3 * n + ax * n;
+        for (int k = 0; k < n; ++k) {
+            float v = 0.f;
+            if (W == 6 * n) {
+                const int col = 3 * n + ax * n + k;
+                v = fmaf(y[col], sigma[col], mu[col]);
+            } else if (Q) {
+                for (int j = 0; j < n; ++j) v = fmaf(q[k * n + j], c[j], v);
+            }
+            lo[k] = v;
+        }
     }
 }
 
-__global__ void encode_kernel(const mmpc_warm_scene* __restrict__ sc, int S, int n, float T,
+__global__ void encode_kernel(const mmpc_warm_scene* __restrict__ sc, int S, int n, float T, int outputs,
                               const float* __restrict__ mu, const float* __restrict__ sigma)
 {
     const int s = blockIdx.x;
     if (s >= S) return;
     const mmpc_warm_scene d = sc[s];
     const float y0 = d.ego[0], v0 = d.ego[1];
-    const int W = 6 * n, B = max(d.B, 0);
+    const int W = outputs, B = max(d.B, 0);
     for (int e = threadIdx.x; e < B * W; e += blockDim.x) {
         const int r = e / W, k = e % W;
         const float t = k < 3 * n ? d.coef[(size_t)r * 3 * n + k] - enc_shift(k, n, T, y0, v0)
@@ -190,6 +213,16 @@ __global__ void __launch_bounds__(256) column_stats_kernel(const float* __restri
         const double sd = sqrt(part[0] / rows);
         mean_out[c] = (float)mean;
         std_out[c] = sd > 0.0 ? (float)sd : 1.f;
+    }
+}
+
+__global__ void standardize_kernel(const float* __restrict__ X, int rows, int cols, const float* __restrict__ mean,
+                                   const float* __restrict__ sd, float* __restrict__ out)
+{
+    const size_t total = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % cols);
+        out[e] = (X[e] - mean[c]) / sd[c];
     }
 }
 
@@ -469,28 +502,28 @@ int mmpc_features(const mmpc_warm_scene* scenes, int S, float a, float b, void* 
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "features_kernel");
 }
 
-int mmpc_warm_decode(const mmpc_warm_scene* scenes, int S, int n, float T, const float* mu, const float* sigma,
-                     void* stream)
+int mmpc_warm_decode(const mmpc_warm_scene* scenes, int S, int n, float T, int outputs, const float* mu,
+                     const float* sigma, const float* Q, void* stream)
 {
     int rc = check_scenes(scenes, S);
     if (rc) return rc;
-    if (n < MMPC_MIN_COEF || n > MMPC_MAX_COEF || !(T > 0.f) || !mu || !sigma)
-        return fail(MMPC_ERR_INVALID_ARG, "bad n, T or NULL mu / sigma");
+    if (n < MMPC_MIN_COEF || n > MMPC_MAX_COEF || !(T > 0.f) || !mu || !sigma || (outputs != 3 * n && outputs != 6 * n))
+        return fail(MMPC_ERR_INVALID_ARG, "bad n, T, outputs or NULL mu / sigma");
     if (S == 0) return MMPC_OK;
-    decode_kernel<<<S, 256, 0, (cudaStream_t)stream>>>(scenes, S, n, T, mu, sigma);
+    decode_kernel<<<S, 256, 0, (cudaStream_t)stream>>>(scenes, S, n, T, outputs, mu, sigma, Q);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "decode_kernel");
 }
 
-int mmpc_warm_encode(const mmpc_warm_scene* scenes, int S, int n, float T, const float* mu, const float* sigma,
-                     void* stream)
+int mmpc_warm_encode(const mmpc_warm_scene* scenes, int S, int n, float T, int outputs, const float* mu,
+                     const float* sigma, void* stream)
 {
     int rc = check_scenes(scenes, S);
     if (rc) return rc;
-    if (n < MMPC_MIN_COEF || n > MMPC_MAX_COEF || !(T > 0.f) || !mu || !sigma)
-        return fail(MMPC_ERR_INVALID_ARG, "bad n, T or NULL mu / sigma");
+    if (n < MMPC_MIN_COEF || n > MMPC_MAX_COEF || !(T > 0.f) || !mu || !sigma || (outputs != 3 * n && outputs != 6 * n))
+        return fail(MMPC_ERR_INVALID_ARG, "bad n, T, outputs or NULL mu / sigma");
     if (S == 0) return MMPC_OK;
-    encode_kernel<<<S, 256, 0, (cudaStream_t)stream>>>(scenes, S, n, T, mu, sigma);
+    encode_kernel<<<S, 256, 0, (cudaStream_t)stream>>>(scenes, S, n, T, outputs, mu, sigma);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "encode_kernel");
 }
@@ -501,6 +534,15 @@ int mmpc_column_stats(const float* X, int rows, int cols, float* mean_out, float
     column_stats_kernel<<<cols, 256, 0, (cudaStream_t)stream>>>(X, rows, cols, mean_out, std_out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "column_stats_kernel");
+}
+
+int mmpc_standardize(const float* X, int rows, int cols, const float* mean, const float* sd, float* out, void* stream)
+{
+    if (!X || !mean || !sd || !out || rows < 0 || cols < 1) return fail(MMPC_ERR_INVALID_ARG, "bad standardize arguments");
+    if (rows == 0) return MMPC_OK;
+    standardize_kernel<<<grid_for((size_t)rows * cols), 256, 0, (cudaStream_t)stream>>>(X, rows, cols, mean, sd, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "standardize_kernel");
 }
 
 int mmpc_gather_rows(const float* src, int src_rows, int cols, const int* idx, int rows, float* out, void* stream)

@@ -1469,10 +1469,11 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 template <int NC, int MAXT>
 __global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value)
-    am_solve_batch_kernel(const SolveArgs* __restrict__ scenes, const int2* __restrict__ items, int total,
-                          unsigned long long* scratch)
+    am_solve_batch_kernel(const SolveArgs* __restrict__ scenes, const int2* __restrict__ items,
+                          const int* __restrict__ total_ptr, unsigned long long* scratch)
 {
     __shared__ int s_item;
+    const int total = *total_ptr;  // written by an earlier launch on the stream
     for (;;) {
         __syncthreads();  // the previous item is finished by every thread
         if (threadIdx.x == 0) {
@@ -1508,10 +1509,33 @@ __global__ void __launch_bounds__(256) score_batch_kernel(const ScoreArgs* __res
     }
 }
 
-__global__ void batch_reset_kernel(unsigned long long* scratch, int S)
+__global__ void batch_reset_kernel(unsigned long long* scratch, int S, int* fb_count)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 + 2 * S; i += gridDim.x * blockDim.x)
         scratch[i] = (i == 1 || i >= 2 + S) ? ~0ull : 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *fb_count = 0;
+}
+
+// Fallback of warm-started trajectories: every item of a scene with a warm
+// start whose convergence residual (the largest of the obstacle,
+// acceleration and non-holonomic residuals) missed the scene's tol > 0, or is
+// NaN, goes to the fallback list, to be solved again from the cold start.
+// The list order depends on timing; each trajectory's solve does not.  Also
+// rewinds the work queue for the next persistent launch.
+__global__ void fallback_compact_kernel(const SolveArgs* __restrict__ warm, const int2* __restrict__ items, int total,
+                                        int2* __restrict__ fb_items, int* __restrict__ fb_count,
+                                        unsigned long long* scratch)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) scratch[0] = 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int2 sl = items[i];
+        const SolveArgs& A = warm[sl.x];
+        if (!A.warm_c || !A.resid_out || !(A.tol > 0.f)) continue;
+        const float* r = A.resid_out + (size_t)sl.y * 4;
+        const float conv = fmaxf(fmaxf(r[0], r[1]), r[2]);
+        const bool nan = isnan(r[0]) || isnan(r[1]) || isnan(r[2]);
+        if (nan || !(conv <= A.tol)) fb_items[atomicAdd(fb_count, 1)] = sl;
+    }
 }
 
 __global__ void batch_finish_kernel(const ScoreArgs* __restrict__ sc, int S, const unsigned long long* keys)
@@ -1994,8 +2018,13 @@ struct mmpc_batch {
     std::vector<mmpc::SolveArgs> args;
     std::vector<mmpc::ScoreArgs> sargs;
     mmpc::SolveArgs* d_args = nullptr;
+    mmpc::SolveArgs* d_args_cold = nullptr;  // the same with the warm starts removed (fallback)
     mmpc::ScoreArgs* d_sargs = nullptr;
     int2* d_items = nullptr;
+    int2* d_fb_items = nullptr;               // fallback list
+    int* d_counts = nullptr;                  // [0] items, [1] fallback items
+    bool fallback = false;
+    bool any_warm = false;
     unsigned long long* d_scratch = nullptr;  // [2 + 2S], laid out as the batch kernels describe
 };
 
@@ -2011,8 +2040,11 @@ void batch_free(mmpc_batch* b)
 {
     if (!b) return;
     cudaFree(b->d_args);
+    cudaFree(b->d_args_cold);
     cudaFree(b->d_sargs);
     cudaFree(b->d_items);
+    cudaFree(b->d_fb_items);
+    cudaFree(b->d_counts);
     cudaFree(b->d_scratch);
     delete b;
 }
@@ -2117,7 +2149,8 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         a.v_min = (float)p.v_min; a.v_max = (float)p.v_max; a.a_max = (float)p.a_max; a.tol = p.tol;
         a.L = c->L;
         a.blob = c->d_blob;
-        a.ego = sc.ego; a.obst = sc.obst; a.goals = sc.goals; a.warm_c = nullptr; a.warm_l = nullptr;
+        a.ego = sc.ego; a.obst = sc.obst; a.goals = sc.goals; a.warm_c = sc.warm_coef; a.warm_l = sc.warm_lam;
+        if (sc.warm_coef) b->any_warm = true;
         a.coef_out = sc.coef_out; a.lam_out = sc.lam_out; a.resid_out = sc.resid_out; a.iters_out = sc.iters_out;
         a.err_flag = reinterpret_cast<unsigned*>(c->d_scratch + 1) + 1;
         a.work = c->d_scratch + 2;  // counted per scene, read with mmpc_take_work_count
@@ -2128,11 +2161,21 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         g.L = c->L; g.blob = c->d_blob; g.coef = sc.coef_out; g.cost_out = sc.cost_out; g.argmin_out = sc.argmin_out;
     }
     const size_t nscratch = 2 + 2 * (size_t)S;
+    std::vector<SolveArgs> cold(b->args);
+    for (auto& a : cold) { a.warm_c = nullptr; a.warm_l = nullptr; }
     e = cudaMalloc(&b->d_args, sizeof(SolveArgs) * S);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_args_cold, sizeof(SolveArgs) * S);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_sargs, sizeof(ScoreArgs) * S);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * std::max(1, b->total));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_fb_items, sizeof(int2) * std::max(1, b->total));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_scratch, sizeof(unsigned long long) * nscratch);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_args, b->args.data(), sizeof(SolveArgs) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_args_cold, cold.data(), sizeof(SolveArgs) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const int counts[2] = {b->total, 0};
+        e = cudaMemcpy(b->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_sargs, b->sargs.data(), sizeof(ScoreArgs) * S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_scratch, 0, sizeof(unsigned long long) * nscratch);
     if (e != cudaSuccess) {
@@ -2161,11 +2204,17 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
     using namespace mmpc;
     if (!b) return batch_fail("mmpc_batch_run: NULL batch", MMPC_ERR_NOT_SETUP);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    batch_reset_kernel<<<1, 256, 0, st>>>(b->d_scratch, b->S);
+    batch_reset_kernel<<<1, 256, 0, st>>>(b->d_scratch, b->S, b->d_counts + 1);
     if (b->total > 0) {
-        using KernT = void (*)(const SolveArgs*, const int2*, int, unsigned long long*);
-        reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args, b->d_items, b->total,
+        using KernT = void (*)(const SolveArgs*, const int2*, const int*, unsigned long long*);
+        reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args, b->d_items, b->d_counts,
                                                                             b->d_scratch);
+        if (b->fallback && b->any_warm) {
+            fallback_compact_kernel<<<std::min(1024, (b->total + 255) / 256), 256, 0, st>>>(
+                b->d_args, b->d_items, b->total, b->d_fb_items, b->d_counts + 1, b->d_scratch);
+            reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args_cold, b->d_fb_items,
+                                                                                b->d_counts + 1, b->d_scratch);
+        }
         const int wpb = 8;
         const int sgrid = (b->total + wpb - 1) / wpb;
         if (b->NC == 12) score_batch_kernel<12><<<sgrid, 32 * wpb, 0, st>>>(b->d_sargs, b->d_items, b->total, b->d_scratch + 2 + b->S);
@@ -2225,6 +2274,21 @@ extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
     rc = mmpc_batch_set_schedule(b, best);
     if (chosen) *chosen = best;
     return rc;
+}
+
+extern "C" int mmpc_batch_set_fallback(mmpc_batch* b, int on)
+{
+    if (!b) return batch_fail("mmpc_batch_set_fallback: NULL batch", MMPC_ERR_NOT_SETUP);
+    b->fallback = on != 0;
+    return MMPC_OK;
+}
+
+extern "C" int mmpc_batch_fallbacks(mmpc_batch* b, int* count)
+{
+    if (!b || !count) return batch_fail("mmpc_batch_fallbacks: NULL argument", b ? MMPC_ERR_INVALID_ARG : MMPC_ERR_NOT_SETUP);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(count, b->d_counts + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MMPC_OK : batch_fail(std::string("mmpc_batch_fallbacks: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
 }
 
 extern "C" void mmpc_batch_destroy(mmpc_batch* b)

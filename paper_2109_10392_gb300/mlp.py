@@ -16,6 +16,7 @@ from . import mmpc
 FEATURES = 64
 MAX_LAYERS = 8
 EXPORTED = ("mmpc_features", "mmpc_warm_decode", "mmpc_warm_encode", "mmpc_column_stats", "mmpc_gather_rows",
+            "mmpc_standardize",
             "mmpc_mlp_create", "mmpc_mlp_forward", "mmpc_mlp_loss_grad", "mmpc_mlp_adamw", "mmpc_mlp_read",
             "mmpc_mlp_write", "mmpc_mlp_destroy", "mmpc_mlp_last_error")
 READ_W, READ_B, READ_DW, READ_DB, READ_MW, READ_VW, READ_MB, READ_VB = range(8)
@@ -58,10 +59,11 @@ def lib():
         return L
     vp, ip, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
     L.mmpc_features.argtypes = [vp, ip, fp, fp, vp]
-    L.mmpc_warm_decode.argtypes = [vp, ip, ip, fp, vp, vp, vp]
-    L.mmpc_warm_encode.argtypes = [vp, ip, ip, fp, vp, vp, vp]
+    L.mmpc_warm_decode.argtypes = [vp, ip, ip, fp, ip, vp, vp, vp, vp]
+    L.mmpc_warm_encode.argtypes = [vp, ip, ip, fp, ip, vp, vp, vp]
     L.mmpc_column_stats.argtypes = [vp, ip, ip, vp, vp, vp]
     L.mmpc_gather_rows.argtypes = [vp, ip, ip, vp, ip, vp, vp]
+    L.mmpc_standardize.argtypes = [vp, ip, ip, vp, vp, vp, vp]
     L.mmpc_mlp_create.argtypes = [ctypes.POINTER(MlpConfig), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.mmpc_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
     L.mmpc_mlp_loss_grad.argtypes = [vp, vp, vp, ip, vp, vp]
@@ -105,6 +107,31 @@ class SceneTable:
         return ctypes.c_void_p(self.dev.data_ptr())
 
 
+def uniform_table(device, ego=None, obst=None, goals=None, X=None, Y=None, coef=None, lam=None, Z=None, S=None):
+    """A SceneTable of S scenes of one shape from stacked tensors: ego [S, 4],
+    obst [S, m, 4], goals [S, B, 3], X [S, B, 64], Y / Z [S, B, 6n],
+    coef / lam [S, B, 3n] (any may be None)."""
+    ts = [t for t in (goals, X, Y, coef, lam, Z) if t is not None]
+    S = int(ts[0].shape[0]) if S is None else S
+    B = int(ts[0].shape[1])
+    m = 0 if obst is None else int(obst.shape[1])
+    arr = np.zeros(max(1, S), dtype=mmpc.ctypes_dtype(WarmScene))
+    i = np.arange(S, dtype=np.uint64)
+    for name, t in (("ego", ego), ("obst", obst), ("goals", goals), ("X", X), ("Y", Y), ("coef", coef), ("lam", lam),
+                    ("Z", Z)):
+        if t is None or (name == "obst" and m == 0):
+            continue
+        _ptr(t)
+        arr[name][:S] = np.uint64(t.data_ptr()) + i * np.uint64(t[0].numel() * 4)
+    arr["m"][:S] = m
+    arr["B"][:S] = B
+    tab = SceneTable([], device)
+    import torch
+    tab.dev = torch.from_numpy(np.frombuffer(arr.tobytes(), dtype=np.uint8).copy()).to(device)
+    tab.S = S
+    return tab
+
+
 def scene_row(ego=None, obst=None, goals=None, X=None, Y=None, coef=None, lam=None, Z=None):
     """Descriptor fields from CUDA tensors (None -> NULL)."""
     m = 0 if obst is None else int(obst.shape[0])
@@ -123,17 +150,26 @@ def features(table: SceneTable, a: float, b: float, stream=None):
     _check(lib().mmpc_features(table.ptr, table.S, float(a), float(b), _stream(stream)))
 
 
-def warm_decode(table: SceneTable, n: int, T: float, mu, sigma, stream=None):
-    _check(lib().mmpc_warm_decode(table.ptr, table.S, int(n), float(T), _ptr(mu), _ptr(sigma), _stream(stream)))
+def warm_decode(table: SceneTable, n: int, T: float, mu, sigma, Q=None, stream=None):
+    """outputs = mu.numel() (3n or 6n); Q: device float32 [n, n] or None."""
+    _check(lib().mmpc_warm_decode(table.ptr, table.S, int(n), float(T), int(mu.numel()), _ptr(mu), _ptr(sigma),
+                                  _ptr(Q), _stream(stream)))
 
 
 def warm_encode(table: SceneTable, n: int, T: float, mu, sigma, stream=None):
-    _check(lib().mmpc_warm_encode(table.ptr, table.S, int(n), float(T), _ptr(mu), _ptr(sigma), _stream(stream)))
+    """outputs = mu.numel() (3n or 6n)."""
+    _check(lib().mmpc_warm_encode(table.ptr, table.S, int(n), float(T), int(mu.numel()), _ptr(mu), _ptr(sigma),
+                                  _stream(stream)))
 
 
 def column_stats(X, mean_out, std_out, stream=None):
     rows, cols = int(X.shape[0]), int(X.shape[1])
     _check(lib().mmpc_column_stats(_ptr(X), rows, cols, _ptr(mean_out), _ptr(std_out), _stream(stream)))
+
+
+def standardize(X, mean, sd, out, stream=None):
+    _check(lib().mmpc_standardize(_ptr(X), int(X.shape[0]), int(X.shape[1]), _ptr(mean), _ptr(sd), _ptr(out),
+                                  _stream(stream)))
 
 
 def gather_rows(src, idx, out, stream=None):

@@ -30,7 +30,7 @@ MMPC_META_ABS = 2
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
             "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
             "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
-            "mmpc_batch_destroy")
+            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_fallbacks")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
 
@@ -77,6 +77,8 @@ class MmpcScene(ctypes.Structure):
         ("iters_out", ctypes.c_void_p),
         ("cost_out", ctypes.c_void_p),
         ("argmin_out", ctypes.c_void_p),
+        ("warm_coef", ctypes.c_void_p),
+        ("warm_lam", ctypes.c_void_p),
     ]
 
 
@@ -134,6 +136,10 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_batch_times.restype = ctypes.c_int
     L.mmpc_batch_destroy.argtypes = [vp]
     L.mmpc_batch_destroy.restype = None
+    L.mmpc_batch_set_fallback.argtypes = [vp, ctypes.c_int]
+    L.mmpc_batch_set_fallback.restype = ctypes.c_int
+    L.mmpc_batch_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.mmpc_batch_fallbacks.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -298,58 +304,142 @@ class Solver:
         return cost, am
 
 
+def ctypes_dtype(cstruct) -> np.dtype:
+    """numpy structured dtype with the field offsets of a ctypes structure
+    (pointer fields as uint64), for building descriptor arrays vectorised."""
+    names, formats, offsets = [], [], []
+    for name, typ in cstruct._fields_:
+        names.append(name)
+        offsets.append(getattr(cstruct, name).offset)
+        formats.append(np.int32 if typ is ctypes.c_int else np.float32 if typ is ctypes.c_float else np.uint64)
+    return np.dtype(dict(names=names, formats=formats, offsets=offsets, itemsize=ctypes.sizeof(cstruct)))
+
+
+def _params_key(params: dict, m: int):
+    return (tuple(sorted((k, float(v)) for k, v in params.items())), int(m))
+
+
 class Batch:
     """Many scenes solved and scored together (mmpc_batch_*): one persistent
     solve launch over all (scene, trajectory) items, one scoring launch, a
     per-scene argmin.  `scenes` is a list of dicts with keys params (dict),
-    ego, obst (CUDA float32 tensors, obst [m, 4] or None) and goals ([B, 3]).
-    The outputs are allocated here once, as flat tensors over all scenes
-    (`flat`) with per-scene views (`out`); `run` only enqueues kernels, so it
-    can be captured in a CUDA graph.  All scenes must have n <= 12, or all
-    n > 12."""
+    ego, obst (CUDA float32 tensors, obst [m, 4] or None), goals ([B, 3]) and
+    optionally warm_coef, warm_lam ([B, 3n]).  Scenes with equal parameters
+    and obstacle counts share one context.  The outputs are allocated here
+    once, as flat tensors over all scenes (`flat`) with per-scene views
+    (`out`); `run` only enqueues kernels, so it can be captured in a CUDA
+    graph.  All scenes must have n <= 12, or all n > 12."""
 
-    def __init__(self, scenes: list, meta: dict | MmpcMeta, want_lam: bool = False):
+    def __init__(self, scenes: list, meta: dict | MmpcMeta, want_lam: bool = False, _desc=None, _solvers=None,
+                 _flat=None, _offsets=None):
         import torch
         self.meta = meta if isinstance(meta, MmpcMeta) else make_meta(**meta)
-        self.solvers, self.inputs, self.out = [], [], []
-        self.S = len(scenes)
         self.handle = None
-        dev = scenes[0]["goals"].device if scenes else torch.device("cuda:0")
-        Bs = [int(sc["goals"].shape[0]) for sc in scenes]
-        ns = [int(sc["params"]["n"]) for sc in scenes]
-        tot_c = sum(3 * b * n for b, n in zip(Bs, ns))
-        tot_b = sum(Bs)
-        z = lambda k, dt=torch.float32: torch.zeros((k,), dtype=dt, device=dev)  # noqa: E731
-        self.flat = dict(coef=z(tot_c), lam=z(tot_c) if want_lam else None, resid=z(4 * tot_b),
-                         iters=z(tot_b, torch.int32), cost=z(tot_b), argmin=z(max(1, self.S), torch.int32))
-        self.offsets = []
-        desc = (MmpcScene * max(1, self.S))()
-        oc = ob = 0
-        for i, sc in enumerate(scenes):
-            obst = sc["obst"]
-            m = 0 if obst is None else int(obst.shape[0])
-            sv = Solver(sc["params"], m)
-            self.solvers.append(sv)
-            B, n = Bs[i], ns[i]
-            F = self.flat
-            o = dict(coef=F["coef"][oc:oc + 3 * n * B].view(B, 3 * n),
-                     lam=None if F["lam"] is None else F["lam"][oc:oc + 3 * n * B].view(B, 3 * n),
-                     resid=F["resid"][4 * ob:4 * (ob + B)].view(B, 4), iters=F["iters"][ob:ob + B],
-                     cost=F["cost"][ob:ob + B], argmin=F["argmin"][i:i + 1])
-            self.offsets.append((oc, ob))
-            oc += 3 * n * B
-            ob += B
-            desc[i] = MmpcScene(sv.ctx, _ptr(sc["ego"]), _ptr(obst) if m else None, _ptr(sc["goals"]), B,
-                                _ptr(o["coef"]), _ptr(o["lam"]), _ptr(o["resid"]), _ptr(o["iters"], "int32"),
-                                _ptr(o["cost"]), _ptr(o["argmin"], "int32"))
-            self.inputs.append(sc)
-            self.out.append(o)
+        if _desc is not None:  # prepared by from_uniform
+            self.solvers, self.inputs, self.out, self.flat, self.offsets = _solvers, scenes, [], _flat, _offsets
+            self.S = len(_offsets)
+            desc = _desc
+        else:
+            self.solvers, self.inputs, self.out = [], [], []
+            self.S = len(scenes)
+            cache = {}
+            dev = scenes[0]["goals"].device if scenes else torch.device("cuda:0")
+            Bs = [int(sc["goals"].shape[0]) for sc in scenes]
+            ns = [int(sc["params"]["n"]) for sc in scenes]
+            tot_c = sum(3 * b * n for b, n in zip(Bs, ns))
+            tot_b = sum(Bs)
+            z = lambda k, dt=torch.float32: torch.zeros((k,), dtype=dt, device=dev)  # noqa: E731
+            self.flat = dict(coef=z(tot_c), lam=z(tot_c) if want_lam else None, resid=z(4 * tot_b),
+                             iters=z(tot_b, torch.int32), cost=z(tot_b), argmin=z(max(1, self.S), torch.int32))
+            self.offsets = []
+            desc = (MmpcScene * max(1, self.S))()
+            oc = ob = 0
+            for i, sc in enumerate(scenes):
+                obst = sc["obst"]
+                m = 0 if obst is None else int(obst.shape[0])
+                key = _params_key(sc["params"], m)
+                if key not in cache:
+                    cache[key] = Solver(sc["params"], m)
+                    self.solvers.append(cache[key])
+                sv = cache[key]
+                B, n = Bs[i], ns[i]
+                F = self.flat
+                o = dict(coef=F["coef"][oc:oc + 3 * n * B].view(B, 3 * n),
+                         lam=None if F["lam"] is None else F["lam"][oc:oc + 3 * n * B].view(B, 3 * n),
+                         resid=F["resid"][4 * ob:4 * (ob + B)].view(B, 4), iters=F["iters"][ob:ob + B],
+                         cost=F["cost"][ob:ob + B], argmin=F["argmin"][i:i + 1])
+                self.offsets.append((oc, ob))
+                oc += 3 * n * B
+                ob += B
+                desc[i] = MmpcScene(sv.ctx, _ptr(sc["ego"]), _ptr(obst) if m else None, _ptr(sc["goals"]), B,
+                                    _ptr(o["coef"]), _ptr(o["lam"]), _ptr(o["resid"]), _ptr(o["iters"], "int32"),
+                                    _ptr(o["cost"]), _ptr(o["argmin"], "int32"), _ptr(sc.get("warm_coef")),
+                                    _ptr(sc.get("warm_lam")))
+                self.inputs.append(sc)
+                self.out.append(o)
         self.handle = ctypes.c_void_p()
         rc = lib().mmpc_batch_create(desc, self.S, ctypes.byref(self.meta), ctypes.byref(self.handle))
         if rc != MMPC_OK:
             self.handle = None
             self.close()
             _err(None, rc)
+
+    @classmethod
+    def from_uniform(cls, params: dict, ego, obst, goals, meta, warm_coef=None, warm_lam=None, want_lam=False):
+        """S scenes of one shape sharing one context, from stacked device
+        tensors ego [S, 4], obst [S, m, 4], goals [S, B, 3] (warm [S, B, 3n]).
+        Outputs in `flat` (coef [S B, 3n], resid [S B, 4], ...), scene-major."""
+        import torch
+        S, B = int(goals.shape[0]), int(goals.shape[1])
+        m = int(obst.shape[1]) if obst is not None else 0
+        sv = Solver(params, m)
+        n = sv.n
+        dev = goals.device
+        z = lambda *shape, dt=torch.float32: torch.zeros(shape, dtype=dt, device=dev)  # noqa: E731
+        flat = dict(coef=z(S * B, 3 * n), lam=z(S * B, 3 * n) if want_lam else None, resid=z(S * B, 4),
+                    iters=z(S * B, dt=torch.int32), cost=z(S * B), argmin=z(max(1, S), dt=torch.int32))
+        for t in (ego, obst, goals, warm_coef, warm_lam):
+            if t is not None:
+                _ptr(t)  # type / contiguity checks
+        arr = np.zeros(max(1, S), dtype=ctypes_dtype(MmpcScene))
+        i = np.arange(S, dtype=np.uint64)
+        base = lambda t: np.uint64(t.data_ptr())  # noqa: E731
+        arr["ctx"][:S] = sv.ctx.value
+        arr["ego"][:S] = base(ego) + i * np.uint64(16)
+        if m:
+            arr["obst"][:S] = base(obst) + i * np.uint64(m * 16)
+        arr["goals"][:S] = base(goals) + i * np.uint64(B * 12)
+        arr["B"][:S] = B
+        row = np.uint64(B * 3 * n * 4)
+        arr["coef_out"][:S] = base(flat["coef"]) + i * row
+        if want_lam:
+            arr["lam_out"][:S] = base(flat["lam"]) + i * row
+        arr["resid_out"][:S] = base(flat["resid"]) + i * np.uint64(B * 16)
+        arr["iters_out"][:S] = base(flat["iters"]) + i * np.uint64(B * 4)
+        arr["cost_out"][:S] = base(flat["cost"]) + i * np.uint64(B * 4)
+        arr["argmin_out"][:S] = base(flat["argmin"]) + i * np.uint64(4)
+        if warm_coef is not None:
+            arr["warm_coef"][:S] = base(warm_coef) + i * row
+        if warm_lam is not None:
+            arr["warm_lam"][:S] = base(warm_lam) + i * row
+        desc = (MmpcScene * max(1, S)).from_buffer_copy(arr.tobytes())
+        offsets = [(i * B * 3 * n, i * B) for i in range(S)]
+        keep = dict(ego=ego, obst=obst, goals=goals, warm_coef=warm_coef, warm_lam=warm_lam)
+        out = cls(keep, meta, want_lam, _desc=desc, _solvers=[sv], _flat=flat, _offsets=offsets)
+        out.S = S
+        return out
+
+    def set_fallback(self, on: bool) -> None:
+        rc = lib().mmpc_batch_set_fallback(self.handle, 1 if on else 0)
+        if rc != MMPC_OK:
+            _err(None, rc)
+
+    def fallbacks(self) -> int:
+        c = ctypes.c_int(0)
+        rc = lib().mmpc_batch_fallbacks(self.handle, ctypes.byref(c))
+        if rc != MMPC_OK:
+            _err(None, rc)
+        return int(c.value)
 
     def set_schedule(self, schedule: int) -> None:
         rc = lib().mmpc_batch_set_schedule(self.handle, int(schedule))

@@ -141,3 +141,40 @@ def mlp_init(seed: int, widths=WARM_WIDTHS):
         Ws.append(rng.uniform(-lim, lim, (i, o)).astype(np.float32))
         bs.append(np.zeros(o, dtype=np.float32))
     return Ws, bs
+
+
+def scene_stack(seed: int, S: int, B: int, m: int = 50, x_range=(-50.0, 250.0), goals: str = "random",
+                clearance: float = 1.2):
+    """S scenes of one shape as stacked float64 arrays (ego [S, 4], obst
+    [S, m, 4], goals [S, B, 3]), drawn like `scene_custom` but vectorised:
+    ego on a random lane centre with v0 ~ U(10, 20); obstacles on random lanes
+    with x ~ U(x_range), vx ~ U(5, 20), redrawn while closer to the ego than
+    `clearance` (ellipse-normalised, t = 0).  Goals: "random" draws lateral
+    offsets from the 8 offsets linspace(-5.25, 5.25, 8) and speeds ~ U(5, 30);
+    "grid" crosses the 8 offsets with B / 8 speeds ~ U(5, 30).  Zero terminal
+    acceleration."""
+    rng = np.random.default_rng(seed)
+    a, b = BASE_PARAMS["a"], BASE_PARAMS["b"]
+    ego = np.zeros((S, 4))
+    ego[:, 0] = LANES[rng.integers(0, 4, S)]
+    ego[:, 1] = rng.uniform(10.0, 20.0, S)
+    obst = np.zeros((S, m, 4))
+    obst[:, :, 0] = rng.uniform(x_range[0], x_range[1], (S, m))
+    obst[:, :, 1] = LANES[rng.integers(0, 4, (S, m))]
+    obst[:, :, 2] = rng.uniform(5.0, 20.0, (S, m))
+    for _ in range(1000):
+        bad = np.hypot(obst[:, :, 0] / a, (obst[:, :, 1] - ego[:, None, 0]) / b) < clearance
+        k = int(bad.sum())
+        if k == 0:
+            break
+        obst[:, :, 0][bad] = rng.uniform(x_range[0], x_range[1], k)
+        obst[:, :, 1][bad] = LANES[rng.integers(0, 4, k)]
+    offsets = np.linspace(-5.25, 5.25, 8)
+    g = np.zeros((S, B, 3))
+    if goals == "grid":
+        assert B % 8 == 0
+        g[:, :, 0] = np.tile(offsets, (S, B // 8))
+    else:
+        g[:, :, 0] = offsets[rng.integers(0, 8, (S, B))]
+    g[:, :, 1] = rng.uniform(5.0, 30.0, (S, B))
+    return ego, obst, g

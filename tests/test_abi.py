@@ -135,7 +135,8 @@ def test_warm_start_calls_check_arguments_first():
     L = mlp.lib()
     assert L.mmpc_features(None, -1, 5.6, 2.5, None) == mmpc.MMPC_ERR_INVALID_ARG
     assert L.mmpc_features(None, 0, 0.0, 2.5, None) == mmpc.MMPC_ERR_INVALID_ARG
-    assert L.mmpc_warm_decode(None, 0, 3, 8.0, None, None, None) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_warm_decode(None, 0, 3, 8.0, 9, None, None, None, None) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_warm_encode(None, 0, 12, 8.0, 37, None, None, None) == mmpc.MMPC_ERR_INVALID_ARG
     assert L.mmpc_column_stats(None, 0, 1, None, None, None) == mmpc.MMPC_ERR_INVALID_ARG
     cfg = mlp.MlpConfig()
     cfg.layers = 0

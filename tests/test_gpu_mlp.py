@@ -92,7 +92,7 @@ def test_encode_decode_match_oracle():
         keep2.append(d)
         rows2.append(mlp.scene_row(**d))
     table2 = mlp.SceneTable(rows2, "cuda:0")
-    mlp.warm_decode(table2, n, T, _dev(mu), _dev(sigma))
+    mlp.warm_decode(table2, n, T, _dev(mu), _dev(sigma))  # 6n outputs: multipliers predicted
     torch.cuda.synchronize()
     for ego, c, l, d, t in zip(egos, coefs, lams, keep2, keep):
         wc, wl = M.decode(_host(t["Z"]) * _f32(sigma) + _f32(mu), ego, T, n)
@@ -229,3 +229,26 @@ def test_column_stats_and_gather():
     got = _host(out)
     assert np.array_equal(got[:4], X64[[5, 0, 999, 5]])
     assert np.all(np.isnan(got[4:]))
+
+
+def test_decode_coefficients_only_with_consistent_multipliers(orc):
+    """3n outputs: the multipliers are Q c per axis (or 0 without Q)."""
+    import torch
+    n, T = 12, 8.0
+    p = dict(scenes.BASE_PARAMS)
+    Q = orc.matrices(orc.params(**p), 0)["Q"]
+    rng = np.random.default_rng(3)
+    ego = np.array([1.75, 12.5, 0.0, 0.0])
+    Y = rng.normal(size=(9, 3 * n))
+    mu, sigma = rng.normal(size=3 * n), rng.uniform(0.5, 2.0, 3 * n)
+    for use_q in (True, False):
+        d = dict(ego=_dev(ego), Y=_dev(Y), coef=torch.zeros((9, 3 * n), device="cuda:0"),
+                 lam=torch.full((9, 3 * n), 7.0, device="cuda:0"))
+        table = mlp.SceneTable([mlp.scene_row(**d)], "cuda:0")
+        mlp.warm_decode(table, n, T, _dev(mu), _dev(sigma), Q=_dev(Q) if use_q else None)
+        torch.cuda.synchronize()
+        t = _f32(Y) * _f32(sigma) + _f32(mu)
+        wc, wl = M.decode(t, ego, T, n, Q=_f32(Q) if use_q else None)
+        assert np.allclose(_host(d["coef"]), wc, rtol=1e-5, atol=1e-4)
+        scale = max(1.0, np.abs(wl).max())
+        assert np.max(np.abs(_host(d["lam"]) - wl)) <= 1e-5 * scale

@@ -159,3 +159,27 @@ def test_loss_is_mean_square(bf16):
     y, _ = M.forward(Ws, bs, X, bf16)
     L, _, _ = M.loss_and_grads(Ws, bs, X, y + 0.5, bf16)
     assert abs(L - 0.25) < 1e-14
+
+
+def test_consistent_multipliers_of_a_straight_run_vanish(orc):
+    """lambda = Q c with Q = Pdd^T Pdd: a constant-speed, constant-lane run has
+    zero second derivative, so its multipliers are 0; and Q c equals
+    Pdd^T (Pdd c) computed from the basis directly."""
+    from paper_2109_10392_gb300 import scenes
+    p = dict(scenes.BASE_PARAMS)
+    n, T = p["n"], p["T"]
+    Mx = orc.matrices(orc.params(**p), 0)
+    Q, Pdd = Mx["Q"], Mx["Pdd"]
+    ego = np.array([-1.75, 16.0, 0.0, 0.0])
+    c, lam = M.decode(np.zeros((1, 3 * n)), ego, T, n, Q=Q)
+    assert np.max(np.abs(lam)) < 1e-9 * np.abs(Q).max() * 16.0 * T
+    rng = np.random.default_rng(1)
+    t = rng.normal(size=(4, 3 * n))
+    c, lam = M.decode(t, ego, T, n, Q=Q)
+    for a in range(3):
+        want = (Pdd @ c[:, a * n:(a + 1) * n].T).T @ Pdd
+        assert np.allclose(lam[:, a * n:(a + 1) * n], want, rtol=1e-10, atol=1e-8)
+    c0, lam0 = M.decode(t, ego, T, n)
+    assert np.array_equal(c0, c) and np.all(lam0 == 0.0)
+    assert M.encode(c, lam, ego, T, n, outputs=3 * n).shape == (4, 3 * n)
+    assert np.allclose(M.encode(c, lam, ego, T, n, outputs=3 * n), t)
