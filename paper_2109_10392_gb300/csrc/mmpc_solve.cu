@@ -61,8 +61,11 @@ void set_global_error(const std::string& msg) { g_error = msg; }
 //                whole warps (rows of samples >= N and every k >= n are zero,
 //                so padded lanes contribute exact zeros); tP [NPT][2] times
 //   common:      brow [6][NC] (P, Pd, Pdd at t = 0 and t = T); lin [NC]; Q,
-//                K11 (x hi, x lo, y hi, y lo), K11_psi [NC][NC]; K12_psi
+//                K11 (x hi, x lo, y hi, y lo), K11_psi [NC][NC]; then the
+//                blocks used only by the first step (from `init`): K12_psi
 //                [NC][4]; K12_x, K12_y, C0_x, C0_y [NC][8]; C0_psi [NC][4]
+// The pair kernel stages [pair rows | common up to init] and reads the
+// first-step blocks from global memory.
 //   sample rows: P, Pd, Pdd [NST][NC]; t [NST], NST = N rounded up to whole
 //                warps (zero rows beyond N)
 // ---------------------------------------------------------------------------
@@ -70,7 +73,7 @@ struct BlobLayout {
     int PP, PdP, PddP, tP;                                                        // pair rows
     int brow, lin, Q, Kxh, Kxl, Kyh, Kyl, Kp11, Kp12, K12x, K12y, C0x, C0y, C0p;  // common
     int P, Pd, Pdd, t;                                                            // sample rows
-    int common, rows1, total;  // region starts (common, sample rows) and end
+    int common, init, rows1, total;  // region starts (common, first-step blocks, sample rows) and end
 };
 
 static BlobLayout blob_layout(int N, int NC)
@@ -95,6 +98,7 @@ static BlobLayout blob_layout(int N, int NC)
     B.Kyh = o; o += NC * NC;
     B.Kyl = o; o += NC * NC;
     B.Kp11 = o; o += NC * NC;
+    B.init = o;
     B.Kp12 = o; o += NC * 4;
     B.K12x = o; o += NC * 8;
     B.K12y = o; o += NC * 8;
@@ -614,12 +618,13 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     constexpr int VD = SolveSmem<NC>::VD;
     constexpr int RSD = SolveSmem<NC>::RSD;
     constexpr int RSB = SolveSmem<NC>::RSB;
+    constexpr int WARPS = MAXT / 32;
     extern __shared__ __align__(16) float smem[];
     // per-warp copies of the coefficient vectors, duplicated: (c_k, c_k)
-    __shared__ __align__(16) float s_cxd[MAX_WARPS][2 * NC];
-    __shared__ __align__(16) float s_cyd[MAX_WARPS][2 * NC];
-    __shared__ __align__(16) float s_cpd[MAX_WARPS][2 * NC];
-    __shared__ __align__(16) float s_vec[MAX_WARPS][2][2 * NC];  // per-warp scratch vectors (x, y)
+    __shared__ __align__(16) float s_cxd[WARPS][2 * NC];
+    __shared__ __align__(16) float s_cyd[WARPS][2 * NC];
+    __shared__ __align__(16) float s_cpd[WARPS][2 * NC];
+    __shared__ __align__(16) float s_vec[WARPS][2][2 * NC];  // per-warp scratch vectors (x, y)
     __shared__ __align__(8) unsigned long long s_mbar;
 
     const int tid = threadIdx.x;
@@ -632,10 +637,10 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     const BlobLayout& L = A.L;
 
     float* blob = smem;
-    float4* obs = reinterpret_cast<float4*>(smem + L.rows1);
+    float4* obs = reinterpret_cast<float4*>(smem + L.init);
     float* red1 = reinterpret_cast<float*>(obs + 2 * m);   // [warp][RSB]: P^T theta
-    float* red2 = red1 + MAX_WARPS * RSB;                   // [warp][RSD]: F^T (F c - g), ...
-    int* olist = reinterpret_cast<int*>(red2 + MAX_WARPS * RSD) + warp * m;  // this warp's active obstacles
+    float* red2 = red1 + WARPS * RSB;                       // [warp][RSD]: F^T (F c - g), ...
+    int* olist = reinterpret_cast<int*>(red2 + WARPS * RSD) + warp * m;  // this warp's active obstacles
     float* cxd = s_cxd[warp];
     float* cyd = s_cyd[warp];
     float* cpd = s_cpd[warp];
@@ -650,7 +655,8 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         obs[2 * j] = make_float4(px, px, pvx, pvx);
         obs[2 * j + 1] = make_float4(py, py, pvy, pvy);
     }
-    if (!stage_blob(blob, A.blob, L.rows1 * 4, &s_mbar, A.err_flag)) return false;
+    if (!stage_blob(blob, A.blob, L.init * 4, &s_mbar, A.err_flag)) return false;
+    const float* __restrict__ gblob = A.blob;  // first-step blocks: read once, from global memory
 
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
@@ -691,7 +697,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             c = act && k < A.n ? __ldg(A.warm_c + (size_t)l * 3 * A.n + (isy ? A.n : 0) + k) : 0.f;
             if (!isy && act && k < A.n) c -= v0 * blob[L.lin + k];
         } else {
-            const float* C0 = blob + (isy ? L.C0y : L.C0x) + kk * 8;
+            const float* C0 = gblob + (isy ? L.C0y : L.C0x) + kk * 8;
             float sacc = 0.f;
 #pragma unroll
             for (int r = 0; r < 6; ++r)
@@ -705,7 +711,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         {
             // boundary rows: x uses (P0, Pd0, Pdd0, PdT, PddT), y (P0, Pd0, Pdd0, PT, PdT, PddT)
             const int rx[6] = {0, 1, 2, 4, 5, 5};
-            const float* K12 = blob + (isy ? L.K12y : L.K12x) + kk * 8;
+            const float* K12 = gblob + (isy ? L.K12y : L.K12x) + kk * 8;
 #pragma unroll
             for (int r = 0; r < 6; ++r) {
                 const int row = isy ? r : rx[r];
@@ -719,7 +725,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             if (!act) corr = 0.f;
         }
         {
-            const float* Kp12 = blob + L.Kp12 + kk * 4;
+            const float* Kp12 = gblob + L.Kp12 + kk * 4;
             float sacc = 0.f;
 #pragma unroll
             for (int r = 0; r < 4; ++r) sacc = fmaf(Kp12[r], bp[r], sacc);
@@ -730,7 +736,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             if (A.warm_c) {
                 cp0 = k < A.n ? __ldg(A.warm_c + (size_t)l * 3 * A.n + 2 * A.n + k) : 0.f;
             } else {
-                const float* C0 = blob + L.C0p + kk * 4;
+                const float* C0 = gblob + L.C0p + kk * 4;
 #pragma unroll
                 for (int r = 0; r < 4; ++r) cp0 = fmaf(C0[r], bp[r], cp0);
             }
@@ -1611,6 +1617,20 @@ struct LaunchShape {
     size_t smem;
 };
 
+// Launch bound (template MAXT) of the pair kernel for a block of `threads`.
+int pair_maxt(int threads) { return threads <= 64 ? 64 : (threads <= 128 ? 128 : 256); }
+
+// Dynamic shared memory of the pair kernel body: the staged rows and common
+// block (`staged` floats), the obstacles, the partial-sum rows of every warp
+// of the launch bound, and the culling lists of the block's warps.
+size_t pair_smem(int staged, int m, int NC, int threads)
+{
+    const int RSD = NC == 12 ? SolveSmem<12>::RSD : SolveSmem<16>::RSD;
+    const int warps = pair_maxt(threads) / 32;
+    return sizeof(float) * (size_t)staged + 32 * (size_t)m + sizeof(float) * (size_t)warps * (NC + RSD) +
+           sizeof(int) * (size_t)(threads / 32) * m;
+}
+
 LaunchShape shape_for(const mmpc_ctx* ctx, int variant, int m)
 {
     const int N = ctx->p.N;
@@ -1626,7 +1646,7 @@ LaunchShape shape_for(const mmpc_ctx* ctx, int variant, int m)
     } else {
         const int NP = (N + 1) / 2;
         s.threads = 32 * ((NP + 31) / 32);
-        s.smem = sizeof(float) * (size_t)ctx->L.rows1 + 32 * (size_t)m + red + sizeof(int) * (size_t)(s.threads / 32) * m;
+        s.smem = pair_smem(ctx->L.init, m, ctx->NC, s.threads);
         s.kern = ctx->NC == 12 ? pair_kernel<12>(s.threads) : pair_kernel<16>(s.threads);
     }
     return s;
@@ -2108,13 +2128,11 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         b->total += sc.B;
         max_m = std::max(max_m, c->m);
         maxN = std::max(maxN, c->p.N);
-        maxRows = std::max(maxRows, c->L.rows1);
+        maxRows = std::max(maxRows, c->L.init);
     }
     const int NP = (maxN + 1) / 2;
     b->threads = 32 * ((NP + 31) / 32);
-    const int RSD = b->NC == 12 ? SolveSmem<12>::RSD : SolveSmem<16>::RSD;
-    b->smem = sizeof(float) * (size_t)maxRows + 32 * (size_t)max_m + sizeof(float) * (size_t)MAX_WARPS * (b->NC + RSD) +
-              sizeof(int) * (size_t)(b->threads / 32) * max_m;
+    b->smem = pair_smem(maxRows, max_m, b->NC, b->threads);
     if (b->smem > 227 * 1024) { batch_free(b); return batch_fail("mmpc_batch_create: scenes do not fit in shared memory", MMPC_ERR_SHAPE); }
     if (b->NC == 12) {
         b->kern = b->threads <= 64 ? (void*)am_solve_batch_kernel<12, 64>
