@@ -50,9 +50,11 @@ SM_MAX_MHZ = 2070.0
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
-def workload(seed: int):
+def workload(seed: int, kind: str = "scene"):
+    """scene: the 1024-goal, 50-obstacle scene (N = 100, n = 12); precision:
+    16384 goals, 30 obstacles, N = 200, n = 16 (the same distribution)."""
     from paper_2109_10392_gb300 import scenes
-    sc = scenes.scene_large(seed)
+    sc = scenes.scene_large(seed) if kind == "scene" else scenes.scene_custom(31 + seed, 16384, 30, N=200, n=16)
     params = dict(sc.params)
     params.update(tol=TOL, check_every=CHECK_EVERY)
     return sc, params
@@ -169,7 +171,7 @@ def run_mine(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    sc, params = workload(seed=rank)
+    sc, params = workload(seed=rank, kind=args.workload)
     params["cull"] = 0 if args.no_cull else 1
     params["variant"] = args.variant
     B, m, n = len(sc.goals), sc.obst.shape[0], params["n"]
@@ -306,7 +308,7 @@ def run_mine(args):
                    "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)},
     }
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sc, params, sample_stride=4)
+        out["cpu_baseline"] = cpu_baseline(sc, params, sample_stride=max(4, B // 256))
     solver.close()
     if dist is not None:
         dist.destroy_process_group()
@@ -521,6 +523,7 @@ def run_warm(args):
     train_rows = int(X.shape[0])
     del X, T, Xv, Tv
     S, B = args.warm_eval_scenes, 256
+    fwd = warmstart.time_forward(ws, S * B, dev)
     sampler = ClockSampler(dev.index or 0)
     sampler.start()
     dense = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=args.steps, seed=10**6 + rank, plain=True)
@@ -557,6 +560,7 @@ def run_warm(args):
         "gpu_launches": 12 * args.steps,
         "clocks": clocks,
         "detail": {"dense_50_obstacles": dense, "sparse_10_obstacles": sparse, "val_loss": val,
+                   "network_forward": fwd,
                    "loss_first_last": [losses[0][1], losses[-1][1]], "dataset_s": t1 - t0, "train_s": t2 - t1},
     }
     if dist is not None:
@@ -634,9 +638,10 @@ def main():
     ap.add_argument("--no-cull", action="store_true", help="evaluate every obstacle-sample pair (no culling)")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                     help="solve kernel: 1 one sample per thread, 2 two samples per thread, 0 automatic")
-    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "warm"],
+    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "warm", "precision"],
                     help="scene: one 1024-goal scene per GPU; batch: 256 uneven scenes per GPU in one graph; "
-                         "warm: learned warm start (trained in the run) against the cold start")
+                         "warm: learned warm start (trained in the run) against the cold start; precision: "
+                         "one 16384-goal scene, 30 obstacles, N = 200, n = 16")
     ap.add_argument("--warm-train-scenes", type=int, default=200_000)
     ap.add_argument("--warm-steps", type=int, default=4000)
     ap.add_argument("--warm-eval-scenes", type=int, default=4096)

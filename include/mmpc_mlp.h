@@ -133,6 +133,18 @@ int mmpc_mlp_adamw(mmpc_mlp* net, float lr, void* stream);
 int mmpc_mlp_read(mmpc_mlp* net, int what, int layer, float* host, size_t count);
 int mmpc_mlp_write(mmpc_mlp* net, int what, int layer, const float* host, size_t count);
 
+/* Inference (mmpc_mlp_forward) on the tensor cores (on != 0) or the FP32
+ * SIMT path (0, the default).  The tensor-core path runs each layer as a
+ * tcgen05 GEMM with bfloat16 operands and float32 accumulation in tensor
+ * memory: each layer's input (the features, then every hidden activation) is
+ * rounded to bfloat16 (nearest even) as it is staged, where the SIMT path
+ * keeps it in float32.  Training always uses the SIMT kernels. */
+int mmpc_mlp_set_tensor_cores(mmpc_mlp* net, int on);
+
+/* Synchronises the device and reports MMPC_ERR_TIMEOUT if a bounded wait of
+ * a tensor-core kernel expired since the network was created. */
+int mmpc_mlp_status(mmpc_mlp* net);
+
 void mmpc_mlp_destroy(mmpc_mlp* net);
 const char* mmpc_mlp_last_error(void);
 

@@ -168,15 +168,19 @@ def gelu_grad(x):
     return 0.5 * (1.0 + _erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
 
 
-def forward(Ws, bs, X, bf16=True):
+def forward(Ws, bs, X, bf16=True, act_bf16=False):
     """Ws[i] [in, out] (float32 master weights), bs[i] [out].  Returns the
-    outputs and the cache (inputs of each layer, pre-activations)."""
+    outputs and the cache (inputs of each layer, pre-activations).  With
+    act_bf16 every layer's input (the features, then each hidden activation,
+    held as float32) is rounded to bfloat16 before its product, as the
+    tensor-core path stages it."""
     h = np.asarray(X, dtype=np.float64)
     acts, pres = [h], []
     L = len(Ws)
     for i, (W, b) in enumerate(zip(Ws, bs)):
         Wq = bf16_round(W) if bf16 else np.asarray(W, dtype=np.float64)
-        z = h @ Wq + np.asarray(b, dtype=np.float64)
+        hin = bf16_round(h.astype(np.float32)) if act_bf16 else h
+        z = hin @ Wq + np.asarray(b, dtype=np.float64)
         pres.append(z)
         h = gelu(z) if i < L - 1 else z
         if i < L - 1:

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -396,6 +397,189 @@ __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __res
         w16[e] = __float2bfloat16_rn(w[e]);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM (tcgen05) for the network's inference pass
+//   C[i][j] = epi(sum_k bf16(A[i][k]) Bt[j][k] + bias[j])
+// A float32 [M][K] (activations, rounded to bfloat16 as they are staged), Bt
+// bfloat16 [N][K] (the transposed weights).  One CTA per 128 rows: the
+// accumulator tile [128][BN] (BN = N rounded up to 16, at most 256 per
+// grid.y slice) lives in tensor memory, lane = row.  Per 64-wide K stage the
+// 128 threads stage both operands into shared memory in the K-major,
+// unswizzled canonical layout (8 x 8 bfloat16 core matrices of 128 B, the
+// core of row group g and K group kc at (8 g + kc) 128 B), one elected thread
+// issues four tcgen05.mma (K = 16 each) and commits them to an mbarrier, and
+// every thread waits on it (bounded) before the stage is overwritten.  The
+// epilogue reads the accumulators with tcgen05.ld (32 lanes x 32 bit, 16
+// columns at a time), adds the bias, applies GELU and stores float32.
+// ---------------------------------------------------------------------------
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int THREADS = 128;
+constexpr int MAXBN = 256;
+constexpr unsigned ERR_MBAR_TIMEOUT = 1u;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading (K direction) and
+// stride (row-group direction) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ int core_off(int r, int kpair_lane)
+{
+    // element pair (k = 2 kpair_lane, 2 kpair_lane + 1) of row r in a 64-wide stage
+    return (((r >> 3) * 8 + (kpair_lane >> 2)) * 128) + (r & 7) * 16 + (kpair_lane & 3) * 4;
+}
+
+// Bounded wait on an mbarrier phase; on timeout sets the error word.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* err)
+{
+    uint32_t done = 0;
+    for (int pass = 0; pass < 2 && !done; ++pass) {
+        for (int it = 0; it < (1 << 22) && !done; ++it) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar), "r"(parity)
+                : "memory");
+        }
+        if (!done && pass == 0) atomicOr(err, ERR_MBAR_TIMEOUT);
+    }
+    return done != 0;
+}
+
+template <bool GELU>
+__global__ void __launch_bounds__(THREADS, 1) gemm_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                          const __nv_bfloat16* __restrict__ Bt,
+                                                          const float* __restrict__ bias, float* __restrict__ C,
+                                                          int ldc, int BN, uint32_t ncols, unsigned* err)
+{
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char* As = tsm;              // [128 rows][64] bfloat16, core-matrix layout: 16 KB
+    unsigned char* Bs = tsm + BM * BK * 2;  // [BN rows][64] bfloat16
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+    const uint32_t bar = saddr(&s_mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    // instruction descriptor: D float32, A and B bfloat16, both K-major, N = BN, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    const uint32_t a_base = saddr(As), b_base = saddr(Bs);
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int k0 = 0; k0 < K && ok; k0 += BK) {
+        const int gk = k0 + 2 * lane;
+        for (int r = warp; r < BM; r += THREADS / 32) {
+            const int gi = i0 + r;
+            float2 v = make_float2(0.f, 0.f);
+            if (gi < M) {
+                const float* row = A + (size_t)gi * lda;
+                if (gk < K) v.x = row[gk];
+                if (gk + 1 < K) v.y = row[gk + 1];
+            }
+            *reinterpret_cast<__nv_bfloat162*>(As + core_off(r, lane)) = __floats2bfloat162_rn(v.x, v.y);
+        }
+        for (int r = warp; r < BN; r += THREADS / 32) {
+            const int gn = j0 + r;
+            __nv_bfloat162 h = __floats2bfloat162_rn(0.f, 0.f);
+            if (gn < N) {
+                const __nv_bfloat16* row = Bt + (size_t)gn * K;
+                if (gk < K) h.x = row[gk];
+                if (gk + 1 < K) h.y = row[gk + 1];
+            }
+            *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(r, lane)) = h;
+        }
+        // generic-proxy stores -> visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t ad = smem_desc(a_base + 256u * kk, 128u, 1024u);
+                const uint64_t bd = smem_desc(b_base + 256u * kk, 128u, 1024u);
+                const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        // the stage is read by the MMAs until they complete
+        ok = __syncthreads_and(mbar_wait(bar, phase, err) ? 1 : 0) != 0;
+        phase ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int gi = i0 + warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(trow + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (gi < M) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int gj = j0 + c0 + c;
+                    if (gj < N) {
+                        float v = __uint_as_float(r[c]) + bias[gj];
+                        if (GELU) v = gelu(v);
+                        C[(size_t)gi * ldc + gj] = v;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// bfloat16 copy of W [K][N] transposed: Wt [N][K]
+__global__ void to_bf16_t_kernel(const float* __restrict__ W, int K, int N, __nv_bfloat16* __restrict__ Wt)
+{
+    const size_t total = (size_t)K * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int n = (int)(e / K), k = (int)(e % K);
+        Wt[e] = __float2bfloat16_rn(W[(size_t)k * N + n]);
+    }
+}
+
+}  // namespace tc
+
 int grid_for(size_t count, int threads = 256)
 {
     return (int)std::max<size_t>(1, std::min<size_t>((count + threads - 1) / threads, 152 * 16));
@@ -411,6 +595,9 @@ struct mmpc_mlp {
     int L = 0, maxw = 0, inf_rows = 0, ksplit_rows = 512;
     std::vector<float*> W, b, gW, gb, mW, vW, mb, vb;
     std::vector<__nv_bfloat16*> W16;
+    std::vector<__nv_bfloat16*> W16T;  // transposed copies [width[i+1]][width[i]] for the tensor-core path
+    bool tensor = false;               // inference with tcgen05
+    unsigned* d_err = nullptr;         // bounded-wait error word of the tensor-core kernels
     std::vector<float*> H;    // H[i]: input of layer i (i >= 1), [max_batch][width[i]]
     std::vector<float*> P;    // P[i]: pre-activation of layer i (hidden), [max_batch][width[i+1]]
     float* Yb = nullptr;      // [max_batch][width[L]]
@@ -434,6 +621,8 @@ void mlp_free(mmpc_mlp* n)
     for (auto* v : {&n->W, &n->b, &n->gW, &n->gb, &n->mW, &n->vW, &n->mb, &n->vb, &n->H, &n->P})
         for (float* p : *v) f(p);
     for (auto* p : n->W16) f(p);
+    for (auto* p : n->W16T) f(p);
+    f(n->d_err);
     f(n->Yb); f(n->D0); f(n->D1); f(n->part); f(n->I0); f(n->I1);
     delete n;
 }
@@ -449,6 +638,55 @@ void gemm(int M, int N, int K, int splits, const float* A, int lda, const TBt* B
 }
 
 int splits_for(const mmpc_mlp* n, int rows) { return std::max(1, (rows + n->ksplit_rows - 1) / n->ksplit_rows); }
+
+void refresh_bf16(mmpc_mlp* n, int i, cudaStream_t st)
+{
+    const size_t wc = wcount(n, i);
+    tc::to_bf16_t_kernel<<<grid_for(wc), 256, 0, st>>>(n->W[i], n->cfg.width[i], n->cfg.width[i + 1], n->W16T[i]);
+}
+
+// Launch shape of the tensor-core GEMM for N outputs: BN columns per CTA, a
+// power-of-two TMEM allocation, and a shared-memory request that keeps the
+// CTAs resident on an SM within its 512 TMEM columns.
+struct TcShape {
+    int BN;
+    uint32_t ncols;
+    size_t smem;
+};
+
+TcShape tc_shape(int N)
+{
+    TcShape t{};
+    t.BN = std::min(tc::MAXBN, (N + 15) / 16 * 16);
+    t.ncols = 32;
+    while ((int)t.ncols < t.BN) t.ncols <<= 1;
+    const size_t need = (size_t)tc::BM * tc::BK * 2 + (size_t)t.BN * tc::BK * 2;
+    const int per_sm = 512 / (int)t.ncols;
+    const size_t cap = (size_t)(227 * 1024) / per_sm;
+    t.smem = std::max(need, std::min<size_t>(cap, 227 * 1024) - 2048);
+    t.smem = std::max(t.smem, need);
+    return t;
+}
+
+void forward_tensor(mmpc_mlp* n, const float* X, int M, float* Y, float* b0, float* b1, cudaStream_t st)
+{
+    const int L = n->L;
+    const float* in = X;
+    for (int i = 0; i < L; ++i) {
+        const int K = n->cfg.width[i], N = n->cfg.width[i + 1];
+        const bool last = i == L - 1;
+        float* out = last ? Y : (i % 2 == 0 ? b0 : b1);
+        const TcShape t = tc_shape(N);
+        dim3 grid((M + tc::BM - 1) / tc::BM, (N + t.BN - 1) / t.BN);
+        if (last)
+            tc::gemm_kernel<false><<<grid, tc::THREADS, t.smem, st>>>(M, N, K, in, K, n->W16T[i], n->b[i], out, N,
+                                                                      t.BN, t.ncols, n->d_err);
+        else
+            tc::gemm_kernel<true><<<grid, tc::THREADS, t.smem, st>>>(M, N, K, in, K, n->W16T[i], n->b[i], out, N,
+                                                                     t.BN, t.ncols, n->d_err);
+        in = out;
+    }
+}
 
 // Forward over M <= rows of the buffers; keep = store pre-activations and
 // layer inputs for the backward pass.
@@ -574,7 +812,9 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
     const int L = n->L;
     n->W.assign(L, nullptr); n->b.assign(L, nullptr); n->gW.assign(L, nullptr); n->gb.assign(L, nullptr);
     n->mW.assign(L, nullptr); n->vW.assign(L, nullptr); n->mb.assign(L, nullptr); n->vb.assign(L, nullptr);
-    n->W16.assign(L, nullptr); n->H.assign(L, nullptr); n->P.assign(L, nullptr);
+    n->W16.assign(L, nullptr); n->W16T.assign(L, nullptr); n->H.assign(L, nullptr); n->P.assign(L, nullptr);
+    if (e == cudaSuccess) e = cudaMalloc(&n->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, sizeof(unsigned));
     size_t maxw_count = 0;
     for (int i = 0; i < L; ++i) {
         const size_t wc = wcount(n, i), bc = cfg->width[i + 1];
@@ -582,6 +822,7 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
         alloc(&n->W[i], wc); alloc(&n->gW[i], wc); alloc(&n->mW[i], wc); alloc(&n->vW[i], wc);
         alloc(&n->b[i], bc); alloc(&n->gb[i], bc); alloc(&n->mb[i], bc); alloc(&n->vb[i], bc);
         if (e == cudaSuccess) e = cudaMalloc(&n->W16[i], sizeof(__nv_bfloat16) * wc);
+        if (e == cudaSuccess) e = cudaMalloc(&n->W16T[i], sizeof(__nv_bfloat16) * wc);
         if (i >= 1) alloc(&n->H[i], mb * cfg->width[i]);
         if (i < L - 1) alloc(&n->P[i], mb * cfg->width[i + 1]);
     }
@@ -605,9 +846,16 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
         if (e == cudaSuccess) e = cudaMemset(n->gb[i], 0, sizeof(float) * bc);
         if (e == cudaSuccess) {
             to_bf16_kernel<<<grid_for(wc), 256>>>(n->W[i], n->W16[i], wc);
+            refresh_bf16(n, i, 0);
             e = cudaGetLastError();
         }
     }
+    size_t tc_smem = 0;  // the attribute must cover every layer's request
+    for (int i = 0; i < L; ++i) tc_smem = std::max(tc_smem, tc_shape(cfg->width[i + 1]).smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         mlp_free(n);
@@ -625,7 +873,10 @@ int mmpc_mlp_forward(mmpc_mlp* n, const float* X, int M, float* Y, void* stream)
     const int in = n->cfg.width[0], outw = n->cfg.width[n->L];
     for (int r0 = 0; r0 < M; r0 += n->inf_rows) {
         const int rows = std::min(n->inf_rows, M - r0);
-        forward_rows(n, X + (size_t)r0 * in, rows, Y + (size_t)r0 * outw, false, n->I0, n->I1, st);
+        if (n->tensor)
+            forward_tensor(n, X + (size_t)r0 * in, rows, Y + (size_t)r0 * outw, n->I0, n->I1, st);
+        else
+            forward_rows(n, X + (size_t)r0 * in, rows, Y + (size_t)r0 * outw, false, n->I0, n->I1, st);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_forward");
@@ -679,6 +930,7 @@ int mmpc_mlp_adamw(mmpc_mlp* n, float lr, void* stream)
                                                    c.beta2, c.eps, c.weight_decay, c1, c2);
         adamw_kernel<<<grid_for(bc), 256, 0, st>>>(n->b[i], n->gb[i], n->mb[i], n->vb[i], nullptr, bc, lr, c.beta1,
                                                    c.beta2, c.eps, 0.f, c1, c2);
+        refresh_bf16(n, i, st);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_adamw");
@@ -696,7 +948,12 @@ int mmpc_mlp_read(mmpc_mlp* n, int what, int layer, float* host, size_t count)
                      : what == 6 ? n->mb[layer] : n->vb[layer];
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(host, src, sizeof(float) * count, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_read");
+    if (e != cudaSuccess) return cuda_fail(e, "mmpc_mlp_read");
+    unsigned err = 0;
+    e = cudaMemcpy(&err, n->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mmpc_mlp_read");
+    if (err) return fail(MMPC_ERR_TIMEOUT, "a tensor-core wait expired in an earlier forward pass");
+    return MMPC_OK;
 }
 
 int mmpc_mlp_write(mmpc_mlp* n, int what, int layer, const float* host, size_t count)
@@ -709,10 +966,28 @@ int mmpc_mlp_write(mmpc_mlp* n, int what, int layer, const float* host, size_t c
     if (e == cudaSuccess) e = cudaMemcpy(what == 0 ? n->W[layer] : n->b[layer], host, sizeof(float) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && what == 0) {
         to_bf16_kernel<<<grid_for(count), 256>>>(n->W[layer], n->W16[layer], count);
+        refresh_bf16(n, layer, 0);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_write");
+}
+
+int mmpc_mlp_set_tensor_cores(mmpc_mlp* n, int on)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    n->tensor = on != 0;
+    return MMPC_OK;
+}
+
+int mmpc_mlp_status(mmpc_mlp* n)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    unsigned err = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&err, n->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mmpc_mlp_status");
+    return err ? fail(MMPC_ERR_TIMEOUT, "a tensor-core wait expired") : MMPC_OK;
 }
 
 void mmpc_mlp_destroy(mmpc_mlp* n)

@@ -18,7 +18,8 @@ MAX_LAYERS = 8
 EXPORTED = ("mmpc_features", "mmpc_warm_decode", "mmpc_warm_encode", "mmpc_column_stats", "mmpc_gather_rows",
             "mmpc_standardize",
             "mmpc_mlp_create", "mmpc_mlp_forward", "mmpc_mlp_loss_grad", "mmpc_mlp_adamw", "mmpc_mlp_read",
-            "mmpc_mlp_write", "mmpc_mlp_destroy", "mmpc_mlp_last_error")
+            "mmpc_mlp_write", "mmpc_mlp_destroy", "mmpc_mlp_last_error", "mmpc_mlp_set_tensor_cores",
+            "mmpc_mlp_status")
 READ_W, READ_B, READ_DW, READ_DB, READ_MW, READ_VW, READ_MB, READ_VB = range(8)
 
 
@@ -70,6 +71,8 @@ def lib():
     L.mmpc_mlp_adamw.argtypes = [vp, fp, vp]
     L.mmpc_mlp_read.argtypes = [vp, ip, ip, vp, ctypes.c_size_t]
     L.mmpc_mlp_write.argtypes = [vp, ip, ip, vp, ctypes.c_size_t]
+    L.mmpc_mlp_set_tensor_cores.argtypes = [vp, ip]
+    L.mmpc_mlp_status.argtypes = [vp]
     L.mmpc_mlp_destroy.argtypes = [vp]
     L.mmpc_mlp_destroy.restype = None
     L.mmpc_mlp_last_error.argtypes = []
@@ -204,6 +207,12 @@ class Mlp:
 
     def loss_grad(self, X, Z, loss=None, stream=None):
         _check(lib().mmpc_mlp_loss_grad(self.handle, _ptr(X), _ptr(Z), int(X.shape[0]), _ptr(loss), _stream(stream)))
+
+    def set_tensor_cores(self, on: bool):
+        _check(lib().mmpc_mlp_set_tensor_cores(self.handle, 1 if on else 0))
+
+    def status(self):
+        _check(lib().mmpc_mlp_status(self.handle))
 
     def adamw(self, lr, stream=None):
         _check(lib().mmpc_mlp_adamw(self.handle, float(lr), _stream(stream)))

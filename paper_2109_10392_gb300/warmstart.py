@@ -51,6 +51,7 @@ class WarmConfig:
     predict_lam: bool = False     # False: the network predicts c; lambda^0 = Q c^0 (or 0, lam_from_q False)
     lam_from_q: bool = True
     converged_only: bool = True   # train on the trajectories that reached tol only
+    tensor_inference: bool = True  # inference on the tensor cores (tcgen05, bfloat16 layer inputs)
     tol: float = 1e-2
     seed: int = 0
     params: dict = field(default_factory=lambda: dict(scenes.BASE_PARAMS))
@@ -184,7 +185,34 @@ def train(cfg: WarmConfig, X, T, device, log_every: int = 250):
         if step % log_every == 0 or step == cfg.steps - 1:
             log.append((step, float(loss.item())))
     Q = q_matrix(cfg.params, device) if (not cfg.predict_lam and cfg.lam_from_q) else None
+    net.set_tensor_cores(cfg.tensor_inference)
     return WarmStart(net, mu, sigma, cfg.params, Q), log
+
+
+def time_forward(ws: WarmStart, rows: int, device, reps: int = 5):
+    """Milliseconds of one network forward over `rows` feature rows, on the
+    SIMT path and on the tensor cores (median of reps, CUDA events)."""
+    import torch
+    X = torch.randn((rows, 64), device=device)
+    Y = torch.empty((rows, ws.outputs), device=device)
+    out = {}
+    for tag, on in (("simt_ms", False), ("tensor_ms", True)):
+        ws.net.set_tensor_cores(on)
+        ws.net.forward(X, Y)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ws.net.forward(X, Y)
+            b.record()
+            torch.cuda.synchronize(device)
+            ts.append(a.elapsed_time(b))
+        out[tag] = float(np.median(ts))
+    ws.net.status()
+    out["rows"] = rows
+    out["flops"] = 2.0 * rows * sum(i * o for i, o in zip(ws.net.widths[:-1], ws.net.widths[1:]))
+    ws.net.set_tensor_cores(True)
+    return out
 
 
 def validation_loss(ws: WarmStart, X, T):

@@ -252,3 +252,36 @@ def test_decode_coefficients_only_with_consistent_multipliers(orc):
         assert np.allclose(_host(d["coef"]), wc, rtol=1e-5, atol=1e-4)
         scale = max(1.0, np.abs(wl).max())
         assert np.max(np.abs(_host(d["lam"]) - wl)) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("widths", [(64, 256, 256, 256, 36), (64, 256, 256, 256, 72), (64, 32, 16)])
+def test_tensor_core_forward_matches_oracle(widths):
+    """tcgen05 inference: bfloat16 layer inputs and weights, float32
+    accumulation -- against the oracle with the same roundings (act_bf16),
+    on ragged row counts (tails of the 128-row tile)."""
+    import torch
+    Ws, bs = scenes.mlp_init(21, widths)
+    rng = np.random.default_rng(22)
+    bs = [rng.normal(0, 0.1, b.shape).astype(np.float32) for b in bs]
+    net = mlp.Mlp(widths, Ws, bs, max_batch=256)
+    net.set_tensor_cores(True)
+    for M_rows in (1, 127, 128, 300, 5000):
+        X = rng.normal(size=(M_rows, widths[0])).astype(np.float32)
+        Y = torch.zeros((M_rows, widths[-1]), device="cuda:0")
+        net.forward(_dev(X), Y)
+        net.status()
+        want, _ = M.forward(Ws, bs, X.astype(np.float64), bf16=True, act_bf16=True)
+        got = _host(Y)
+        scale = np.abs(want).max()
+        assert np.max(np.abs(got - want)) <= 3e-3 * scale, (M_rows, np.max(np.abs(got - want)), scale)
+    # against the float32-activation path: the bfloat16 staging is the only difference
+    X = rng.normal(size=(700, widths[0])).astype(np.float32)
+    Yt = torch.zeros((700, widths[-1]), device="cuda:0")
+    Ys = torch.zeros((700, widths[-1]), device="cuda:0")
+    net.forward(_dev(X), Yt)
+    net.set_tensor_cores(False)
+    net.forward(_dev(X), Ys)
+    torch.cuda.synchronize()
+    d = np.abs(_host(Yt) - _host(Ys)).max() / np.abs(_host(Ys)).max()
+    assert 0 < d < 3e-2, d
+    net.close()

@@ -183,3 +183,18 @@ def test_consistent_multipliers_of_a_straight_run_vanish(orc):
     assert np.array_equal(c0, c) and np.all(lam0 == 0.0)
     assert M.encode(c, lam, ego, T, n, outputs=3 * n).shape == (4, 3 * n)
     assert np.allclose(M.encode(c, lam, ego, T, n, outputs=3 * n), t)
+
+
+def test_bf16_activations_round_every_layer_input():
+    """act_bf16: the result equals the plain forward of a network whose every
+    layer input is replaced by its bfloat16 rounding (built layer by layer)."""
+    Ws, bs = _tiny_net(8)
+    X = np.random.default_rng(9).normal(size=(6, 5))
+    y, _ = M.forward(Ws, bs, X, bf16=True, act_bf16=True)
+    h = X
+    for i, (W, b) in enumerate(zip(Ws, bs)):
+        z = M.bf16_round(h.astype(np.float32)) @ M.bf16_round(W) + b.astype(np.float64)
+        h = M.gelu(z) if i < len(Ws) - 1 else z
+    assert np.array_equal(y, h)
+    y0, _ = M.forward(Ws, bs, X, bf16=True)
+    assert 0 < np.max(np.abs(y - y0)) < 0.05 * np.abs(y0).max()
