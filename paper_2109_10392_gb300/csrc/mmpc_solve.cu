@@ -56,8 +56,9 @@ void set_global_error(const std::string& msg) { g_error = msg; }
 // The pair-sample kernel stages [pair rows | common] into shared memory, the
 // one-sample kernel [common | sample rows]; the scoring kernels read the
 // sample rows from global memory.
-//   pair rows:   PP, PdP, PddP [NPT][NC][2]  basis rows of samples (2i, 2i+1)
-//                interleaved per coefficient, NPT = ceil(N/2) rounded up to
+//   pair rows:   PP, PdP, PddP [NPT][RS]  basis rows of samples (2i, 2i+1)
+//                interleaved per coefficient ([NC][2], RS = pair_stride(NC)
+//                floats with the padding), NPT = ceil(N/2) rounded up to
 //                whole warps (rows of samples >= N and every k >= n are zero,
 //                so padded lanes contribute exact zeros); tP [NPT][2] times
 //   common:      brow [6][NC] (P, Pd, Pdd at t = 0 and t = T); lin [NC]; Q,
@@ -76,6 +77,13 @@ struct BlobLayout {
     int common, init, rows1, total;  // region starts (common, first-step blocks, sample rows) and end
 };
 
+// Floats per sample-pair basis row.  A warp's 128-bit row loads are served
+// 8 threads at a time; they are conflict-free when the row stride is an odd
+// multiple of 16 B.  2 NC = 32 floats (128 B, NC = 16) would put all 8 on the
+// same banks, so those rows are padded to 36 floats (144 B); 2 NC = 24 (96 B,
+// NC = 12) leaves a 2-way conflict, kept for the smaller footprint.
+__host__ __device__ constexpr int pair_stride(int NC) { return NC == 16 ? 2 * NC + 4 : 2 * NC; }
+
 static BlobLayout blob_layout(int N, int NC)
 {
     auto up4 = [](int v) { return (v + 3) & ~3; };
@@ -85,9 +93,9 @@ static BlobLayout blob_layout(int N, int NC)
     const int NS = 32 * ((N + 31) / 32);
     BlobLayout B{};
     int o = 0;
-    B.PP = o; o += NP * NC * 2;
-    B.PdP = o; o += NP * NC * 2;
-    B.PddP = o; o += NP * NC * 2;
+    B.PP = o; o += NP * pair_stride(NC);
+    B.PdP = o; o += NP * pair_stride(NC);
+    B.PddP = o; o += NP * pair_stride(NC);
     B.tP = o; o += up4(NP * 2);
     B.common = o;
     B.brow = o; o += 6 * NC;
@@ -584,9 +592,11 @@ struct SolveSmem {
 
 constexpr int MAX_WARPS = 8;
 
-template <int MAXT>
+template <int NC, int MAXT>
 struct MinBlocks {
-    static constexpr int value = MAXT <= 64 ? 8 : (MAXT <= 128 ? 4 : 2);
+    // NC = 16 with 128 threads (N = 129..256) holds ~60 KB of shared memory,
+    // so at most 3 CTAs fit an SM: the register budget follows (no spills)
+    static constexpr int value = MAXT <= 64 ? 8 : (MAXT <= 128 ? (NC == 16 ? 3 : 4) : 2);
 };
 
 // dot product of a 16-byte aligned row of NC floats with a vector given as
@@ -661,9 +671,10 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
     const int ip = idle ? 0 : tid;  // rows are padded to whole warps (zero rows beyond N)
-    const float* PP = blob + L.PP + ip * 2 * NC;
-    const float* PdP = blob + L.PdP + ip * 2 * NC;
-    const float* PddP = blob + L.PddP + ip * 2 * NC;
+    constexpr int RS = pair_stride(NC);
+    const float* PP = blob + L.PP + ip * RS;
+    const float* PdP = blob + L.PdP + ip * RS;
+    const float* PddP = blob + L.PddP + ip * RS;
     const float2 tt = f2(blob[L.tP + 2 * ip], blob[L.tP + 2 * ip + 1]);
     const bool has_pair = !idle && tid < NP;
     const float2 valid = f2(has_pair ? 1.f : 0.f, (has_pair && 2 * ip + 1 < N) ? 1.f : 0.f);
@@ -963,7 +974,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
 }
 
 template <int NC, int MAXT>
-__global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value) am_solve_kernel(const __grid_constant__ SolveArgs A)
+__global__ void __launch_bounds__(MAXT, MinBlocks<NC, MAXT>::value) am_solve_kernel(const __grid_constant__ SolveArgs A)
 {
     pair_body<NC, MAXT>(A, blockIdx.x);
 }
@@ -1474,7 +1485,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 template <int NC, int MAXT>
-__global__ void __launch_bounds__(MAXT, MinBlocks<MAXT>::value)
+__global__ void __launch_bounds__(MAXT, MinBlocks<NC, MAXT>::value)
     am_solve_batch_kernel(const SolveArgs* __restrict__ scenes, const int2* __restrict__ items,
                           const int* __restrict__ total_ptr, unsigned long long* scratch)
 {
@@ -1688,7 +1699,7 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
             for (int h = 0; h < 2; ++h) {
                 const int smp = 2 * i + h;
                 if (smp >= N) continue;
-                for (int c = 0; c < n; ++c) h_set(dst + (i * NC + c) * 2 + h, (float)buf[src + (size_t)smp * n + c]);
+                for (int c = 0; c < n; ++c) h_set(dst + i * pair_stride(NC) + c * 2 + h, (float)buf[src + (size_t)smp * n + c]);
             }
     };
     pairs(PL.P, L.PP);
