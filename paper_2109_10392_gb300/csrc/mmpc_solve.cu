@@ -62,7 +62,8 @@ void set_global_error(const std::string& msg) { g_error = msg; }
 //                whole warps (rows of samples >= N and every k >= n are zero,
 //                so padded lanes contribute exact zeros); tP [NPT][2] times
 //   common:      brow [6][NC] (P, Pd, Pdd at t = 0 and t = T); lin [NC]; Q,
-//                K11 (x hi, x lo, y hi, y lo), K11_psi [NC][NC]; then the
+//                K11 (x hi, x lo, y hi, y lo), K11_psi [NC][KS] (KS =
+//                k_stride(NC) floats per row with the padding); then the
 //                blocks used only by the first step (from `init`): K12_psi
 //                [NC][4]; K12_x, K12_y, C0_x, C0_y [NC][8]; C0_psi [NC][4]
 // The pair kernel stages [pair rows | common up to init] and reads the
@@ -77,12 +78,14 @@ struct BlobLayout {
     int common, init, rows1, total;  // region starts (common, first-step blocks, sample rows) and end
 };
 
-// Floats per sample-pair basis row.  A warp's 128-bit row loads are served
-// 8 threads at a time; they are conflict-free when the row stride is an odd
-// multiple of 16 B.  2 NC = 32 floats (128 B, NC = 16) would put all 8 on the
-// same banks, so those rows are padded to 36 floats (144 B); 2 NC = 24 (96 B,
-// NC = 12) leaves a 2-way conflict, kept for the smaller footprint.
-__host__ __device__ constexpr int pair_stride(int NC) { return NC == 16 ? 2 * NC + 4 : 2 * NC; }
+// Floats per row of the per-thread (or per-lane) matrices in shared memory.
+// A warp's 128-bit loads are served 8 threads at a time and are conflict-free
+// when the row stride is an odd multiple of 16 B.  Sample-pair rows: 2 NC + 4
+// floats (112 B for NC = 12, 144 B for 16; unpadded, 96 B gave a 2-way and
+// 128 B an 8-way conflict).  Rows of Q and K11 (one per lane): NC floats for
+// NC = 12 (48 B), 20 for NC = 16 (80 B instead of 64 B).
+__host__ __device__ constexpr int pair_stride(int NC) { return 2 * NC + 4; }
+__host__ __device__ constexpr int k_stride(int NC) { return NC == 16 ? 20 : NC; }
 
 static BlobLayout blob_layout(int N, int NC)
 {
@@ -100,12 +103,12 @@ static BlobLayout blob_layout(int N, int NC)
     B.common = o;
     B.brow = o; o += 6 * NC;
     B.lin = o; o += up4(NC);
-    B.Q = o; o += NC * NC;
-    B.Kxh = o; o += NC * NC;
-    B.Kxl = o; o += NC * NC;
-    B.Kyh = o; o += NC * NC;
-    B.Kyl = o; o += NC * NC;
-    B.Kp11 = o; o += NC * NC;
+    B.Q = o; o += NC * k_stride(NC);
+    B.Kxh = o; o += NC * k_stride(NC);
+    B.Kxl = o; o += NC * k_stride(NC);
+    B.Kyh = o; o += NC * k_stride(NC);
+    B.Kyl = o; o += NC * k_stride(NC);
+    B.Kp11 = o; o += NC * k_stride(NC);
     B.init = o;
     B.Kp12 = o; o += NC * 4;
     B.K12x = o; o += NC * 8;
@@ -876,7 +879,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         if (!isy && act) reinterpret_cast<float2*>(vec)[k] = f2(fmaf(rho, pth, lampsi));
         __syncwarp();
         if (!isy && act) {
-            const float cp = cbp + dot_dup<NC>(blob + L.Kp11 + kk * NC, vec);
+            const float cp = cbp + dot_dup<NC>(blob + L.Kp11 + kk * k_stride(NC), vec);
             reinterpret_cast<float2*>(cpd)[k] = f2(cp);
         }
         __syncwarp();
@@ -904,7 +907,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             lam = fmaf(-rho, ftd, lam);
             if (!isy) lampsi = fmaf(-rho, pd, lampsi);
         }
-        const float qc = dot_dup<NC>(blob + L.Q + kk * NC, own);
+        const float qc = dot_dup<NC>(blob + L.Q + kk * k_stride(NC), own);
         const float u = act ? (lam - qc - rho * ftd) : 0.f;
         bool done = kit >= iters;
         if (!first && check && A.tol > 0.f && kit % A.check_every == 0) {
@@ -916,8 +919,8 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             if (act) reinterpret_cast<float2*>(vec)[k] = f2(u);
             __syncwarp();
             if (act) {
-                const float d0 = dot_dup<NC>(blob + (isy ? L.Kyh : L.Kxh) + kk * NC, vec);
-                const float d1 = dot_dup<NC>(blob + (isy ? L.Kyl : L.Kxl) + kk * NC, vec);
+                const float d0 = dot_dup<NC>(blob + (isy ? L.Kyh : L.Kxh) + kk * k_stride(NC), vec);
+                const float d1 = dot_dup<NC>(blob + (isy ? L.Kyl : L.Kxl) + kk * k_stride(NC), vec);
                 const float dd = (d0 + d1) + (first ? e + corr : e);
                 const float snew = c + dd;
                 e = dd - (snew - c);
@@ -1301,7 +1304,7 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
         for (int w = 0; w < nwarps; ++w) pth += red1[w * RSB + kk];
         if (!isy && act) vec[k] = fmaf(rho, pth, lampsi);
         __syncwarp();
-        if (!isy && act) cpv[k] = cbp + dot_plain<NC>(blob + (L.Kp11 - base) + kk * NC, vec);
+        if (!isy && act) cpv[k] = cbp + dot_plain<NC>(blob + (L.Kp11 - base) + kk * k_stride(NC), vec);
         __syncwarp();
     };
 
@@ -1323,7 +1326,7 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
             lam = fmaf(-rho, ftd, lam);
             if (!isy) lampsi = fmaf(-rho, pd, lampsi);
         }
-        const float qc = dot_plain<NC>(blob + (L.Q - base) + kk * NC, own);
+        const float qc = dot_plain<NC>(blob + (L.Q - base) + kk * k_stride(NC), own);
         const float u = act ? (lam - qc - rho * ftd) : 0.f;
         bool done = kit >= iters;
         if (!first && check && A.tol > 0.f && kit % A.check_every == 0) {
@@ -1334,8 +1337,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
             if (act) vec[k] = u;
             __syncwarp();
             if (act) {
-                const float d0 = dot_plain<NC>(blob + ((isy ? L.Kyh : L.Kxh) - base) + kk * NC, vec);
-                const float d1 = dot_plain<NC>(blob + ((isy ? L.Kyl : L.Kxl) - base) + kk * NC, vec);
+                const float d0 = dot_plain<NC>(blob + ((isy ? L.Kyh : L.Kxh) - base) + kk * k_stride(NC), vec);
+                const float d1 = dot_plain<NC>(blob + ((isy ? L.Kyl : L.Kxl) - base) + kk * k_stride(NC), vec);
                 const float dd = (d0 + d1) + (first ? e + corr : e);
                 const float snew = c + dd;
                 e = dd - (snew - c);
@@ -1714,12 +1717,12 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
     mat(PL.Pdd, L.Pdd, N, n, NC, false);
     mat(PL.t, L.t, 1, N, N, false);
     mat(PL.lin, L.lin, 1, n, n, false);
-    mat(PL.Q, L.Q, n, n, NC, false);
-    mat(PL.K11x, L.Kxh, n, n, NC, false);
-    mat(PL.K11x, L.Kxl, n, n, NC, true);
-    mat(PL.K11y, L.Kyh, n, n, NC, false);
-    mat(PL.K11y, L.Kyl, n, n, NC, true);
-    mat(PL.K11p, L.Kp11, n, n, NC, false);
+    mat(PL.Q, L.Q, n, n, k_stride(NC), false);
+    mat(PL.K11x, L.Kxh, n, n, k_stride(NC), false);
+    mat(PL.K11x, L.Kxl, n, n, k_stride(NC), true);
+    mat(PL.K11y, L.Kyh, n, n, k_stride(NC), false);
+    mat(PL.K11y, L.Kyl, n, n, k_stride(NC), true);
+    mat(PL.K11p, L.Kp11, n, n, k_stride(NC), false);
     mat(PL.K12p, L.Kp12, n, MMPC_NEQ_PSI, 4, false);
     mat(PL.K12x, L.K12x, n, MMPC_NEQ_X, 8, false);
     mat(PL.K12y, L.K12y, n, MMPC_NEQ_Y, 8, false);
