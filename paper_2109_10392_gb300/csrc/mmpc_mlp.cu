@@ -399,25 +399,30 @@ __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __res
 
 // ---------------------------------------------------------------------------
 // Tensor-core GEMM (tcgen05) for the network's inference pass
-//   C[i][j] = epi(sum_k bf16(A[i][k]) Bt[j][k] + bias[j])
-// A float32 [M][K] (activations, rounded to bfloat16 as they are staged), Bt
-// bfloat16 [N][K] (the transposed weights).  One CTA per 128 rows: the
-// accumulator tile [128][BN] (BN = N rounded up to 16, at most 256 per
-// grid.y slice) lives in tensor memory, lane = row.  Per 64-wide K stage the
-// 128 threads stage both operands into shared memory in the K-major,
-// unswizzled canonical layout (8 x 8 bfloat16 core matrices of 128 B, the
-// core of row group g and K group kc at (8 g + kc) 128 B), one elected thread
-// issues four tcgen05.mma (K = 16 each) and commits them to an mbarrier, and
-// every thread waits on it (bounded) before the stage is overwritten.  The
-// epilogue reads the accumulators with tcgen05.ld (32 lanes x 32 bit, 16
-// columns at a time), adds the bias, applies GELU and stores float32.
+//   C[i][j] = epi(sum_k A[i][k] Bt[j][k] + bias[j])
+// A [M][K]: float32 (the features; rounded to bfloat16 as they are staged) or
+// bfloat16 (hidden activations written by the previous layer's epilogue);
+// Bt bfloat16 [N][K] (the transposed weights).  One CTA per 128 rows and BN
+// (<= 128, a multiple of 16) columns; the accumulator tile lives in tensor
+// memory, lane = row.  Operands are staged K-major in the unswizzled
+// canonical layout of 8 x 8 bfloat16 core matrices (128 B, row r at 16 r),
+// with the cores of one K group adjacent along the rows (stride-dimension
+// offset 128 B) and K groups R / 8 x 128 B apart (leading-dimension offset),
+// so that each thread writes whole 16-byte core rows and a warp's stores are
+// contiguous.  Two stage buffers: while the MMAs of one 64-wide K stage run,
+// the threads stage the next one; one elected thread issues the four
+// tcgen05.mma (K = 16 each) of a stage and commits them to that buffer's
+// mbarrier, which is waited (bounded) before the buffer is refilled.  The
+// epilogue reads the accumulators with tcgen05.ld, adds the bias, applies
+// GELU, and stores float32 or bfloat16 (the next layer's input; the same
+// rounding the staging would apply).
 // ---------------------------------------------------------------------------
 namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int THREADS = 128;
-constexpr int MAXBN = 256;
+constexpr int MAXBN = 128;
 constexpr unsigned ERR_MBAR_TIMEOUT = 1u;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -428,12 +433,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ int core_off(int r, int kpair_lane)
-{
-    // element pair (k = 2 kpair_lane, 2 kpair_lane + 1) of row r in a 64-wide stage
-    return (((r >> 3) * 8 + (kpair_lane >> 2)) * 128) + (r & 7) * 16 + (kpair_lane & 3) * 4;
 }
 
 // Bounded wait on an mbarrier phase; on timeout sets the error word.
@@ -455,20 +454,63 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     return done != 0;
 }
 
-template <bool GELU>
-__global__ void __launch_bounds__(THREADS, 1) gemm_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// One 16-byte core row (8 consecutive K elements of row `row`), as bfloat16.
+template <typename TA>
+__device__ __forceinline__ uint4 load_core_row(const TA* __restrict__ A, int lda, int row, int rows, int k, int K);
+
+template <>
+__device__ __forceinline__ uint4 load_core_row<float>(const float* __restrict__ A, int lda, int row, int rows, int k,
+                                                      int K)
+{
+    float v[8];
+    if (row < rows && k + 8 <= K && (lda & 3) == 0) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(A + (size_t)row * lda + k));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(A + (size_t)row * lda + k + 4));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (row < rows && k + e < K) ? A[(size_t)row * lda + k + e] : 0.f;
+    }
+    return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+
+template <>
+__device__ __forceinline__ uint4 load_core_row<__nv_bfloat16>(const __nv_bfloat16* __restrict__ A, int lda, int row,
+                                                              int rows, int k, int K)
+{
+    if (row < rows && k + 8 <= K && (lda & 7) == 0)
+        return __ldg(reinterpret_cast<const uint4*>(A + (size_t)row * lda + k));
+    uint16_t u[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const __nv_bfloat16 h = (row < rows && k + e < K) ? A[(size_t)row * lda + k + e] : __float2bfloat16_rn(0.f);
+        u[e] = *reinterpret_cast<const uint16_t*>(&h);
+    }
+    return make_uint4(u[0] | (uint32_t)u[1] << 16, u[2] | (uint32_t)u[3] << 16, u[4] | (uint32_t)u[5] << 16,
+                      u[6] | (uint32_t)u[7] << 16);
+}
+
+template <typename TA, typename TC, bool GELU>
+__global__ void __launch_bounds__(THREADS, 1) umma_gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int lda,
                                                           const __nv_bfloat16* __restrict__ Bt,
-                                                          const float* __restrict__ bias, float* __restrict__ C,
-                                                          int ldc, int BN, uint32_t ncols, unsigned* err)
+                                                          const float* __restrict__ bias, TC* __restrict__ C, int ldc,
+                                                          int BN, uint32_t ncols, unsigned* err)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char* As = tsm;              // [128 rows][64] bfloat16, core-matrix layout: 16 KB
-    unsigned char* Bs = tsm + BM * BK * 2;  // [BN rows][64] bfloat16
-    __shared__ __align__(8) unsigned long long s_mbar;
+    // per buffer: A [8 K groups][128 rows] core rows (16 KB), then B [8][BN] core rows
+    const int a_bytes = BM * BK * 2, b_bytes = BN * BK * 2;
+    unsigned char* buf[2] = {tsm, tsm + a_bytes + b_bytes};
+    __shared__ __align__(8) unsigned long long s_mbar[2];
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
-    const uint32_t bar = saddr(&s_mbar);
+    const uint32_t bar[2] = {saddr(&s_mbar[0]), saddr(&s_mbar[1])};
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
                      "r"(ncols)
@@ -476,7 +518,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(int M, int N, int K, c
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar[0]), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar[1]), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -485,30 +528,29 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(int M, int N, int K, c
     const uint32_t tmem = s_tmem;
     // instruction descriptor: D float32, A and B bfloat16, both K-major, N = BN, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    const uint32_t a_base = saddr(As), b_base = saddr(Bs);
+    const int stages = (K + BK - 1) / BK;
     bool ok = true;
-    uint32_t phase = 0;
-    for (int k0 = 0; k0 < K && ok; k0 += BK) {
-        const int gk = k0 + 2 * lane;
-        for (int r = warp; r < BM; r += THREADS / 32) {
-            const int gi = i0 + r;
-            float2 v = make_float2(0.f, 0.f);
-            if (gi < M) {
-                const float* row = A + (size_t)gi * lda;
-                if (gk < K) v.x = row[gk];
-                if (gk + 1 < K) v.y = row[gk + 1];
-            }
-            *reinterpret_cast<__nv_bfloat162*>(As + core_off(r, lane)) = __floats2bfloat162_rn(v.x, v.y);
+    for (int st = 0; st < stages && ok; ++st) {
+        const int b = st & 1;
+        if (st >= 2) ok = __syncthreads_and(mbar_wait(bar[b], (uint32_t)(((st - 2) >> 1) & 1), err) ? 1 : 0) != 0;
+        if (!ok) break;
+        const int k0 = st * BK;
+        unsigned char* As = buf[b];
+        unsigned char* Bs = buf[b] + a_bytes;
+        {   // A: thread = row, 8 core rows (all loads first)
+            uint4 v[8];
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) v[kc] = load_core_row<TA>(A, lda, i0 + tid, M, k0 + 8 * kc, K);
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) *reinterpret_cast<uint4*>(As + kc * (BM * 16) + tid * 16) = v[kc];
         }
-        for (int r = warp; r < BN; r += THREADS / 32) {
-            const int gn = j0 + r;
-            __nv_bfloat162 h = __floats2bfloat162_rn(0.f, 0.f);
-            if (gn < N) {
-                const __nv_bfloat16* row = Bt + (size_t)gn * K;
-                if (gk < K) h.x = row[gk];
-                if (gk + 1 < K) h.y = row[gk + 1];
-            }
-            *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(r, lane)) = h;
+        for (int r = tid; r < BN; r += THREADS) {  // B: thread = output column
+            uint4 v[8];
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc)
+                v[kc] = load_core_row<__nv_bfloat16>(Bt, K, j0 + r, N, k0 + 8 * kc, K);
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) *reinterpret_cast<uint4*>(Bs + kc * (BN * 16) + r * 16) = v[kc];
         }
         // generic-proxy stores -> visible to the tensor core's async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -516,11 +558,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(int M, int N, int K, c
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
+            const uint32_t a_base = saddr(As), b_base = saddr(Bs);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t ad = smem_desc(a_base + 256u * kk, 128u, 1024u);
-                const uint64_t bd = smem_desc(b_base + 256u * kk, 128u, 1024u);
-                const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+                // K groups 2 kk, 2 kk + 1: leading offset = one K group; stride offset = 8 rows
+                const uint64_t ad = smem_desc(a_base + (uint32_t)(2 * kk * BM * 16), (uint32_t)(BM * 16), 128u);
+                const uint64_t bd = smem_desc(b_base + (uint32_t)(2 * kk * BN * 16), (uint32_t)(BN * 16), 128u);
+                const uint32_t acc = (st > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
                     "setp.ne.b32 p, %4, 0;\n\t"
@@ -528,13 +572,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(int M, int N, int K, c
                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                     : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar[b])
                          : "memory");
         }
-        // the stage is read by the MMAs until they complete
-        ok = __syncthreads_and(mbar_wait(bar, phase, err) ? 1 : 0) != 0;
-        phase ^= 1u;
     }
+    // the last commit tracks every MMA issued before it
+    if (ok && stages > 0)
+        ok = __syncthreads_and(mbar_wait(bar[(stages - 1) & 1], (uint32_t)(((stages - 1) >> 1) & 1), err) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         const int gi = i0 + warp * 32 + lane;
@@ -550,13 +594,35 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(int M, int N, int K, c
                 : "r"(trow + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (gi < M) {
+                float v[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const int gj = j0 + c0 + c;
-                    if (gj < N) {
-                        float v = __uint_as_float(r[c]) + bias[gj];
-                        if (GELU) v = gelu(v);
-                        C[(size_t)gi * ldc + gj] = v;
+                    v[c] = __uint_as_float(r[c]) + (gj < N ? bias[gj] : 0.f);
+                    if (GELU) v[c] = gelu(v[c]);
+                }
+                TC* out = C + (size_t)gi * ldc + j0 + c0;
+                const bool full = j0 + c0 + 16 <= N;
+                if (sizeof(TC) == 4) {
+                    if (full && (ldc & 3) == 0) {
+#pragma unroll
+                        for (int c = 0; c < 16; c += 4)
+                            *reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + c) =
+                                make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+                    } else {
+                        for (int c = 0; c < 16; ++c)
+                            if (j0 + c0 + c < N) reinterpret_cast<float*>(out)[c] = v[c];
+                    }
+                } else {
+                    if (full && (ldc & 7) == 0) {
+#pragma unroll
+                        for (int c = 0; c < 16; c += 8)
+                            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + c) =
+                                make_uint4(pack_bf16(v[c], v[c + 1]), pack_bf16(v[c + 2], v[c + 3]),
+                                           pack_bf16(v[c + 4], v[c + 5]), pack_bf16(v[c + 6], v[c + 7]));
+                    } else {
+                        for (int c = 0; c < 16; ++c)
+                            if (j0 + c0 + c < N) reinterpret_cast<__nv_bfloat16*>(out)[c] = __float2bfloat16_rn(v[c]);
                     }
                 }
             }
@@ -645,9 +711,10 @@ void refresh_bf16(mmpc_mlp* n, int i, cudaStream_t st)
     tc::to_bf16_t_kernel<<<grid_for(wc), 256, 0, st>>>(n->W[i], n->cfg.width[i], n->cfg.width[i + 1], n->W16T[i]);
 }
 
-// Launch shape of the tensor-core GEMM for N outputs: BN columns per CTA, a
-// power-of-two TMEM allocation, and a shared-memory request that keeps the
-// CTAs resident on an SM within its 512 TMEM columns.
+// Launch shape of the tensor-core GEMM for N outputs: BN columns per CTA
+// (grid.y covers the rest), a power-of-two TMEM allocation, and a
+// shared-memory request that keeps the CTAs resident on an SM within its 512
+// TMEM columns.
 struct TcShape {
     int BN;
     uint32_t ncols;
@@ -660,31 +727,42 @@ TcShape tc_shape(int N)
     t.BN = std::min(tc::MAXBN, (N + 15) / 16 * 16);
     t.ncols = 32;
     while ((int)t.ncols < t.BN) t.ncols <<= 1;
-    const size_t need = (size_t)tc::BM * tc::BK * 2 + (size_t)t.BN * tc::BK * 2;
+    const size_t need = 2 * ((size_t)tc::BM * tc::BK * 2 + (size_t)t.BN * tc::BK * 2);
     const int per_sm = 512 / (int)t.ncols;
-    const size_t cap = (size_t)(227 * 1024) / per_sm;
-    t.smem = std::max(need, std::min<size_t>(cap, 227 * 1024) - 2048);
-    t.smem = std::max(t.smem, need);
+    const size_t cap = (size_t)(227 * 1024) / per_sm - 2048;
+    t.smem = std::max(need, std::min<size_t>(cap, 227 * 1024));
     return t;
 }
 
+template <typename TA, typename TC, bool GELU>
+void tc_launch(int M, int N, int K, const TA* A, const __nv_bfloat16* Bt, const float* bias, TC* C, unsigned* err,
+               cudaStream_t st)
+{
+    const TcShape t = tc_shape(N);
+    dim3 grid((M + tc::BM - 1) / tc::BM, (N + t.BN - 1) / t.BN);
+    tc::umma_gemm_kernel<TA, TC, GELU><<<grid, tc::THREADS, t.smem, st>>>(M, N, K, A, K, Bt, bias, C, N, t.BN, t.ncols, err);
+}
+
+// Inference on the tensor cores: the first layer reads the float32
+// features, hidden activations travel as bfloat16, the last layer writes
+// float32.
 void forward_tensor(mmpc_mlp* n, const float* X, int M, float* Y, float* b0, float* b1, cudaStream_t st)
 {
     const int L = n->L;
-    const float* in = X;
+    __nv_bfloat16* h[2] = {reinterpret_cast<__nv_bfloat16*>(b0), reinterpret_cast<__nv_bfloat16*>(b1)};
     for (int i = 0; i < L; ++i) {
         const int K = n->cfg.width[i], N = n->cfg.width[i + 1];
         const bool last = i == L - 1;
-        float* out = last ? Y : (i % 2 == 0 ? b0 : b1);
-        const TcShape t = tc_shape(N);
-        dim3 grid((M + tc::BM - 1) / tc::BM, (N + t.BN - 1) / t.BN);
-        if (last)
-            tc::gemm_kernel<false><<<grid, tc::THREADS, t.smem, st>>>(M, N, K, in, K, n->W16T[i], n->b[i], out, N,
-                                                                      t.BN, t.ncols, n->d_err);
+        const __nv_bfloat16* in = h[(i + 1) & 1];
+        __nv_bfloat16* out = h[i & 1];
+        if (i == 0 && last)
+            tc_launch<float, float, false>(M, N, K, X, n->W16T[i], n->b[i], Y, n->d_err, st);
+        else if (i == 0)
+            tc_launch<float, __nv_bfloat16, true>(M, N, K, X, n->W16T[i], n->b[i], out, n->d_err, st);
+        else if (last)
+            tc_launch<__nv_bfloat16, float, false>(M, N, K, in, n->W16T[i], n->b[i], Y, n->d_err, st);
         else
-            tc::gemm_kernel<true><<<grid, tc::THREADS, t.smem, st>>>(M, N, K, in, K, n->W16T[i], n->b[i], out, N,
-                                                                     t.BN, t.ncols, n->d_err);
-        in = out;
+            tc_launch<__nv_bfloat16, __nv_bfloat16, true>(M, N, K, in, n->W16T[i], n->b[i], out, n->d_err, st);
     }
 }
 
@@ -852,10 +930,12 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
     }
     size_t tc_smem = 0;  // the attribute must cover every layer's request
     for (int i = 0; i < L; ++i) tc_smem = std::max(tc_smem, tc_shape(cfg->width[i + 1]).smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
+    const void* tc_kernels[] = {(const void*)tc::umma_gemm_kernel<float, float, false>,
+                                (const void*)tc::umma_gemm_kernel<float, __nv_bfloat16, true>,
+                                (const void*)tc::umma_gemm_kernel<__nv_bfloat16, float, false>,
+                                (const void*)tc::umma_gemm_kernel<__nv_bfloat16, __nv_bfloat16, true>};
+    for (const void* kf : tc_kernels)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         mlp_free(n);
