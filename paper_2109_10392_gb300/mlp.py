@@ -242,3 +242,48 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def _time_forward(rows: int, reps: int = 10, seed: int = 0) -> list:
+    """Times one forward pass of the warm-start network (64 -> 256 x 3 -> 36,
+    seeded random weights) over `rows` random rows, FP32 SIMT path and tensor
+    cores (CUDA events, median of reps)."""
+    import torch
+
+    from . import scenes
+    widths = (64, 256, 256, 256, 36)
+    Ws, bs = scenes.mlp_init(seed, widths)
+    net = Mlp(widths, Ws, bs, max_batch=4096)
+    flops = 2.0 * rows * sum(i * o for i, o in zip(widths[:-1], widths[1:]))
+    X = torch.randn((rows, widths[0]), device="cuda:0")
+    Y = torch.empty((rows, widths[-1]), device="cuda:0")
+    out = []
+    for on in (False, True):
+        net.set_tensor_cores(on)
+        net.forward(X, Y)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            net.forward(X, Y)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        out.append(dict(rows=rows, tensor_cores=on, ms=ms, tflops=flops / (ms * 1e-3) / 1e12))
+    net.status()
+    net.close()
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="time the warm-start network's forward pass")
+    ap.add_argument("--rows", type=int, nargs="+", default=[65536, 1 << 20])
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args()
+    for r in a.rows:
+        for line in _time_forward(r, a.reps):
+            print(json.dumps(line), flush=True)
