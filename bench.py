@@ -645,7 +645,7 @@ def main():
     ap.add_argument("--warm-train-scenes", type=int, default=200_000)
     ap.add_argument("--warm-steps", type=int, default=4000)
     ap.add_argument("--warm-eval-scenes", type=int, default=4096)
-    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="batch item order (0: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -204,13 +204,17 @@ typedef struct mmpc_batch mmpc_batch;
  * be captured in a CUDA graph.  Synchronous. */
 int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_meta* meta, mmpc_batch** out);
 
-/* Order in which the persistent CTAs take (scene, trajectory) items:
- * 1 scene by scene as given, 2 scenes by decreasing work per trajectory
- * (N (m + 32)), 3 round-robin over the scenes of 2, one trajectory of each
- * at a time.  Synchronous. */
+/* Schedule of the solve: 1-3 are one persistent launch sized for the
+ * longest horizon, taking (scene, trajectory) items scene by scene as given
+ * (1), scenes by decreasing work per trajectory N (m + 32) (2), or
+ * round-robin over the scenes of 2, one trajectory of each at a time (3);
+ * 4 groups the scenes by horizon (the CTA size ceil(N / 2) rounded up to
+ * whole warps) and runs one right-sized persistent launch per group, on
+ * streams forked from and joined back to the run's stream, so that no warp
+ * idles through a shorter horizon.  Synchronous. */
 int mmpc_batch_set_schedule(mmpc_batch* b, int schedule);
 
-/* Times the three schedules (a warm-up and two timed runs each, on `stream`),
+/* Times the four schedules (a warm-up and two timed runs each, on `stream`),
  * keeps the fastest and writes it to *chosen (may be NULL).  Synchronous. */
 int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen);
 

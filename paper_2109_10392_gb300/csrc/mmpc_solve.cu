@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -1478,7 +1479,8 @@ __global__ void __launch_bounds__(256) score_kernel(const ScoreArgs S)
 // its trajectories.  Scoring is one launch over all items with a packed
 // 64-bit atomicMin key per scene, and a finalising launch.
 // Scratch words: [0] queue counter, [1] earliest CTA start, [2, 2 + S) scene
-// completion times, [2 + S, 2 + 2S) scene argmin keys.
+// completion times, [2 + S, 2 + 2S) scene argmin keys, then one queue counter
+// per horizon group (the grouped schedule launches one kernel per group).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -1490,14 +1492,15 @@ __device__ __forceinline__ unsigned long long global_ns()
 template <int NC, int MAXT>
 __global__ void __launch_bounds__(MAXT, MinBlocks<NC, MAXT>::value)
     am_solve_batch_kernel(const SolveArgs* __restrict__ scenes, const int2* __restrict__ items,
-                          const int* __restrict__ total_ptr, unsigned long long* scratch)
+                          const int* __restrict__ total_ptr, unsigned long long* scratch,
+                          unsigned long long* queue)
 {
     __shared__ int s_item;
     const int total = *total_ptr;  // written by an earlier launch on the stream
     for (;;) {
         __syncthreads();  // the previous item is finished by every thread
         if (threadIdx.x == 0) {
-            s_item = (int)atomicAdd(reinterpret_cast<unsigned*>(scratch), 1u);
+            s_item = (int)atomicAdd(reinterpret_cast<unsigned*>(queue), 1u);
             atomicMin(scratch + 1, global_ns());
         }
         __syncthreads();
@@ -1529,10 +1532,10 @@ __global__ void __launch_bounds__(256) score_batch_kernel(const ScoreArgs* __res
     }
 }
 
-__global__ void batch_reset_kernel(unsigned long long* scratch, int S, int* fb_count)
+__global__ void batch_reset_kernel(unsigned long long* scratch, int S, int G, int* fb_count)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 + 2 * S; i += gridDim.x * blockDim.x)
-        scratch[i] = (i == 1 || i >= 2 + S) ? ~0ull : 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 + 2 * S + G; i += gridDim.x * blockDim.x)
+        scratch[i] = (i == 1 || (i >= 2 + S && i < 2 + 2 * S)) ? ~0ull : 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) *fb_count = 0;
 }
 
@@ -2056,9 +2059,22 @@ struct mmpc_batch {
     mmpc::ScoreArgs* d_sargs = nullptr;
     int2* d_items = nullptr;
     int2* d_fb_items = nullptr;               // fallback list
-    int* d_counts = nullptr;                  // [0] items, [1] fallback items
+    int* d_counts = nullptr;                  // [0] items, [1] fallback items, [2 + g] items of group g
     bool fallback = false;
     bool any_warm = false;
+    // horizon groups (schedule 4): scenes with the same pair-thread count,
+    // one right-sized persistent launch each, on forked streams
+    struct Group {
+        int threads = 0, grid = 0, total = 0, offset = 0;
+        size_t smem = 0;
+        void* kern = nullptr;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<Group> groups;
+    std::vector<int> scene_threads;
+    int2* d_gitems = nullptr;  // all groups' items, group after group
+    cudaEvent_t fork = nullptr;
     unsigned long long* d_scratch = nullptr;  // [2 + 2S], laid out as the batch kernels describe
 };
 
@@ -2080,6 +2096,12 @@ void batch_free(mmpc_batch* b)
     cudaFree(b->d_fb_items);
     cudaFree(b->d_counts);
     cudaFree(b->d_scratch);
+    cudaFree(b->d_gitems);
+    for (auto& g : b->groups) {
+        if (g.stream) cudaStreamDestroy(g.stream);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
@@ -2116,6 +2138,23 @@ std::vector<int2> batch_items(const mmpc_batch* b, int schedule)
 
 }  // namespace
 
+namespace {
+
+void* batch_kernel_for(int NC, int threads)
+{
+    if (NC == 12)
+        return threads <= 64 ? (void*)am_solve_batch_kernel<12, 64>
+             : threads <= 128 ? (void*)am_solve_batch_kernel<12, 128> : (void*)am_solve_batch_kernel<12, 256>;
+    return threads <= 64 ? (void*)am_solve_batch_kernel<16, 64>
+         : threads <= 128 ? (void*)am_solve_batch_kernel<16, 128> : (void*)am_solve_batch_kernel<16, 256>;
+}
+
+// Work per trajectory of a scene, for ordering: N (m + 32), obstacle-sample
+// pairs plus the per-sample work.
+double scene_cost(const mmpc_ctx* c) { return (double)c->p.N * (double)(c->m + 32); }
+
+}  // namespace
+
 extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_meta* meta, mmpc_batch** out)
 {
     using namespace mmpc;
@@ -2148,18 +2187,62 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
     b->threads = 32 * ((NP + 31) / 32);
     b->smem = pair_smem(maxRows, max_m, b->NC, b->threads);
     if (b->smem > 227 * 1024) { batch_free(b); return batch_fail("mmpc_batch_create: scenes do not fit in shared memory", MMPC_ERR_SHAPE); }
-    if (b->NC == 12) {
-        b->kern = b->threads <= 64 ? (void*)am_solve_batch_kernel<12, 64>
-                : b->threads <= 128 ? (void*)am_solve_batch_kernel<12, 128> : (void*)am_solve_batch_kernel<12, 256>;
-    } else {
-        b->kern = b->threads <= 64 ? (void*)am_solve_batch_kernel<16, 64>
-                : b->threads <= 128 ? (void*)am_solve_batch_kernel<16, 128> : (void*)am_solve_batch_kernel<16, 256>;
+    b->kern = batch_kernel_for(b->NC, b->threads);
+
+    // horizon groups: scenes with the same pair-thread count, longest first;
+    // inside a group, scenes by decreasing work per trajectory
+    b->scene_threads.resize(S);
+    std::vector<int> keys;
+    for (int s = 0; s < S; ++s) {
+        const int np = (scenes[s].ctx->p.N + 1) / 2;
+        b->scene_threads[s] = 32 * ((np + 31) / 32);
+        if (std::find(keys.begin(), keys.end(), b->scene_threads[s]) == keys.end()) keys.push_back(b->scene_threads[s]);
     }
-    cudaError_t e = cudaFuncSetAttribute(b->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    std::sort(keys.begin(), keys.end(), std::greater<int>());
+    std::vector<int2> gitems;
+    for (int th : keys) {
+        mmpc_batch::Group g;
+        g.threads = th;
+        g.offset = (int)gitems.size();
+        int gm = 0, grows = 0;
+        std::vector<int> ss;
+        for (int s = 0; s < S; ++s)
+            if (b->scene_threads[s] == th) {
+                ss.push_back(s);
+                gm = std::max(gm, scenes[s].ctx->m);
+                grows = std::max(grows, scenes[s].ctx->L.init);
+            }
+        std::stable_sort(ss.begin(), ss.end(), [&](int x, int y) { return scene_cost(scenes[x].ctx) > scene_cost(scenes[y].ctx); });
+        for (int s : ss)
+            for (int l = 0; l < scenes[s].B; ++l) gitems.push_back(make_int2(s, l));
+        g.total = (int)gitems.size() - g.offset;
+        g.smem = pair_smem(grows, gm, b->NC, th);
+        g.kern = batch_kernel_for(b->NC, th);
+        b->groups.push_back(g);
+    }
+    // each kernel's dynamic shared memory attribute covers its largest request
+    cudaError_t e = cudaSuccess;
+    std::vector<std::pair<void*, size_t>> attrs{{b->kern, b->smem}};
+    for (const auto& g : b->groups) {
+        bool found = false;
+        for (auto& a : attrs)
+            if (a.first == g.kern) { a.second = std::max(a.second, g.smem); found = true; }
+        if (!found) attrs.push_back({g.kern, g.smem});
+    }
+    for (const auto& a : attrs)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(a.first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.second);
     int dev = 0, sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kern, b->threads, b->smem);
+    for (auto& g : b->groups) {
+        int per = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, g.kern, g.threads, g.smem);
+        g.grid = std::max(1, std::min(g.total, sms * std::max(per, 1)));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e != cudaSuccess || per_sm < 1) {
         batch_free(b);
         return batch_fail(std::string("mmpc_batch_create: occupancy query: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
@@ -2192,7 +2275,8 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         g.w1 = meta->w1; g.w2 = meta->w2; g.v_ref = meta->v_ref; g.y_ref = meta->y_ref; g.psi_max = meta->psi_max;
         g.L = c->L; g.blob = c->d_blob; g.coef = sc.coef_out; g.cost_out = sc.cost_out; g.argmin_out = sc.argmin_out;
     }
-    const size_t nscratch = 2 + 2 * (size_t)S;
+    const int G = (int)b->groups.size();
+    const size_t nscratch = 2 + 2 * (size_t)S + G;
     std::vector<SolveArgs> cold(b->args);
     for (auto& a : cold) { a.warm_c = nullptr; a.warm_l = nullptr; }
     e = cudaMalloc(&b->d_args, sizeof(SolveArgs) * S);
@@ -2200,13 +2284,17 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
     if (e == cudaSuccess) e = cudaMalloc(&b->d_sargs, sizeof(ScoreArgs) * S);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * std::max(1, b->total));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_fb_items, sizeof(int2) * std::max(1, b->total));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * (2 + G));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_gitems, sizeof(int2) * std::max<size_t>(1, gitems.size()));
+    if (e == cudaSuccess && !gitems.empty())
+        e = cudaMemcpy(b->d_gitems, gitems.data(), sizeof(int2) * gitems.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_scratch, sizeof(unsigned long long) * nscratch);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_args, b->args.data(), sizeof(SolveArgs) * S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_args_cold, cold.data(), sizeof(SolveArgs) * S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        const int counts[2] = {b->total, 0};
-        e = cudaMemcpy(b->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice);
+        std::vector<int> counts{b->total, 0};
+        for (const auto& g : b->groups) counts.push_back(g.total);
+        e = cudaMemcpy(b->d_counts, counts.data(), sizeof(int) * counts.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_sargs, b->sargs.data(), sizeof(ScoreArgs) * S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_scratch, 0, sizeof(unsigned long long) * nscratch);
@@ -2221,8 +2309,8 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
 extern "C" int mmpc_batch_set_schedule(mmpc_batch* b, int schedule)
 {
     if (!b) return batch_fail("mmpc_batch_set_schedule: NULL batch", MMPC_ERR_NOT_SETUP);
-    if (schedule < 1 || schedule > 3) return batch_fail("mmpc_batch_set_schedule: schedule must be 1, 2 or 3", MMPC_ERR_INVALID_ARG);
-    const std::vector<int2> items = batch_items(b, schedule);
+    if (schedule < 1 || schedule > 4) return batch_fail("mmpc_batch_set_schedule: schedule must be 1 to 4", MMPC_ERR_INVALID_ARG);
+    std::vector<int2> items = batch_items(b, schedule == 4 ? 2 : schedule);
     if (b->total > 0) {
         cudaError_t e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return batch_fail(std::string("mmpc_batch_set_schedule: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
@@ -2236,16 +2324,33 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
     using namespace mmpc;
     if (!b) return batch_fail("mmpc_batch_run: NULL batch", MMPC_ERR_NOT_SETUP);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    batch_reset_kernel<<<1, 256, 0, st>>>(b->d_scratch, b->S, b->d_counts + 1);
+    const int G = (int)b->groups.size();
+    batch_reset_kernel<<<1, 256, 0, st>>>(b->d_scratch, b->S, G, b->d_counts + 1);
     if (b->total > 0) {
-        using KernT = void (*)(const SolveArgs*, const int2*, const int*, unsigned long long*);
-        reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args, b->d_items, b->d_counts,
-                                                                            b->d_scratch);
+        using KernT = void (*)(const SolveArgs*, const int2*, const int*, unsigned long long*, unsigned long long*);
+        if (b->schedule == 4) {
+            // one right-sized persistent launch per horizon group, on forked
+            // streams joined back before scoring (capturable in a graph)
+            cudaEventRecord(b->fork, st);
+            for (int gi = 0; gi < G; ++gi) {
+                const auto& g = b->groups[gi];
+                cudaStreamWaitEvent(g.stream, b->fork, 0);
+                reinterpret_cast<KernT>(g.kern)<<<g.grid, g.threads, g.smem, g.stream>>>(
+                    b->d_args, b->d_gitems + g.offset, b->d_counts + 2 + gi, b->d_scratch,
+                    b->d_scratch + 2 + 2 * b->S + gi);
+                cudaEventRecord(g.done, g.stream);
+                cudaStreamWaitEvent(st, g.done, 0);
+            }
+        } else {
+            reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args, b->d_items, b->d_counts,
+                                                                                b->d_scratch, b->d_scratch);
+        }
         if (b->fallback && b->any_warm) {
             fallback_compact_kernel<<<std::min(1024, (b->total + 255) / 256), 256, 0, st>>>(
                 b->d_args, b->d_items, b->total, b->d_fb_items, b->d_counts + 1, b->d_scratch);
             reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args_cold, b->d_fb_items,
-                                                                                b->d_counts + 1, b->d_scratch);
+                                                                                b->d_counts + 1, b->d_scratch,
+                                                                                b->d_scratch);
         }
         const int wpb = 8;
         const int sgrid = (b->total + wpb - 1) / wpb;
@@ -2285,7 +2390,7 @@ extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
     int best = 1;
     float best_ms = 1e30f;
     int rc = MMPC_OK;
-    for (int sch = 1; sch <= 3 && rc == MMPC_OK; ++sch) {
+    for (int sch = 1; sch <= 4 && rc == MMPC_OK; ++sch) {
         rc = mmpc_batch_set_schedule(b, sch);
         if (rc == MMPC_OK) rc = mmpc_batch_run(b, stream);  // warm-up
         float total = 0.f;
