@@ -64,6 +64,11 @@ def workload_name(params, B, m):
     return f"highway_B{B}_m{m}_N{params['N']}_n{params['n']}_K{params['iters']}_tol{TOL:g}"
 
 
+# DRAM bytes (read + write) of one solve launch, from an ncu capture of that
+# workload's kernel as it stands (profiles/am_solve_kernel_*.md); an entry must
+# be measured again whenever the kernel changes.
+SOLVE_DRAM_BYTES = {"highway_B1024_m50_N100_n12_K100_tol0.01": 128256}
+
 OPS_PER_ELEMENT = 10  # FP32 lane ops per evaluated obstacle-sample pair
 
 
@@ -286,7 +291,10 @@ def run_mine(args):
                    "check_every": CHECK_EVERY, "scenes_per_gpu": 1, "start": "cold",
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
         "roofline": {"bound": "alu", "kernel": "am_solve_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": None,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak,
+                     "traffic": (SOLVE_DRAM_BYTES.get(workload_name(params, B, m))
+                                 if params["cull"] and params["variant"] == 0 else None),
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz",
                      "ops_per_launch": ops, "launch_ms": solve_avg,
                      "ops_basis": "every obstacle-sample pair of Eq. split_alpha_o at 10 ops plus 15 n contraction "
@@ -579,15 +587,19 @@ def _oracle_run(sc, params, idx, threads):
     return dt, conv
 
 
-def cpu_baseline(sc, params, sample_stride=4):
+def cpu_baseline(sc, params, sample_stride=4, single_sample=16):
     """The FP64 oracle, as it stands, on the host cores, on every
-    `sample_stride`-th goal of the same scene."""
+    `sample_stride`-th goal of the same scene (all cores, OpenMP over
+    trajectories), and on `single_sample` of those goals single-threaded."""
     threads = os.cpu_count() or 1
     idx = np.arange(0, len(sc.goals), sample_stride)
     dt, conv = _oracle_run(sc, params, idx, threads)
+    dt1, _ = _oracle_run(sc, params, idx[:single_sample], 1)
     return {"value": len(idx) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{len(idx)} of {len(sc.goals)} goals (every {sample_stride}th), same scene and stopping rule",
-            "converged_fraction": conv / len(idx), "seconds": dt}
+            "converged_fraction": conv / len(idx), "seconds": dt,
+            "single_thread": {"value": min(single_sample, len(idx)) / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"the first {min(single_sample, len(idx))} goals of that sample"}}
 
 
 def run_reference(args):

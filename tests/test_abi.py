@@ -88,9 +88,10 @@ def test_builder_argument_errors():
         with pytest.raises(mmpc.MmpcError) as ei:
             mmpc.mmpc_build(mmpc.make_params(**kw), 10)
         assert ei.value.code == code, bad
-    with pytest.raises(mmpc.MmpcError) as ei:
-        mmpc.mmpc_build(mmpc.make_params(**good), -1)
-    assert ei.value.code == mmpc.MMPC_ERR_SHAPE
+    for m in (-1, 1025):
+        with pytest.raises(mmpc.MmpcError) as ei:
+            mmpc.mmpc_build(mmpc.make_params(**good), m)
+        assert ei.value.code == mmpc.MMPC_ERR_SHAPE
     assert mmpc.mmpc_problem_size(4, 12) == 0
     assert mmpc.mmpc_problem_size(100, 17) == 0
 

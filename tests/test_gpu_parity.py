@@ -338,3 +338,24 @@ def test_precision_workload_sampled(capsys):
               f"all: median {np.median(err):.2e}; meta cost rel error max {rel.max() if rel.size else 0:.2e}; "
               f"argmin gpu {am_gpu} oracle {am_orc}")
     assert rel.size == 0 or rel.max() <= U.COST_RTOL * 10
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("N,n,m,B,iters", [
+    (8, 7, 2, 1, 10),       # the smallest horizon, one goal
+    (32, 12, 1024, 2, 5),   # the largest obstacle count
+    (100, 12, 50, 3, 0),    # no iteration: the cold start itself
+])
+def test_extreme_shapes(N, n, m, B, iters, variant):
+    sc = scenes.scene_custom(seed=N + m + B, B=B, m=m, N=N, n=n, x_range=(-100.0, 400.0))
+    params = dict(sc.params)
+    params.update(iters=iters, variant=variant, tol=0.0)
+    ego, obst, goals = _scene_arrays(sc)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    gpu = U.gpu_solve(params, ego, obst, goals)
+    if iters == 0:
+        # the boundary-only QP: well conditioned, no iteration to amplify rounding
+        assert np.max(U.pos_err(params, gpu["coef"], orc["coef"])) <= 1e-4
+        assert np.all(gpu["iters"] == 0)
+    else:
+        _check_parity(params, ego, obst, goals, gpu, orc)
