@@ -235,28 +235,25 @@ def run_mine(args):
     ms = sum(step_ms) / K
     solve_avg = sum(solve_ms) / K
 
-    # end to end through the public API with host buffers: pinned inputs
-    # copied in, result (coefficients, residuals, costs, argmin) copied out
+    # end to end through the public API with host buffers: one mmpc_step_host
+    # call per step copies the pinned inputs in, solves, scores, copies the
+    # coefficients, residuals, costs and argmin back and waits for the stream
     Ke = min(K, args.e2e_steps)
-    h_in = [torch.tensor(np.asarray(a, dtype=np.float32)).pin_memory() for a in (sc.ego, sc.obst, sc.goals)]
+    h_in = [torch.tensor(np.asarray(a, dtype=np.float32)).contiguous().pin_memory()
+            for a in (sc.ego, sc.obst.reshape(-1, 4), sc.goals)]
     h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (coef, resid, cost, argmin)]
-    d_in = [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in h_in]
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = sum(t.numel() * t.element_size() for t in h_out)
     e2e_units = 0
+    best = -1
     torch.cuda.synchronize(dev)
     te = time.perf_counter()
     for _ in range(Ke):
-        for d, h in zip(d_in, h_in):
-            d.copy_(h, non_blocking=True)
-        mmpc.mmpc_solve(solver.ctx, d_in[0], d_in[1], d_in[2], coef, None, None, None, resid, iters, stream)
-        mmpc.mmpc_score(solver.ctx, meta, coef, cost, argmin, stream)
-        for h, d in zip(h_out, (coef, resid, cost, argmin)):
-            h.copy_(d, non_blocking=True)
-        stream.synchronize()
-        e2e_units += int((h_out[1][:, :3].max(dim=1).values <= TOL).sum())
+        mmpc.mmpc_step_host(solver.ctx, meta, h_in[0], h_in[1] if m else None, h_in[2], h_out[0], h_out[2], h_out[3],
+                            h_out[1], stream)
+        best = int(h_out[3][0])  # the step's result, read on the host
     e2e_ms = (time.perf_counter() - te) * 1e3 / Ke
-
+    e2e_units = int((h_out[1][:, :3].max(dim=1).values <= TOL).sum()) * Ke
     e2e_conv = e2e_units / Ke
     agg = combine_ranks(dict(units=B, ms=ms, e2e_units=B, e2e_ms=e2e_ms), world, dist)
     conv_agg = combine_ranks(dict(units=units_per_step, ms=ms, e2e_units=e2e_conv, e2e_ms=e2e_ms), world, dist)
@@ -305,7 +302,8 @@ def run_mine(args):
                      "executed_achieved": exec_ops / (solve_avg * 1e-3) / 1e12,
                      "sfu_frac": sfu_ops / (solve_avg * 1e-3) / (SM_COUNT * SFU_PER_SM * SM_MAX_MHZ * 1e6)},
         "e2e": {"value": agg["e2e_units"] / (agg["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": agg["e2e_ms"], "steps": Ke},
+                "d2h_bytes_per_step": d2h, "ms_per_step": agg["e2e_ms"], "steps": Ke,
+                "api": "mmpc_step_host (one C-ABI call per step, pinned host buffers)", "best_goal": best},
         "gpu_launches": 2 * K,
         "clocks": clocks,
         "detail": {"converged_per_step": conv_agg["units"], "trajectories_per_step": B * world,

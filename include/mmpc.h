@@ -173,6 +173,19 @@ typedef struct {
 int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coef, int B, float* cost_out,
                int* argmin_out, void* stream);
 
+/* One MPC step through host memory (Sec. III: solve the batch, score it,
+ * take the best): copies ego [4], obst [m][4] and goals [B][3] from host
+ * buffers into device buffers the context owns, runs mmpc_solve (cold start)
+ * and mmpc_score on `stream`, copies coef [B][3n], resid [B][4] (may be
+ * NULL), cost [B] and argmin [1] back to host buffers, and waits for the
+ * stream.  Host buffers should be page-locked for the copies to run
+ * asynchronously.  The device buffers grow on demand: the first call with a
+ * larger B allocates (after synchronising the stream), later calls allocate
+ * nothing.  m must be the m of mmpc_setup.  Errors as mmpc_solve / mmpc_score. */
+int mmpc_step_host(mmpc_ctx* ctx, const mmpc_meta* meta, const float* ego, const float* obst, int m,
+                   const float* goals, int B, float* coef_out, float* resid_out, float* cost_out, int* argmin_out,
+                   void* stream);
+
 /* ---- Batches of scenes ---------------------------------------------------
  * Many independent scenes (MPC problems of different vehicles, or of one
  * vehicle at different times) solved and scored together: one persistent

@@ -1582,6 +1582,11 @@ struct mmpc_ctx {
     int sm_count = -1;                        // SMs of the device (queried on the first solve)
     int last_variant = 0;
     std::string err = "no error";
+    // device buffers of mmpc_step_host, grown on demand: inputs (ego, obstacles,
+    // goals) and outputs (coef, resid, iters, cost, argmin) for up to host_cap goals
+    float* h_in = nullptr;
+    float* h_out = nullptr;
+    int host_cap = 0;
 };
 
 namespace {
@@ -1843,12 +1848,65 @@ extern "C" int mmpc_take_work_count(mmpc_ctx* ctx, unsigned long long* elements)
     return e == cudaSuccess ? MMPC_OK : cuda_fail(ctx, e, "mmpc_take_work_count");
 }
 
+extern "C" int mmpc_step_host(mmpc_ctx* ctx, const mmpc_meta* meta, const float* ego, const float* obst, int m,
+                              const float* goals, int B, float* coef_out, float* resid_out, float* cost_out,
+                              int* argmin_out, void* stream)
+{
+    if (!ctx || !ctx->d_blob) return fail(nullptr, MMPC_ERR_NOT_SETUP, "context not set up");
+    if (!meta || !ego || (m > 0 && !obst) || !argmin_out || (B > 0 && (!goals || !coef_out || !cost_out)))
+        return fail(ctx, MMPC_ERR_INVALID_ARG, "NULL pointer argument");
+    if (B < 0) return fail(ctx, MMPC_ERR_SHAPE, "B < 0");
+    if (m != ctx->m) return fail(ctx, MMPC_ERR_SHAPE, "m differs from the m of mmpc_setup");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int n = ctx->p.n;
+    // device layout: in = [ego 4 | obst 4m | goals 3B], out = [coef 3nB | resid 4B | cost B | iters B | argmin 1]
+    if (B > ctx->host_cap || !ctx->h_in) {
+        const int cap = std::max(B, std::max(1, 2 * ctx->host_cap));
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) { cudaFree(ctx->h_in); cudaFree(ctx->h_out); ctx->h_in = nullptr; ctx->h_out = nullptr; }
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_in, sizeof(float) * (4 + 4 * (size_t)m + 3 * (size_t)cap));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_out, sizeof(float) * ((3 * (size_t)n + 6) * cap + 1));
+        if (e != cudaSuccess) { ctx->host_cap = 0; return cuda_fail(ctx, e, "mmpc_step_host buffers"); }
+        ctx->host_cap = cap;
+    }
+    float* d_ego = ctx->h_in;
+    float* d_obst = d_ego + 4;
+    float* d_goals = d_obst + 4 * (size_t)m;
+    float* d_coef = ctx->h_out;
+    float* d_resid = d_coef + 3 * (size_t)n * B;
+    float* d_cost = d_resid + 4 * (size_t)B;
+    int* d_iters = reinterpret_cast<int*>(d_cost + B);
+    int* d_argmin = d_iters + B;
+    // one host->device copy of the inputs when they are contiguous in host memory
+    cudaError_t e = cudaMemcpyAsync(d_ego, ego, sizeof(float) * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(d_obst, obst, sizeof(float) * 4 * (size_t)m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && B > 0) e = cudaMemcpyAsync(d_goals, goals, sizeof(float) * 3 * (size_t)B, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mmpc_step_host input copy");
+    int rc = mmpc_solve(ctx, d_ego, m ? d_obst : nullptr, m, d_goals, B, nullptr, nullptr, d_coef, nullptr, d_resid,
+                        d_iters, stream);
+    if (rc != MMPC_OK) return rc;
+    rc = mmpc_score(ctx, meta, d_coef, B, d_cost, d_argmin, stream);
+    if (rc != MMPC_OK) return rc;
+    // the outputs are contiguous on the device: coef, resid, cost as one block when the host asks for all three
+    e = cudaSuccess;
+    if (B > 0) e = cudaMemcpyAsync(coef_out, d_coef, sizeof(float) * 3 * (size_t)n * B, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && B > 0 && resid_out)
+        e = cudaMemcpyAsync(resid_out, d_resid, sizeof(float) * 4 * (size_t)B, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && B > 0)
+        e = cudaMemcpyAsync(cost_out, d_cost, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(argmin_out, d_argmin, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(ctx, e, "mmpc_step_host");
+}
+
 extern "C" void mmpc_destroy(mmpc_ctx* ctx)
 {
     if (!ctx) return;
     cudaDeviceSynchronize();
     cudaFree(ctx->d_blob);
     cudaFree(ctx->d_scratch);
+    cudaFree(ctx->h_in);
+    cudaFree(ctx->h_out);
     delete ctx;
 }
 

@@ -30,7 +30,7 @@ MMPC_META_ABS = 2
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
             "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
             "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
-            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_fallbacks")
+            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_fallbacks", "mmpc_step_host")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
 
@@ -136,6 +136,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_batch_times.restype = ctypes.c_int
     L.mmpc_batch_destroy.argtypes = [vp]
     L.mmpc_batch_destroy.restype = None
+    L.mmpc_step_host.argtypes = [vp, ctypes.POINTER(MmpcMeta), fp, fp, ctypes.c_int, fp, ctypes.c_int, fp, fp, fp, ip,
+                                 vp]
+    L.mmpc_step_host.restype = ctypes.c_int
     L.mmpc_batch_set_fallback.argtypes = [vp, ctypes.c_int]
     L.mmpc_batch_set_fallback.restype = ctypes.c_int
     L.mmpc_batch_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
@@ -233,6 +236,33 @@ def mmpc_score_static(meta: MmpcMeta, N: int, n: int, P, Pd, coef, cost_out, arg
                                  _ptr(cost_out), _ptr(argmin_out, "int32"), _stream(stream))
     if rc != MMPC_OK:
         _err(None, rc)
+
+
+def _hptr(t, dtype_name="float32"):
+    """Host pointer of a contiguous CPU tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("expected a CPU tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mmpc_step_host(ctx, meta: MmpcMeta, ego, obst, goals, coef_out, cost_out, argmin_out, resid_out=None,
+                   stream=None) -> None:
+    """One MPC step through host memory (CPU tensors, ideally pinned):
+    inputs copied in, solve + score, outputs copied back, stream waited."""
+    m = 0 if obst is None else int(obst.shape[0])
+    B = int(goals.shape[0])
+    rc = lib().mmpc_step_host(ctx, ctypes.byref(meta), _hptr(ego), _hptr(obst) if m else None, m, _hptr(goals), B,
+                              _hptr(coef_out), _hptr(resid_out), _hptr(cost_out), _hptr(argmin_out, "int32"),
+                              _stream(stream))
+    if rc != MMPC_OK:
+        _err(ctx, rc)
 
 
 def mmpc_take_work_count(ctx) -> int:

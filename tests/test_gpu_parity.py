@@ -359,3 +359,34 @@ def test_extreme_shapes(N, n, m, B, iters, variant):
         assert np.all(gpu["iters"] == 0)
     else:
         _check_parity(params, ego, obst, goals, gpu, orc)
+
+
+def test_step_through_host_memory():
+    """mmpc_step_host (copies in, solve, score, copies out) returns exactly what
+    the device-buffer calls return; the device buffers it grows are reused."""
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc
+    sc = scenes.scene_custom(41, 64, 12, N=100)
+    params = dict(sc.params)
+    m = sc.obst.shape[0]
+    meta = mmpc.make_meta(**sc.meta)
+    s = mmpc.Solver(params, m)
+    n = s.n
+    t = lambda a: torch.tensor(np.asarray(a, dtype=np.float32)).contiguous()  # noqa: E731
+    ego, obst, goals = t(sc.ego), t(sc.obst).reshape(m, 4), t(sc.goals)
+    for B in (64, 16, 64):  # grows once, then reuses
+        hc = torch.zeros((B, 3 * n)).pin_memory()
+        hr = torch.zeros((B, 4)).pin_memory()
+        hcost = torch.zeros(B).pin_memory()
+        ham = torch.zeros(1, dtype=torch.int32).pin_memory()
+        mmpc.mmpc_step_host(s.ctx, meta, ego.pin_memory(), obst.pin_memory(), goals[:B].contiguous().pin_memory(),
+                            hc, hcost, ham, hr)
+        d = s.solve(ego.cuda(), obst.cuda(), goals[:B].contiguous().cuda(), want_lam=False)
+        cost, am = s.score(meta, d.coef)
+        torch.cuda.synchronize()
+        assert torch.equal(hc, d.coef.cpu()) and torch.equal(hr, d.resid.cpu())
+        assert torch.equal(hcost, cost.cpu()) and int(ham.item()) == int(am.item())
+    with pytest.raises(mmpc.MmpcError):
+        mmpc.mmpc_step_host(s.ctx, meta, ego, obst[:3].contiguous(), goals, hc, hcost, ham)
+    s.close()
