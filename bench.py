@@ -40,6 +40,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "trajectories/s to residual<=1e-2 m, warm-started vs plain GPU; % of roofline"
+STALL = (1.0, 0.5)  # opt-in stall stop: residual > 1 m and not halved over the last two checks
 UNIT = "trajectories/s"
 TOL = 1e-2
 CHECK_EVERY = 10
@@ -178,6 +179,8 @@ def run_mine(args):
 
     sc, params = workload(seed=rank, kind=args.workload)
     params["cull"] = 0 if args.no_cull else 1
+    if args.stall:
+        params.update(stall_tol=STALL[0], stall_ratio=STALL[1])
     params["variant"] = args.variant
     B, m, n = len(sc.goals), sc.obst.shape[0], params["n"]
     solver = mmpc.Solver(params, m)
@@ -286,6 +289,7 @@ def run_mine(args):
                    "culling": bool(params["cull"]), "kernel_variant": params["variant"],
                    "samples": N, "coefficients": n, "max_iters": params["iters"], "tol_m": TOL,
                    "check_every": CHECK_EVERY, "scenes_per_gpu": 1, "start": "cold",
+                   "stall_stop": list(STALL) if args.stall else None,
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
         "roofline": {"bound": "alu", "kernel": "am_solve_kernel", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak,
@@ -357,6 +361,9 @@ def run_batch(args):
     # all inputs in one flat device buffer (one host->device copy per step)
     pieces, views = [], []
     off = 0
+    if args.stall:
+        for _, p in work:
+            p.update(stall_tol=STALL[0], stall_ratio=STALL[1])
     for sc, _ in work:
         shapes = [(4,), (sc.obst.shape[0], 4), (len(sc.goals), 3)]
         arrs = [sc.ego, sc.obst.reshape(-1, 4), sc.goals]
@@ -472,6 +479,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"highway_batch_S{S}_B16-512_m5-40_N{'-'.join(map(str, Ns))}_n12_K100_tol{TOL:g}",
                    "scenes_per_gpu": S, "trajectories_per_gpu": Btot, "schedule": schedule,
+                   "stall_stop": list(STALL) if args.stall else None,
                    "graph": "one CUDA graph replay per step", "start": "cold",
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
         "roofline": {"bound": "alu", "kernel": "am_solve_batch_kernel", "achieved": achieved, "peak": peak,
@@ -534,6 +542,11 @@ def run_warm(args):
     sampler.start()
     dense = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=args.steps, seed=10**6 + rank, plain=True)
     clocks = sampler.stop()
+    dense_stall = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=args.steps, seed=10**6 + rank, stall=STALL)
+    for k in ("cold", "warm", "warm_fallback"):
+        dense_stall[f"{k}_vs_plain"] = dense_stall[k]["trajectories_per_s"] / dense["plain"]["trajectories_per_s"]
+        dense_stall[f"{k}_converged_vs_plain"] = (dense_stall[k]["converged_per_s"] /
+                                                  dense["plain"]["converged_per_s"])
     sparse = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=max(3, args.steps // 2), seed=2 * 10**6 + rank,
                                 obstacles=10, x_range=(-30.0, 120.0))
     ws.close()
@@ -565,7 +578,8 @@ def run_warm(args):
         "e2e": None,
         "gpu_launches": 12 * args.steps,
         "clocks": clocks,
-        "detail": {"dense_50_obstacles": dense, "sparse_10_obstacles": sparse, "val_loss": val,
+        "detail": {"dense_50_obstacles": dense, "dense_50_obstacles_stall_stop": dense_stall,
+                   "sparse_10_obstacles": sparse, "val_loss": val,
                    "network_forward": fwd,
                    "loss_first_last": [losses[0][1], losses[-1][1]], "dataset_s": t1 - t0, "train_s": t2 - t1},
     }
@@ -652,6 +666,8 @@ def main():
                     help="scene: one 1024-goal scene per GPU; batch: 256 uneven scenes per GPU in one graph; "
                          "warm: learned warm start (trained in the run) against the cold start; precision: "
                          "one 16384-goal scene, 30 obstacles, N = 200, n = 16")
+    ap.add_argument("--stall", action="store_true",
+                    help="opt-in stall stop (residual > 1 m and not halved over two checks) for scene and batch")
     ap.add_argument("--warm-train-scenes", type=int, default=200_000)
     ap.add_argument("--warm-steps", type=int, default=4000)
     ap.add_argument("--warm-eval-scenes", type=int, default=4096)

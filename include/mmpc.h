@@ -88,6 +88,13 @@ typedef struct {
     int variant;     /* kernel: 1 = one time sample per thread (N <= 256), 2 = two
                         samples per thread; 0 = automatic (1 for batches of at most one
                         trajectory per SM, else 2).  Results agree to rounding. */
+    float stall_tol;   /* stall stop (opt-in, <= 0 disables): at a residual check k >= 2
+                          check_every, a trajectory also stops when its convergence
+                          residual is above stall_tol and above stall_ratio times the
+                          residual of two checks earlier (it is far from the target and
+                          no longer closing in).  Not in the paper: a serving option for
+                          scenes whose infeasible goals would spend the whole budget. */
+    float stall_ratio; /* in (0, 1] when stall_tol > 0 */
 } mmpc_params;
 
 typedef struct mmpc_ctx mmpc_ctx;

@@ -150,6 +150,8 @@ std::string check_params(const mmpc_params* p)
     if (p->check_every < 1) return "check_every must be >= 1";
     if (std::isnan(p->tol)) return "tol is NaN";
     if (p->variant < 0 || p->variant > 2) return "variant must be 0, 1 or 2";
+    if (std::isnan(p->stall_tol)) return "stall_tol is NaN";
+    if (p->stall_tol > 0.f && !(p->stall_ratio > 0.f && p->stall_ratio <= 1.f)) return "stall_ratio must be in (0, 1]";
     if (p->variant == 1 && p->N > 256) return "variant 1 needs N <= 256";
     return "";
 }

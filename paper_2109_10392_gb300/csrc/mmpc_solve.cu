@@ -129,7 +129,7 @@ static BlobLayout blob_layout(int N, int NC)
 
 struct SolveArgs {
     int N, n, m, B, iters, check_every, cull;
-    float rho, a, b, inv_a, inv_b, v_min, v_max, a_max, tol;
+    float rho, a, b, inv_a, inv_b, v_min, v_max, a_max, tol, stall_tol, stall_ratio;
     BlobLayout L;
     const float* blob;
     const float* ego;
@@ -769,6 +769,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
 
     float2 xd = f2(0.f), yd = f2(0.f), theta = f2(0.f);
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
+    float rh1 = INFINITY, rh2 = INFINITY;  // convergence residuals of the last two checks
     float* const dstB = rs_dst(RSB, red1, warp, RSB, lane);  // this lane's reduce-scatter outputs
     float* const dstD = rs_dst(VD, red2, warp, RSD, lane);
     int kit = 0;
@@ -911,9 +912,17 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         const float qc = dot_dup<NC>(blob + L.Q + kk * k_stride(NC), own);
         const float u = act ? (lam - qc - rho * ftd) : 0.f;
         bool done = kit >= iters;
-        if (!first && check && A.tol > 0.f && kit % A.check_every == 0) {
+        if (check && kit % A.check_every == 0 && (A.tol > 0.f || A.stall_tol > 0.f)) {
             const float conv = fmaxf(sqrtf(rsum[0]), fmaxf(sqrtf(rsum[1]), sqrtf(rsum[2])));
-            done = done || conv <= A.tol;
+            if (!first) {
+                if (A.tol > 0.f) done = done || conv <= A.tol;
+                // stall stop: far from the target and not closing in over two checks
+                if (A.stall_tol > 0.f && kit >= 2 * A.check_every && conv > A.stall_tol &&
+                    conv > A.stall_ratio * rh2)
+                    done = true;
+            }
+            rh2 = rh1;
+            rh1 = conv;
         }
         if (!done) {
             // Eq. lin_solve_xy_2 in increment form, K11 applied as hi + lo
@@ -1214,6 +1223,7 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
 
     float xd = 0.f, yd = 0.f, theta = 0.f;
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
+    float rh1 = INFINITY, rh2 = INFINITY;  // convergence residuals of the last two checks
     float* const dstB = rs_dst(RSB, red1, warp, RSB, lane);
     float* const dstD = rs_dst(VD, red2, warp, RSD, lane);
     int kit = 0;
@@ -1330,9 +1340,17 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
         const float qc = dot_plain<NC>(blob + (L.Q - base) + kk * k_stride(NC), own);
         const float u = act ? (lam - qc - rho * ftd) : 0.f;
         bool done = kit >= iters;
-        if (!first && check && A.tol > 0.f && kit % A.check_every == 0) {
+        if (check && kit % A.check_every == 0 && (A.tol > 0.f || A.stall_tol > 0.f)) {
             const float conv = fmaxf(sqrtf(rsum[0]), fmaxf(sqrtf(rsum[1]), sqrtf(rsum[2])));
-            done = done || conv <= A.tol;
+            if (!first) {
+                if (A.tol > 0.f) done = done || conv <= A.tol;
+                // stall stop: far from the target and not closing in over two checks
+                if (A.stall_tol > 0.f && kit >= 2 * A.check_every && conv > A.stall_tol &&
+                    conv > A.stall_ratio * rh2)
+                    done = true;
+            }
+            rh2 = rh1;
+            rh1 = conv;
         }
         if (!done) {
             if (act) vec[k] = u;
@@ -1777,6 +1795,7 @@ extern "C" int mmpc_solve(mmpc_ctx* ctx, const float* ego, const float* obst, in
     a.rho = (float)p.rho; a.a = (float)p.a; a.b = (float)p.b;
     a.inv_a = (float)(1.0 / p.a); a.inv_b = (float)(1.0 / p.b);
     a.v_min = (float)p.v_min; a.v_max = (float)p.v_max; a.a_max = (float)p.a_max; a.tol = p.tol;
+    a.stall_tol = p.stall_tol; a.stall_ratio = p.stall_ratio;
     a.L = ctx->L;
     a.blob = ctx->d_blob;
     a.ego = ego; a.obst = obst; a.goals = goals; a.warm_c = warm_coef; a.warm_l = warm_lam;
@@ -2320,6 +2339,7 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         a.rho = (float)p.rho; a.a = (float)p.a; a.b = (float)p.b;
         a.inv_a = (float)(1.0 / p.a); a.inv_b = (float)(1.0 / p.b);
         a.v_min = (float)p.v_min; a.v_max = (float)p.v_max; a.a_max = (float)p.a_max; a.tol = p.tol;
+        a.stall_tol = p.stall_tol; a.stall_ratio = p.stall_ratio;
         a.L = c->L;
         a.blob = c->d_blob;
         a.ego = sc.ego; a.obst = sc.obst; a.goals = sc.goals; a.warm_c = sc.warm_coef; a.warm_l = sc.warm_lam;

@@ -50,6 +50,8 @@ class MmpcParams(ctypes.Structure):
         ("check_every", ctypes.c_int),
         ("cull", ctypes.c_int),
         ("variant", ctypes.c_int),
+        ("stall_tol", ctypes.c_float),
+        ("stall_ratio", ctypes.c_float),
     ]
 
 
@@ -148,9 +150,10 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
 
 
 def make_params(T, N, n, rho, a, b, v_min, v_max, a_max, iters=100, tol=0.0, check_every=10, cull=1, variant=0,
-                **_ignored) -> MmpcParams:
+                stall_tol=0.0, stall_ratio=0.5, **_ignored) -> MmpcParams:
     return MmpcParams(float(T), int(N), int(n), float(rho), float(a), float(b), float(v_min), float(v_max),
-                      float(a_max), int(iters), float(tol), int(check_every), int(cull), int(variant))
+                      float(a_max), int(iters), float(tol), int(check_every), int(cull), int(variant),
+                      float(stall_tol), float(stall_ratio))
 
 
 def make_meta(kind=MMPC_META_ABS, w1=1.0, w2=0.25, v_ref=20.0, y_ref=-5.25, psi_max_deg=13.0, psi_max=None,

@@ -231,7 +231,8 @@ def validation_loss(ws: WarmStart, X, T):
 
 
 def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256, seed: int = 10**6,
-             reps: int = 3, tol: float = 1e-2, obstacles=None, x_range=None, plain: bool = False):
+             reps: int = 3, tol: float = 1e-2, obstacles=None, x_range=None, plain: bool = False,
+             stall: tuple | None = None):
     """Cold start against warm start (+ cold fallback) on S fresh scenes x B
     goals, each timed as one CUDA graph replay (warm: features, network,
     decode, solve, fallback solve, score).  Returns a dict of results."""
@@ -242,6 +243,9 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
     ego, obst, goals = _dev(ego, device), _dev(obst, device), _dev(goals, device)
     p = dict(cfg.params)
     p.update(tol=tol, check_every=10)
+    pb = dict(p)  # the batched variants: with the opt-in stall stop when given
+    if stall is not None:
+        pb.update(stall_tol=float(stall[0]), stall_ratio=float(stall[1]))
     meta = mmpc.make_meta(**scenes.META_ABS)
     stream = torch.cuda.Stream(device)
     out = {}
@@ -297,13 +301,13 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
         del g_plain
         sv.close()
 
-    cold = mmpc.Batch.from_uniform(p, ego, obst, goals, meta)
+    cold = mmpc.Batch.from_uniform(pb, ego, obst, goals, meta)
     g_cold, ms = timed(cold.run)
     stats(cold, ms, "cold")
     cold_conv = (cold.flat["resid"].view(-1, 4)[:, :3].max(dim=1).values <= tol)
 
     buf = ws.buffers(S, B, device)
-    warm = mmpc.Batch.from_uniform(p, ego, obst, goals, meta, warm_coef=buf["coef"], warm_lam=buf["lam"])
+    warm = mmpc.Batch.from_uniform(pb, ego, obst, goals, meta, warm_coef=buf["coef"], warm_lam=buf["lam"])
     table = mlp.uniform_table(device, ego=ego, obst=obst, goals=goals, X=buf["X"], Y=buf["Y"], coef=buf["coef"],
                               lam=buf["lam"])
 
@@ -340,6 +344,7 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
         out["iters_both_converged"] = dict(cold=float(cold.flat["iters"][both].double().mean().item()),
                                            warm=float(warm_iters[both].double().mean().item()))
     out["scenes"], out["goals"], out["obstacles"], out["x_range"] = S, B, m, list(xr)
+    out["stall"] = None if stall is None else list(stall)
     out["speedup_trajectories_per_s"] = out["warm_fallback"]["trajectories_per_s"] / out["cold"]["trajectories_per_s"]
     if plain:
         out["batched_cold_vs_plain"] = out["cold"]["trajectories_per_s"] / out["plain"]["trajectories_per_s"]

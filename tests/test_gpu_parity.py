@@ -390,3 +390,40 @@ def test_step_through_host_memory():
     with pytest.raises(mmpc.MmpcError):
         mmpc.mmpc_step_host(s.ctx, meta, ego, obst[:3].contiguous(), goals, hc, hcost, ham)
     s.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_stall_stop(variant):
+    """The opt-in stall stop on a dense scene: (1) a trajectory it stops had,
+    at its last check, a residual above stall_tol and above stall_ratio times
+    the residual of two checks earlier (both read from fixed-count GPU runs);
+    (2) every trajectory that reaches tol without the rule reaches it with the
+    rule, at the same iteration, bit for bit; (3) the stopped iterates match the
+    oracle run for the same iteration counts (conditioning-aware bar)."""
+    sc = scenes.scene_large(0)
+    sel = np.arange(0, 1024, 8)
+    ego, obst, goals = _scene_arrays(sc)
+    goals = goals[sel]
+    base = dict(sc.params)
+    base.update(tol=1e-2, check_every=10, variant=variant)
+    stall = dict(base, stall_tol=1.0, stall_ratio=0.5)
+    g0 = U.gpu_solve(base, ego, obst, goals)
+    g1 = U.gpu_solve(stall, ego, obst, goals)
+    conv0 = np.max(g0["resid"][:, :3], axis=1) <= 1e-2
+    conv1 = np.max(g1["resid"][:, :3], axis=1) <= 1e-2
+    assert np.all(conv1[conv0])
+    assert np.array_equal(g1["coef"][conv0], g0["coef"][conv0]) and np.array_equal(g1["iters"][conv0], g0["iters"][conv0])
+    stopped = (g1["iters"] < base["iters"]) & ~conv1
+    assert stopped.mean() > 0.3, stopped.mean()  # the dense scene is mostly infeasible
+    assert g1["iters"].mean() < 0.75 * g0["iters"].mean()
+    fixed = dict(base, tol=0.0)
+    for K in np.unique(g1["iters"][stopped]):
+        idx = np.where(stopped & (g1["iters"] == K))[0]
+        rk = U.gpu_solve(dict(fixed, iters=int(K)), ego, obst, goals[idx])["resid"]
+        r2 = U.gpu_solve(dict(fixed, iters=int(K) - 20), ego, obst, goals[idx])["resid"]
+        ck, c2 = np.max(rk[:, :3], axis=1), np.max(r2[:, :3], axis=1)
+        assert np.all(ck > 1.0) and np.all(ck > 0.5 * c2), (K, ck, c2)
+        assert np.array_equal(rk, g1["resid"][idx])
+        pk = dict(fixed, iters=int(K))
+        orc = U.oracle_solve(pk, ego, obst, goals[idx])
+        _check_parity(pk, ego, obst, goals[idx], {"coef": g1["coef"][idx]}, orc, min_frac=0.0)
