@@ -49,6 +49,8 @@ class OrcParams(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("check_every", ctypes.c_int),
         ("psi_sign_printed", ctypes.c_int),
+        ("basis_bits", ctypes.c_int),
+        ("basis_split", ctypes.c_int),
     ]
 
 
@@ -77,6 +79,8 @@ def lib() -> ctypes.CDLL:
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         pp = ctypes.POINTER(OrcParams)
+        L.orc_round_bits.argtypes = [ctypes.c_double, ctypes.c_int]
+        L.orc_round_bits.restype = ctypes.c_double
         L.orc_invert.argtypes = [ctypes.c_int, dp, dp]
         L.orc_bernstein.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp]
         L.orc_boundary.argtypes = [dp, dp, dp, dp]
@@ -126,6 +130,8 @@ def params(**kw) -> OrcParams:
     p.iters = int(kw.get("iters", 100))
     p.tol = float(kw.get("tol", 0.0))
     p.check_every = int(kw.get("check_every", 1))
+    p.basis_bits = int(kw.get("basis_bits", 0))
+    p.basis_split = int(kw.get("basis_split", 0))
     p.psi_sign_printed = int(kw.get("psi_sign_printed", 0))
     return p
 
@@ -244,3 +250,9 @@ def positions(p: OrcParams, coef):
     coef = _f64(coef).reshape(-1, 3 * p.n)
     n = p.n
     return coef[:, :n] @ P.T, coef[:, n:2 * n] @ P.T, coef[:, 2 * n:] @ P.T
+
+
+def round_bits(x: float, k: int) -> float:
+    """x rounded to k significant bits, ties to even (the oracle's operand
+    rounding for the reduced-precision emulation)."""
+    return float(lib().orc_round_bits(float(x), int(k)))

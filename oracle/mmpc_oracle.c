@@ -78,6 +78,11 @@ typedef struct {
     double tol;    /* early-exit tolerance on the residual; <= 0: none */
     int check_every;      /* residual checked after iterations k*check_every */
     int psi_sign_printed; /* 1: lambda_psi update with the printed sign */
+    int basis_bits;       /* > 0: the basis operands (P, Pdot, Pddot and F) are rounded to this
+                             many significant bits (8: bfloat16, 11: TF32, 24: float32) after the
+                             KKT inverses are formed, to emulate reduced-precision operands of
+                             the contractions; 0: exact (the default) */
+    int basis_split;      /* 1: operands held as hi + lo, each rounded to basis_bits */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -222,6 +227,23 @@ static int params_ok(const orc_params* p)
     return 1;
 }
 
+/* x rounded to k significant bits, ties to even (the rounding of a float
+ * with a k-bit significand: 8 for bfloat16, 11 for TF32, 24 for float32;
+ * exponent range unlimited). */
+double orc_round_bits(double x, int k)
+{
+    if (x == 0.0 || !isfinite(x) || k <= 0) return x;
+    int e;
+    const double m = frexp(x, &e); /* x = m 2^e, 0.5 <= |m| < 1 */
+    return ldexp(nearbyint(ldexp(m, k)), e - k);
+}
+
+static double round_operand(double x, int k, int split)
+{
+    const double hi = orc_round_bits(x, k);
+    return split ? hi + orc_round_bits(x - hi, k) : hi;
+}
+
 static int prob_build(const orc_params* p, int m, orc_problem* pr)
 {
     memset(pr, 0, sizeof(*pr));
@@ -325,6 +347,17 @@ static int prob_build(const orc_params* p, int m, orc_problem* pr)
         if (rc == ORC_OK) rc = orc_invert(Dp, Kp, pass == 0 ? pr->Kpsi_inv : pr->K0psi_inv);
     }
     free(FtF); free(PtP); free(Kx); free(Kp);
+    if (rc == ORC_OK && p->basis_bits > 0) {
+        /* reduced-precision operands of the contractions (evaluations and
+         * transposed products); the KKT inverses stay exact */
+        const size_t Nn = (size_t)N * n, nf = (size_t)2 * pr->rows_axis * 2 * n;
+        for (size_t q = 0; q < Nn; ++q) {
+            pr->P[q] = round_operand(pr->P[q], p->basis_bits, p->basis_split);
+            pr->Pd[q] = round_operand(pr->Pd[q], p->basis_bits, p->basis_split);
+            pr->Pdd[q] = round_operand(pr->Pdd[q], p->basis_bits, p->basis_split);
+        }
+        for (size_t q = 0; q < nf; ++q) pr->F[q] = round_operand(pr->F[q], p->basis_bits, p->basis_split);
+    }
     if (rc != ORC_OK) prob_free(pr);
     return rc;
 }
