@@ -133,12 +133,18 @@ int mmpc_mlp_adamw(mmpc_mlp* net, float lr, void* stream);
 int mmpc_mlp_read(mmpc_mlp* net, int what, int layer, float* host, size_t count);
 int mmpc_mlp_write(mmpc_mlp* net, int what, int layer, const float* host, size_t count);
 
-/* Inference (mmpc_mlp_forward) on the tensor cores (on != 0) or the FP32
- * SIMT path (0, the default).  The tensor-core path runs each layer as a
- * tcgen05 GEMM with bfloat16 operands and float32 accumulation in tensor
- * memory: each layer's input (the features, then every hidden activation) is
- * rounded to bfloat16 (nearest even) as it is staged, where the SIMT path
- * keeps it in float32.  Training always uses the SIMT kernels. */
+/* Inference (mmpc_mlp_forward) on the tensor cores or the FP32 SIMT path.
+ * on = 0: SIMT (the default).  on = 1: the pipelined tcgen05 GEMM, operands
+ * fed by TMA through a ring of shared-memory stages, warp-specialised, two
+ * TMEM accumulators, persistent CTAs; it needs every layer input width to be
+ * a multiple of 8 and takes the single-stage kernel for any layer where that
+ * (or the tensor map) fails.  on = 2: the single-stage tcgen05 GEMM for every
+ * layer.  Both tensor-core paths use bfloat16 operands and float32
+ * accumulation in tensor memory: each layer's input (the features, then every
+ * hidden activation) is rounded to bfloat16 (nearest even), where the SIMT
+ * path keeps it in float32; the two give the same result up to the order of
+ * the float32 sums.  Other values of on: MMPC_ERR_INVALID_ARG.  Training
+ * always uses the SIMT kernels. */
 int mmpc_mlp_set_tensor_cores(mmpc_mlp* net, int on);
 
 /* Synchronises the device and reports MMPC_ERR_TIMEOUT if a bounded wait of

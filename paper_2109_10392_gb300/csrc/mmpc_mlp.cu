@@ -10,6 +10,7 @@
 // backward pass), the GELU derivative on the backward product, split-K
 // partial sums for the weight gradients reduced in a fixed order (so training
 // is deterministic).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -634,6 +635,313 @@ __global__ void __launch_bounds__(THREADS, 1) umma_gemm_kernel(int M, int N, int
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// The same GEMM fed by TMA and pipelined (the inference path when every width
+// is a multiple of 8): bfloat16 A [M][K] and Bt [N][K] come from tensor maps
+// into a ring of S stages; each K step of an operand is one TMA box of {64
+// elements, rows} in the 128-byte swizzle (rows of 128 B, their 16-byte chunks
+// permuted within 8-row atoms), which the MMA descriptors read as is.  Warp specialisation (one
+// elected lane each): warp 16 issues the TMA copies up to S stages ahead,
+// warp 17 the MMAs, committing each stage to its `empty` barrier and each
+// finished tile to its TMEM buffer's `full` barrier, so the tensor pipe is
+// never left waiting for a copy to be issued; warps 0-15 drain the
+// accumulators (four warps per TMEM sub-partition, every fourth 16-column
+// chunk each), add the bias, apply GELU, store, and release the buffer.  Two
+// TMEM accumulators, so the epilogue of one tile overlaps the loads and MMAs
+// of the next; persistent CTAs loop over the tiles.  Every wait is bounded and
+// records its expiry in the error word.
+// ---------------------------------------------------------------------------
+constexpr int TMA_STAGES = 4;
+constexpr int EPI_WARPS = 16;
+constexpr int TMA_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
+constexpr int TMA_THREADS = 32 * (EPI_WARPS + 2);
+
+// GELU of two lanes with fused multiply-adds only: x / 2 + g(x), where
+// g(x) = x (Phi(x) - 1/2) is even and entire in t = x^2; for |x| <= 5 a
+// degree-12 polynomial in u = 2 t / 25 - 1 (coefficients from
+// csrc/fit_gelu.py: least squares on Chebyshev nodes refined towards the
+// minimax), beyond it g = |x| / 2.  |error| < 2e-6 in float32 -- far below
+// the bfloat16 rounding the activations then undergo.
+__device__ __forceinline__ float2 gelu_poly2(float2 x)
+{
+    constexpr float P[13] = {-1.302992459e-02f, 2.610467188e-02f, -1.061521657e-02f, 1.563348621e-02f,
+                             -6.101960689e-02f, 8.403629065e-02f, -8.500314504e-02f, 9.675235301e-02f,
+                             -1.126994267e-01f, 1.391513944e-01f,  -2.346803546e-01f, 8.883196115e-01f,
+                             1.767047167e+00f};
+    const float2 t = __fmul2_rn(x, x);
+    const float2 u = __ffma2_rn(make_float2(fminf(t.x, 25.f), fminf(t.y, 25.f)), make_float2(0.08f, 0.08f),
+                                make_float2(-1.f, -1.f));
+    float2 p = make_float2(P[0], P[0]);
+#pragma unroll
+    for (int i = 1; i < 13; ++i) p = __ffma2_rn(p, u, make_float2(P[i], P[i]));
+    const float ax = fabsf(x.x), ay = fabsf(x.y);
+    const float2 g = make_float2(ax > 5.f ? 0.5f * ax : p.x, ay > 5.f ? 0.5f * ay : p.y);
+    return __ffma2_rn(make_float2(0.5f, 0.5f), x, g);
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout that TMA writes with CU_TENSOR_MAP_SWIZZLE_128B: rows of
+// 64 bfloat16 (128 B), 8-row atoms of 1024 B (the stride-dimension offset),
+// the 16-byte chunks of row r at chunk ^ (r mod 8); atoms 1024-byte aligned so
+// that the K offset inside an atom can be added to the start address.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// 16 accumulator columns of this thread's TMEM lane (row)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// bias[j0 .. j0 + 16) (zeros past N); j0 is a multiple of 16
+__device__ __forceinline__ void load_bias16(const float* __restrict__ bias, int j0, int N, float (&bv)[16])
+{
+    if (j0 + 16 <= N) {
+#pragma unroll
+        for (int c = 0; c < 16; c += 4) {
+            const float4 t4 = __ldg(reinterpret_cast<const float4*>(bias + j0 + c));
+            bv[c] = t4.x; bv[c + 1] = t4.y; bv[c + 2] = t4.z; bv[c + 3] = t4.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) bv[c] = j0 + c < N ? bias[j0 + c] : 0.f;
+    }
+}
+
+// accumulators + bias (+ GELU) of columns j0 .. j0 + 16 of row gi, stored
+template <typename TC, bool GELU>
+__device__ __forceinline__ void epilogue16(const uint32_t (&r)[16], const float (&bv)[16], int gi, int M, int j0, int N,
+                                           TC* __restrict__ C, int ldc)
+{
+    float2 v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        v[c] = __fadd2_rn(make_float2(__uint_as_float(r[2 * c]), __uint_as_float(r[2 * c + 1])),
+                          make_float2(bv[2 * c], bv[2 * c + 1]));
+        if (GELU) v[c] = gelu_poly2(v[c]);
+    }
+    if (gi >= M) return;
+    TC* out = C + (size_t)gi * ldc + j0;
+    const bool full = j0 + 16 <= N;
+    if (sizeof(TC) == 2 && full && (ldc & 7) == 0) {
+        uint4* o = reinterpret_cast<uint4*>(out);
+        o[0] = make_uint4(pack_bf16(v[0].x, v[0].y), pack_bf16(v[1].x, v[1].y), pack_bf16(v[2].x, v[2].y),
+                          pack_bf16(v[3].x, v[3].y));
+        o[1] = make_uint4(pack_bf16(v[4].x, v[4].y), pack_bf16(v[5].x, v[5].y), pack_bf16(v[6].x, v[6].y),
+                          pack_bf16(v[7].x, v[7].y));
+    } else if (sizeof(TC) == 4 && full && (ldc & 3) == 0) {
+        float4* o = reinterpret_cast<float4*>(out);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o[c] = make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (j0 + c < N) {
+                const float val = (c & 1) ? v[c >> 1].y : v[c >> 1].x;
+                if (sizeof(TC) == 2) reinterpret_cast<__nv_bfloat16*>(out)[c] = __float2bfloat16_rn(val);
+                else reinterpret_cast<float*>(out)[c] = val;
+            }
+    }
+}
+
+template <typename TC, bool GELU>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    umma_tma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
+                         int N, int K, const float* __restrict__ bias, TC* __restrict__ C, int ldc, int BN,
+                         uint32_t ncols, unsigned* err)
+{
+    extern __shared__ __align__(1024) unsigned char tsm_raw[];
+    // the ring starts on a 1024-byte boundary (the request carries 1 KB of slack)
+    unsigned char* tsm = tsm_raw + ((1024u - (saddr(tsm_raw) & 1023u)) & 1023u);
+    const int a_bytes = BM * BK * 2, b_bytes = BN * BK * 2, st_bytes = a_bytes + b_bytes;
+    __shared__ __align__(8) unsigned long long s_full[TMA_STAGES], s_empty[TMA_STAGES], s_tfull[2], s_tempty[2];
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN, tiles = mt * nt, KS = (K + BK - 1) / BK;
+    if (warp == TMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < TMA_STAGES; ++i) {
+            mbar_init(saddr(&s_full[i]), 1);
+            mbar_init(saddr(&s_empty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(saddr(&s_tfull[i]), 1);
+            mbar_init(saddr(&s_tempty[i]), 32 * EPI_WARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t half = ncols / 2;  // columns per accumulator buffer
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    bool ok = true;
+    // local tiles of this CTA: blockIdx.x, + gridDim.x, ...
+    const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_tiles * KS;  // K steps of this CTA, over its tiles in order
+    if (warp == TMA_WARP) {
+        // producer: fill stage g % S with the A and B tiles of K step g once
+        // the MMAs of step g - S have released it
+        if (lane == 0) {
+            for (int g = 0; g < total && ok; ++g) {
+                const int s = g % TMA_STAGES;
+                if (g >= TMA_STAGES) ok = mbar_wait(saddr(&s_empty[s]), (uint32_t)(((g / TMA_STAGES) - 1) & 1), err);
+                if (!ok) break;
+                const int ti = g / KS, ks = g % KS;
+                const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
+                const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN, k0 = ks * BK;
+                const uint32_t full = saddr(&s_full[s]);
+                const uint32_t base = saddr(tsm + (size_t)s * st_bytes);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(st_bytes)
+                             : "memory");
+                tma_load_2d(base, &mapA, k0, m0, full);
+                tma_load_2d(base + (uint32_t)a_bytes, &mapB, k0, n0, full);
+            }
+        }
+        __syncwarp();
+    } else if (warp == MMA_WARP) {
+        // MMA issuer: step g once its stage has landed (and, at a tile's
+        // first step, once the epilogue has drained the TMEM buffer of two
+        // tiles back); each step's commit frees its stage, a tile's last
+        // commit hands the accumulator to the epilogue
+        if (lane == 0) {
+            int g = 0;
+            for (; g < total && ok; ++g) {
+                const int s = g % TMA_STAGES;
+                const int ti = g / KS, ks = g % KS, b = ti & 1;
+                if (ks == 0 && ti >= 2) {
+                    ok = mbar_wait(saddr(&s_tempty[b]), (uint32_t)(((ti - 2) >> 1) & 1), err);
+                    if (!ok) break;
+                }
+                ok = mbar_wait(saddr(&s_full[s]), (uint32_t)((g / TMA_STAGES) & 1), err);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a_base = saddr(tsm + (size_t)s * st_bytes), b_base = a_base + (uint32_t)a_bytes;
+                const uint32_t dtm = tmem + (uint32_t)b * half;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {  // 16 K elements = 32 B further along each row
+                    const uint64_t ad = sw128_desc(a_base + (uint32_t)(kk * 32));
+                    const uint64_t bd = sw128_desc(b_base + (uint32_t)(kk * 32));
+                    const uint32_t acc = (ks > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 saddr(&s_empty[s]))
+                             : "memory");
+                if (ks == KS - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     saddr(&s_tfull[b]))
+                                 : "memory");
+            }
+            // after an expired wait, let the copies the producer issued land
+            // before the CTA exits (bounded as well)
+            for (int gg = g; gg < total && gg < g + TMA_STAGES; ++gg)
+                mbar_wait(saddr(&s_full[gg % TMA_STAGES]), (uint32_t)((gg / TMA_STAGES) & 1), err);
+        }
+        __syncwarp();
+    } else {
+        // warp: TMEM sub-partition q (its 32 rows of the tile), and every
+        // fourth 16-column chunk starting at `part`
+        const int q = warp & 3, part = warp >> 2, chunks = BN / 16;
+        for (int ti = 0; ti < my_tiles && ok; ++ti) {
+            const int b = ti & 1;
+            const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
+            const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+            const int gi = m0 + q * 32 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * half;
+            ok = mbar_wait(saddr(&s_tfull[b]), (uint32_t)((ti >> 1) & 1), err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // this warp's chunks part, part + 4, ...: the TMEM load and the
+            // bias of the next chunk are issued before the current one is
+            // processed (a wait::ld covers every load issued so far)
+            const int nch = chunks > part ? (chunks - part + 3) / 4 : 0;
+            uint32_t ra[16], rb[16];
+            float ba[16], bb[16];
+            if (nch > 0) {
+                load_bias16(bias, n0 + part * 16, N, ba);
+                tmem_ld16(trow + (uint32_t)(part * 16), ra);
+            }
+            for (int i = 0; i < nch; i += 2) {
+                const int ca = part + 4 * i, cb = ca + 4;
+                tmem_wait_ld();
+                if (i + 1 < nch) {
+                    load_bias16(bias, n0 + cb * 16, N, bb);
+                    tmem_ld16(trow + (uint32_t)(cb * 16), rb);
+                }
+                epilogue16<TC, GELU>(ra, ba, gi, M, n0 + ca * 16, N, C, ldc);
+                if (i + 1 < nch) {
+                    tmem_wait_ld();
+                    if (i + 2 < nch) {
+                        load_bias16(bias, n0 + (cb + 4) * 16, N, ba);
+                        tmem_ld16(trow + (uint32_t)((cb + 4) * 16), ra);
+                    }
+                    epilogue16<TC, GELU>(rb, bb, gi, M, n0 + cb * 16, N, C, ldc);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(saddr(&s_tempty[b]));
+        }
+    }
+    // the last MMAs are complete once the epilogue has drained the last tile;
+    // a CTA that gave up waits (bounded) for its outstanding commits first
+    if (!ok && warp == MMA_WARP && lane == 0 && my_tiles > 0) {
+        const int last = my_tiles - 1;
+        mbar_wait(saddr(&s_tfull[last & 1]), (uint32_t)((last >> 1) & 1), err);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == TMA_WARP)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// features (float32) -> bfloat16 rows, the first layer's TMA operand
+__global__ void rows_to_bf16_kernel(const float* __restrict__ X, size_t count, __nv_bfloat16* __restrict__ Y)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        Y[e] = __float2bfloat16_rn(X[e]);
+}
+
 // bfloat16 copy of W [K][N] transposed: Wt [N][K]
 __global__ void to_bf16_t_kernel(const float* __restrict__ W, int K, int N, __nv_bfloat16* __restrict__ Wt)
 {
@@ -662,7 +970,10 @@ struct mmpc_mlp {
     std::vector<float*> W, b, gW, gb, mW, vW, mb, vb;
     std::vector<__nv_bfloat16*> W16;
     std::vector<__nv_bfloat16*> W16T;  // transposed copies [width[i+1]][width[i]] for the tensor-core path
-    bool tensor = false;               // inference with tcgen05
+    int tensor = 0;                    // inference: 0 SIMT, 1 TMA-fed tcgen05 pipeline, 2 single-stage tcgen05
+    bool tma_widths = false;           // every layer input width a multiple of 8 (16-byte TMA rows)
+    int sms = 0;
+    __nv_bfloat16* Xb = nullptr;       // the features as bfloat16 [inf_rows][width[0]], the pipeline's first operand
     unsigned* d_err = nullptr;         // bounded-wait error word of the tensor-core kernels
     std::vector<float*> H;    // H[i]: input of layer i (i >= 1), [max_batch][width[i]]
     std::vector<float*> P;    // P[i]: pre-activation of layer i (hidden), [max_batch][width[i+1]]
@@ -689,7 +1000,7 @@ void mlp_free(mmpc_mlp* n)
     for (auto* p : n->W16) f(p);
     for (auto* p : n->W16T) f(p);
     f(n->d_err);
-    f(n->Yb); f(n->D0); f(n->D1); f(n->part); f(n->I0); f(n->I1);
+    f(n->Yb); f(n->D0); f(n->D1); f(n->part); f(n->I0); f(n->I1); f(n->Xb);
     delete n;
 }
 
@@ -743,19 +1054,111 @@ void tc_launch(int M, int N, int K, const TA* A, const __nv_bfloat16* Bt, const 
     tc::umma_gemm_kernel<TA, TC, GELU><<<grid, tc::THREADS, t.smem, st>>>(M, N, K, A, K, Bt, bias, C, N, t.BN, t.ncols, err);
 }
 
-// Inference on the tensor cores: the first layer reads the float32
-// features, hidden activations travel as bfloat16, the last layer writes
-// float32.
+// cuTensorMapEncodeTiled, resolved once through the runtime (no link
+// against the driver library); nullptr when the driver does not offer it.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder()
+{
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Row-major bfloat16 matrix [rows][cols] (cols a multiple of 8, base 16-byte
+// aligned) as a 2-D tensor map with boxes of {64 columns, box_rows rows} in
+// the 128-byte swizzle: one K step (64 elements = 128 B per row) of box_rows
+// rows per copy, landing in the layout the MMA descriptors read; outside the
+// matrix the box reads zeros.
+bool encode_rows(CUtensorMap* map, const void* base, int cols, int rows, int box_rows)
+{
+    const EncodeTiledFn fn = tensor_map_encoder();
+    if (!fn || cols % 8 != 0 || rows < 1 || box_rows < 1 || box_rows > 256 ||
+        (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Pipelined kernel's tile width for N outputs (one tile spans N <= 256), its
+// TMEM allocation (two accumulators, a power of two >= 32 columns) and its
+// shared memory (the ring of stages).  With the ring's size the CTAs that fit
+// on an SM never ask for more than its 512 TMEM columns.
+int tma_bn(int N) { return std::min(256, (N + 15) / 16 * 16); }
+
+size_t tma_smem(int BN)
+{
+    return (size_t)tc::TMA_STAGES * ((size_t)tc::BM * tc::BK * 2 + (size_t)BN * tc::BK * 2) + 1024;
+}
+
+template <typename TC, bool GELU>
+bool tma_launch(const mmpc_mlp* n, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
+                const float* bias, TC* C, cudaStream_t st)
+{
+    const int BN = tma_bn(N);
+    CUtensorMap ma, mb;
+    if (!encode_rows(&ma, A, K, M, tc::BM) || !encode_rows(&mb, Bt, K, N, BN)) return false;
+    uint32_t ncols = 32;
+    while ((int)ncols < 2 * BN) ncols <<= 1;
+    const size_t smem = tma_smem(BN);
+    const int tiles = ((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN);
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::umma_tma_gemm_kernel<TC, GELU>, tc::TMA_THREADS,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    const int grid = std::max(1, std::min(tiles, n->sms * per_sm));
+    tc::umma_tma_gemm_kernel<TC, GELU>
+        <<<grid, tc::TMA_THREADS, smem, st>>>(ma, mb, M, N, K, bias, C, N, BN, ncols, n->d_err);
+    return true;
+}
+
+// Inference on the tensor cores: hidden activations travel as bfloat16, the
+// last layer writes float32.  The pipelined kernel reads its operands through
+// tensor maps, so the features are first rounded to bfloat16 rows; the
+// single-stage kernel (and any layer whose maps cannot be made) reads the
+// float32 features itself.
 void forward_tensor(mmpc_mlp* n, const float* X, int M, float* Y, float* b0, float* b1, cudaStream_t st)
 {
     const int L = n->L;
     __nv_bfloat16* h[2] = {reinterpret_cast<__nv_bfloat16*>(b0), reinterpret_cast<__nv_bfloat16*>(b1)};
+    const bool tma = n->tensor == 1 && n->tma_widths;
+    if (tma) {
+        const size_t cnt = (size_t)M * n->cfg.width[0];
+        tc::rows_to_bf16_kernel<<<grid_for(cnt), 256, 0, st>>>(X, cnt, n->Xb);
+    }
     for (int i = 0; i < L; ++i) {
         const int K = n->cfg.width[i], N = n->cfg.width[i + 1];
         const bool last = i == L - 1;
-        const __nv_bfloat16* in = h[(i + 1) & 1];
+        const __nv_bfloat16* in = i == 0 ? n->Xb : h[(i + 1) & 1];
         __nv_bfloat16* out = h[i & 1];
-        if (i == 0 && last)
+        if (tma && (last ? tma_launch<float, false>(n, M, N, K, in, n->W16T[i], n->b[i], Y, st)
+                         : tma_launch<__nv_bfloat16, true>(n, M, N, K, in, n->W16T[i], n->b[i], out, st)))
+            continue;
+        if (tma && i == 0) {
+            if (last)
+                tc_launch<__nv_bfloat16, float, false>(M, N, K, in, n->W16T[i], n->b[i], Y, n->d_err, st);
+            else
+                tc_launch<__nv_bfloat16, __nv_bfloat16, true>(M, N, K, in, n->W16T[i], n->b[i], out, n->d_err, st);
+        } else if (i == 0 && last)
             tc_launch<float, float, false>(M, N, K, X, n->W16T[i], n->b[i], Y, n->d_err, st);
         else if (i == 0)
             tc_launch<float, __nv_bfloat16, true>(M, N, K, X, n->W16T[i], n->b[i], out, n->d_err, st);
@@ -881,7 +1284,14 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
     n->cfg = *cfg;
     n->L = cfg->layers;
     n->maxw = *std::max_element(cfg->width, cfg->width + cfg->layers + 1);
-    n->inf_rows = std::max(cfg->max_batch, 65536);
+    // inference chunk: four 128-row tiles per SM (every persistent CTA of
+    // the pipelined GEMM gets the same share), at least 65536 rows; the
+    // bfloat16 activations of a chunk stay in L2 between layers
+    int dev0 = 0, sms0 = 0;
+    if (cudaGetDevice(&dev0) != cudaSuccess || cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0) != cudaSuccess)
+        sms0 = 128;
+    cudaGetLastError();
+    n->inf_rows = std::max(cfg->max_batch, std::max(65536, sms0 * 128 * 4));
     const size_t mb = (size_t)cfg->max_batch;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](float** p, size_t cnt) {
@@ -912,6 +1322,12 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
     alloc(&n->part, n->part_count);
     alloc(&n->I0, (size_t)n->inf_rows * n->maxw);
     alloc(&n->I1, (size_t)n->inf_rows * n->maxw);
+    if (e == cudaSuccess) e = cudaMalloc(&n->Xb, sizeof(__nv_bfloat16) * (size_t)n->inf_rows * cfg->width[0]);
+    n->tma_widths = true;
+    for (int i = 0; i < L; ++i) n->tma_widths = n->tma_widths && cfg->width[i] % 8 == 0;
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev);
     for (int i = 0; i < L && e == cudaSuccess; ++i) {
         const size_t wc = wcount(n, i), bc = cfg->width[i + 1];
         e = cudaMemcpy(n->W[i], W[i], sizeof(float) * wc, cudaMemcpyHostToDevice);
@@ -936,6 +1352,12 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
                                 (const void*)tc::umma_gemm_kernel<__nv_bfloat16, __nv_bfloat16, true>};
     for (const void* kf : tc_kernels)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
+    size_t tma_max = 0;
+    for (int i = 0; i < L; ++i) tma_max = std::max(tma_max, tma_smem(tma_bn(cfg->width[i + 1])));
+    const void* tma_kernels[] = {(const void*)tc::umma_tma_gemm_kernel<float, false>,
+                                 (const void*)tc::umma_tma_gemm_kernel<__nv_bfloat16, true>};
+    for (const void* kf : tma_kernels)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_max);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         mlp_free(n);
@@ -1056,7 +1478,8 @@ int mmpc_mlp_write(mmpc_mlp* n, int what, int layer, const float* host, size_t c
 int mmpc_mlp_set_tensor_cores(mmpc_mlp* n, int on)
 {
     if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
-    n->tensor = on != 0;
+    if (on < 0 || on > 2) return fail(MMPC_ERR_INVALID_ARG, "tensor-core mode must be 0, 1 or 2");
+    n->tensor = on;
     return MMPC_OK;
 }
 

@@ -208,8 +208,9 @@ class Mlp:
     def loss_grad(self, X, Z, loss=None, stream=None):
         _check(lib().mmpc_mlp_loss_grad(self.handle, _ptr(X), _ptr(Z), int(X.shape[0]), _ptr(loss), _stream(stream)))
 
-    def set_tensor_cores(self, on: bool):
-        _check(lib().mmpc_mlp_set_tensor_cores(self.handle, 1 if on else 0))
+    def set_tensor_cores(self, on):
+        """False/0: SIMT; True/1: the TMA-fed tcgen05 pipeline; 2: the single-stage tcgen05 GEMM."""
+        _check(lib().mmpc_mlp_set_tensor_cores(self.handle, int(on)))
 
     def status(self):
         _check(lib().mmpc_mlp_status(self.handle))
@@ -246,8 +247,9 @@ class Mlp:
 
 def _time_forward(rows: int, reps: int = 10, seed: int = 0) -> list:
     """Times one forward pass of the warm-start network (64 -> 256 x 3 -> 36,
-    seeded random weights) over `rows` random rows, FP32 SIMT path and tensor
-    cores (CUDA events, median of reps)."""
+    seeded random weights) over `rows` random rows: FP32 SIMT path (mode 0),
+    the single-stage tcgen05 GEMM (2) and the TMA-fed pipeline (1); CUDA
+    events, median of reps."""
     import torch
 
     from . import scenes
@@ -258,7 +260,7 @@ def _time_forward(rows: int, reps: int = 10, seed: int = 0) -> list:
     X = torch.randn((rows, widths[0]), device="cuda:0")
     Y = torch.empty((rows, widths[-1]), device="cuda:0")
     out = []
-    for on in (False, True):
+    for on in (0, 2, 1):
         net.set_tensor_cores(on)
         net.forward(X, Y)
         torch.cuda.synchronize()

@@ -254,17 +254,22 @@ def test_decode_coefficients_only_with_consistent_multipliers(orc):
         assert np.max(np.abs(_host(d["lam"]) - wl)) <= 1e-5 * scale
 
 
-@pytest.mark.parametrize("widths", [(64, 256, 256, 256, 36), (64, 256, 256, 256, 72), (64, 32, 16)])
-def test_tensor_core_forward_matches_oracle(widths):
-    """tcgen05 inference: bfloat16 layer inputs and weights, float32
-    accumulation -- against the oracle with the same roundings (act_bf16),
-    on ragged row counts (tails of the 128-row tile)."""
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("widths", [(64, 256, 256, 256, 36), (64, 256, 256, 256, 72), (64, 32, 16),
+                                    (64, 320, 40), (60, 256, 36), (8, 16, 8, 24)])
+def test_tensor_core_forward_matches_oracle(widths, mode):
+    """tcgen05 inference (mode 1: TMA-fed pipeline, mode 2: single-stage
+    kernel): bfloat16 layer inputs and weights, float32 accumulation --
+    against the oracle with the same roundings (act_bf16), on ragged row
+    counts (tails of the 128-row tile), a layer wider than one 256-column
+    tile, an input width that is not a multiple of 8 (the pipeline falls back
+    to the single-stage kernel), and layers narrower than one K step."""
     import torch
     Ws, bs = scenes.mlp_init(21, widths)
     rng = np.random.default_rng(22)
     bs = [rng.normal(0, 0.1, b.shape).astype(np.float32) for b in bs]
     net = mlp.Mlp(widths, Ws, bs, max_batch=256)
-    net.set_tensor_cores(True)
+    net.set_tensor_cores(mode)
     for M_rows in (1, 127, 128, 300, 5000):
         X = rng.normal(size=(M_rows, widths[0])).astype(np.float32)
         Y = torch.zeros((M_rows, widths[-1]), device="cuda:0")
@@ -284,4 +289,42 @@ def test_tensor_core_forward_matches_oracle(widths):
     torch.cuda.synchronize()
     d = np.abs(_host(Yt) - _host(Ys)).max() / np.abs(_host(Ys)).max()
     assert 0 < d < 3e-2, d
+    net.close()
+
+
+def test_tensor_core_paths_agree_at_scale():
+    """The pipelined and single-stage tcgen05 GEMMs over the warm-start
+    network's widths, across the inference chunk boundary (max(65536, SMs x
+    512) rows): same roundings, so they differ only by the order of the
+    float32 sums and the GELU evaluation; a sample of rows against the
+    oracle."""
+    import torch
+    widths = (64, 256, 256, 256, 36)
+    Ws, bs = scenes.mlp_init(5, widths)
+    net = mlp.Mlp(widths, Ws, bs, max_batch=256)
+    chunk = max(65536, torch.cuda.get_device_properties(0).multi_processor_count * 512)
+    rows = chunk + 4465
+    X = torch.randn((rows, widths[0]), device="cuda:0", generator=torch.Generator("cuda:0").manual_seed(6))
+    Y1 = torch.zeros((rows, widths[-1]), device="cuda:0")
+    Y2 = torch.zeros((rows, widths[-1]), device="cuda:0")
+    net.set_tensor_cores(1)
+    net.forward(X, Y1)
+    net.set_tensor_cores(2)
+    net.forward(X, Y2)
+    net.status()
+    scale = Y2.abs().max().item()
+    assert (Y1 - Y2).abs().max().item() <= 2e-2 * scale
+    idx = np.r_[0:5, chunk - 6:chunk + 5, rows - 5:rows]
+    want, _ = M.forward(Ws, bs, _host(X)[idx].astype(np.float64), bf16=True, act_bf16=True)
+    assert np.max(np.abs(_host(Y1)[idx] - want)) <= 3e-3 * np.abs(want).max()
+    net.close()
+
+
+def test_tensor_core_mode_checked():
+    widths = (64, 32, 16)
+    Ws, bs = scenes.mlp_init(1, widths)
+    net = mlp.Mlp(widths, Ws, bs, max_batch=16)
+    for bad in (-1, 3):
+        with pytest.raises(RuntimeError):
+            net.set_tensor_cores(bad)
     net.close()
