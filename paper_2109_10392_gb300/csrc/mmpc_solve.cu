@@ -689,6 +689,10 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     unsigned long long work = 0;  // evaluated obstacle-sample pairs (lane 0)
     CullState cull;
     cull_init(cull);
+    if (!A.cull && !idle) {  // one code path for the obstacle sum: the identity list
+        for (int j = lane; j < m; j += 32) olist[j] = j;
+        __syncwarp();
+    }
 
     // ---- coefficient state, identical in every warp ---------------------------
     const bool isy = lane >= 16;
@@ -804,19 +808,15 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             // Eq. split_alpha_o, summed over the obstacles
             const float2 Xn = __fmul2_rn(x, f2(A.inv_a)), Yn = __fmul2_rn(y, f2(A.inv_b));
             float2 Sx, Sy, R2;
+            int cnt = m;  // without culling the list holds every obstacle in order
             if (A.cull) {
                 float bxlo, bxhi, bylo, byhi;
                 const bool bad = box_pair(Xn, Yn, valid, bxlo, bxhi, bylo, byhi);
-                const int cnt =
-                    cull_update<true>(cull, m, bxlo, bxhi, bylo, byhi, bad, tw_lo, tw_hi, olist, lane, obs);
-                if (lane == 0) work += (unsigned long long)cnt * (unsigned)(w_last - w_first + 1);
-                if (resid) obstacle_sum2<true, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-                else obstacle_sum2<false, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-            } else {
-                if (lane == 0) work += (unsigned long long)m * (unsigned)(w_last - w_first + 1);
-                if (resid) obstacle_sum2<true, false>(obs, nullptr, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-                else obstacle_sum2<false, false>(obs, nullptr, m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+                cnt = cull_update<true>(cull, m, bxlo, bxhi, bylo, byhi, bad, tw_lo, tw_hi, olist, lane, obs);
             }
+            if (lane == 0) work += (unsigned long long)cnt * (unsigned)(w_last - w_first + 1);
+            if (resid) obstacle_sum2<true, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+            else obstacle_sum2<false, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
             if (isnan(Sx.x) || isnan(Sy.x)) obstacle_sum_exact(obs, m, Xn.x, Yn.x, tt.x, a2, b2, Sx.x, Sy.x, R2.x);
             if (isnan(Sx.y) || isnan(Sy.y)) obstacle_sum_exact(obs, m, Xn.y, Yn.y, tt.y, a2, b2, Sx.y, Sy.y, R2.y);
             const float2 eox = __fmul2_rn(Sx, f2(-A.a));
