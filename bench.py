@@ -68,7 +68,9 @@ def workload_name(params, B, m):
 # DRAM bytes (read + write) of one solve launch, from an ncu capture of that
 # workload's kernel as it stands (profiles/am_solve_kernel_*.md); an entry must
 # be measured again whenever the kernel changes.
-SOLVE_DRAM_BYTES = {"highway_B1024_m50_N100_n12_K100_tol0.01": 128256}
+SOLVE_DRAM_BYTES = {"highway_B1024_m50_N100_n12_K100_tol0.01": 132608}
+# per step, summed over the three horizon-group launches of schedule 4
+BATCH_DRAM_BYTES = {"highway_batch_S256_B16-512_m5-40_N50-100-150_n12_K100_tol0.01": 5119744}
 
 OPS_PER_ELEMENT = 10  # FP32 lane ops per evaluated obstacle-sample pair
 
@@ -483,7 +485,12 @@ def run_batch(args):
                    "graph": "one CUDA graph replay per step", "start": "cold",
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
         "roofline": {"bound": "alu", "kernel": "am_solve_batch_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": None,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak,
+                     "traffic": (BATCH_DRAM_BYTES.get(f"highway_batch_S{S}_B16-512_m5-40_N{'-'.join(map(str, Ns))}"
+                                                      f"_n12_K100_tol{TOL:g}")
+                                 if schedule == 4 and not args.stall else None),
+                     "traffic_unit": "bytes per step (ncu dram__bytes_read.sum + dram__bytes_write.sum over the "
+                                     "three horizon-group launches)",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz",
                      "ops_per_launch": ops, "launch_ms": ms,
                      "ops_basis": "dense algorithmic ops summed over scenes, over the whole graph step (reset, "
@@ -651,6 +658,21 @@ def run_reference(args):
     }
 
 
+def add_measured_peak(roofline: dict) -> None:
+    """Beside the derived peak: the FP32 lane-op rate the device reaches on
+    saturating FFMA / packed FFMA2 chains (mmpc_measure_peaks, run after the
+    timed region), and the fraction of it."""
+    from paper_2109_10392_gb300 import mmpc
+    pk = mmpc.mmpc_measure_peaks(reps=3)
+    lane = max(pk["ffma"], pk["ffma2"]) / 1e12
+    roofline["measured_peak"] = {
+        "fp32_lane_ops": lane, "ffma": pk["ffma"] / 1e12, "ffma2": pk["ffma2"] / 1e12,
+        "rsqrt": pk["rsqrt"] / 1e12, "unit": "T ops/s",
+        "lanes_per_sm_per_clk_at_max_clock": lane * 1e12 / (pk["sms"] * pk["clock_khz"] * 1e3),
+        "basis": "mmpc_measure_peaks: 8 dependent chains per thread, 64 warps per SM, best of 3"}
+    roofline["frac_of_measured"] = roofline["achieved"] / lane
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -680,6 +702,8 @@ def main():
         out = run_reference(args)
     else:
         out = {"batch": run_batch, "warm": run_warm}.get(args.workload, run_mine)(args)
+        if out is not None and out.get("roofline", {}).get("bound") == "alu":
+            add_measured_peak(out["roofline"])
     if out is not None:
         print(json.dumps(out), flush=True)
 

@@ -14,9 +14,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libmmpc.so")
-SOURCES = ["mmpc_solve.cu", "mmpc_build.cpp", "mmpc_mlp.cu"]
+SOURCES = ["mmpc_solve.cu", "mmpc_build.cpp", "mmpc_mlp.cu", "mmpc_peaks.cu"]
 HEADERS = ["mmpc_internal.h", os.path.join("..", "..", "include", "mmpc.h"),
-           os.path.join("..", "..", "include", "mmpc_mlp.h")]
+           os.path.join("..", "..", "include", "mmpc_mlp.h"), os.path.join("..", "..", "include", "mmpc_peaks.h")]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -30,7 +30,8 @@ MMPC_META_ABS = 2
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
             "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
             "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
-            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_fallbacks", "mmpc_step_host")
+            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_fallbacks", "mmpc_step_host",
+            "mmpc_measure_peaks")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
 
@@ -82,6 +83,12 @@ class MmpcScene(ctypes.Structure):
         ("warm_coef", ctypes.c_void_p),
         ("warm_lam", ctypes.c_void_p),
     ]
+
+
+class MmpcPeaks(ctypes.Structure):
+    _fields_ = [("ffma", ctypes.c_double), ("ffma2", ctypes.c_double), ("rsqrt", ctypes.c_double),
+                ("ms_ffma", ctypes.c_double), ("ms_ffma2", ctypes.c_double), ("ms_rsqrt", ctypes.c_double),
+                ("sms", ctypes.c_int), ("clock_khz", ctypes.c_int)]
 
 
 class MmpcError(RuntimeError):
@@ -145,6 +152,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_batch_set_fallback.restype = ctypes.c_int
     L.mmpc_batch_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.mmpc_batch_fallbacks.restype = ctypes.c_int
+    L.mmpc_measure_peaks.argtypes = [ctypes.POINTER(MmpcPeaks), ctypes.c_int, vp]
+    L.mmpc_measure_peaks.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -276,6 +285,16 @@ def mmpc_take_work_count(ctx) -> int:
     if rc != MMPC_OK:
         _err(ctx, rc)
     return int(out.value)
+
+
+def mmpc_measure_peaks(reps: int = 3, stream=None) -> dict:
+    """Measured FP32 pipe throughput of the current device (mmpc_peaks.h):
+    scalar FFMA and packed FFMA2 lane operations/s, MUFU rsqrt/s."""
+    pk = MmpcPeaks()
+    rc = lib().mmpc_measure_peaks(ctypes.byref(pk), int(reps), _stream(stream))
+    if rc != MMPC_OK:
+        raise MmpcError(rc, "mmpc_measure_peaks failed")
+    return {f: getattr(pk, f) for f, _ in MmpcPeaks._fields_}
 
 
 def mmpc_destroy(ctx) -> None:

@@ -116,6 +116,10 @@ def test_calls_without_context_fail_cleanly():
     assert L.mmpc_batch_set_schedule(None, 1) == mmpc.MMPC_ERR_NOT_SETUP
     assert L.mmpc_batch_times(None, None, None) == mmpc.MMPC_ERR_NOT_SETUP
     L.mmpc_batch_destroy(None)
+    # the peak probe checks its arguments before touching the device
+    pk = mmpc.MmpcPeaks()
+    assert L.mmpc_measure_peaks(None, 3, None) == mmpc.MMPC_ERR_INVALID_ARG
+    assert L.mmpc_measure_peaks(ctypes.byref(pk), 0, None) == mmpc.MMPC_ERR_INVALID_ARG
 
 
 def test_setup_rejects_bad_buffers():

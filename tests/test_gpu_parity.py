@@ -427,3 +427,18 @@ def test_stall_stop(variant):
         pk = dict(fixed, iters=int(K))
         orc = U.oracle_solve(pk, ego, obst, goals[idx])
         _check_parity(pk, ego, obst, goals[idx], {"coef": g1["coef"][idx]}, orc, min_frac=0.0)
+
+
+def test_measured_fp32_peaks_plausible():
+    """mmpc_measure_peaks: the saturating FFMA, FFMA2 and rsqrt kernels run
+    at rates that the unit counts allow (at most 128 FP32 lanes and 16 MUFU
+    units per SM and clock, at the maximum clock, plus timing slack) and
+    that are not far below them either."""
+    from paper_2109_10392_gb300 import mmpc
+    pk = mmpc.mmpc_measure_peaks(reps=2)
+    per_clk = lambda v: v / (pk["sms"] * pk["clock_khz"] * 1e3)  # noqa: E731
+    assert 48 <= per_clk(pk["ffma"]) <= 128 * 1.05, pk
+    assert 48 <= per_clk(pk["ffma2"]) <= 128 * 1.05, pk
+    assert 4 <= per_clk(pk["rsqrt"]) <= 16 * 1.05, pk
+    with pytest.raises(mmpc.MmpcError):
+        mmpc.mmpc_measure_peaks(reps=0)
