@@ -287,21 +287,49 @@ __device__ __forceinline__ bool stage_blob(float* dst, const float* src, int byt
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// Dot products of the basis rows of one sample pair ([NC][2], interleaved)
-// with NC coefficients held duplicated ([NC][2] = (c_k, c_k)): both samples'
-// values in one FFMA2 chain.
+// Basis evaluations at a sample pair.  The rows of the pair ([NC][2]: the two
+// samples' values of coefficient k side by side) meet coefficient vectors
+// held duplicated ([NC][2] = (c_k, c_k)), so one FFMA2 chain in k order gives
+// both samples' values.  The five evaluations of the projection phase, each
+// 16-byte chunk of the P and Pddot rows and of the three coefficient vectors
+// loaded once: x = P cx, y = P cy, xdd = Pdd cx, ydd = Pdd cy, psi = P cpsi.
 template <int NC>
-__device__ __forceinline__ float2 dot_pair(const float* __restrict__ rows, const float* __restrict__ cd)
+__device__ __forceinline__ void eval_pair5(const float* __restrict__ P, const float* __restrict__ Pdd,
+                                           const float* __restrict__ cx, const float* __restrict__ cy,
+                                           const float* __restrict__ cp, float2& x, float2& y, float2& xdd,
+                                           float2& ydd, float2& ps)
 {
-    float2 s = f2(0.f);
+    x = y = xdd = ydd = ps = f2(0.f);
 #pragma unroll
     for (int k = 0; k < NC; k += 2) {
-        const float4 r = *reinterpret_cast<const float4*>(rows + 2 * k);
-        const float4 c = *reinterpret_cast<const float4*>(cd + 2 * k);
-        s = __ffma2_rn(f2(r.x, r.y), f2(c.x, c.y), s);
-        s = __ffma2_rn(f2(r.z, r.w), f2(c.z, c.w), s);
+        const float4 r = *reinterpret_cast<const float4*>(P + 2 * k);
+        const float4 d = *reinterpret_cast<const float4*>(Pdd + 2 * k);
+        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
+        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
+        const float4 c = *reinterpret_cast<const float4*>(cp + 2 * k);
+        x = __ffma2_rn(f2(r.z, r.w), f2(a.z, a.w), __ffma2_rn(f2(r.x, r.y), f2(a.x, a.y), x));
+        y = __ffma2_rn(f2(r.z, r.w), f2(b.z, b.w), __ffma2_rn(f2(r.x, r.y), f2(b.x, b.y), y));
+        ps = __ffma2_rn(f2(r.z, r.w), f2(c.z, c.w), __ffma2_rn(f2(r.x, r.y), f2(c.x, c.y), ps));
+        xdd = __ffma2_rn(f2(d.z, d.w), f2(a.z, a.w), __ffma2_rn(f2(d.x, d.y), f2(a.x, a.y), xdd));
+        ydd = __ffma2_rn(f2(d.z, d.w), f2(b.z, b.w), __ffma2_rn(f2(d.x, d.y), f2(b.x, b.y), ydd));
     }
-    return s;
+}
+
+// The heading phase's two evaluations, xd = Pd cx and yd = Pd cy, sharing the
+// row loads.
+template <int NC>
+__device__ __forceinline__ void eval_pair2(const float* __restrict__ Pd, const float* __restrict__ cx,
+                                           const float* __restrict__ cy, float2& xd, float2& yd)
+{
+    xd = yd = f2(0.f);
+#pragma unroll
+    for (int k = 0; k < NC; k += 2) {
+        const float4 r = *reinterpret_cast<const float4*>(Pd + 2 * k);
+        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
+        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
+        xd = __ffma2_rn(f2(r.z, r.w), f2(a.z, a.w), __ffma2_rn(f2(r.x, r.y), f2(a.x, a.y), xd));
+        yd = __ffma2_rn(f2(r.z, r.w), f2(b.z, b.w), __ffma2_rn(f2(r.x, r.y), f2(b.x, b.y), yd));
+    }
 }
 
 // Sum over obstacles at the sample pair (Eq. split_alpha_o).  With n = w / (a,
@@ -787,11 +815,8 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
 #pragma unroll
         for (int i = 0; i < VD; ++i) v[i] = 0.f;
         {  // lanes without a sample pair read zero rows: their terms vanish
-            const float2 x = dot_pair<NC>(PP, cxd);
-            const float2 y = dot_pair<NC>(PP, cyd);
-            const float2 xdd = dot_pair<NC>(PddP, cxd);
-            const float2 ydd = dot_pair<NC>(PddP, cyd);
-            const float2 ps = dot_pair<NC>(PP, cpd);
+            float2 x, y, xdd, ydd, ps;
+            eval_pair5<NC>(PP, PddP, cxd, cyd, cpd, x, y, xdd, ydd, ps);
             // Eq. v_update and the non-holonomic rows v (cos psi, sin psi)
             const float2 sp2 = __ffma2_rn(xd, xd, __fmul2_rn(yd, yd));
             const float2 nvel = f2(-fminf(fmaxf(sqrtf(sp2.x), A.v_min), A.v_max),
@@ -856,8 +881,9 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     // Velocity directions and the heading target theta = atan2(ydot, xdot)
     // (Eq. split_psi), and the partial sums of P^T theta.
     auto heading = [&](bool reduce) {
-        xd = __fadd2_rn(dot_pair<NC>(PdP, cxd), f2(v0));
-        yd = dot_pair<NC>(PdP, cyd);
+        float2 xd0;
+        eval_pair2<NC>(PdP, cxd, cyd, xd0, yd);
+        xd = __fadd2_rn(xd0, f2(v0));
         theta = atan2_pair(yd, xd);
         if (reduce) {
             float v[NC];
