@@ -41,7 +41,7 @@ extern "C" {
 #define MMPC_ERR_INVALID_ARG (-1) /* bad pointer, NaN or out-of-range scalar */
 #define MMPC_ERR_SHAPE (-2)       /* size outside the supported range, or m != the m of setup */
 #define MMPC_ERR_CUDA (-3)        /* a CUDA runtime call failed (message in mmpc_last_error) */
-#define MMPC_ERR_TIMEOUT (-4)     /* reserved: a bounded device wait expired */
+#define MMPC_ERR_TIMEOUT (-4)     /* a bounded device wait expired (reported by mmpc_status) */
 #define MMPC_ERR_NOT_SETUP (-5)   /* NULL or destroyed context */
 
 /* Boundary rows per axis (the boundary set C_b,l of Eq. boundary):
@@ -267,6 +267,30 @@ void mmpc_batch_destroy(mmpc_batch* b);
  * trajectories (m N per trajectory-iteration without culling).  Synchronises
  * the device, writes the count to *elements (host) and resets it. */
 int mmpc_take_work_count(mmpc_ctx* ctx, unsigned long long* elements);
+
+/* Device-side failures of the solves on this context since the last call.
+ * Every wait of the solve kernels is bounded: the staging of the constants
+ * (a TMA bulk copy completing an mbarrier) gives up after about 0.2 s,
+ * records the expiry in the context's error word, waits once more (again
+ * bounded) so that no copy is left in flight, and the CTA then returns
+ * without writing its trajectory's outputs.  mmpc_status synchronises
+ * `stream` (a cudaStream_t as void*, NULL = the legacy default stream),
+ * reads and clears the word, and returns MMPC_ERR_TIMEOUT if a wait expired,
+ * else MMPC_OK (MMPC_ERR_NOT_SETUP for a NULL context, MMPC_ERR_CUDA if the
+ * synchronisation or the copy fails).  The context stays usable. */
+int mmpc_status(mmpc_ctx* ctx, void* stream);
+
+/* The same for a batch: the error words of every context its scenes use. */
+int mmpc_batch_status(mmpc_batch* b, void* stream);
+
+/* Test hook of the failure path.  With on != 0 the solves launched on this
+ * context afterwards (mmpc_solve, mmpc_step_host, and batches created
+ * afterwards from it) have their staging wait expect 16 bytes that no copy
+ * delivers, so every CTA's wait runs out after its time limit -- a wait on
+ * something nothing completes: no fault, no hang -- and mmpc_status reports
+ * MMPC_ERR_TIMEOUT.  on = 0 restores normal operation.  Returns MMPC_OK, or
+ * MMPC_ERR_NOT_SETUP for a NULL context. */
+int mmpc_debug_expire_wait(mmpc_ctx* ctx, int on);
 
 /* Frees the context's device memory (synchronises the device first).  NULL is a no-op. */
 void mmpc_destroy(mmpc_ctx* ctx);

@@ -143,6 +143,7 @@ struct SolveArgs {
     int* iters_out;
     unsigned* err_flag;
     unsigned long long* work;  // evaluated obstacle-sample pairs (summed over CTAs)
+    int missing_tx;            // 0; 16 under the failure-path test hook (mmpc_debug_expire_wait)
 };
 
 struct ScoreArgs {
@@ -242,8 +243,20 @@ __device__ __forceinline__ float* rs_dst(int c, float* red, int warp, int stride
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long WAIT_LIMIT_NS = 200000000ull;  // 0.2 s per pass of a bounded wait
+constexpr int WAIT_MAX_POLLS = 1 << 24;                     // backstop should the timer stall
+
+// `missing`: bytes the barrier expects beyond the copy (0; a test of the
+// failure path sets 16 so that the wait runs out).
 __device__ __forceinline__ bool stage_blob(float* dst, const float* src, int bytes, unsigned long long* mbar,
-                                           unsigned* err_flag)
+                                           unsigned* err_flag, int missing)
 {
     const uint32_t bar = smem_u32(mbar);
     if (threadIdx.x == 0) {
@@ -253,20 +266,22 @@ __device__ __forceinline__ bool stage_blob(float* dst, const float* src, int byt
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes + missing)
+                     : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(dst)),
             "l"(src), "r"(bytes), "r"(bar)
             : "memory");
     }
-    // Bounded wait: a copy that has not landed after ~2^22 polls (well over a
-    // second) flags an error, and the CTA waits once more, again bounded,
-    // before it gives up, so that it never leaves with the copy in flight
-    // unless the second bound also expires.
+    // Bounded wait: a copy that has not landed after 0.2 s (device global
+    // timer; a poll count as a backstop) flags an error, and the CTA waits
+    // once more, again bounded, before it gives up, so that it never leaves
+    // with the copy in flight unless the second bound also expires.
     uint32_t done = 0;
     for (int pass = 0; pass < 2 && !done; ++pass) {
-        for (int it = 0; it < (1 << 22) && !done; ++it) {
+        const unsigned long long t0 = global_ns();
+        for (int it = 0; it < WAIT_MAX_POLLS && !done; ++it) {
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -274,6 +289,7 @@ __device__ __forceinline__ bool stage_blob(float* dst, const float* src, int byt
                 : "=r"(done)
                 : "r"(bar), "r"(0)
                 : "memory");
+            if (!done && (it & 63) == 63 && global_ns() - t0 > WAIT_LIMIT_NS) break;
         }
         if (!done && pass == 0 && threadIdx.x == 0) atomicOr(err_flag, ERR_TMA_TIMEOUT);
     }
@@ -697,7 +713,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         obs[2 * j] = make_float4(px, px, pvx, pvx);
         obs[2 * j + 1] = make_float4(py, py, pvy, pvy);
     }
-    if (!stage_blob(blob, A.blob, L.init * 4, &s_mbar, A.err_flag)) return false;
+    if (!stage_blob(blob, A.blob, L.init * 4, &s_mbar, A.err_flag, A.missing_tx)) return false;
     const float* __restrict__ gblob = A.blob;  // first-step blocks: read once, from global memory
 
     const float rho = A.rho;
@@ -1159,7 +1175,7 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
         obs[j] = make_float4(-__ldg(o + 0) * A.inv_a, -__ldg(o + 1) * A.inv_b, -(__ldg(o + 2) - v0) * A.inv_a,
                              -__ldg(o + 3) * A.inv_b);
     }
-    if (!stage_blob(blob, A.blob + base, (L.total - base) * 4, &s_mbar, A.err_flag)) return;
+    if (!stage_blob(blob, A.blob + base, (L.total - base) * 4, &s_mbar, A.err_flag, A.missing_tx)) return;
 
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
@@ -1526,12 +1542,7 @@ __global__ void __launch_bounds__(256) score_kernel(const ScoreArgs S)
 // completion times, [2 + S, 2 + 2S) scene argmin keys, then one queue counter
 // per horizon group (the grouped schedule launches one kernel per group).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+// (global_ns: the device global timer, defined with the staging wait)
 
 template <int NC, int MAXT>
 __global__ void __launch_bounds__(MAXT, MinBlocks<NC, MAXT>::value)
@@ -1625,6 +1636,7 @@ struct mmpc_ctx {
     unsigned long long* d_scratch = nullptr;  // [0] packed argmin key, [1] low: ticket, high: error flags, [2] work count
     int sm_count = -1;                        // SMs of the device (queried on the first solve)
     int last_variant = 0;
+    int debug_missing = 0;  // mmpc_debug_expire_wait: bytes the staging wait expects beyond the copy
     std::string err = "no error";
     // device buffers of mmpc_step_host, grown on demand: inputs (ego, obstacles,
     // goals) and outputs (coef, resid, iters, cost, argmin) for up to host_cap goals
@@ -1828,6 +1840,7 @@ extern "C" int mmpc_solve(mmpc_ctx* ctx, const float* ego, const float* obst, in
     a.coef_out = coef_out; a.lam_out = lam_out; a.resid_out = resid_out; a.iters_out = iters_out;
     a.err_flag = reinterpret_cast<unsigned*>(ctx->d_scratch + 1) + 1;
     a.work = ctx->d_scratch + 2;
+    a.missing_tx = ctx->debug_missing;
     a.cull = p.cull ? 1 : 0;
     int variant = p.variant;
     if (variant == 0) {
@@ -1891,6 +1904,37 @@ extern "C" int mmpc_take_work_count(mmpc_ctx* ctx, unsigned long long* elements)
     if (e == cudaSuccess) e = cudaMemcpy(elements, ctx->d_scratch + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_scratch + 2, 0, sizeof(unsigned long long));
     return e == cudaSuccess ? MMPC_OK : cuda_fail(ctx, e, "mmpc_take_work_count");
+}
+
+namespace {
+
+// Reads and clears the device error word of a context (device scratch [1],
+// high half) after the stream has drained.
+int take_error_word(mmpc_ctx* ctx, cudaStream_t st, unsigned* word)
+{
+    unsigned* d_word = reinterpret_cast<unsigned*>(ctx->d_scratch + 1) + 1;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(word, d_word, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && *word) e = cudaMemset(d_word, 0, sizeof(unsigned));
+    return e == cudaSuccess ? MMPC_OK : cuda_fail(ctx, e, "mmpc_status");
+}
+
+}  // namespace
+
+extern "C" int mmpc_status(mmpc_ctx* ctx, void* stream)
+{
+    if (!ctx || !ctx->d_blob) return fail(nullptr, MMPC_ERR_NOT_SETUP, "context not set up");
+    unsigned word = 0;
+    const int rc = take_error_word(ctx, reinterpret_cast<cudaStream_t>(stream), &word);
+    if (rc != MMPC_OK) return rc;
+    return word ? fail(ctx, MMPC_ERR_TIMEOUT, "a bounded device wait expired (staging of the constants)") : MMPC_OK;
+}
+
+extern "C" int mmpc_debug_expire_wait(mmpc_ctx* ctx, int on)
+{
+    if (!ctx || !ctx->d_blob) return fail(nullptr, MMPC_ERR_NOT_SETUP, "context not set up");
+    ctx->debug_missing = on ? 16 : 0;
+    return MMPC_OK;
 }
 
 extern "C" int mmpc_step_host(mmpc_ctx* ctx, const mmpc_meta* meta, const float* ego, const float* obst, int m,
@@ -2373,6 +2417,7 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         a.coef_out = sc.coef_out; a.lam_out = sc.lam_out; a.resid_out = sc.resid_out; a.iters_out = sc.iters_out;
         a.err_flag = reinterpret_cast<unsigned*>(c->d_scratch + 1) + 1;
         a.work = c->d_scratch + 2;  // counted per scene, read with mmpc_take_work_count
+        a.missing_tx = c->debug_missing;
         ScoreArgs& g = b->sargs[s];
         g = ScoreArgs{};
         g.N = p.N; g.n = p.n; g.B = sc.B; g.kind = meta->kind;
@@ -2522,6 +2567,20 @@ extern "C" int mmpc_batch_set_fallback(mmpc_batch* b, int on)
     if (!b) return batch_fail("mmpc_batch_set_fallback: NULL batch", MMPC_ERR_NOT_SETUP);
     b->fallback = on != 0;
     return MMPC_OK;
+}
+
+extern "C" int mmpc_batch_status(mmpc_batch* b, void* stream)
+{
+    if (!b) return fail(nullptr, MMPC_ERR_NOT_SETUP, "batch not created");
+    bool expired = false;
+    for (const mmpc_scene& sc : b->scenes) {
+        unsigned word = 0;
+        const int rc = take_error_word(sc.ctx, reinterpret_cast<cudaStream_t>(stream), &word);
+        if (rc != MMPC_OK) return rc;
+        expired = expired || word != 0;
+    }
+    return expired ? fail(nullptr, MMPC_ERR_TIMEOUT, "a bounded device wait expired (staging of the constants)")
+                   : MMPC_OK;
 }
 
 extern "C" int mmpc_batch_fallbacks(mmpc_batch* b, int* count)

@@ -31,7 +31,7 @@ EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc
             "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
             "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
             "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_fallbacks", "mmpc_step_host",
-            "mmpc_measure_peaks")
+            "mmpc_measure_peaks", "mmpc_status", "mmpc_batch_status", "mmpc_debug_expire_wait")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
 
@@ -154,6 +154,12 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_batch_fallbacks.restype = ctypes.c_int
     L.mmpc_measure_peaks.argtypes = [ctypes.POINTER(MmpcPeaks), ctypes.c_int, vp]
     L.mmpc_measure_peaks.restype = ctypes.c_int
+    L.mmpc_status.argtypes = [vp, vp]
+    L.mmpc_status.restype = ctypes.c_int
+    L.mmpc_batch_status.argtypes = [vp, vp]
+    L.mmpc_batch_status.restype = ctypes.c_int
+    L.mmpc_debug_expire_wait.argtypes = [vp, ctypes.c_int]
+    L.mmpc_debug_expire_wait.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -346,6 +352,19 @@ class Solver:
         mmpc_solve(self.ctx, ego, obst, goals, coef, warm_coef, warm_lam, lam, resid, iters, stream)
         return SolveResult(coef, lam, resid, iters)
 
+    def status(self, stream=None) -> None:
+        """Raises MmpcError(MMPC_ERR_TIMEOUT) if a bounded device wait of a
+        solve on this context expired since the last call (mmpc_status)."""
+        rc = lib().mmpc_status(self.ctx, _stream(stream))
+        if rc != MMPC_OK:
+            _err(self.ctx, rc)
+
+    def expire_waits(self, on: bool) -> None:
+        """Test hook of the failure path (mmpc_debug_expire_wait)."""
+        rc = lib().mmpc_debug_expire_wait(self.ctx, 1 if on else 0)
+        if rc != MMPC_OK:
+            _err(self.ctx, rc)
+
     def score(self, meta: dict | MmpcMeta, coef, stream=None):
         import torch
         mt = meta if isinstance(meta, MmpcMeta) else make_meta(**meta)
@@ -376,8 +395,10 @@ class Batch:
     solve launch over all (scene, trajectory) items, one scoring launch, a
     per-scene argmin.  `scenes` is a list of dicts with keys params (dict),
     ego, obst (CUDA float32 tensors, obst [m, 4] or None), goals ([B, 3]) and
-    optionally warm_coef, warm_lam ([B, 3n]).  Scenes with equal parameters
-    and obstacle counts share one context.  The outputs are allocated here
+    optionally warm_coef, warm_lam ([B, 3n]) and solver (a caller-owned
+    Solver of the scene's parameters and obstacle count, used as is and not
+    closed here).  Other scenes with equal parameters and obstacle counts
+    share one context.  The outputs are allocated here
     once, as flat tensors over all scenes (`flat`) with per-scene views
     (`out`); `run` only enqueues kernels, so it can be captured in a CUDA
     graph.  All scenes must have n <= 12, or all n > 12."""
@@ -409,11 +430,14 @@ class Batch:
             for i, sc in enumerate(scenes):
                 obst = sc["obst"]
                 m = 0 if obst is None else int(obst.shape[0])
-                key = _params_key(sc["params"], m)
-                if key not in cache:
-                    cache[key] = Solver(sc["params"], m)
-                    self.solvers.append(cache[key])
-                sv = cache[key]
+                if sc.get("solver") is not None:  # a caller-owned context, shared, not closed here
+                    sv = sc["solver"]
+                else:
+                    key = _params_key(sc["params"], m)
+                    if key not in cache:
+                        cache[key] = Solver(sc["params"], m)
+                        self.solvers.append(cache[key])
+                    sv = cache[key]
                 B, n = Bs[i], ns[i]
                 F = self.flat
                 o = dict(coef=F["coef"][oc:oc + 3 * n * B].view(B, 3 * n),
@@ -483,6 +507,13 @@ class Batch:
 
     def set_fallback(self, on: bool) -> None:
         rc = lib().mmpc_batch_set_fallback(self.handle, 1 if on else 0)
+        if rc != MMPC_OK:
+            _err(None, rc)
+
+    def status(self, stream=None) -> None:
+        """Raises MmpcError(MMPC_ERR_TIMEOUT) if a bounded device wait of the
+        batch's solves expired since the last call (mmpc_batch_status)."""
+        rc = lib().mmpc_batch_status(self.handle, _stream(stream))
         if rc != MMPC_OK:
             _err(None, rc)
 

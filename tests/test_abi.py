@@ -120,6 +120,10 @@ def test_calls_without_context_fail_cleanly():
     pk = mmpc.MmpcPeaks()
     assert L.mmpc_measure_peaks(None, 3, None) == mmpc.MMPC_ERR_INVALID_ARG
     assert L.mmpc_measure_peaks(ctypes.byref(pk), 0, None) == mmpc.MMPC_ERR_INVALID_ARG
+    # status and the failure-path hook need a context or batch
+    assert L.mmpc_status(None, None) == mmpc.MMPC_ERR_NOT_SETUP
+    assert L.mmpc_batch_status(None, None) == mmpc.MMPC_ERR_NOT_SETUP
+    assert L.mmpc_debug_expire_wait(None, 1) == mmpc.MMPC_ERR_NOT_SETUP
 
 
 def test_setup_rejects_bad_buffers():

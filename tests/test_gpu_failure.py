@@ -1,0 +1,72 @@
+"""The failure path of the solve kernels, without a GPU fault.
+
+Every device wait is bounded.  A test hook (mmpc_debug_expire_wait) makes the
+staging wait of the constants expect 16 bytes that no copy delivers -- a wait
+on something nothing completes -- so each CTA's wait runs out after its time
+limit (0.2 s, then a second bounded wait), the expiry lands in the context's
+error word, the CTA returns, and mmpc_status / mmpc_batch_status report
+MMPC_ERR_TIMEOUT.  The context stays usable: with the hook off, the next
+solve is bit-identical to one before the failure.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2109_10392_gb300 import mmpc, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda:0")
+
+
+def test_expired_wait_is_reported_and_the_context_stays_usable():
+    import torch
+    sc = scenes.scene_small(3)
+    ego, obst, goals = _dev(sc.ego), _dev(sc.obst), _dev(sc.goals)
+    s = mmpc.Solver(sc.params, sc.obst.shape[0])
+    ref = s.solve(ego, obst, goals)
+    s.status()  # nothing expired
+    ref_coef = ref.coef.clone()
+
+    s.expire_waits(True)
+    t0 = time.time()
+    s.solve(ego, obst, goals)
+    with pytest.raises(mmpc.MmpcError) as ei:
+        s.status()
+    dt = time.time() - t0
+    assert ei.value.code == mmpc.MMPC_ERR_TIMEOUT
+    assert 0.3 < dt < 20.0, dt  # two bounded passes of 0.2 s, all CTAs at once
+    s.status()  # the word was cleared
+
+    s.expire_waits(False)
+    again = s.solve(ego, obst, goals)
+    s.status()
+    torch.cuda.synchronize()
+    assert torch.equal(again.coef, ref_coef)
+    s.close()
+
+
+def test_expired_wait_in_a_batch_is_reported():
+    sc = scenes.scene_small(4)
+    ego, obst, goals = _dev(sc.ego), _dev(sc.obst), _dev(sc.goals)
+    s = mmpc.Solver(sc.params, sc.obst.shape[0])
+    s.expire_waits(True)  # taken by batches created from now on
+    desc = [dict(params=sc.params, ego=ego, obst=obst, goals=goals, solver=s)]
+    bad = mmpc.Batch(desc, sc.meta)
+    bad.run()
+    with pytest.raises(mmpc.MmpcError) as ei:
+        bad.status()
+    assert ei.value.code == mmpc.MMPC_ERR_TIMEOUT
+    bad.close()
+    s.expire_waits(False)
+    good = mmpc.Batch(desc, sc.meta)
+    good.run()
+    good.status()
+    assert np.all(np.isfinite(good.out[0]["coef"].cpu().numpy()))
+    good.close()
+    s.status()
+    s.close()
