@@ -188,7 +188,9 @@ int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coef, int B, f
  * stream.  Host buffers should be page-locked for the copies to run
  * asynchronously.  The device buffers grow on demand: the first call with a
  * larger B allocates (after synchronising the stream), later calls allocate
- * nothing.  m must be the m of mmpc_setup.  Errors as mmpc_solve / mmpc_score. */
+ * nothing.  m must be the m of mmpc_setup.  Errors as mmpc_solve / mmpc_score,
+ * and MMPC_ERR_TIMEOUT (read and cleared as by mmpc_status) when a bounded
+ * device wait of the step expired: the outputs are then not valid. */
 int mmpc_step_host(mmpc_ctx* ctx, const mmpc_meta* meta, const float* ego, const float* obst, int m,
                    const float* goals, int B, float* coef_out, float* resid_out, float* cost_out, int* argmin_out,
                    void* stream);

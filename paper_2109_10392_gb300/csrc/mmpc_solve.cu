@@ -1984,7 +1984,15 @@ extern "C" int mmpc_step_host(mmpc_ctx* ctx, const mmpc_meta* meta, const float*
     if (e == cudaSuccess && B > 0)
         e = cudaMemcpyAsync(cost_out, d_cost, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(argmin_out, d_argmin, sizeof(int), cudaMemcpyDeviceToHost, st);
+    // the context's error word rides along: an expired device wait is reported here
+    unsigned word = 0;
+    unsigned* d_word = reinterpret_cast<unsigned*>(ctx->d_scratch + 1) + 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&word, d_word, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && word) {
+        e = cudaMemset(d_word, 0, sizeof(unsigned));
+        if (e == cudaSuccess) return fail(ctx, MMPC_ERR_TIMEOUT, "a bounded device wait expired (staging of the constants)");
+    }
     return e == cudaSuccess ? MMPC_OK : cuda_fail(ctx, e, "mmpc_step_host");
 }
 

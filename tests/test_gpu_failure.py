@@ -50,6 +50,31 @@ def test_expired_wait_is_reported_and_the_context_stays_usable():
     s.close()
 
 
+def test_expired_wait_in_a_host_step_is_reported():
+    """mmpc_step_host is synchronous: it reports the expiry itself."""
+    import torch
+    sc = scenes.scene_small(5)
+    m, B = sc.obst.shape[0], len(sc.goals)
+    s = mmpc.Solver(sc.params, m)
+    meta = mmpc.make_meta(**sc.meta)
+    pin = lambda a: torch.tensor(np.asarray(a, dtype=np.float32)).pin_memory()  # noqa: E731
+    ego, obst, goals = pin(sc.ego), pin(sc.obst), pin(sc.goals)
+    coef = torch.zeros((B, 3 * s.n)).pin_memory()
+    cost = torch.zeros((B,)).pin_memory()
+    am = torch.zeros((1,), dtype=torch.int32).pin_memory()
+    mmpc.mmpc_step_host(s.ctx, meta, ego, obst, goals, coef, cost, am)
+    ref = coef.clone()
+    s.expire_waits(True)
+    with pytest.raises(mmpc.MmpcError) as ei:
+        mmpc.mmpc_step_host(s.ctx, meta, ego, obst, goals, coef, cost, am)
+    assert ei.value.code == mmpc.MMPC_ERR_TIMEOUT
+    s.expire_waits(False)
+    mmpc.mmpc_step_host(s.ctx, meta, ego, obst, goals, coef, cost, am)
+    assert torch.equal(coef, ref)
+    s.status()
+    s.close()
+
+
 def test_expired_wait_in_a_batch_is_reported():
     sc = scenes.scene_small(4)
     ego, obst, goals = _dev(sc.ego), _dev(sc.obst), _dev(sc.goals)
