@@ -244,9 +244,15 @@ def run_mine(args):
     # call per step copies the pinned inputs in, solves, scores, copies the
     # coefficients, residuals, costs and argmin back and waits for the stream
     Ke = min(K, args.e2e_steps)
-    h_in = [torch.tensor(np.asarray(a, dtype=np.float32)).contiguous().pin_memory()
-            for a in (sc.ego, sc.obst.reshape(-1, 4), sc.goals)]
-    h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (coef, resid, cost, argmin)]
+    # one pinned block per direction, in the device order (ego, obstacles, goals /
+    # coef, resid, cost): mmpc_step_host then makes one copy each way
+    parts = [np.asarray(a, dtype=np.float32).reshape(-1) for a in (sc.ego, sc.obst.reshape(-1, 4), sc.goals)]
+    blk_in = torch.from_numpy(np.concatenate(parts)).pin_memory()
+    h_in = [blk_in[:4], blk_in[4:4 + 4 * m].view(m, 4), blk_in[4 + 4 * m:].view(-1, 3)]
+    nc, nr = coef.numel(), resid.numel()
+    blk_out = torch.empty(nc + nr + cost.numel(), dtype=torch.float32).pin_memory()
+    h_out = [blk_out[:nc].view(coef.shape), blk_out[nc:nc + nr].view(resid.shape), blk_out[nc + nr:].view(cost.shape),
+             torch.empty(argmin.shape, dtype=argmin.dtype).pin_memory()]
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = sum(t.numel() * t.element_size() for t in h_out)
     e2e_units = 0

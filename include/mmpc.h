@@ -186,7 +186,9 @@ int mmpc_score(mmpc_ctx* ctx, const mmpc_meta* meta, const float* coef, int B, f
  * and mmpc_score on `stream`, copies coef [B][3n], resid [B][4] (may be
  * NULL), cost [B] and argmin [1] back to host buffers, and waits for the
  * stream.  Host buffers should be page-locked for the copies to run
- * asynchronously.  The device buffers grow on demand: the first call with a
+ * asynchronously; when ego, obst and goals are contiguous in that order in
+ * host memory the inputs go in one copy, and when coef, resid and cost are
+ * contiguous in that order the outputs come back in one copy.  The device buffers grow on demand: the first call with a
  * larger B allocates (after synchronising the stream), later calls allocate
  * nothing.  m must be the m of mmpc_setup.  Errors as mmpc_solve / mmpc_score,
  * and MMPC_ERR_TIMEOUT (read and cleared as by mmpc_status) when a bounded

@@ -1966,23 +1966,37 @@ extern "C" int mmpc_step_host(mmpc_ctx* ctx, const mmpc_meta* meta, const float*
     float* d_cost = d_resid + 4 * (size_t)B;
     int* d_iters = reinterpret_cast<int*>(d_cost + B);
     int* d_argmin = d_iters + B;
-    // one host->device copy of the inputs when they are contiguous in host memory
-    cudaError_t e = cudaMemcpyAsync(d_ego, ego, sizeof(float) * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(d_obst, obst, sizeof(float) * 4 * (size_t)m, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && B > 0) e = cudaMemcpyAsync(d_goals, goals, sizeof(float) * 3 * (size_t)B, cudaMemcpyHostToDevice, st);
+    // one host->device copy of the inputs when the host holds them contiguously in the
+    // device order (ego, obstacles, goals), else one copy per array
+    cudaError_t e = cudaSuccess;
+    const bool in_contig = (m == 0 || obst == ego + 4) && (B == 0 || goals == ego + 4 + 4 * (size_t)m);
+    if (in_contig) {
+        e = cudaMemcpyAsync(d_ego, ego, sizeof(float) * (4 + 4 * (size_t)m + 3 * (size_t)B), cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaMemcpyAsync(d_ego, ego, sizeof(float) * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpyAsync(d_obst, obst, sizeof(float) * 4 * (size_t)m, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && B > 0)
+            e = cudaMemcpyAsync(d_goals, goals, sizeof(float) * 3 * (size_t)B, cudaMemcpyHostToDevice, st);
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "mmpc_step_host input copy");
     int rc = mmpc_solve(ctx, d_ego, m ? d_obst : nullptr, m, d_goals, B, nullptr, nullptr, d_coef, nullptr, d_resid,
                         d_iters, stream);
     if (rc != MMPC_OK) return rc;
     rc = mmpc_score(ctx, meta, d_coef, B, d_cost, d_argmin, stream);
     if (rc != MMPC_OK) return rc;
-    // the outputs are contiguous on the device: coef, resid, cost as one block when the host asks for all three
+    // the outputs are contiguous on the device (coef, resid, cost): one device->host
+    // copy when the host asks for all three, contiguously in that order
     e = cudaSuccess;
-    if (B > 0) e = cudaMemcpyAsync(coef_out, d_coef, sizeof(float) * 3 * (size_t)n * B, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && B > 0 && resid_out)
-        e = cudaMemcpyAsync(resid_out, d_resid, sizeof(float) * 4 * (size_t)B, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && B > 0)
-        e = cudaMemcpyAsync(cost_out, d_cost, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, st);
+    const bool out_contig = resid_out && resid_out == coef_out + 3 * (size_t)n * B && cost_out == resid_out + 4 * (size_t)B;
+    if (B > 0 && out_contig) {
+        e = cudaMemcpyAsync(coef_out, d_coef, sizeof(float) * (3 * (size_t)n + 5) * B, cudaMemcpyDeviceToHost, st);
+    } else if (B > 0) {
+        e = cudaMemcpyAsync(coef_out, d_coef, sizeof(float) * 3 * (size_t)n * B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && resid_out)
+            e = cudaMemcpyAsync(resid_out, d_resid, sizeof(float) * 4 * (size_t)B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cost_out, d_cost, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, st);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(argmin_out, d_argmin, sizeof(int), cudaMemcpyDeviceToHost, st);
     // the context's error word rides along: an expired device wait is reported here
     unsigned word = 0;

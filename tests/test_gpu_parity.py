@@ -387,6 +387,15 @@ def test_step_through_host_memory():
         torch.cuda.synchronize()
         assert torch.equal(hc, d.coef.cpu()) and torch.equal(hr, d.resid.cpu())
         assert torch.equal(hcost, cost.cpu()) and int(ham.item()) == int(am.item())
+        # the same through one contiguous pinned block per direction (one copy each way)
+        blk_in = torch.cat([ego.reshape(-1), obst.reshape(-1), goals[:B].reshape(-1)]).pin_memory()
+        blk_out = torch.zeros(B * (3 * n + 5)).pin_memory()
+        bc = blk_out[:3 * n * B].view(B, 3 * n)
+        br = blk_out[3 * n * B:(3 * n + 4) * B].view(B, 4)
+        bcost = blk_out[(3 * n + 4) * B:]
+        mmpc.mmpc_step_host(s.ctx, meta, blk_in[:4], blk_in[4:4 + 4 * m].view(m, 4), blk_in[4 + 4 * m:].view(B, 3),
+                            bc, bcost, ham, br)
+        assert torch.equal(bc, hc) and torch.equal(br, hr) and torch.equal(bcost, hcost)
     with pytest.raises(mmpc.MmpcError):
         mmpc.mmpc_step_host(s.ctx, meta, ego, obst[:3].contiguous(), goals, hc, hcost, ham)
     s.close()
