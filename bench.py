@@ -664,6 +664,86 @@ def run_reference(args):
     }
 
 
+SWEEP_B = (11, 32, 128, 512, 1024, 2048, 4096, 16384, 65536)
+
+
+def run_sweep(args):
+    """Trajectories/s against the batch size (the counterpart of the paper's
+    time-vs-batch-size experiment, Fig. 2b): one dense scene of the
+    1024-goal distribution (50 obstacles, N = 100, n = 12, 100 iterations,
+    residual target 1e-2 m) per B, solve + score timed with CUDA events
+    between L2 flushes; and one MPC cycle of the paper's own setting (11 goals,
+    10 obstacles), the figure its Table V times on a CPU."""
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc, scenes
+    rank, world, _ = rank_env()
+    if world > 1:
+        raise SystemExit("--workload sweep runs on one GPU")
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    f32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).contiguous()  # noqa: E731
+
+    def time_scene(sc, target_s=0.5):
+        params = dict(sc.params, tol=TOL, check_every=CHECK_EVERY)
+        B, m, n = len(sc.goals), sc.obst.shape[0], params["n"]
+        solver = mmpc.Solver(params, m)
+        meta = mmpc.make_meta(**sc.meta)
+        ego, obst, goals = f32(sc.ego), f32(sc.obst), f32(sc.goals)
+        coef = torch.empty((B, 3 * n), dtype=torch.float32, device=dev)
+        resid = torch.empty((B, 4), dtype=torch.float32, device=dev)
+        iters = torch.empty((B,), dtype=torch.int32, device=dev)
+        cost = torch.empty((B,), dtype=torch.float32, device=dev)
+        argmin = torch.empty((1,), dtype=torch.int32, device=dev)
+
+        def step(e0=None, e1=None):
+            flush.zero_()
+            if e0 is not None:
+                e0.record(stream)
+            mmpc.mmpc_solve(solver.ctx, ego, obst, goals, coef, None, None, None, resid, iters, stream)
+            mmpc.mmpc_score(solver.ctx, meta, coef, cost, argmin, stream)
+            if e1 is not None:
+                e1.record(stream)
+
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
+            step(a, b)
+        torch.cuda.synchronize(dev)
+        est = max(a.elapsed_time(b), 1e-3)
+        K = int(min(2000, max(5, target_s * 1e3 / est)))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for e0, e1 in ev:
+            step(e0, e1)
+        torch.cuda.synchronize(dev)
+        solver.status()
+        ms = sorted(e0.elapsed_time(e1) for e0, e1 in ev)
+        conv = int((resid[:, :3].max(dim=1).values <= TOL).sum().item())
+        solver.close()
+        return dict(B=B, obstacles=m, steps=K, ms_median=ms[K // 2], ms_mean=sum(ms) / K,
+                    trajectories_per_s=B / (sum(ms) / K * 1e-3), us_per_trajectory=sum(ms) / K * 1e3 / B,
+                    converged=conv)
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    curve = [time_scene(scenes.scene_custom(seed=B, B=B, m=50, N=100, n=12)) for B in SWEEP_B]
+    cycle = time_scene(scenes.scene_small(0))
+    clocks = sampler.stop()
+    best = max(curve, key=lambda r: r["trajectories_per_s"])
+    return {
+        "metric": "trajectories/s against the batch size (one scene per solve)", "value": best["trajectories_per_s"],
+        "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": args.warmup, "ms_per_step": best["ms_mean"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "highway_sweep_B11-65536_m50_N100_n12_K100_tol0.01", "sizes": list(SWEEP_B),
+                   "l2": "flushed between timed steps (256 MiB memset outside the event brackets)",
+                   "timing": "solve + score per step, CUDA events, about 0.5 s of steps per size"},
+        "detail": {"curve": curve, "mpc_cycle_paper_setting": cycle,
+                   "paper_context": "Table V of the paper: 0.07 s per MPC cycle at batch 11 on an i7-8750 CPU"},
+        "clocks": clocks,
+    }
+
+
 def add_measured_peak(roofline: dict) -> None:
     """Beside the derived peak: the FP32 lane-op rate the device reaches on
     saturating FFMA / packed FFMA2 chains (mmpc_measure_peaks, run after the
@@ -690,10 +770,11 @@ def main():
     ap.add_argument("--no-cull", action="store_true", help="evaluate every obstacle-sample pair (no culling)")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                     help="solve kernel: 1 one sample per thread, 2 two samples per thread, 0 automatic")
-    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "warm", "precision"],
+    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "warm", "precision", "sweep"],
                     help="scene: one 1024-goal scene per GPU; batch: 256 uneven scenes per GPU in one graph; "
                          "warm: learned warm start (trained in the run) against the cold start; precision: "
-                         "one 16384-goal scene, 30 obstacles, N = 200, n = 16")
+                         "one 16384-goal scene, 30 obstacles, N = 200, n = 16; sweep: trajectories/s against the "
+                         "batch size (11 to 65536 goals) and one MPC cycle of the paper's 11-goal setting")
     ap.add_argument("--stall", action="store_true",
                     help="opt-in stall stop (residual > 1 m and not halved over two checks) for scene and batch")
     ap.add_argument("--warm-train-scenes", type=int, default=200_000)
@@ -707,7 +788,7 @@ def main():
     if args.impl == "reference":
         out = run_reference(args)
     else:
-        out = {"batch": run_batch, "warm": run_warm}.get(args.workload, run_mine)(args)
+        out = {"batch": run_batch, "warm": run_warm, "sweep": run_sweep}.get(args.workload, run_mine)(args)
         if out is not None and out.get("roofline", {}).get("bound") == "alu":
             add_measured_peak(out["roofline"])
     if out is not None:
