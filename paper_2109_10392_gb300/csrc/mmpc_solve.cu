@@ -91,9 +91,10 @@ __host__ __device__ constexpr int k_stride(int NC) { return NC == 16 ? 20 : NC; 
 static BlobLayout blob_layout(int N, int NC)
 {
     auto up4 = [](int v) { return (v + 3) & ~3; };
-    // pair rows cover 32 ceil(ceil(N/2) / 32) pairs and sample rows 32
-    // ceil(N/32) samples: one per thread of the launch, zero beyond N
-    const int NP = 32 * (((N + 1) / 2 + 31) / 32);
+    // pair rows: the ceil(N/2) pairs, then one zero row that every lane
+    // beyond them reads; sample rows 32 ceil(N/32) samples, one per thread of
+    // the launch, zero beyond N
+    const int NP = (N + 1) / 2 + 1;
     const int NS = 32 * ((N + 31) / 32);
     BlobLayout B{};
     int o = 0;
@@ -642,8 +643,9 @@ constexpr int MAX_WARPS = 8;
 
 template <int NC, int MAXT>
 struct MinBlocks {
-    // NC = 16 with 128 threads (N = 129..256) holds ~60 KB of shared memory,
-    // so at most 3 CTAs fit an SM: the register budget follows (no spills)
+    // NC = 16 with 128 threads (N = 129..256): 3 CTAs per SM and the
+    // register budget that allows (no spills); a fourth CTA at 128 registers
+    // spills and was slower (11.0 against 10.4 ms at N = 200)
     static constexpr int value = MAXT <= 64 ? 8 : (MAXT <= 128 ? (NC == 16 ? 3 : 4) : 2);
 };
 
@@ -718,7 +720,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
 
     const float rho = A.rho;
     const float a2 = A.a * A.a, b2 = A.b * A.b;
-    const int ip = idle ? 0 : tid;  // rows are padded to whole warps (zero rows beyond N)
+    const int ip = (idle || tid >= NP) ? NP : tid;  // lanes beyond the pairs read the zero row NP
     constexpr int RS = pair_stride(NC);
     const float* PP = blob + L.PP + ip * RS;
     const float* PdP = blob + L.PdP + ip * RS;
