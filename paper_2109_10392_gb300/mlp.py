@@ -91,6 +91,7 @@ def _check(rc):
 
 _ptr = mmpc._ptr
 _stream = mmpc._stream
+_need = mmpc._need
 
 
 class SceneTable:
@@ -167,15 +168,21 @@ def warm_encode(table: SceneTable, n: int, T: float, mu, sigma, stream=None):
 
 def column_stats(X, mean_out, std_out, stream=None):
     rows, cols = int(X.shape[0]), int(X.shape[1])
+    _need(mean_out, cols, "mean_out")
+    _need(std_out, cols, "std_out")
     _check(lib().mmpc_column_stats(_ptr(X), rows, cols, _ptr(mean_out), _ptr(std_out), _stream(stream)))
 
 
 def standardize(X, mean, sd, out, stream=None):
+    _need(mean, int(X.shape[1]), "mean")
+    _need(sd, int(X.shape[1]), "sd")
+    _need(out, X.numel(), "out")
     _check(lib().mmpc_standardize(_ptr(X), int(X.shape[0]), int(X.shape[1]), _ptr(mean), _ptr(sd), _ptr(out),
                                   _stream(stream)))
 
 
 def gather_rows(src, idx, out, stream=None):
+    _need(out, int(idx.shape[0]) * int(src.shape[1]), "out")
     _check(lib().mmpc_gather_rows(_ptr(src), int(src.shape[0]), int(src.shape[1]), _ptr(idx, "int32"),
                                   int(idx.shape[0]), _ptr(out), _stream(stream)))
 
@@ -203,9 +210,16 @@ class Mlp:
         self.max_batch = int(max_batch)
 
     def forward(self, X, Y, stream=None):
+        M = int(X.shape[0])
+        _need(X, M * self.widths[0], "X")
+        _need(Y, M * self.widths[-1], "Y")
         _check(lib().mmpc_mlp_forward(self.handle, _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)))
 
     def loss_grad(self, X, Z, loss=None, stream=None):
+        M = int(X.shape[0])
+        _need(X, M * self.widths[0], "X")
+        _need(Z, M * self.widths[-1], "Z")
+        _need(loss, 1, "loss")
         _check(lib().mmpc_mlp_loss_grad(self.handle, _ptr(X), _ptr(Z), int(X.shape[0]), _ptr(loss), _stream(stream)))
 
     def set_tensor_cores(self, on):

@@ -196,6 +196,32 @@ def mmpc_build(params: MmpcParams, m: int) -> np.ndarray:
     return buf[:size]
 
 
+# (N, n, m) of every context set up here, so that the calls below can refuse
+# buffers too small for the batch before anything is launched (the C ABI
+# takes raw pointers and trusts their sizes)
+_CTX_SHAPE: dict = {}
+
+
+def _ctx_shape(ctx):
+    return _CTX_SHAPE.get(getattr(ctx, "value", ctx))
+
+
+def _need(t, count: int, what: str) -> None:
+    if t is not None and t.numel() < count:
+        raise ValueError(f"{what} holds {t.numel()} elements, the call needs {count}")
+
+
+def _check_batch_inputs(ego, obst, m: int, goals) -> int:
+    """B of a [B, 3] goal tensor; ego holds 4 values, obst [m, 4]."""
+    B = int(goals.shape[0])
+    if goals.numel() != 3 * B:
+        raise ValueError("goals must be [B, 3]")
+    _need(ego, 4, "ego")
+    if m:
+        _need(obst, 4 * m, "obst")
+    return B
+
+
 def mmpc_setup(params: MmpcParams, m: int, buf: np.ndarray) -> ctypes.c_void_p:
     buf = np.ascontiguousarray(buf, dtype=np.float64)
     ctx = ctypes.c_void_p()
@@ -203,6 +229,7 @@ def mmpc_setup(params: MmpcParams, m: int, buf: np.ndarray) -> ctypes.c_void_p:
                           buf.size, ctypes.byref(ctx))
     if rc != MMPC_OK:
         _err(None, rc)
+    _CTX_SHAPE[ctx.value] = (int(params.N), int(params.n), int(m))
     return ctx
 
 
@@ -230,7 +257,15 @@ def mmpc_solve(ctx, ego, obst, goals, coef_out, warm_coef=None, warm_lam=None, l
     """Enqueue Algorithm 1 for the batch on `stream` (default: torch's current
     stream).  All tensors are CUDA, contiguous, float32 (iters_out int32)."""
     m = 0 if obst is None else int(obst.shape[0])
-    B = int(goals.shape[0])
+    B = _check_batch_inputs(ego, obst, m, goals)
+    shp = _ctx_shape(ctx)
+    if shp is not None:
+        n = shp[1]
+        for t, what in ((coef_out, "coef_out"), (lam_out, "lam_out"), (warm_coef, "warm_coef"),
+                        (warm_lam, "warm_lam")):
+            _need(t, 3 * n * B, what)
+        _need(resid_out, 4 * B, "resid_out")
+        _need(iters_out, B, "iters_out")
     rc = lib().mmpc_solve(ctx, _ptr(ego), _ptr(obst) if m else None, m, _ptr(goals), B, _ptr(warm_coef),
                           _ptr(warm_lam), _ptr(coef_out), _ptr(lam_out), _ptr(resid_out),
                           _ptr(iters_out, "int32"), _stream(stream))
@@ -240,6 +275,11 @@ def mmpc_solve(ctx, ego, obst, goals, coef_out, warm_coef=None, warm_lam=None, l
 
 def mmpc_score(ctx, meta: MmpcMeta, coef, cost_out, argmin_out, stream=None) -> None:
     B = int(coef.shape[0])
+    shp = _ctx_shape(ctx)
+    if shp is not None:
+        _need(coef, 3 * shp[1] * B, "coef")
+    _need(cost_out, B, "cost_out")
+    _need(argmin_out, 1, "argmin_out")
     rc = lib().mmpc_score(ctx, ctypes.byref(meta), _ptr(coef), B, _ptr(cost_out), _ptr(argmin_out, "int32"),
                           _stream(stream))
     if rc != MMPC_OK:
@@ -250,6 +290,11 @@ def mmpc_score_static(meta: MmpcMeta, N: int, n: int, P, Pd, coef, cost_out, arg
     """Allocation-free scoring without a context (see include/mmpc.h): P and Pd
     are device float32 [N, n]; no device memory is allocated by the call."""
     B = int(coef.shape[0])
+    _need(P, int(N) * int(n), "P")
+    _need(Pd, int(N) * int(n), "Pd")
+    _need(coef, 3 * int(n) * B, "coef")
+    _need(cost_out, B, "cost_out")
+    _need(argmin_out, 1, "argmin_out")
     rc = lib().mmpc_score_static(ctypes.byref(meta), int(N), int(n), _ptr(P), _ptr(Pd), _ptr(coef), B,
                                  _ptr(cost_out), _ptr(argmin_out, "int32"), _stream(stream))
     if rc != MMPC_OK:
@@ -275,7 +320,13 @@ def mmpc_step_host(ctx, meta: MmpcMeta, ego, obst, goals, coef_out, cost_out, ar
     """One MPC step through host memory (CPU tensors, ideally pinned):
     inputs copied in, solve + score, outputs copied back, stream waited."""
     m = 0 if obst is None else int(obst.shape[0])
-    B = int(goals.shape[0])
+    B = _check_batch_inputs(ego, obst, m, goals)
+    shp = _ctx_shape(ctx)
+    if shp is not None:
+        _need(coef_out, 3 * shp[1] * B, "coef_out")
+    _need(resid_out, 4 * B, "resid_out")
+    _need(cost_out, B, "cost_out")
+    _need(argmin_out, 1, "argmin_out")
     rc = lib().mmpc_step_host(ctx, ctypes.byref(meta), _hptr(ego), _hptr(obst) if m else None, m, _hptr(goals), B,
                               _hptr(coef_out), _hptr(resid_out), _hptr(cost_out), _hptr(argmin_out, "int32"),
                               _stream(stream))
@@ -305,6 +356,7 @@ def mmpc_measure_peaks(reps: int = 3, stream=None) -> dict:
 
 def mmpc_destroy(ctx) -> None:
     if ctx:
+        _CTX_SHAPE.pop(getattr(ctx, "value", ctx), None)
         lib().mmpc_destroy(ctx)
 
 
@@ -439,6 +491,9 @@ class Batch:
                         self.solvers.append(cache[key])
                     sv = cache[key]
                 B, n = Bs[i], ns[i]
+                _check_batch_inputs(sc["ego"], obst, m, sc["goals"])
+                _need(sc.get("warm_coef"), 3 * n * B, "warm_coef")
+                _need(sc.get("warm_lam"), 3 * n * B, "warm_lam")
                 F = self.flat
                 o = dict(coef=F["coef"][oc:oc + 3 * n * B].view(B, 3 * n),
                          lam=None if F["lam"] is None else F["lam"][oc:oc + 3 * n * B].view(B, 3 * n),
@@ -477,6 +532,18 @@ class Batch:
         for t in (ego, obst, goals, warm_coef, warm_lam):
             if t is not None:
                 _ptr(t)  # type / contiguity checks
+        if goals.numel() != 3 * S * B:
+            sv.close()
+            raise ValueError("goals must be [S, B, 3]")
+        try:  # the per-scene pointers below step through these with fixed strides
+            _need(ego, 4 * S, "ego")
+            if m:
+                _need(obst, 4 * m * S, "obst")
+            _need(warm_coef, 3 * n * B * S, "warm_coef")
+            _need(warm_lam, 3 * n * B * S, "warm_lam")
+        except ValueError:
+            sv.close()
+            raise
         arr = np.zeros(max(1, S), dtype=ctypes_dtype(MmpcScene))
         i = np.arange(S, dtype=np.uint64)
         base = lambda t: np.uint64(t.data_ptr())  # noqa: E731

@@ -95,3 +95,51 @@ def test_expired_wait_in_a_batch_is_reported():
     good.close()
     s.status()
     s.close()
+
+
+def test_undersized_buffers_are_refused_before_any_launch():
+    """The binding knows each context's N, n and m and refuses buffers too
+    small for the batch (the kernels would write past them), before anything
+    is enqueued; the context keeps working."""
+    import torch
+
+    from paper_2109_10392_gb300 import mlp
+    sc = scenes.scene_small(6)
+    m = sc.obst.shape[0]
+    ego, obst, goals = _dev(sc.ego), _dev(sc.obst), _dev(sc.goals)
+    B = goals.shape[0]
+    s = mmpc.Solver(sc.params, m)
+    n = s.n
+    meta = mmpc.make_meta(**sc.meta)
+    z = lambda *shape: torch.zeros(shape, device="cuda:0")  # noqa: E731
+    with pytest.raises(ValueError):
+        mmpc.mmpc_solve(s.ctx, ego, obst, goals, z(B, 3 * n - 1))
+    with pytest.raises(ValueError):
+        mmpc.mmpc_solve(s.ctx, ego, obst, goals, z(B, 3 * n), resid_out=z(B, 3))
+    with pytest.raises(ValueError):
+        mmpc.mmpc_solve(s.ctx, ego, obst, goals, z(B, 3 * n), warm_coef=z(B - 1, 3 * n))
+    with pytest.raises(ValueError):
+        mmpc.mmpc_solve(s.ctx, ego, obst, goals.reshape(-1)[: 3 * B - 1].reshape(1, -1), z(B, 3 * n))
+    with pytest.raises(ValueError):
+        mmpc.mmpc_score(s.ctx, meta, z(B, 3 * n), z(B - 1), torch.zeros(1, dtype=torch.int32, device="cuda:0"))
+    pin = lambda *shape: torch.zeros(shape).pin_memory()  # noqa: E731
+    with pytest.raises(ValueError):
+        mmpc.mmpc_step_host(s.ctx, meta, ego.cpu(), obst.cpu(), goals.cpu(), pin(B, 3 * n - 2), pin(B),
+                            torch.zeros(1, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        mmpc.Batch([dict(params=sc.params, ego=ego, obst=obst, goals=goals, solver=s, warm_coef=z(B, n))], sc.meta)
+    with pytest.raises(ValueError):
+        mmpc.Batch.from_uniform(sc.params, ego.reshape(1, 4), obst.reshape(1, m, 4), goals.reshape(1, B, 3)[:, :-1]
+                                .contiguous().reshape(1, -1), sc.meta)
+    res = s.solve(ego, obst, goals)  # still fine
+    torch.cuda.synchronize()
+    s.status()
+    assert torch.isfinite(res.coef).all()
+    s.close()
+    widths = (64, 32, 16)
+    from paper_2109_10392_gb300 import scenes as S_
+    Ws, bs = S_.mlp_init(0, widths)
+    net = mlp.Mlp(widths, Ws, bs, max_batch=16)
+    with pytest.raises(ValueError):
+        net.forward(z(8, 64), z(8, 15))
+    net.close()
