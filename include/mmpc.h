@@ -95,7 +95,29 @@ typedef struct {
                           no longer closing in).  Not in the paper: a serving option for
                           scenes whose infeasible goals would spend the whole budget. */
     float stall_ratio; /* in (0, 1] when stall_tol > 0 */
+    int precision;     /* operands of the basis products (the evaluations P c and the
+                          contractions P^T e of Algorithm 1, both operands) as the
+                          tensor cores would take them, FP32 accumulation:
+                          MMPC_PREC_FP32 (0, the default: full FP32), MMPC_PREC_TF32 /
+                          MMPC_PREC_BF16 (both operands rounded to TF32 -- 10-bit
+                          significand, round to nearest, ties away -- or to BF16 --
+                          7-bit, round to nearest even), MMPC_PREC_TF32_SPLIT /
+                          MMPC_PREC_BF16_SPLIT (each operand as hi + lo of that type,
+                          a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi).  The projections, the
+                          QP steps (K11 applied as FP32 hi + lo) and the multipliers stay
+                          FP32; the KKT inverse is FP64 from mmpc_build.  A study of the
+                          accuracy each dtype would give (the error table of the
+                          precision workload), not a faster path: the rounding runs on
+                          the CUDA cores.  Other than 0 it needs the pair kernel with 128
+                          threads (N in 129..256), n in 13..16 and variant 0 or 2;
+                          otherwise mmpc_setup returns MMPC_ERR_INVALID_ARG. */
 } mmpc_params;
+
+#define MMPC_PREC_FP32 0
+#define MMPC_PREC_TF32 1
+#define MMPC_PREC_TF32_SPLIT 2
+#define MMPC_PREC_BF16 3
+#define MMPC_PREC_BF16_SPLIT 4
 
 typedef struct mmpc_ctx mmpc_ctx;
 
@@ -325,7 +347,7 @@ const char* mmpc_last_error(const mmpc_ctx* ctx);
 int mmpc_score_static(const mmpc_meta* meta, int N, int n, const float* P, const float* Pd, const float* coef,
                       int B, float* cost_out, int* argmin_out, void* stream);
 
-/* ABI version of this header (1). */
+/* ABI version of this header (2: mmpc_params.precision). */
 int mmpc_version(void);
 
 #ifdef __cplusplus

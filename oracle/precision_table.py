@@ -6,7 +6,12 @@ run.  This script solves seeded scenes with the FP64 oracle twice: exact,
 and with those operands rounded to bfloat16 (8 significant bits) or TF32
 (11), alone or as a hi + lo pair, or to float32 (24), the KKT inverses and
 all arithmetic staying FP64; it prints the position error of each against
-the exact solve after 100 iterations.
+the exact solve after 100 iterations.  The oracle takes the direct form of
+the QP step (rho F^T g + lambda through K11), so the rounding of F multiplies
+the large F^T g: the table measures the dtype in that form.  The GPU kernel
+contracts residuals (the increment form), where the same rounding multiplies
+small quantities; its own error table comes from the kernel's precision
+modes, measured against this oracle by the GPU tests.
 
     python oracle/precision_table.py [--sample 16]
 

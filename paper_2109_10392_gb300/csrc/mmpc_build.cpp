@@ -152,6 +152,9 @@ std::string check_params(const mmpc_params* p)
     if (p->variant < 0 || p->variant > 2) return "variant must be 0, 1 or 2";
     if (std::isnan(p->stall_tol)) return "stall_tol is NaN";
     if (p->stall_tol > 0.f && !(p->stall_ratio > 0.f && p->stall_ratio <= 1.f)) return "stall_ratio must be in (0, 1]";
+    if (p->precision < MMPC_PREC_FP32 || p->precision > MMPC_PREC_BF16_SPLIT) return "unknown precision";
+    if (p->precision != MMPC_PREC_FP32 && (p->N < 129 || p->N > 256 || p->n < 13 || p->variant == 1))
+        return "precision variants need N in 129..256, n in 13..16 and the pair kernel";
     if (p->variant == 1 && p->N > 256) return "variant 1 needs N <= 256";
     return "";
 }

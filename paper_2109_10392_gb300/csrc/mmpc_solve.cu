@@ -74,6 +74,7 @@ void set_global_error(const std::string& msg) { g_error = msg; }
 // ---------------------------------------------------------------------------
 struct BlobLayout {
     int PP, PdP, PddP, tP;                                                        // pair rows
+    int PPl, PdPl, PddPl;  // lo parts of the pair rows (split precision modes; else = the hi rows)
     int brow, lin, Q, Kxh, Kxl, Kyh, Kyl, Kp11, Kp12, K12x, K12y, C0x, C0y, C0p;  // common
     int P, Pd, Pdd, t;                                                            // sample rows
     int common, init, rows1, total;  // region starts (common, first-step blocks, sample rows) and end
@@ -88,7 +89,7 @@ struct BlobLayout {
 __host__ __device__ constexpr int pair_stride(int NC) { return 2 * NC + 4; }
 __host__ __device__ constexpr int k_stride(int NC) { return NC == 16 ? 20 : NC; }
 
-static BlobLayout blob_layout(int N, int NC)
+static BlobLayout blob_layout(int N, int NC, bool split = false)
 {
     auto up4 = [](int v) { return (v + 3) & ~3; };
     // pair rows: the ceil(N/2) pairs, then one zero row that every lane
@@ -101,6 +102,13 @@ static BlobLayout blob_layout(int N, int NC)
     B.PP = o; o += NP * pair_stride(NC);
     B.PdP = o; o += NP * pair_stride(NC);
     B.PddP = o; o += NP * pair_stride(NC);
+    if (split) {
+        B.PPl = o; o += NP * pair_stride(NC);
+        B.PdPl = o; o += NP * pair_stride(NC);
+        B.PddPl = o; o += NP * pair_stride(NC);
+    } else {
+        B.PPl = B.PP; B.PdPl = B.PdP; B.PddPl = B.PddP;
+    }
     B.tP = o; o += up4(NP * 2);
     B.common = o;
     B.brow = o; o += 6 * NC;
@@ -346,6 +354,114 @@ __device__ __forceinline__ void eval_pair2(const float* __restrict__ Pd, const f
         const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
         xd = __ffma2_rn(f2(r.z, r.w), f2(a.z, a.w), __ffma2_rn(f2(r.x, r.y), f2(a.x, a.y), xd));
         yd = __ffma2_rn(f2(r.z, r.w), f2(b.z, b.w), __ffma2_rn(f2(r.x, r.y), f2(b.x, b.y), yd));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Precision modes (mmpc_params.precision): the operands of the basis products
+// rounded as the tensor cores take them, FP32 products and accumulation.  The
+// same integer rounding on the host (staged basis rows) and in the kernels
+// (coefficients, per-sample targets, theta): TF32 keeps 10 significand bits,
+// to nearest with ties away from zero; BF16 keeps 7, ties to even; non-finite
+// values pass unchanged.  Split modes carry hi = rnd(a), lo = rnd(a - hi) and
+// form a b as a_hi b_hi + a_hi b_lo + a_lo b_hi.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline float round_operand(float x, int prec)
+{
+    if (prec == MMPC_PREC_FP32) return x;
+    unsigned u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        if (prec == MMPC_PREC_TF32 || prec == MMPC_PREC_TF32_SPLIT) u = (u + 0x1000u) & 0xffffe000u;
+        else u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    }
+    memcpy(&x, &u, 4);
+    return x;
+}
+
+__host__ __device__ constexpr bool prec_split(int prec)
+{
+    return prec == MMPC_PREC_TF32_SPLIT || prec == MMPC_PREC_BF16_SPLIT;
+}
+
+template <int PREC>
+__device__ __forceinline__ float2 rnd2(float2 a)
+{
+    return f2(round_operand(a.x, PREC), round_operand(a.y, PREC));
+}
+
+// acc + a b with a = (ah, al) and b = (bh, bl) as the mode takes them
+template <int PREC>
+__device__ __forceinline__ float2 pfma(float2 ah, float2 al, float2 bh, float2 bl, float2 acc)
+{
+    acc = __ffma2_rn(ah, bh, acc);
+    if constexpr (prec_split(PREC)) {
+        acc = __ffma2_rn(ah, bl, acc);
+        acc = __ffma2_rn(al, bh, acc);
+    }
+    return acc;
+}
+
+// eval_pair5 / eval_pair2 in a precision mode: rows (hi, and lo rows in the
+// split modes) staged rounded by the host, coefficients rounded here.
+template <int NC, int PREC>
+__device__ __forceinline__ void eval_pair5_prec(const float* __restrict__ P, const float* __restrict__ Pdd,
+                                                const float* __restrict__ Pl, const float* __restrict__ Pddl,
+                                                const float* __restrict__ cx, const float* __restrict__ cy,
+                                                const float* __restrict__ cp, float2& x, float2& y, float2& xdd,
+                                                float2& ydd, float2& ps)
+{
+    x = y = xdd = ydd = ps = f2(0.f);
+#pragma unroll
+    for (int k = 0; k < NC; k += 2) {
+        const float4 r = *reinterpret_cast<const float4*>(P + 2 * k);
+        const float4 d = *reinterpret_cast<const float4*>(Pdd + 2 * k);
+        const float4 rl = *reinterpret_cast<const float4*>(Pl + 2 * k);
+        const float4 dl = *reinterpret_cast<const float4*>(Pddl + 2 * k);
+        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
+        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
+        const float4 c = *reinterpret_cast<const float4*>(cp + 2 * k);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 rh = h ? f2(r.z, r.w) : f2(r.x, r.y), rlo = h ? f2(rl.z, rl.w) : f2(rl.x, rl.y);
+            const float2 dh = h ? f2(d.z, d.w) : f2(d.x, d.y), dlo = h ? f2(dl.z, dl.w) : f2(dl.x, dl.y);
+            const float2 av = h ? f2(a.z, a.w) : f2(a.x, a.y), bv = h ? f2(b.z, b.w) : f2(b.x, b.y);
+            const float2 cv = h ? f2(c.z, c.w) : f2(c.x, c.y);
+            const float2 ah = rnd2<PREC>(av), bh = rnd2<PREC>(bv), ch = rnd2<PREC>(cv);
+            const float2 al = rnd2<PREC>(__fadd2_rn(av, f2(-ah.x, -ah.y)));
+            const float2 bl = rnd2<PREC>(__fadd2_rn(bv, f2(-bh.x, -bh.y)));
+            const float2 cl = rnd2<PREC>(__fadd2_rn(cv, f2(-ch.x, -ch.y)));
+            x = pfma<PREC>(rh, rlo, ah, al, x);
+            y = pfma<PREC>(rh, rlo, bh, bl, y);
+            ps = pfma<PREC>(rh, rlo, ch, cl, ps);
+            xdd = pfma<PREC>(dh, dlo, ah, al, xdd);
+            ydd = pfma<PREC>(dh, dlo, bh, bl, ydd);
+        }
+    }
+}
+
+template <int NC, int PREC>
+__device__ __forceinline__ void eval_pair2_prec(const float* __restrict__ Pd, const float* __restrict__ Pdl,
+                                                const float* __restrict__ cx, const float* __restrict__ cy,
+                                                float2& xd, float2& yd)
+{
+    xd = yd = f2(0.f);
+#pragma unroll
+    for (int k = 0; k < NC; k += 2) {
+        const float4 r = *reinterpret_cast<const float4*>(Pd + 2 * k);
+        const float4 rl = *reinterpret_cast<const float4*>(Pdl + 2 * k);
+        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
+        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 rh = h ? f2(r.z, r.w) : f2(r.x, r.y), rlo = h ? f2(rl.z, rl.w) : f2(rl.x, rl.y);
+            const float2 av = h ? f2(a.z, a.w) : f2(a.x, a.y), bv = h ? f2(b.z, b.w) : f2(b.x, b.y);
+            const float2 ah = rnd2<PREC>(av), bh = rnd2<PREC>(bv);
+            const float2 al = rnd2<PREC>(__fadd2_rn(av, f2(-ah.x, -ah.y)));
+            const float2 bl = rnd2<PREC>(__fadd2_rn(bv, f2(-bh.x, -bh.y)));
+            xd = pfma<PREC>(rh, rlo, ah, al, xd);
+            yd = pfma<PREC>(rh, rlo, bh, bl, yd);
+        }
     }
 }
 
@@ -672,7 +788,7 @@ __device__ __forceinline__ float dot_dup(const float* __restrict__ row, const fl
 // Warps beyond ceil(ceil(N/2) / 32) (a CTA sized for a longer horizon, in a
 // batch of scenes) hold no samples: they only follow the coefficient state
 // through the barriers.
-template <int NC, int MAXT>
+template <int NC, int MAXT, int PREC = MMPC_PREC_FP32>
 __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
 {
     constexpr int VD = SolveSmem<NC>::VD;
@@ -725,6 +841,9 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     const float* PP = blob + L.PP + ip * RS;
     const float* PdP = blob + L.PdP + ip * RS;
     const float* PddP = blob + L.PddP + ip * RS;
+    const float* PPl = blob + L.PPl + ip * RS;  // lo parts (split precision modes)
+    const float* PdPl = blob + L.PdPl + ip * RS;
+    const float* PddPl = blob + L.PddPl + ip * RS;
     const float2 tt = f2(blob[L.tP + 2 * ip], blob[L.tP + 2 * ip + 1]);
     const bool has_pair = !idle && tid < NP;
     const float2 valid = f2(has_pair ? 1.f : 0.f, (has_pair && 2 * ip + 1 < N) ? 1.f : 0.f);
@@ -834,7 +953,10 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         for (int i = 0; i < VD; ++i) v[i] = 0.f;
         {  // lanes without a sample pair read zero rows: their terms vanish
             float2 x, y, xdd, ydd, ps;
-            eval_pair5<NC>(PP, PddP, cxd, cyd, cpd, x, y, xdd, ydd, ps);
+            if constexpr (PREC != MMPC_PREC_FP32)
+                eval_pair5_prec<NC, PREC>(PP, PddP, PPl, PddPl, cxd, cyd, cpd, x, y, xdd, ydd, ps);
+            else
+                eval_pair5<NC>(PP, PddP, cxd, cyd, cpd, x, y, xdd, ydd, ps);
             // Eq. v_update and the non-holonomic rows v (cos psi, sin psi)
             const float2 sp2 = __ffma2_rn(xd, xd, __fmul2_rn(yd, yd));
             const float2 nvel = f2(-fminf(fmaxf(sqrtf(sp2.x), A.v_min), A.v_max),
@@ -865,6 +987,44 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             const float2 eox = __fmul2_rn(Sx, f2(-A.a));
             const float2 eoy = __fmul2_rn(Sy, f2(-A.b));
             const float2 dpsi = __fadd2_rn(ps, f2(-theta.x, -theta.y));
+            if constexpr (PREC != MMPC_PREC_FP32) {
+                // the per-sample operands of the contractions, hi and lo
+                float2 eh[7], el[7];
+                const float2 ev[7] = {eox, eax, evx, eoy, eay, evy, dpsi};
+#pragma unroll
+                for (int i = 0; i < 7; ++i) {
+                    eh[i] = rnd2<PREC>(ev[i]);
+                    el[i] = rnd2<PREC>(__fadd2_rn(ev[i], f2(-eh[i].x, -eh[i].y)));
+                }
+#pragma unroll
+                for (int q = 0; q < NC; q += 2) {
+                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
+                    const float4 d4 = *reinterpret_cast<const float4*>(PdP + 2 * q);
+                    const float4 dd4 = *reinterpret_cast<const float4*>(PddP + 2 * q);
+                    const float4 pl4 = *reinterpret_cast<const float4*>(PPl + 2 * q);
+                    const float4 dl4 = *reinterpret_cast<const float4*>(PdPl + 2 * q);
+                    const float4 ddl4 = *reinterpret_cast<const float4*>(PddPl + 2 * q);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 pr = h ? f2(p4.z, p4.w) : f2(p4.x, p4.y);
+                        const float2 dr = h ? f2(d4.z, d4.w) : f2(d4.x, d4.y);
+                        const float2 ddr = h ? f2(dd4.z, dd4.w) : f2(dd4.x, dd4.y);
+                        const float2 prl = h ? f2(pl4.z, pl4.w) : f2(pl4.x, pl4.y);
+                        const float2 drl = h ? f2(dl4.z, dl4.w) : f2(dl4.x, dl4.y);
+                        const float2 ddrl = h ? f2(ddl4.z, ddl4.w) : f2(ddl4.x, ddl4.y);
+                        float2 sx = pfma<PREC>(dr, drl, eh[2], el[2], f2(0.f));
+                        sx = pfma<PREC>(ddr, ddrl, eh[1], el[1], sx);
+                        sx = pfma<PREC>(pr, prl, eh[0], el[0], sx);
+                        float2 sy = pfma<PREC>(dr, drl, eh[5], el[5], f2(0.f));
+                        sy = pfma<PREC>(ddr, ddrl, eh[4], el[4], sy);
+                        sy = pfma<PREC>(pr, prl, eh[3], el[3], sy);
+                        const float2 sp = pfma<PREC>(pr, prl, eh[6], el[6], f2(0.f));
+                        v[q + h] = sx.x + sx.y;
+                        v[NC + q + h] = sy.x + sy.y;
+                        v[2 * NC + q + h] = sp.x + sp.y;
+                    }
+                }
+            } else {
 #pragma unroll
             for (int q = 0; q < NC; q += 2) {
                 const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
@@ -883,6 +1043,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
                     v[2 * NC + q + h] = sp.x + sp.y;
                 }
             }
+            }
             if (resid) {
                 const float2 ra = __ffma2_rn(eax, eax, __fmul2_rn(eay, eay));
                 const float2 rv = __ffma2_rn(evx, evx, __fmul2_rn(evy, evy));
@@ -900,18 +1061,33 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     // (Eq. split_psi), and the partial sums of P^T theta.
     auto heading = [&](bool reduce) {
         float2 xd0;
-        eval_pair2<NC>(PdP, cxd, cyd, xd0, yd);
+        if constexpr (PREC != MMPC_PREC_FP32) eval_pair2_prec<NC, PREC>(PdP, PdPl, cxd, cyd, xd0, yd);
+        else eval_pair2<NC>(PdP, cxd, cyd, xd0, yd);
         xd = __fadd2_rn(xd0, f2(v0));
         theta = atan2_pair(yd, xd);
         if (reduce) {
             float v[NC];
+            if constexpr (PREC != MMPC_PREC_FP32) {
+                const float2 th = rnd2<PREC>(theta);
+                const float2 tl = rnd2<PREC>(__fadd2_rn(theta, f2(-th.x, -th.y)));
 #pragma unroll
-            for (int q = 0; q < NC; q += 2) {
-                const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
-                const float2 s0 = __fmul2_rn(f2(p4.x, p4.y), theta);
-                const float2 s1 = __fmul2_rn(f2(p4.z, p4.w), theta);
-                v[q] = s0.x + s0.y;
-                v[q + 1] = s1.x + s1.y;
+                for (int q = 0; q < NC; q += 2) {
+                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
+                    const float4 l4 = *reinterpret_cast<const float4*>(PPl + 2 * q);
+                    const float2 s0 = pfma<PREC>(f2(p4.x, p4.y), f2(l4.x, l4.y), th, tl, f2(0.f));
+                    const float2 s1 = pfma<PREC>(f2(p4.z, p4.w), f2(l4.z, l4.w), th, tl, f2(0.f));
+                    v[q] = s0.x + s0.y;
+                    v[q + 1] = s1.x + s1.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NC; q += 2) {
+                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
+                    const float2 s0 = __fmul2_rn(f2(p4.x, p4.y), theta);
+                    const float2 s1 = __fmul2_rn(f2(p4.z, p4.w), theta);
+                    v[q] = s0.x + s0.y;
+                    v[q + 1] = s1.x + s1.y;
+                }
             }
             reduce_store<NC>(v, dstB, lane);
         }
@@ -1030,10 +1206,10 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     return true;
 }
 
-template <int NC, int MAXT>
+template <int NC, int MAXT, int PREC = MMPC_PREC_FP32>
 __global__ void __launch_bounds__(MAXT, MinBlocks<NC, MAXT>::value) am_solve_kernel(const __grid_constant__ SolveArgs A)
 {
-    pair_body<NC, MAXT>(A, blockIdx.x);
+    pair_body<NC, MAXT, PREC>(A, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1750,7 +1926,8 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
         if (!std::isfinite(buf[i])) return fail(nullptr, MMPC_ERR_INVALID_ARG, "problem buffer holds a non-finite value");
 
     const int NC = n <= 12 ? 12 : 16;
-    const BlobLayout L = blob_layout(N, NC);
+    const int prec = p->precision;
+    const BlobLayout L = blob_layout(N, NC, prec_split(prec));
     std::vector<float> h(L.total, 0.f);
     auto h_set = [&](int i, float v) { h[i] = v; };
     auto mat = [&](size_t src, int dst, int rows, int cols, int dcols, bool lo) {
@@ -1763,17 +1940,24 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
     };
     // basis rows of the sample pairs (2i, 2i+1), interleaved per coefficient
     const int NP = (N + 1) / 2;
-    auto pairs = [&](size_t src, int dst) {
+    // (precision modes: the rows rounded as the tensor cores would take them,
+    // hi into the rows and lo into the lo rows in the split modes)
+    auto pairs = [&](size_t src, int dst, int dst_lo) {
         for (int i = 0; i < NP; ++i)
             for (int h = 0; h < 2; ++h) {
                 const int smp = 2 * i + h;
                 if (smp >= N) continue;
-                for (int c = 0; c < n; ++c) h_set(dst + i * pair_stride(NC) + c * 2 + h, (float)buf[src + (size_t)smp * n + c]);
+                for (int c = 0; c < n; ++c) {
+                    const float f = (float)buf[src + (size_t)smp * n + c];
+                    const float hi = round_operand(f, prec);
+                    h_set(dst + i * pair_stride(NC) + c * 2 + h, hi);
+                    if (prec_split(prec)) h_set(dst_lo + i * pair_stride(NC) + c * 2 + h, round_operand(f - hi, prec));
+                }
             }
     };
-    pairs(PL.P, L.PP);
-    pairs(PL.Pd, L.PdP);
-    pairs(PL.Pdd, L.PddP);
+    pairs(PL.P, L.PP, L.PPl);
+    pairs(PL.Pd, L.PdP, L.PdPl);
+    pairs(PL.Pdd, L.PddP, L.PddPl);
     for (int smp = 0; smp < N; ++smp) h_set(L.tP + smp, (float)buf[PL.t + smp]);
     const size_t brow_src[6] = {PL.P, PL.Pd, PL.Pdd, PL.P + (size_t)(N - 1) * n, PL.Pd + (size_t)(N - 1) * n,
                                 PL.Pdd + (size_t)(N - 1) * n};
@@ -1861,7 +2045,14 @@ extern "C" int mmpc_solve(mmpc_ctx* ctx, const float* ego, const float* obst, in
             if (B <= ctx->sm_count) variant = 1;
         }
     }
-    const LaunchShape sh = shape_for(ctx, variant, m);
+    if (p.precision != MMPC_PREC_FP32) variant = 2;  // the precision modes exist in the pair kernel only
+    LaunchShape sh = shape_for(ctx, variant, m);
+    if (p.precision != MMPC_PREC_FP32) {  // NC = 16, 128 threads (checked at setup)
+        using K = void (*)(const SolveArgs);
+        const K kp[5] = {nullptr, am_solve_kernel<16, 128, MMPC_PREC_TF32>, am_solve_kernel<16, 128, MMPC_PREC_TF32_SPLIT>,
+                         am_solve_kernel<16, 128, MMPC_PREC_BF16>, am_solve_kernel<16, 128, MMPC_PREC_BF16_SPLIT>};
+        sh.kern = (void*)kp[p.precision];
+    }
     if (sh.smem > 227 * 1024) return fail(ctx, MMPC_ERR_SHAPE, "scene does not fit in shared memory");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     using KernT = void (*)(const SolveArgs);
@@ -2029,7 +2220,7 @@ extern "C" const char* mmpc_last_error(const mmpc_ctx* ctx)
     return mmpc::g_error.c_str();
 }
 
-extern "C" int mmpc_version(void) { return 1; }
+extern "C" int mmpc_version(void) { return 2; }
 
 // ---------------------------------------------------------------------------
 // Allocation-free scoring (mmpc_score_static).
@@ -2345,6 +2536,10 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         if (!c || !c->d_blob) { batch_free(b); return batch_fail("mmpc_batch_create: scene without a set-up context", MMPC_ERR_NOT_SETUP); }
         if (s == 0) b->NC = c->NC;
         if (c->NC != b->NC) { batch_free(b); return batch_fail("mmpc_batch_create: scenes mix n <= 12 and n > 12", MMPC_ERR_SHAPE); }
+        if (c->p.precision != MMPC_PREC_FP32) {
+            batch_free(b);
+            return batch_fail("mmpc_batch_create: precision modes run through mmpc_solve only", MMPC_ERR_INVALID_ARG);
+        }
         if (sc.B < 0 || !sc.ego || (c->m > 0 && !sc.obst) || (sc.B > 0 && (!sc.goals || !sc.coef_out || !sc.cost_out)) || !sc.argmin_out) {
             batch_free(b);
             return batch_fail("mmpc_batch_create: NULL pointer in scene " + std::to_string(s), MMPC_ERR_INVALID_ARG);

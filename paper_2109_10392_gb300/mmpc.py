@@ -17,6 +17,7 @@ import numpy as np
 from . import _build
 
 MMPC_OK = 0
+MMPC_PREC_FP32, MMPC_PREC_TF32, MMPC_PREC_TF32_SPLIT, MMPC_PREC_BF16, MMPC_PREC_BF16_SPLIT = 0, 1, 2, 3, 4
 MMPC_ERR_INVALID_ARG = -1
 MMPC_ERR_SHAPE = -2
 MMPC_ERR_CUDA = -3
@@ -53,6 +54,7 @@ class MmpcParams(ctypes.Structure):
         ("variant", ctypes.c_int),
         ("stall_tol", ctypes.c_float),
         ("stall_ratio", ctypes.c_float),
+        ("precision", ctypes.c_int),
     ]
 
 
@@ -165,10 +167,10 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
 
 
 def make_params(T, N, n, rho, a, b, v_min, v_max, a_max, iters=100, tol=0.0, check_every=10, cull=1, variant=0,
-                stall_tol=0.0, stall_ratio=0.5, **_ignored) -> MmpcParams:
+                stall_tol=0.0, stall_ratio=0.5, precision=0, **_ignored) -> MmpcParams:
     return MmpcParams(float(T), int(N), int(n), float(rho), float(a), float(b), float(v_min), float(v_max),
                       float(a_max), int(iters), float(tol), int(check_every), int(cull), int(variant),
-                      float(stall_tol), float(stall_ratio))
+                      float(stall_tol), float(stall_ratio), int(precision))
 
 
 def make_meta(kind=MMPC_META_ABS, w1=1.0, w2=0.25, v_ref=20.0, y_ref=-5.25, psi_max_deg=13.0, psi_max=None,

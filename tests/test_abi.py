@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol():
     assert set(names) == set(mmpc.EXPORTED) | set(mlp.EXPORTED)
     for name in names:
         assert hasattr(L, name), name
-    assert L.mmpc_version() == 1
+    assert L.mmpc_version() == 2
 
 
 def _split(buf, N, n):
