@@ -1026,23 +1026,23 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
                 }
             } else {
 #pragma unroll
-            for (int q = 0; q < NC; q += 2) {
-                const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
-                const float4 d4 = *reinterpret_cast<const float4*>(PdP + 2 * q);
-                const float4 dd4 = *reinterpret_cast<const float4*>(PddP + 2 * q);
+                for (int q = 0; q < NC; q += 2) {
+                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
+                    const float4 d4 = *reinterpret_cast<const float4*>(PdP + 2 * q);
+                    const float4 dd4 = *reinterpret_cast<const float4*>(PddP + 2 * q);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 pr = h ? f2(p4.z, p4.w) : f2(p4.x, p4.y);
-                    const float2 dr = h ? f2(d4.z, d4.w) : f2(d4.x, d4.y);
-                    const float2 ddr = h ? f2(dd4.z, dd4.w) : f2(dd4.x, dd4.y);
-                    const float2 sx = __ffma2_rn(pr, eox, __ffma2_rn(ddr, eax, __fmul2_rn(dr, evx)));
-                    const float2 sy = __ffma2_rn(pr, eoy, __ffma2_rn(ddr, eay, __fmul2_rn(dr, evy)));
-                    const float2 sp = __fmul2_rn(pr, dpsi);
-                    v[q + h] = sx.x + sx.y;
-                    v[NC + q + h] = sy.x + sy.y;
-                    v[2 * NC + q + h] = sp.x + sp.y;
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 pr = h ? f2(p4.z, p4.w) : f2(p4.x, p4.y);
+                        const float2 dr = h ? f2(d4.z, d4.w) : f2(d4.x, d4.y);
+                        const float2 ddr = h ? f2(dd4.z, dd4.w) : f2(dd4.x, dd4.y);
+                        const float2 sx = __ffma2_rn(pr, eox, __ffma2_rn(ddr, eax, __fmul2_rn(dr, evx)));
+                        const float2 sy = __ffma2_rn(pr, eoy, __ffma2_rn(ddr, eay, __fmul2_rn(dr, evy)));
+                        const float2 sp = __fmul2_rn(pr, dpsi);
+                        v[q + h] = sx.x + sx.y;
+                        v[NC + q + h] = sy.x + sy.y;
+                        v[2 * NC + q + h] = sp.x + sp.y;
+                    }
                 }
-            }
             }
             if (resid) {
                 const float2 ra = __ffma2_rn(eax, eax, __fmul2_rn(eay, eay));
