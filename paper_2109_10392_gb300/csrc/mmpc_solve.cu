@@ -817,9 +817,14 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     float* red1 = reinterpret_cast<float*>(obs + 2 * m);   // [warp][RSB]: P^T theta
     float* red2 = red1 + WARPS * RSB;                       // [warp][RSD]: F^T (F c - g), ...
     int* olist = reinterpret_cast<int*>(red2 + WARPS * RSD) + warp * m;  // this warp's active obstacles
-    float* cxd = s_cxd[warp];
-    float* cyd = s_cyd[warp];
-    float* cpd = s_cpd[warp];
+    // SOLO (CTAs of more than 2 warps): warp 0 alone runs the QP steps and
+    // every warp reads its coefficient vectors after a CTA barrier (two more
+    // barriers per iteration, the other warps' issue slots freed); with 1-2
+    // warps every warp runs them on its own copy (two barriers per iteration)
+    constexpr bool SOLO = MAXT > 64;
+    float* cxd = s_cxd[SOLO ? 0 : warp];
+    float* cyd = s_cyd[SOLO ? 0 : warp];
+    float* cpd = s_cpd[SOLO ? 0 : warp];
 
     // Scene: ego (Sec. III, x0 = 0) and obstacles, normalised by the ellipse
     // axes, negated, duplicated for the sample pair, in the frame moving with v0.
@@ -929,12 +934,13 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             lam = __ldg(A.warm_l + (size_t)l * 3 * A.n + (isy ? A.n : 0) + k);
             if (!isy) lampsi = __ldg(A.warm_l + (size_t)l * 3 * A.n + 2 * A.n + k);
         }
-        if (act) {
+        if ((!SOLO || warp == 0) && act) {
             reinterpret_cast<float2*>(own)[k] = f2(c);
             if (!isy) reinterpret_cast<float2*>(cpd)[k] = f2(cp0);
         }
     }
-    __syncwarp();
+    if constexpr (SOLO) __syncthreads();
+    else __syncwarp();
 
     float2 xd = f2(0.f), yd = f2(0.f), theta = f2(0.f);
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1169,7 +1175,18 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         project(true);
     }
     __syncthreads();
-    bool done = finish(true, true);
+    __shared__ int s_done;
+    bool done;
+    if constexpr (SOLO) {
+        if (warp == 0) {
+            const bool d = finish(true, true);
+            if (lane == 0) s_done = d;
+        }
+        __syncthreads();
+        done = s_done != 0;
+    } else {
+        done = finish(true, true);
+    }
 
     // ---- Algorithm 1 ---------------------------------------------------------
     while (!done) {
@@ -1177,10 +1194,24 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         const bool check = (kit % A.check_every == 0) || kit >= iters;
         if (!idle) heading(true);   // theta and the partial sums of P^T theta
         __syncthreads();
-        psi_step();                 // Eq. split_psi
+        if constexpr (SOLO) {
+            if (warp == 0) psi_step();  // Eq. split_psi
+            __syncthreads();
+        } else {
+            psi_step();
+        }
         if (!idle) project(check);  // Eqs. split_v, split_alpha_o, split_alpha_a; partial sums
         __syncthreads();
-        done = finish(false, check);  // multipliers, residual check, step (split_xy)
+        if constexpr (SOLO) {       // multipliers, residual check, step (split_xy)
+            if (warp == 0) {
+                const bool d = finish(false, check);
+                if (lane == 0) s_done = d;
+            }
+            __syncthreads();
+            done = s_done != 0;
+        } else {
+            done = finish(false, check);
+        }
     }
 
     // ---- outputs -------------------------------------------------------------
