@@ -70,7 +70,7 @@ def workload_name(params, B, m):
 # be measured again whenever the kernel changes.
 SOLVE_DRAM_BYTES = {"highway_B1024_m50_N100_n12_K100_tol0.01": 126464}
 # per step, summed over the three horizon-group launches of schedule 4
-BATCH_DRAM_BYTES = {"highway_batch_S256_B16-512_m5-40_N50-100-150_n12_K100_tol0.01": 4646656}
+BATCH_DRAM_BYTES = {"highway_batch_S256_B16-512_m5-40_N50-100-150_n12_K100_tol0.01": 5001216}
 
 OPS_PER_ELEMENT = 10  # FP32 lane ops per evaluated obstacle-sample pair
 
