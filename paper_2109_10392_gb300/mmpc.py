@@ -636,3 +636,54 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _time_scene(goals: int, obstacles: int, N: int, n: int, iters: int, reps: int, seed: int) -> dict:
+    """Times solve + score of one seeded highway scene (goals, obstacles, N, n)
+    with CUDA events between L2 flushes: median of `reps` steps."""
+    import torch
+
+    from . import scenes
+    sc = scenes.scene_custom(seed, goals, obstacles, N=N, n=n, x_range=(-50.0, 250.0))
+    params = dict(sc.params, iters=iters, tol=1e-2, check_every=10)
+    s = Solver(params, obstacles)
+    meta = make_meta(**sc.meta)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).contiguous()  # noqa: E731
+    ego, obst, gl = t(sc.ego), t(sc.obst), t(sc.goals)
+    coef = torch.empty((goals, 3 * s.n), device=dev)
+    resid = torch.empty((goals, 4), device=dev)
+    cost = torch.empty(goals, device=dev)
+    am = torch.empty(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ms = []
+    for i in range(reps + 3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mmpc_solve(s.ctx, ego, obst if obstacles else None, gl, coef, resid_out=resid)
+        mmpc_score(s.ctx, meta, coef, cost, am)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ms.append(a.elapsed_time(b))
+    s.status()
+    s.close()
+    ms.sort()
+    return dict(goals=goals, obstacles=obstacles, N=N, n=n, iters=iters, reps=reps, ms_median=ms[len(ms) // 2],
+                trajectories_per_s=goals / (ms[len(ms) // 2] * 1e-3), best_goal=int(am.item()))
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="time solve + score of one seeded highway scene on cuda:0")
+    ap.add_argument("--goals", type=int, default=11)
+    ap.add_argument("--obstacles", type=int, default=10)
+    ap.add_argument("--N", type=int, default=100)
+    ap.add_argument("--n", type=int, default=12)
+    ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--reps", type=int, default=100)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    print(json.dumps(_time_scene(a.goals, a.obstacles, a.N, a.n, a.iters, a.reps, a.seed)))
