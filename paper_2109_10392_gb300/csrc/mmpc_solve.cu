@@ -57,11 +57,13 @@ void set_global_error(const std::string& msg) { g_error = msg; }
 // The pair-sample kernel stages [pair rows | common] into shared memory, the
 // one-sample kernel [common | sample rows]; the scoring kernels read the
 // sample rows from global memory.
-//   pair rows:   PP, PdP, PddP [NPT][RS]  basis rows of samples (2i, 2i+1)
-//                interleaved per coefficient ([NC][2], RS = pair_stride(NC)
-//                floats with the padding), NPT = ceil(N/2) rounded up to
-//                whole warps (rows of samples >= N and every k >= n are zero,
-//                so padded lanes contribute exact zeros); tP [NPT][2] times
+//   pair rows:   PP, PdP, PddP [NPT][RS]  basis rows of samples (2i, 2i+1),
+//                per coefficient pair (2j, 2j+1) the 16-byte block (2i: 2j,
+//                2j+1; 2i+1: 2j, 2j+1) (RS = pair_stride(NC) floats with the
+//                padding), NPT = ceil(N/2) + 1: the pairs and one zero row
+//                that lanes without a pair read (values of samples >= N and
+//                of every k >= n are zero, so they contribute exact zeros);
+//                tP [NPT][2] times
 //   common:      brow [6][NC] (P, Pd, Pdd at t = 0 and t = T); lin [NC]; Q,
 //                K11 (x hi, x lo, y hi, y lo), K11_psi [NC][KS] (KS =
 //                k_stride(NC) floats per row with the padding); then the
@@ -312,32 +314,52 @@ __device__ __forceinline__ bool stage_blob(float* dst, const float* src, int byt
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// Basis evaluations at a sample pair.  The rows of the pair ([NC][2]: the two
-// samples' values of coefficient k side by side) meet coefficient vectors
-// held duplicated ([NC][2] = (c_k, c_k)), so one FFMA2 chain in k order gives
-// both samples' values.  The five evaluations of the projection phase, each
-// 16-byte chunk of the P and Pddot rows and of the three coefficient vectors
-// loaded once: x = P cx, y = P cy, xdd = Pdd cx, ydd = Pdd cy, psi = P cpsi.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float2 lo2(float4 v) { return f2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return f2(v.z, v.w); }
+__device__ __forceinline__ float2 hsum2(float2 a, float2 b) { return f2(a.x + a.y, b.x + b.y); }
+
+// Basis evaluations at a sample pair.  A pair row holds, for each coefficient
+// pair (2j, 2j + 1), the 16-byte block (P[s0][2j], P[s0][2j+1], P[s1][2j],
+// P[s1][2j+1]) of its two samples s0 = 2i, s1 = 2i + 1; coefficient vectors
+// are plain [NC] arrays, so one 16-byte load covers two blocks.  Each
+// sample's value runs through one FFMA2 chain over the coefficient pairs
+// (even coefficients in the low half, odd in the high half) and the halves
+// are added at the end.  The five evaluations of the projection phase share
+// every load: x = P cx, y = P cy, xdd = Pdd cx, ydd = Pdd cy, psi = P cpsi.
 template <int NC>
 __device__ __forceinline__ void eval_pair5(const float* __restrict__ P, const float* __restrict__ Pdd,
                                            const float* __restrict__ cx, const float* __restrict__ cy,
                                            const float* __restrict__ cp, float2& x, float2& y, float2& xdd,
                                            float2& ydd, float2& ps)
 {
-    x = y = xdd = ydd = ps = f2(0.f);
+    static_assert(NC % 4 == 0, "coefficient vectors are read 16 bytes at a time");
+    const float2 z = f2(0.f);
+    float2 x0 = z, x1 = z, y0 = z, y1 = z, p0 = z, p1 = z, xa0 = z, xa1 = z, ya0 = z, ya1 = z;
 #pragma unroll
-    for (int k = 0; k < NC; k += 2) {
-        const float4 r = *reinterpret_cast<const float4*>(P + 2 * k);
-        const float4 d = *reinterpret_cast<const float4*>(Pdd + 2 * k);
-        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
-        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
-        const float4 c = *reinterpret_cast<const float4*>(cp + 2 * k);
-        x = __ffma2_rn(f2(r.z, r.w), f2(a.z, a.w), __ffma2_rn(f2(r.x, r.y), f2(a.x, a.y), x));
-        y = __ffma2_rn(f2(r.z, r.w), f2(b.z, b.w), __ffma2_rn(f2(r.x, r.y), f2(b.x, b.y), y));
-        ps = __ffma2_rn(f2(r.z, r.w), f2(c.z, c.w), __ffma2_rn(f2(r.x, r.y), f2(c.x, c.y), ps));
-        xdd = __ffma2_rn(f2(d.z, d.w), f2(a.z, a.w), __ffma2_rn(f2(d.x, d.y), f2(a.x, a.y), xdd));
-        ydd = __ffma2_rn(f2(d.z, d.w), f2(b.z, b.w), __ffma2_rn(f2(d.x, d.y), f2(b.x, b.y), ydd));
+    for (int k = 0; k < NC; k += 4) {
+        const float4 a = ld4(cx + k), b = ld4(cy + k), c = ld4(cp + k);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 r = ld4(P + 2 * k + 4 * h), d = ld4(Pdd + 2 * k + 4 * h);
+            const float2 av = h ? hi2(a) : lo2(a), bv = h ? hi2(b) : lo2(b), cv = h ? hi2(c) : lo2(c);
+            x0 = __ffma2_rn(lo2(r), av, x0);
+            x1 = __ffma2_rn(hi2(r), av, x1);
+            y0 = __ffma2_rn(lo2(r), bv, y0);
+            y1 = __ffma2_rn(hi2(r), bv, y1);
+            p0 = __ffma2_rn(lo2(r), cv, p0);
+            p1 = __ffma2_rn(hi2(r), cv, p1);
+            xa0 = __ffma2_rn(lo2(d), av, xa0);
+            xa1 = __ffma2_rn(hi2(d), av, xa1);
+            ya0 = __ffma2_rn(lo2(d), bv, ya0);
+            ya1 = __ffma2_rn(hi2(d), bv, ya1);
+        }
     }
+    x = hsum2(x0, x1);
+    y = hsum2(y0, y1);
+    ps = hsum2(p0, p1);
+    xdd = hsum2(xa0, xa1);
+    ydd = hsum2(ya0, ya1);
 }
 
 // The heading phase's two evaluations, xd = Pd cx and yd = Pd cy, sharing the
@@ -346,15 +368,23 @@ template <int NC>
 __device__ __forceinline__ void eval_pair2(const float* __restrict__ Pd, const float* __restrict__ cx,
                                            const float* __restrict__ cy, float2& xd, float2& yd)
 {
-    xd = yd = f2(0.f);
+    const float2 z = f2(0.f);
+    float2 x0 = z, x1 = z, y0 = z, y1 = z;
 #pragma unroll
-    for (int k = 0; k < NC; k += 2) {
-        const float4 r = *reinterpret_cast<const float4*>(Pd + 2 * k);
-        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
-        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
-        xd = __ffma2_rn(f2(r.z, r.w), f2(a.z, a.w), __ffma2_rn(f2(r.x, r.y), f2(a.x, a.y), xd));
-        yd = __ffma2_rn(f2(r.z, r.w), f2(b.z, b.w), __ffma2_rn(f2(r.x, r.y), f2(b.x, b.y), yd));
+    for (int k = 0; k < NC; k += 4) {
+        const float4 a = ld4(cx + k), b = ld4(cy + k);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 r = ld4(Pd + 2 * k + 4 * h);
+            const float2 av = h ? hi2(a) : lo2(a), bv = h ? hi2(b) : lo2(b);
+            x0 = __ffma2_rn(lo2(r), av, x0);
+            x1 = __ffma2_rn(hi2(r), av, x1);
+            y0 = __ffma2_rn(lo2(r), bv, y0);
+            y1 = __ffma2_rn(hi2(r), bv, y1);
+        }
     }
+    xd = hsum2(x0, x1);
+    yd = hsum2(y0, y1);
 }
 
 // ---------------------------------------------------------------------------
@@ -402,6 +432,14 @@ __device__ __forceinline__ float2 pfma(float2 ah, float2 al, float2 bh, float2 b
     return acc;
 }
 
+// hi and lo parts of a pair of values as the mode takes them
+template <int PREC>
+__device__ __forceinline__ void split2(float2 v, float2& h, float2& l)
+{
+    h = rnd2<PREC>(v);
+    l = rnd2<PREC>(__fadd2_rn(v, f2(-h.x, -h.y)));
+}
+
 // eval_pair5 / eval_pair2 in a precision mode: rows (hi, and lo rows in the
 // split modes) staged rounded by the host, coefficients rounded here.
 template <int NC, int PREC>
@@ -411,33 +449,36 @@ __device__ __forceinline__ void eval_pair5_prec(const float* __restrict__ P, con
                                                 const float* __restrict__ cp, float2& x, float2& y, float2& xdd,
                                                 float2& ydd, float2& ps)
 {
-    x = y = xdd = ydd = ps = f2(0.f);
+    const float2 z = f2(0.f);
+    float2 x0 = z, x1 = z, y0 = z, y1 = z, p0 = z, p1 = z, xa0 = z, xa1 = z, ya0 = z, ya1 = z;
 #pragma unroll
-    for (int k = 0; k < NC; k += 2) {
-        const float4 r = *reinterpret_cast<const float4*>(P + 2 * k);
-        const float4 d = *reinterpret_cast<const float4*>(Pdd + 2 * k);
-        const float4 rl = *reinterpret_cast<const float4*>(Pl + 2 * k);
-        const float4 dl = *reinterpret_cast<const float4*>(Pddl + 2 * k);
-        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
-        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
-        const float4 c = *reinterpret_cast<const float4*>(cp + 2 * k);
+    for (int k = 0; k < NC; k += 4) {
+        const float4 a = ld4(cx + k), b = ld4(cy + k), c = ld4(cp + k);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float2 rh = h ? f2(r.z, r.w) : f2(r.x, r.y), rlo = h ? f2(rl.z, rl.w) : f2(rl.x, rl.y);
-            const float2 dh = h ? f2(d.z, d.w) : f2(d.x, d.y), dlo = h ? f2(dl.z, dl.w) : f2(dl.x, dl.y);
-            const float2 av = h ? f2(a.z, a.w) : f2(a.x, a.y), bv = h ? f2(b.z, b.w) : f2(b.x, b.y);
-            const float2 cv = h ? f2(c.z, c.w) : f2(c.x, c.y);
-            const float2 ah = rnd2<PREC>(av), bh = rnd2<PREC>(bv), ch = rnd2<PREC>(cv);
-            const float2 al = rnd2<PREC>(__fadd2_rn(av, f2(-ah.x, -ah.y)));
-            const float2 bl = rnd2<PREC>(__fadd2_rn(bv, f2(-bh.x, -bh.y)));
-            const float2 cl = rnd2<PREC>(__fadd2_rn(cv, f2(-ch.x, -ch.y)));
-            x = pfma<PREC>(rh, rlo, ah, al, x);
-            y = pfma<PREC>(rh, rlo, bh, bl, y);
-            ps = pfma<PREC>(rh, rlo, ch, cl, ps);
-            xdd = pfma<PREC>(dh, dlo, ah, al, xdd);
-            ydd = pfma<PREC>(dh, dlo, bh, bl, ydd);
+            const float4 r = ld4(P + 2 * k + 4 * h), d = ld4(Pdd + 2 * k + 4 * h);
+            const float4 rl = ld4(Pl + 2 * k + 4 * h), dl = ld4(Pddl + 2 * k + 4 * h);
+            float2 ah, al, bh, bl, ch, cl;
+            split2<PREC>(h ? hi2(a) : lo2(a), ah, al);
+            split2<PREC>(h ? hi2(b) : lo2(b), bh, bl);
+            split2<PREC>(h ? hi2(c) : lo2(c), ch, cl);
+            x0 = pfma<PREC>(lo2(r), lo2(rl), ah, al, x0);
+            x1 = pfma<PREC>(hi2(r), hi2(rl), ah, al, x1);
+            y0 = pfma<PREC>(lo2(r), lo2(rl), bh, bl, y0);
+            y1 = pfma<PREC>(hi2(r), hi2(rl), bh, bl, y1);
+            p0 = pfma<PREC>(lo2(r), lo2(rl), ch, cl, p0);
+            p1 = pfma<PREC>(hi2(r), hi2(rl), ch, cl, p1);
+            xa0 = pfma<PREC>(lo2(d), lo2(dl), ah, al, xa0);
+            xa1 = pfma<PREC>(hi2(d), hi2(dl), ah, al, xa1);
+            ya0 = pfma<PREC>(lo2(d), lo2(dl), bh, bl, ya0);
+            ya1 = pfma<PREC>(hi2(d), hi2(dl), bh, bl, ya1);
         }
     }
+    x = hsum2(x0, x1);
+    y = hsum2(y0, y1);
+    ps = hsum2(p0, p1);
+    xdd = hsum2(xa0, xa1);
+    ydd = hsum2(ya0, ya1);
 }
 
 template <int NC, int PREC>
@@ -445,24 +486,25 @@ __device__ __forceinline__ void eval_pair2_prec(const float* __restrict__ Pd, co
                                                 const float* __restrict__ cx, const float* __restrict__ cy,
                                                 float2& xd, float2& yd)
 {
-    xd = yd = f2(0.f);
+    const float2 z = f2(0.f);
+    float2 x0 = z, x1 = z, y0 = z, y1 = z;
 #pragma unroll
-    for (int k = 0; k < NC; k += 2) {
-        const float4 r = *reinterpret_cast<const float4*>(Pd + 2 * k);
-        const float4 rl = *reinterpret_cast<const float4*>(Pdl + 2 * k);
-        const float4 a = *reinterpret_cast<const float4*>(cx + 2 * k);
-        const float4 b = *reinterpret_cast<const float4*>(cy + 2 * k);
+    for (int k = 0; k < NC; k += 4) {
+        const float4 a = ld4(cx + k), b = ld4(cy + k);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float2 rh = h ? f2(r.z, r.w) : f2(r.x, r.y), rlo = h ? f2(rl.z, rl.w) : f2(rl.x, rl.y);
-            const float2 av = h ? f2(a.z, a.w) : f2(a.x, a.y), bv = h ? f2(b.z, b.w) : f2(b.x, b.y);
-            const float2 ah = rnd2<PREC>(av), bh = rnd2<PREC>(bv);
-            const float2 al = rnd2<PREC>(__fadd2_rn(av, f2(-ah.x, -ah.y)));
-            const float2 bl = rnd2<PREC>(__fadd2_rn(bv, f2(-bh.x, -bh.y)));
-            xd = pfma<PREC>(rh, rlo, ah, al, xd);
-            yd = pfma<PREC>(rh, rlo, bh, bl, yd);
+            const float4 r = ld4(Pd + 2 * k + 4 * h), rl = ld4(Pdl + 2 * k + 4 * h);
+            float2 ah, al, bh, bl;
+            split2<PREC>(h ? hi2(a) : lo2(a), ah, al);
+            split2<PREC>(h ? hi2(b) : lo2(b), bh, bl);
+            x0 = pfma<PREC>(lo2(r), lo2(rl), ah, al, x0);
+            x1 = pfma<PREC>(hi2(r), hi2(rl), ah, al, x1);
+            y0 = pfma<PREC>(lo2(r), lo2(rl), bh, bl, y0);
+            y1 = pfma<PREC>(hi2(r), hi2(rl), bh, bl, y1);
         }
     }
+    xd = hsum2(x0, x1);
+    yd = hsum2(y0, y1);
 }
 
 // Sum over obstacles at the sample pair (Eq. split_alpha_o).  With n = w / (a,
@@ -765,21 +807,19 @@ struct MinBlocks {
     static constexpr int value = MAXT <= 64 ? 8 : (MAXT <= 128 ? (NC == 16 ? 3 : 4) : 2);
 };
 
-// dot product of a 16-byte aligned row of NC floats with a vector given as
-// duplicated pairs ([NC][2] = (v_k, v_k)); four partial sums for ILP.
+// dot product of two 16-byte aligned vectors of NC floats; four partial
+// sums for ILP.
 template <int NC>
-__device__ __forceinline__ float dot_dup(const float* __restrict__ row, const float* __restrict__ vd)
+__device__ __forceinline__ float dot_vec(const float* __restrict__ row, const float* __restrict__ v)
 {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < NC; j += 4) {
-        const float4 r = *reinterpret_cast<const float4*>(row + j);
-        const float4 v0 = *reinterpret_cast<const float4*>(vd + 2 * j);
-        const float4 v1 = *reinterpret_cast<const float4*>(vd + 2 * j + 4);
-        acc[0] = fmaf(r.x, v0.x, acc[0]);
-        acc[1] = fmaf(r.y, v0.z, acc[1]);
-        acc[2] = fmaf(r.z, v1.x, acc[2]);
-        acc[3] = fmaf(r.w, v1.z, acc[3]);
+        const float4 r = ld4(row + j), w = ld4(v + j);
+        acc[0] = fmaf(r.x, w.x, acc[0]);
+        acc[1] = fmaf(r.y, w.y, acc[1]);
+        acc[2] = fmaf(r.z, w.z, acc[2]);
+        acc[3] = fmaf(r.w, w.w, acc[3]);
     }
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
@@ -796,11 +836,11 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     constexpr int RSB = SolveSmem<NC>::RSB;
     constexpr int WARPS = MAXT / 32;
     extern __shared__ __align__(16) float smem[];
-    // per-warp copies of the coefficient vectors, duplicated: (c_k, c_k)
-    __shared__ __align__(16) float s_cxd[WARPS][2 * NC];
-    __shared__ __align__(16) float s_cyd[WARPS][2 * NC];
-    __shared__ __align__(16) float s_cpd[WARPS][2 * NC];
-    __shared__ __align__(16) float s_vec[WARPS][2][2 * NC];  // per-warp scratch vectors (x, y)
+    // per-warp copies of the coefficient vectors
+    __shared__ __align__(16) float s_cx[WARPS][NC];
+    __shared__ __align__(16) float s_cy[WARPS][NC];
+    __shared__ __align__(16) float s_cp[WARPS][NC];
+    __shared__ __align__(16) float s_vec[WARPS][2][NC];  // per-warp scratch vectors (x, y)
     __shared__ __align__(8) unsigned long long s_mbar;
 
     const int tid = threadIdx.x;
@@ -822,9 +862,9 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     // barriers per iteration, the other warps' issue slots freed); with 1-2
     // warps every warp runs them on its own copy (two barriers per iteration)
     constexpr bool SOLO = MAXT > 64;
-    float* cxd = s_cxd[SOLO ? 0 : warp];
-    float* cyd = s_cyd[SOLO ? 0 : warp];
-    float* cpd = s_cpd[SOLO ? 0 : warp];
+    float* cxv = s_cx[SOLO ? 0 : warp];
+    float* cyv = s_cy[SOLO ? 0 : warp];
+    float* cpv = s_cp[SOLO ? 0 : warp];
 
     // Scene: ego (Sec. III, x0 = 0) and obstacles, normalised by the ellipse
     // axes, negated, duplicated for the sample pair, in the frame moving with v0.
@@ -870,7 +910,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     const bool act = k < NC;
     const int kk = act ? k : 0;
     float c = 0.f, e = 0.f, lam = 0.f, lampsi = 0.f, cbp = 0.f, corr = 0.f;
-    float* own = isy ? cyd : cxd;
+    float* own = isy ? cyv : cxv;
     float* vec = s_vec[warp][isy ? 1 : 0];
     {
         const float* g = A.goals + 3 * l;
@@ -935,8 +975,8 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             if (!isy) lampsi = __ldg(A.warm_l + (size_t)l * 3 * A.n + 2 * A.n + k);
         }
         if ((!SOLO || warp == 0) && act) {
-            reinterpret_cast<float2*>(own)[k] = f2(c);
-            if (!isy) reinterpret_cast<float2*>(cpd)[k] = f2(cp0);
+            own[k] = c;
+            if (!isy) cpv[k] = cp0;
         }
     }
     if constexpr (SOLO) __syncthreads();
@@ -960,9 +1000,9 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         {  // lanes without a sample pair read zero rows: their terms vanish
             float2 x, y, xdd, ydd, ps;
             if constexpr (PREC != MMPC_PREC_FP32)
-                eval_pair5_prec<NC, PREC>(PP, PddP, PPl, PddPl, cxd, cyd, cpd, x, y, xdd, ydd, ps);
+                eval_pair5_prec<NC, PREC>(PP, PddP, PPl, PddPl, cxv, cyv, cpv, x, y, xdd, ydd, ps);
             else
-                eval_pair5<NC>(PP, PddP, cxd, cyd, cpd, x, y, xdd, ydd, ps);
+                eval_pair5<NC>(PP, PddP, cxv, cyv, cpv, x, y, xdd, ydd, ps);
             // Eq. v_update and the non-holonomic rows v (cos psi, sin psi)
             const float2 sp2 = __ffma2_rn(xd, xd, __fmul2_rn(yd, yd));
             const float2 nvel = f2(-fminf(fmaxf(sqrtf(sp2.x), A.v_min), A.v_max),
@@ -993,61 +1033,73 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             const float2 eox = __fmul2_rn(Sx, f2(-A.a));
             const float2 eoy = __fmul2_rn(Sy, f2(-A.b));
             const float2 dpsi = __fadd2_rn(ps, f2(-theta.x, -theta.y));
+            // The contractions P^T e over the pair: for each coefficient pair
+            // one FFMA2 chain through both samples' rows, the per-sample
+            // operands duplicated (e_s, e_s).
             if constexpr (PREC != MMPC_PREC_FP32) {
                 // the per-sample operands of the contractions, hi and lo
                 float2 eh[7], el[7];
                 const float2 ev[7] = {eox, eax, evx, eoy, eay, evy, dpsi};
 #pragma unroll
-                for (int i = 0; i < 7; ++i) {
-                    eh[i] = rnd2<PREC>(ev[i]);
-                    el[i] = rnd2<PREC>(__fadd2_rn(ev[i], f2(-eh[i].x, -eh[i].y)));
-                }
+                for (int i = 0; i < 7; ++i) split2<PREC>(ev[i], eh[i], el[i]);
 #pragma unroll
                 for (int q = 0; q < NC; q += 2) {
-                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
-                    const float4 d4 = *reinterpret_cast<const float4*>(PdP + 2 * q);
-                    const float4 dd4 = *reinterpret_cast<const float4*>(PddP + 2 * q);
-                    const float4 pl4 = *reinterpret_cast<const float4*>(PPl + 2 * q);
-                    const float4 dl4 = *reinterpret_cast<const float4*>(PdPl + 2 * q);
-                    const float4 ddl4 = *reinterpret_cast<const float4*>(PddPl + 2 * q);
+                    const float4 p4 = ld4(PP + 2 * q), d4 = ld4(PdP + 2 * q), dd4 = ld4(PddP + 2 * q);
+                    const float4 pl4 = ld4(PPl + 2 * q), dl4 = ld4(PdPl + 2 * q), ddl4 = ld4(PddPl + 2 * q);
+                    float2 sx = f2(0.f), sy = f2(0.f), sp = f2(0.f);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float2 pr = h ? f2(p4.z, p4.w) : f2(p4.x, p4.y);
-                        const float2 dr = h ? f2(d4.z, d4.w) : f2(d4.x, d4.y);
-                        const float2 ddr = h ? f2(dd4.z, dd4.w) : f2(dd4.x, dd4.y);
-                        const float2 prl = h ? f2(pl4.z, pl4.w) : f2(pl4.x, pl4.y);
-                        const float2 drl = h ? f2(dl4.z, dl4.w) : f2(dl4.x, dl4.y);
-                        const float2 ddrl = h ? f2(ddl4.z, ddl4.w) : f2(ddl4.x, ddl4.y);
-                        float2 sx = pfma<PREC>(dr, drl, eh[2], el[2], f2(0.f));
-                        sx = pfma<PREC>(ddr, ddrl, eh[1], el[1], sx);
-                        sx = pfma<PREC>(pr, prl, eh[0], el[0], sx);
-                        float2 sy = pfma<PREC>(dr, drl, eh[5], el[5], f2(0.f));
-                        sy = pfma<PREC>(ddr, ddrl, eh[4], el[4], sy);
-                        sy = pfma<PREC>(pr, prl, eh[3], el[3], sy);
-                        const float2 sp = pfma<PREC>(pr, prl, eh[6], el[6], f2(0.f));
-                        v[q + h] = sx.x + sx.y;
-                        v[NC + q + h] = sy.x + sy.y;
-                        v[2 * NC + q + h] = sp.x + sp.y;
+                        const float2 pr = h ? hi2(p4) : lo2(p4), prl = h ? hi2(pl4) : lo2(pl4);
+                        const float2 dr = h ? hi2(d4) : lo2(d4), drl = h ? hi2(dl4) : lo2(dl4);
+                        const float2 ddr = h ? hi2(dd4) : lo2(dd4), ddrl = h ? hi2(ddl4) : lo2(ddl4);
+                        float2 H[7], Lo[7];
+#pragma unroll
+                        for (int i = 0; i < 7; ++i) {
+                            H[i] = f2(h ? eh[i].y : eh[i].x);
+                            Lo[i] = f2(h ? el[i].y : el[i].x);
+                        }
+                        sx = pfma<PREC>(dr, drl, H[2], Lo[2], sx);
+                        sx = pfma<PREC>(ddr, ddrl, H[1], Lo[1], sx);
+                        sx = pfma<PREC>(pr, prl, H[0], Lo[0], sx);
+                        sy = pfma<PREC>(dr, drl, H[5], Lo[5], sy);
+                        sy = pfma<PREC>(ddr, ddrl, H[4], Lo[4], sy);
+                        sy = pfma<PREC>(pr, prl, H[3], Lo[3], sy);
+                        sp = pfma<PREC>(pr, prl, H[6], Lo[6], sp);
                     }
+                    v[q] = sx.x;
+                    v[q + 1] = sx.y;
+                    v[NC + q] = sy.x;
+                    v[NC + q + 1] = sy.y;
+                    v[2 * NC + q] = sp.x;
+                    v[2 * NC + q + 1] = sp.y;
                 }
             } else {
+                const float2 ox0 = f2(eox.x), ox1 = f2(eox.y), ax0 = f2(eax.x), ax1 = f2(eax.y);
+                const float2 vx0 = f2(evx.x), vx1 = f2(evx.y), oy0 = f2(eoy.x), oy1 = f2(eoy.y);
+                const float2 ay0 = f2(eay.x), ay1 = f2(eay.y), vy0 = f2(evy.x), vy1 = f2(evy.y);
+                const float2 dp0 = f2(dpsi.x), dp1 = f2(dpsi.y);
 #pragma unroll
                 for (int q = 0; q < NC; q += 2) {
-                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
-                    const float4 d4 = *reinterpret_cast<const float4*>(PdP + 2 * q);
-                    const float4 dd4 = *reinterpret_cast<const float4*>(PddP + 2 * q);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float2 pr = h ? f2(p4.z, p4.w) : f2(p4.x, p4.y);
-                        const float2 dr = h ? f2(d4.z, d4.w) : f2(d4.x, d4.y);
-                        const float2 ddr = h ? f2(dd4.z, dd4.w) : f2(dd4.x, dd4.y);
-                        const float2 sx = __ffma2_rn(pr, eox, __ffma2_rn(ddr, eax, __fmul2_rn(dr, evx)));
-                        const float2 sy = __ffma2_rn(pr, eoy, __ffma2_rn(ddr, eay, __fmul2_rn(dr, evy)));
-                        const float2 sp = __fmul2_rn(pr, dpsi);
-                        v[q + h] = sx.x + sx.y;
-                        v[NC + q + h] = sy.x + sy.y;
-                        v[2 * NC + q + h] = sp.x + sp.y;
-                    }
+                    const float4 p4 = ld4(PP + 2 * q), d4 = ld4(PdP + 2 * q), dd4 = ld4(PddP + 2 * q);
+                    float2 sx = __fmul2_rn(lo2(d4), vx0);
+                    sx = __ffma2_rn(lo2(dd4), ax0, sx);
+                    sx = __ffma2_rn(lo2(p4), ox0, sx);
+                    sx = __ffma2_rn(hi2(d4), vx1, sx);
+                    sx = __ffma2_rn(hi2(dd4), ax1, sx);
+                    sx = __ffma2_rn(hi2(p4), ox1, sx);
+                    float2 sy = __fmul2_rn(lo2(d4), vy0);
+                    sy = __ffma2_rn(lo2(dd4), ay0, sy);
+                    sy = __ffma2_rn(lo2(p4), oy0, sy);
+                    sy = __ffma2_rn(hi2(d4), vy1, sy);
+                    sy = __ffma2_rn(hi2(dd4), ay1, sy);
+                    sy = __ffma2_rn(hi2(p4), oy1, sy);
+                    const float2 sp = __ffma2_rn(hi2(p4), dp1, __fmul2_rn(lo2(p4), dp0));
+                    v[q] = sx.x;
+                    v[q + 1] = sx.y;
+                    v[NC + q] = sy.x;
+                    v[NC + q + 1] = sy.y;
+                    v[2 * NC + q] = sp.x;
+                    v[2 * NC + q + 1] = sp.y;
                 }
             }
             if (resid) {
@@ -1067,32 +1119,31 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     // (Eq. split_psi), and the partial sums of P^T theta.
     auto heading = [&](bool reduce) {
         float2 xd0;
-        if constexpr (PREC != MMPC_PREC_FP32) eval_pair2_prec<NC, PREC>(PdP, PdPl, cxd, cyd, xd0, yd);
-        else eval_pair2<NC>(PdP, cxd, cyd, xd0, yd);
+        if constexpr (PREC != MMPC_PREC_FP32) eval_pair2_prec<NC, PREC>(PdP, PdPl, cxv, cyv, xd0, yd);
+        else eval_pair2<NC>(PdP, cxv, cyv, xd0, yd);
         xd = __fadd2_rn(xd0, f2(v0));
         theta = atan2_pair(yd, xd);
         if (reduce) {
             float v[NC];
             if constexpr (PREC != MMPC_PREC_FP32) {
-                const float2 th = rnd2<PREC>(theta);
-                const float2 tl = rnd2<PREC>(__fadd2_rn(theta, f2(-th.x, -th.y)));
+                float2 th, tl;
+                split2<PREC>(theta, th, tl);
+                const float2 th0 = f2(th.x), th1 = f2(th.y), tl0 = f2(tl.x), tl1 = f2(tl.y);
 #pragma unroll
                 for (int q = 0; q < NC; q += 2) {
-                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
-                    const float4 l4 = *reinterpret_cast<const float4*>(PPl + 2 * q);
-                    const float2 s0 = pfma<PREC>(f2(p4.x, p4.y), f2(l4.x, l4.y), th, tl, f2(0.f));
-                    const float2 s1 = pfma<PREC>(f2(p4.z, p4.w), f2(l4.z, l4.w), th, tl, f2(0.f));
-                    v[q] = s0.x + s0.y;
-                    v[q + 1] = s1.x + s1.y;
+                    const float4 p4 = ld4(PP + 2 * q), l4 = ld4(PPl + 2 * q);
+                    const float2 s = pfma<PREC>(hi2(p4), hi2(l4), th1, tl1, pfma<PREC>(lo2(p4), lo2(l4), th0, tl0, f2(0.f)));
+                    v[q] = s.x;
+                    v[q + 1] = s.y;
                 }
             } else {
+                const float2 th0 = f2(theta.x), th1 = f2(theta.y);
 #pragma unroll
                 for (int q = 0; q < NC; q += 2) {
-                    const float4 p4 = *reinterpret_cast<const float4*>(PP + 2 * q);
-                    const float2 s0 = __fmul2_rn(f2(p4.x, p4.y), theta);
-                    const float2 s1 = __fmul2_rn(f2(p4.z, p4.w), theta);
-                    v[q] = s0.x + s0.y;
-                    v[q + 1] = s1.x + s1.y;
+                    const float4 p4 = ld4(PP + 2 * q);
+                    const float2 s = __ffma2_rn(hi2(p4), th1, __fmul2_rn(lo2(p4), th0));
+                    v[q] = s.x;
+                    v[q + 1] = s.y;
                 }
             }
             reduce_store<NC>(v, dstB, lane);
@@ -1104,12 +1155,9 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
     auto psi_step = [&]() {
         float pth = 0.f;
         for (int w = 0; w < nwarps; ++w) pth += red1[w * RSB + kk];
-        if (!isy && act) reinterpret_cast<float2*>(vec)[k] = f2(fmaf(rho, pth, lampsi));
+        if (!isy && act) vec[k] = fmaf(rho, pth, lampsi);
         __syncwarp();
-        if (!isy && act) {
-            const float cp = cbp + dot_dup<NC>(blob + L.Kp11 + kk * k_stride(NC), vec);
-            reinterpret_cast<float2*>(cpd)[k] = f2(cp);
-        }
+        if (!isy && act) cpv[k] = cbp + dot_vec<NC>(blob + L.Kp11 + kk * k_stride(NC), vec);
         __syncwarp();
     };
 
@@ -1135,7 +1183,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             lam = fmaf(-rho, ftd, lam);
             if (!isy) lampsi = fmaf(-rho, pd, lampsi);
         }
-        const float qc = dot_dup<NC>(blob + L.Q + kk * k_stride(NC), own);
+        const float qc = dot_vec<NC>(blob + L.Q + kk * k_stride(NC), own);
         const float u = act ? (lam - qc - rho * ftd) : 0.f;
         bool done = kit >= iters;
         if (check && kit % A.check_every == 0 && (A.tol > 0.f || A.stall_tol > 0.f)) {
@@ -1152,18 +1200,18 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         }
         if (!done) {
             // Eq. lin_solve_xy_2 in increment form, K11 applied as hi + lo
-            if (act) reinterpret_cast<float2*>(vec)[k] = f2(u);
+            if (act) vec[k] = u;
             __syncwarp();
             if (act) {
-                const float d0 = dot_dup<NC>(blob + (isy ? L.Kyh : L.Kxh) + kk * k_stride(NC), vec);
-                const float d1 = dot_dup<NC>(blob + (isy ? L.Kyl : L.Kxl) + kk * k_stride(NC), vec);
+                const float d0 = dot_vec<NC>(blob + (isy ? L.Kyh : L.Kxh) + kk * k_stride(NC), vec);
+                const float d1 = dot_vec<NC>(blob + (isy ? L.Kyl : L.Kxl) + kk * k_stride(NC), vec);
                 const float dd = (d0 + d1) + (first ? e + corr : e);
                 const float snew = c + dd;
                 e = dd - (snew - c);
                 c = snew;
             }
             __syncwarp();
-            if (act) reinterpret_cast<float2*>(own)[k] = f2(c);
+            if (act) own[k] = c;
             __syncwarp();
         }
         return done;
@@ -1221,7 +1269,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
         if (act && k < n) {
             if (!isy) {
                 A.coef_out[o + k] = (c + e) + v0 * blob[L.lin + k];
-                A.coef_out[o + 2 * n + k] = cpd[2 * k];
+                A.coef_out[o + 2 * n + k] = cpv[k];
             } else {
                 A.coef_out[o + n + k] = c + e;
             }
@@ -1969,7 +2017,8 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
                 h[dst + r * dcols + c] = lo ? (float)(v - (double)hi) : hi;
             }
     };
-    // basis rows of the sample pairs (2i, 2i+1), interleaved per coefficient
+    // basis rows of the sample pairs (2i, 2i+1): per coefficient pair (2j,
+    // 2j+1) the block (s0 2j, s0 2j+1, s1 2j, s1 2j+1)
     const int NP = (N + 1) / 2;
     // (precision modes: the rows rounded as the tensor cores would take them,
     // hi into the rows and lo into the lo rows in the split modes)
@@ -1981,8 +2030,9 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
                 for (int c = 0; c < n; ++c) {
                     const float f = (float)buf[src + (size_t)smp * n + c];
                     const float hi = round_operand(f, prec);
-                    h_set(dst + i * pair_stride(NC) + c * 2 + h, hi);
-                    if (prec_split(prec)) h_set(dst_lo + i * pair_stride(NC) + c * 2 + h, round_operand(f - hi, prec));
+                    const int at = i * pair_stride(NC) + 4 * (c >> 1) + 2 * h + (c & 1);
+                    h_set(dst + at, hi);
+                    if (prec_split(prec)) h_set(dst_lo + at, round_operand(f - hi, prec));
                 }
             }
     };
