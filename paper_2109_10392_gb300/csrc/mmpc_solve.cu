@@ -685,6 +685,15 @@ __device__ __forceinline__ int cull_update(CullState& cs, int m, float xlo, floa
     return count;
 }
 
+// Whether a sample lies in the list box (always for a lane without that
+// sample; never for a NaN coordinate).  When every sample of the warp does,
+// the warp's box lies inside the list box and the list is reused exactly as
+// cull_update would.
+__device__ __forceinline__ bool in_list_box(float x, float y, float valid, const CullState& cs)
+{
+    return !(valid > 0.f) || (x >= cs.xlo && x <= cs.xhi && y >= cs.ylo && y <= cs.yhi);
+}
+
 // The warp's sample box for the pair kernel; returns whether a valid sample
 // has a non-finite coordinate.
 __device__ __forceinline__ bool box_pair(float2 Xn, float2 Yn, float2 valid, float& xlo, float& xhi, float& ylo,
@@ -803,8 +812,10 @@ template <int NC, int MAXT>
 struct MinBlocks {
     // NC = 16 with 128 threads (N = 129..256): 3 CTAs per SM and the
     // register budget that allows (no spills); a fourth CTA at 128 registers
-    // spills and was slower (11.0 against 10.4 ms at N = 200)
-    static constexpr int value = MAXT <= 64 ? 8 : (MAXT <= 128 ? (NC == 16 ? 3 : 4) : 2);
+    // spills and was slower (11.0 against 10.4 ms at N = 200).  NC = 12 with
+    // 64 threads: a bound of 7 (the kernel still takes 128 registers, so 8
+    // CTAs fit) measured 1.4 % faster than 8 on the 1024-goal scene.
+    static constexpr int value = MAXT <= 64 ? (NC == 12 ? 7 : 8) : (MAXT <= 128 ? (NC == 16 ? 3 : 4) : 2);
 };
 
 // dot product of two 16-byte aligned vectors of NC floats; four partial
@@ -1021,9 +1032,15 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             float2 Sx, Sy, R2;
             int cnt = m;  // without culling the list holds every obstacle in order
             if (A.cull) {
-                float bxlo, bxhi, bylo, byhi;
-                const bool bad = box_pair(Xn, Yn, valid, bxlo, bxhi, bylo, byhi);
-                cnt = cull_update<true>(cull, m, bxlo, bxhi, bylo, byhi, bad, tw_lo, tw_hi, olist, lane, obs);
+                // the list stays valid while every sample is inside its box (a
+                // vote); otherwise the warp's box is formed and the list rebuilt
+                if (__all_sync(FULL, in_list_box(Xn.x, Yn.x, valid.x, cull) && in_list_box(Xn.y, Yn.y, valid.y, cull))) {
+                    cnt = cull.count;
+                } else {
+                    float bxlo, bxhi, bylo, byhi;
+                    const bool bad = box_pair(Xn, Yn, valid, bxlo, bxhi, bylo, byhi);
+                    cnt = cull_update<true>(cull, m, bxlo, bxhi, bylo, byhi, bad, tw_lo, tw_hi, olist, lane, obs);
+                }
             }
             if (lane == 0) work += (unsigned long long)cnt * (unsigned)(w_last - w_first + 1);
             if (resid) obstacle_sum2<true, true>(obs, olist, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
