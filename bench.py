@@ -68,9 +68,9 @@ def workload_name(params, B, m):
 # DRAM bytes (read + write) of one solve launch, from an ncu capture of that
 # workload's kernel as it stands (profiles/am_solve_kernel_*.md); an entry must
 # be measured again whenever the kernel changes.
-SOLVE_DRAM_BYTES = {"highway_B1024_m50_N100_n12_K100_tol0.01": 126464}
+SOLVE_DRAM_BYTES = {"highway_B1024_m50_N100_n12_K100_tol0.01": 124160}
 # per step, summed over the three horizon-group launches of schedule 4
-BATCH_DRAM_BYTES = {"highway_batch_S256_B16-512_m5-40_N50-100-150_n12_K100_tol0.01": 5001216}
+BATCH_DRAM_BYTES = {"highway_batch_S256_B16-512_m5-40_N50-100-150_n12_K100_tol0.01": 4440576}
 
 OPS_PER_ELEMENT = 10  # FP32 lane ops per evaluated obstacle-sample pair
 
@@ -762,7 +762,9 @@ def add_measured_peak(roofline: dict) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default per workload: scene 2000, precision 20, batch 100, warm 3; "
+                         "--impl reference: 3); a warm step replays the whole 1M-trajectory evaluation")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=500)
@@ -783,6 +785,11 @@ def main():
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="batch item order (0: autotuned)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = (3 if args.impl == "reference" else
+                      {"precision": 20, "batch": 100, "warm": 3}.get(args.workload, 2000))
+    if args.steps < 1:
+        ap.error("--steps must be >= 1")
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
