@@ -3,11 +3,14 @@
 //
 // Solve kernel: one CTA per trajectory l of the batch, one thread per pair of
 // time samples (2i, 2i+1), whose arithmetic runs as packed f32x2 operations
-// (FFMA2 / FADD2 / FMUL2: one issue slot for two samples).  Every quantity
-// that Algorithm 1 carries from one iteration to the next for trajectory l --
+// (FFMA2 / FADD2 / FMUL2: one issue slot for two samples in the projections,
+// for two coefficients in the basis products).  Every quantity that
+// Algorithm 1 carries from one iteration to the next for trajectory l --
 // c_x, c_y, c_psi and lambda_x, lambda_y, lambda_psi -- stays on chip for all
-// iterations (registers of every warp, which all run the small QP steps on
-// the same partial sums); the auxiliary variables v, alpha, d, alpha_a, d_a of Eqs.
+// iterations (in registers: with 1-2 warps per trajectory every warp runs the
+// small QP steps on the same partial sums, with more warps warp 0 alone does
+// and shares the coefficients through shared memory); the auxiliary
+// variables v, alpha, d, alpha_a, d_a of Eqs.
 // split_v, split_alpha_o and split_alpha_a are closed-form functions of the
 // coefficients and are recomputed in registers where they are used.  The
 // shared matrices (basis rows, KKT inverse blocks) are staged once per CTA
@@ -792,12 +795,14 @@ __device__ __forceinline__ void heading_sincos(float ps, float* sn, float* cs)
 
 // ---------------------------------------------------------------------------
 // The fused AM kernel.  Grid: one CTA per trajectory; block: 32 ceil(ceil(N/2)
-// / 32) threads (at most 8 warps), thread i owns samples 2i and 2i+1.  Every
-// warp holds the whole coefficient state -- lane k (k < NC) coefficient k of
-// the x axis and of psi, lane 16 + k coefficient k of the y axis -- and runs
-// the two small QP steps itself from the CTA's partial sums: all warps
-// compute bit-identical values, so an iteration needs only two CTA barriers
-// (after the partial sums of P^T theta and after those of F^T (F c - g)).
+// / 32) threads (at most 8 warps), thread i owns samples 2i and 2i+1.  A warp
+// that runs the QP steps holds the whole coefficient state -- lane k (k < NC)
+// coefficient k of the x axis and of psi, lane 16 + k coefficient k of the y
+// axis.  With 1-2 warps every warp runs the two small QP steps itself from the
+// CTA's partial sums: all warps compute bit-identical values, so an iteration
+// needs only two CTA barriers (after the partial sums of P^T theta and after
+// those of F^T (F c - g)).  With more warps warp 0 alone runs them and the
+// others read its coefficient vectors after two more barriers.
 // ---------------------------------------------------------------------------
 template <int NC>
 struct SolveSmem {
