@@ -759,7 +759,7 @@ def add_measured_peak(roofline: dict) -> None:
     roofline["frac_of_measured"] = roofline["achieved"] / lane
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
@@ -784,7 +784,7 @@ def main():
     ap.add_argument("--warm-eval-scenes", type=int, default=4096)
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="batch item order (0: autotuned)")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = (3 if args.impl == "reference" else
                       {"precision": 20, "batch": 100, "warm": 3}.get(args.workload, 2000))
@@ -792,6 +792,11 @@ def main():
         ap.error("--steps must be >= 1")
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    return args
+
+
+def main():
+    args = parse_args()
     if args.impl == "reference":
         out = run_reference(args)
     else:
