@@ -321,8 +321,9 @@ int mmpc_debug_expire_wait(mmpc_ctx* ctx, int on);
 /* Frees the context's device memory (synchronises the device first).  NULL is a no-op. */
 void mmpc_destroy(mmpc_ctx* ctx);
 
-/* Message of the last failing call on ctx (or of the last failing mmpc_setup
- * / mmpc_build when ctx is NULL).  Never NULL. */
+/* Message of the last failing call on ctx (or, when ctx is NULL, of the last
+ * failing call that takes no context: mmpc_setup, mmpc_build and
+ * mmpc_score_static).  Never NULL. */
 const char* mmpc_last_error(const mmpc_ctx* ctx);
 
 /* Allocation-free scoring, for callers that cannot allocate device memory
@@ -341,8 +342,11 @@ const char* mmpc_last_error(const mmpc_ctx* ctx);
  * until the process exits, and shared by all calls: calls whose work overlaps
  * on the GPU race and must be serialised by the caller.  It calls no
  * cudaMalloc or cudaFree.  The first call on a device looks up the array's
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture. */
+ * address (cudaGetSymbolAddress, with that device current) and keeps it for
+ * the life of the process; make that first call before any stream capture.
+ * The kept address belongs to the device's primary context: after
+ * cudaDeviceReset (or anything else that destroys that context) the library
+ * must not be called through this entry point again in the same process. */
 #define MMPC_STATIC_SCORE_MAX_B 65536
 int mmpc_score_static(const mmpc_meta* meta, int N, int n, const float* P, const float* Pd, const float* coef,
                       int B, float* cost_out, int* argmin_out, void* stream);

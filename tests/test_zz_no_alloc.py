@@ -38,9 +38,21 @@ def _static(meta, params, P, Pd, coef):
     return cost.cpu().numpy(), int(am.item())
 
 
+# the three meta-cost kinds (cruise, high-speed right lane, absolute), and one
+# heading limit tight enough that some trajectories are rejected (+inf)
+METAS = {
+    "cruise": dict(kind=0, w1=1.0, w2=0.0, v_ref=18.0, y_ref=0.0, psi_max_deg=13.0),
+    "hsrl": dict(kind=1, w1=1.0, w2=0.5, v_ref=30.0, y_ref=-5.25, psi_max_deg=13.0),
+    "abs": dict(scenes.META_ABS),
+    "abs_tight_heading": dict(scenes.META_ABS, psi_max_deg=0.5),
+}
+
+
 @pytest.mark.parametrize("n", [12, 16])
-def test_static_score_matches_context_score(n):
+@pytest.mark.parametrize("kind", sorted(METAS))
+def test_static_score_matches_context_score(n, kind):
     import torch
+    meta = METAS[kind]
     sc = scenes.scene_custom(seed=5, B=3000, m=6, N=100, n=n, x_range=(10.0, 150.0))
     params = dict(sc.params); params["iters"] = 20
     ego, obst, goals = U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
@@ -49,21 +61,28 @@ def test_static_score_matches_context_score(n):
     res = s.solve(torch.tensor(ego, dtype=torch.float32, device=dev),
                   torch.tensor(obst, dtype=torch.float32, device=dev),
                   torch.tensor(goals, dtype=torch.float32, device=dev))
-    ref_cost, ref_am = s.score(sc.meta, res.coef)
+    ref_cost, ref_am = s.score(meta, res.coef)
     torch.cuda.synchronize()
     ref_cost, ref_am = ref_cost.cpu().numpy(), int(ref_am.item())
+    if kind == "abs_tight_heading":
+        # the case exercises the rejection path on some but not all trajectories
+        assert 0 < int(np.isinf(ref_cost).sum()) < len(ref_cost)
     P, Pd = _basis(params)
     for _ in range(2):  # two calls in a row share the scratch array
-        cost, am = _static(sc.meta, params, P, Pd, res.coef)
-        assert np.allclose(cost, ref_cost, rtol=1e-6, atol=1e-6, equal_nan=False)
+        cost, am = _static(meta, params, P, Pd, res.coef)
         assert np.array_equal(np.isinf(cost), np.isinf(ref_cost))
+        fin = np.isfinite(ref_cost)
+        assert np.allclose(cost[fin], ref_cost[fin], rtol=1e-6, atol=1e-6, equal_nan=False)
         assert am == ref_am
     # a different batch after those calls: the previous contents do not leak
     sub = res.coef[:37].contiguous()
-    ref2_cost, ref2_am = s.score(sc.meta, sub)
+    ref2_cost, ref2_am = s.score(meta, sub)
     torch.cuda.synchronize()
-    cost, am = _static(sc.meta, params, P, Pd, sub)
-    assert np.allclose(cost, ref2_cost.cpu().numpy(), rtol=1e-6, atol=1e-6)
+    ref2_cost = ref2_cost.cpu().numpy()
+    cost, am = _static(meta, params, P, Pd, sub)
+    assert np.array_equal(np.isinf(cost), np.isinf(ref2_cost))
+    fin = np.isfinite(ref2_cost)
+    assert np.allclose(cost[fin], ref2_cost[fin], rtol=1e-6, atol=1e-6)
     assert am == int(ref2_am.item())
     s.close()
 
