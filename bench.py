@@ -2,24 +2,28 @@
 """Benchmark of the batch non-holonomic AM trajectory optimizer (arXiv
 2109.10392, Algorithm 1 + meta-cost argmin) on GB300.
 
-Workload: one synthetic highway scene per GPU with B = 1024 goals (8 lateral
-offsets x 128 speeds ~ U(5, 30) m/s), 50 constant-velocity obstacles, N = 100
-samples, 12 Bernstein coefficients per axis, at most 100 AM iterations with
-early exit once a trajectory's residual is <= 1e-2 m (checked every 10
-iterations), FP32.  A step is one mmpc_solve (cold start + Algorithm 1) and one
-mmpc_score (meta cost + argmin) over the batch.
+Default workload (--workload warm), the metric "trajectories/s to residual
+<= 1e-2 m, warm-started vs plain GPU": 4096 fresh synthetic highway scenes x
+256 goals (8 lateral offsets x 32 speeds ~ U(5, 30) m/s), 50 constant-velocity
+obstacles, N = 100 samples, 12 Bernstein coefficients per axis, at most 100
+AM iterations with early exit once a trajectory's residual is <= 1e-2 m
+(checked every 10 iterations), FP32.  A network trained in the run on scenes
+solved by the method itself gives the warm starts.  A step is one CUDA graph
+replay of the target form over all scenes: features, network, decode, one
+persistent solve launch, cold fallback of every miss, scoring, per-scene
+argmin, with the opt-in stall stop.  `value` is the number of trajectories
+that reach the residual target per second; `detail` holds the same figure for
+the plain method (one mmpc_solve + mmpc_score per scene), the batched cold
+start and every warm-start variant, with and without the stall stop, and the
+plain 1024-goal scene's throughput.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                    [--workload warm|scene|batch|precision|sweep]
 
-One JSON line on stdout (rank 0).  `value`: trajectories per second, all
-ranks together, each trajectory iterated until its residual is <= 1e-2 m or
-the 100-iteration budget is spent (the stopping rule of the metric); the
-fraction that reached the residual target is reported beside it
-(detail.converged_fraction; in this dense 50-vehicle scene most goals are
-infeasible and end on the budget).  Each rank solves its own scene: weak
+One JSON line on stdout (rank 0).  Each rank solves its own scenes: weak
 scaling, no collective on the data path.  --impl reference times the FP64
-CPU oracle on the host cores instead (a bounded sample of the same scene per
-step, same stopping rule).
+CPU oracle (the plain cold-started method) on the host cores instead, on a
+bounded sample of the same evaluation scenes per step, same stopping rule.
 """
 from __future__ import annotations
 
@@ -65,33 +69,51 @@ def workload_name(params, B, m):
     return f"highway_B{B}_m{m}_N{params['N']}_n{params['n']}_K{params['iters']}_tol{TOL:g}"
 
 
-# DRAM bytes (read + write) of one solve launch, from an ncu capture of that
-# workload's kernel as it stands (profiles/am_solve_kernel_*.md); an entry must
-# be measured again whenever the kernel changes.
-SOLVE_DRAM_BYTES = {"highway_B1024_m50_N100_n12_K100_tol0.01": 124160}
-# per step, summed over the three horizon-group launches of schedule 4
-BATCH_DRAM_BYTES = {"highway_batch_S256_B16-512_m5-40_N50-100-150_n12_K100_tol0.01": 4440576}
+UNIT_CONV = "trajectories/s reaching residual <= 1e-2 m"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def _sha256(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload`, from
+    the ncu figures recorded in profiles/dram_traffic.json, or None when no
+    figure was taken with the kernel source as it is now (the entry stores
+    the SHA-256 of the source file it was measured with)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            entries = json.load(f)["entries"]
+    except (OSError, ValueError, KeyError):
+        return None
+    for e in entries:
+        if e.get("kernel") == kernel and e.get("workload") == workload:
+            try:
+                if _sha256(os.path.join(ROOT, e["source"])) == e["sha256"]:
+                    return e["bytes_per_launch"]
+            except (OSError, KeyError):
+                return None
+    return None
+
 
 OPS_PER_ELEMENT = 10  # FP32 lane ops per evaluated obstacle-sample pair
 
 
-def contraction_ops_per_sample(n):
-    """FP32 lane ops of the basis contractions per sample and pass: 7
-    evaluations (x, y, xdot, ydot, xddot, yddot, psi) and 8 transposed products
-    (F^T (F c - g) for x and y, 3 blocks each; P^T theta; P^T (psi - theta)),
-    n multiply-adds each."""
-    return 15 * n
-
-
 def alu_ops(N, n, passes, elements):
-    """Algorithmic FP32 lane operations of a solve: `elements` evaluated
-    obstacle-sample pairs of Eq. split_alpha_o at 10 ops each (predicted
-    position and offset 4, normalised squared distance 2, max(1/r - 1, 0) 2,
-    accumulation 2; the reciprocal square root runs on the SFU and is counted
-    separately), plus the contractions of every sample in every pass (the
-    initial one and one per iteration).  Element-wise trigonometry is not
-    counted.  Without culling, elements = passes N m."""
-    return elements * OPS_PER_ELEMENT + passes * N * contraction_ops_per_sample(n)
+    """FP32 lane operations of a solve, per trajectory-iteration (every AM
+    pass: the initial one and one per iteration run): 14 N n basis products
+    (2 N n for xdot, ydot; N n for P^T theta; N n for psi; 4 N n for x, y,
+    xddot, yddot; 6 N n for F^T g) + 7 n^2 for the QP and multiplier products
+    + 60 N element-wise (velocity, heading trigonometry, acceleration
+    projection, residuals), plus 10 per obstacle-sample pair of Eq.
+    split_alpha_o (predicted offset 4, normalised squared distance 2,
+    max(1/r - 1, 0) 2, accumulation 2).  `elements` = passes N m gives the
+    algorithm's dense count (culled pairs are exact zeros); the evaluated
+    pair count gives the work the kernel executed."""
+    return elements * OPS_PER_ELEMENT + passes * (14 * N * n + 7 * n * n + 60 * N)
 
 
 def rank_env():
@@ -301,17 +323,19 @@ def run_mine(args):
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
         "roofline": {"bound": "alu", "kernel": "am_solve_kernel", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak,
-                     "traffic": (SOLVE_DRAM_BYTES.get(workload_name(params, B, m))
-                                 if params["cull"] and params["variant"] == 0 else None),
+                     "traffic": (measured_traffic("am_solve_kernel", workload_name(params, B, m))
+                                 if params["cull"] and params["variant"] == 0 and not args.stall else None),
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz",
                      "ops_per_launch": ops, "launch_ms": solve_avg,
-                     "ops_basis": "every obstacle-sample pair of Eq. split_alpha_o at 10 ops plus 15 n contraction "
-                                  "ops per sample and pass; culled pairs are exact zeros, so this is the "
-                                  "algorithm's work whether or not the kernel skips them",
+                     "ops_basis": "per trajectory-iteration 14 N n + 7 n^2 (basis and QP products) + 10 m N "
+                                  "(obstacle projections) + 60 N (element-wise); culled obstacle-sample pairs "
+                                  "are exact zeros, so this is the algorithm's work whether or not the kernel "
+                                  "skips them",
                      "evaluated_pairs_per_launch": elements, "dense_pairs_per_launch": passes * N * m,
                      "executed_ops_per_launch": exec_ops,
                      "executed_achieved": exec_ops / (solve_avg * 1e-3) / 1e12,
+                     "executed_frac": exec_ops / (solve_avg * 1e-3) / 1e12 / peak,
                      "sfu_frac": sfu_ops / (solve_avg * 1e-3) / (SM_COUNT * SFU_PER_SM * SM_MAX_MHZ * 1e6)},
         "e2e": {"value": agg["e2e_units"] / (agg["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": agg["e2e_ms"], "steps": Ke,
@@ -492,8 +516,8 @@ def run_batch(args):
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},
         "roofline": {"bound": "alu", "kernel": "am_solve_batch_kernel", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak,
-                     "traffic": (BATCH_DRAM_BYTES.get(f"highway_batch_S{S}_B16-512_m5-40_N{'-'.join(map(str, Ns))}"
-                                                      f"_n12_K100_tol{TOL:g}")
+                     "traffic": (measured_traffic("am_solve_batch_kernel", f"highway_batch_S{S}_B16-512_m5-40_N"
+                                                  f"{'-'.join(map(str, Ns))}_n12_K100_tol{TOL:g}")
                                  if schedule == 4 and not args.stall else None),
                      "traffic_unit": "bytes per step (ncu dram__bytes_read.sum + dram__bytes_write.sum over the "
                                      "three horizon-group launches)",
@@ -521,14 +545,25 @@ def run_batch(args):
     return out
 
 
+HEADLINE = "warm_fallback"  # the target form: batched, learned warm start, cold fallback of every miss, stall stop
+
+
+def _warm_ops(N, n, m, passes):
+    """Dense algorithmic lane operations of `passes` AM passes (alu_ops)."""
+    return alu_ops(N, n, passes, passes * N * m)
+
+
 def run_warm(args):
-    """Learned warm start (trained here, on the GPU, by the library's kernels)
-    against the cold start on fresh scenes; one step = one CUDA graph replay
-    over all evaluation scenes (warm: features, network, decode, solve,
-    cold fallback of the misses, score)."""
+    """The metric: trajectories/s that reach residual <= 1e-2 m on fresh dense
+    highway scenes (4096 scenes x 256 goals, 50 obstacles), for the
+    warm-started, batched form (the network trained here, on the GPU, by the
+    library's kernels; cold fallback of the misses; opt-in stall stop)
+    against the plain cold-started GPU method on the same scenes.  One step =
+    one CUDA graph replay over all evaluation scenes (features, network,
+    decode, persistent solve, fallback solve, score)."""
     import torch
 
-    from paper_2109_10392_gb300 import warmstart
+    from paper_2109_10392_gb300 import mmpc, warmstart
 
     rank, world, local = rank_env()
     dist = None
@@ -550,55 +585,212 @@ def run_warm(args):
     train_rows = int(X.shape[0])
     del X, T, Xv, Tv
     S, B = args.warm_eval_scenes, 256
+    seed = 10**6 + rank
     fwd = warmstart.time_forward(ws, S * B, dev)
+    reps = 3
+    dense = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=seed, plain=True)
+    ev = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=seed, stall=STALL, keep=True)
+    keep = ev.pop("_keep")
+    plain = dense["plain"]
+    for k in ("cold", "warm", "warm_fallback", "warm_fallback_budget"):
+        ev[f"{k}_vs_plain"] = ev[k]["trajectories_per_s"] / plain["trajectories_per_s"]
+        ev[f"{k}_converged_vs_plain"] = ev[k]["converged_per_s"] / plain["converged_per_s"]
+        ev[f"{k}_converged_vs_batched_cold"] = ev[k]["converged_per_s"] / dense["cold"]["converged_per_s"]
+        ev[f"{k}_converged_vs_batched_cold_stall"] = ev[k]["converged_per_s"] / ev["cold"]["converged_per_s"]
+    warm, stream = keep["warm"], keep["stream"]
+    graph = keep["graphs"][HEADLINE]
+    converged = ev[HEADLINE]["converged"]
+
+    # the headline: K replays of the target form's graph between L2-sized
+    # input sets (the 1M-trajectory outputs alone exceed L2), CUDA events on
+    # the replay stream, clocks sampled meanwhile
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.replay()
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
     sampler = ClockSampler(dev.index or 0)
     sampler.start()
-    dense = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=args.steps, seed=10**6 + rank, plain=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    tw = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            evs[i][0].record(stream)
+            graph.replay()
+            evs[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - tw
     clocks = sampler.stop()
-    dense_stall = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=args.steps, seed=10**6 + rank, stall=STALL)
-    for k in ("cold", "warm", "warm_fallback"):
-        dense_stall[f"{k}_vs_plain"] = dense_stall[k]["trajectories_per_s"] / dense["plain"]["trajectories_per_s"]
-        dense_stall[f"{k}_converged_vs_plain"] = (dense_stall[k]["converged_per_s"] /
-                                                  dense["plain"]["converged_per_s"])
-    sparse = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=max(3, args.steps // 2), seed=2 * 10**6 + rank,
-                                obstacles=10, x_range=(-30.0, 120.0))
-    ws.close()
-    wf = dense["warm_fallback"]
-    agg = combine_ranks(dict(units=S * B, ms=wf["ms"], e2e_units=S * B, e2e_ms=wf["ms"]), world, dist)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / K
+    conv_now = int((warm.flat["resid"].view(-1, 4)[:, :3].max(dim=1).values <= TOL).sum().item())
+
+    # the dominant kernel: am_solve_batch_kernel (the warm solve and the
+    # fallback solve of each step), timed by events the library records on
+    # the run's stream around the two launches, in eager runs of the same step
+    p = cfg.params
+    N, n, m = int(p["N"]), int(p["n"]), cfg.obstacles
+    tev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    warm.set_fallback(1)
+    warm.set_timing(tev)
+    warm.take_work_count()
+    solve_ms, fb_ms, R = 0.0, 0.0, 3
+    for _ in range(R):
+        with torch.cuda.stream(stream):
+            keep["step"]()
+        torch.cuda.synchronize(dev)
+        solve_ms += tev[0].elapsed_time(tev[1]) / R
+        fb_ms += tev[2].elapsed_time(tev[3]) / R
+    warm.set_timing(None)
+    elements = warm.take_work_count() / R
+    passes = ev[HEADLINE]["passes"]
+    ops = _warm_ops(N, n, m, passes)  # two launches per step
+    exec_ops = alu_ops(N, n, passes, elements)
+    launch_ms = (solve_ms + fb_ms) / 2
+    achieved = ops / 2 / (launch_ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = measured_traffic("am_solve_batch_kernel", f"highway_warm_S{S}_B{B}_m{m}_N{N}_n{n}")
+
+    # end to end through the library's public calls with host buffers: the
+    # step's inputs copied in from pinned memory, the graph replayed, every
+    # output (coefficients, residuals, iterations, costs, per-scene argmin)
+    # copied back, the stream synchronised
+    ins = keep["inputs"]
+    h_in = {k: v.cpu().pin_memory() for k, v in ins.items()}
+    outs = [warm.flat[k] for k in ("coef", "resid", "iters", "cost", "argmin")]
+    h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
+    h2d = sum(t.numel() * t.element_size() for t in h_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in h_out)
+    Ke = max(1, min(K, args.e2e_steps))
+    e2e_conv = 0
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(Ke):
+            for k, v in ins.items():
+                v.copy_(h_in[k], non_blocking=True)
+            graph.replay()
+            for h, d in zip(h_out, outs):
+                h.copy_(d, non_blocking=True)
+            stream.synchronize()
+            e2e_conv = int((h_out[1][:, :3].max(dim=1).values <= TOL).sum())
+    e2e_ms = (time.perf_counter() - te) * 1e3 / Ke
+
+    agg = combine_ranks(dict(units=converged, ms=ms, e2e_units=e2e_conv, e2e_ms=e2e_ms), world, dist)
+    tagg = combine_ranks(dict(units=S * B, ms=ms, e2e_units=S * B, e2e_ms=e2e_ms), world, dist)
     if rank != 0:
+        keep["warm"].close()
+        keep["cold"].close()
+        ws.close()
         if dist is not None:
             dist.destroy_process_group()
         return None
-    p = cfg.params
-    N, n, m = p["N"], p["n"], cfg.obstacles
-    ops = alu_ops(N, n, wf["passes"], wf["passes"] * N * m)
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = ops / (wf["ms"] * 1e-3) / 1e12
+
+    sparse = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=2 * 10**6 + rank,
+                                obstacles=10, x_range=(-30.0, 120.0))
+    ws.close()
+    scene = _scene_throughput(dev)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_warm(p, S, B, m, cfg.x_range, seed)
     out = {
-        "metric": METRIC, "value": agg["units"] / (agg["ms"] * 1e-3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms"], "higher_is_better": True,
+        "metric": METRIC, "value": agg["units"] / (agg["ms"] * 1e-3), "unit": UNIT_CONV, "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": agg["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"highway_warm_S{S}_B{B}_m{m}_N{N}_n{n}_K100_tol{TOL:g}", "start": "learned warm start "
-                   "(lambda0 = Q c0) with cold fallback of the misses", "train_scenes": cfg.train_scenes,
-                   "train_rows": train_rows, "train_steps": cfg.steps, "network": list(cfg.widths),
-                   "graph": "one CUDA graph replay per step",
-                   "l2": "inputs and per-step outputs (1M trajectories) exceed L2"},
+        "config": {"workload": f"highway_warm_S{S}_B{B}_m{m}_N{N}_n{n}_K{p['iters']}_tol{TOL:g}",
+                   "form": "batched (one persistent launch over all scenes), learned warm start (lambda0 = Q c0), "
+                           "cold fallback of every miss, stall stop (residual > 1 m and not halved over two "
+                           "checks)", "scenes_per_gpu": S, "goals_per_scene": B, "obstacles": m,
+                   "samples": N, "coefficients": n, "max_iters": int(p["iters"]), "tol_m": TOL,
+                   "check_every": CHECK_EVERY, "stall_stop": list(STALL),
+                   "train_scenes": cfg.train_scenes, "train_rows": train_rows, "train_steps": cfg.steps,
+                   "network": list(cfg.widths), "graph": "one CUDA graph replay per step",
+                   "l2": "inputs larger than L2: each step reads 4096 scenes and writes 1M trajectories' "
+                         "outputs (>150 MB)"},
         "roofline": {"bound": "alu", "kernel": "am_solve_batch_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": None,
-                     "ops_basis": "dense algorithmic ops of every AM pass run (warm passes + cold passes of the "
-                                  "fallback), over the whole graph step",
-                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz"},
-        "e2e": None,
-        "gpu_launches": 12 * args.steps,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum), "
+                                     "null when not measured for this kernel source",
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz",
+                     "ops_basis": "per trajectory-iteration 14 N n + 7 n^2 (basis and QP products) + 10 m N "
+                                  "(obstacle projections) + 60 N (element-wise), over every AM pass the two "
+                                  "launches of a step ran (warm solve, cold fallback)",
+                     "ops_per_launch": ops / 2, "launch_ms": launch_ms, "launches_per_step": 2,
+                     "solve_launch_ms": solve_ms, "fallback_launch_ms": fb_ms,
+                     "evaluated_pairs_per_step": elements, "dense_pairs_per_step": passes * N * m,
+                     "executed_ops_per_launch": exec_ops / 2,
+                     "executed_frac": exec_ops / 2 / (launch_ms * 1e-3) / 1e12 / peak},
+        "e2e": {"value": agg["e2e_units"] / (agg["e2e_ms"] * 1e-3), "unit": UNIT_CONV,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": agg["e2e_ms"], "steps": Ke,
+                "trajectories_per_s": tagg["e2e_units"] / (tagg["e2e_ms"] * 1e-3),
+                "api": "inputs copied from pinned host memory, the step's CUDA graph (features, network, decode, "
+                       "mmpc_batch_run) replayed, all outputs copied back, stream synchronised"},
+        "gpu_launches": 14 * K,
         "clocks": clocks,
-        "detail": {"dense_50_obstacles": dense, "dense_50_obstacles_stall_stop": dense_stall,
-                   "sparse_10_obstacles": sparse, "val_loss": val,
-                   "network_forward": fwd,
-                   "loss_first_last": [losses[0][1], losses[-1][1]], "dataset_s": t1 - t0, "train_s": t2 - t1},
+        "detail": {"converged_per_step": converged, "converged_in_timed_steps": conv_now,
+                   "trajectories_per_step": S * B, "trajectories_per_s": tagg["units"] / (tagg["ms"] * 1e-3),
+                   "mpc_solves_per_s": S * world / (agg["ms"] * 1e-3),
+                   "plain_converged_per_s": plain["converged_per_s"],
+                   "ratio_vs_plain": ev[HEADLINE]["converged_per_s"] / plain["converged_per_s"],
+                   "ratio_vs_batched_cold": ev[HEADLINE]["converged_per_s"] / dense["cold"]["converged_per_s"],
+                   "ratio_vs_batched_cold_stall": ev[HEADLINE]["converged_per_s"] / ev["cold"]["converged_per_s"],
+                   "variants_no_stall": dense, "variants_stall_stop": ev, "sparse_10_obstacles": sparse,
+                   "scene_1024_goals_plain_cold": scene, "val_loss": val, "network_forward": fwd,
+                   "loss_first_last": [losses[0][1], losses[-1][1]], "dataset_s": t1 - t0, "train_s": t2 - t1,
+                   "wall_s": wall, "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)},
     }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    keep["warm"].close()
+    keep["cold"].close()
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+def _scene_throughput(dev, target_s=0.5):
+    """Plain cold-started solve + score of the 1024-goal, 50-obstacle scene
+    (N = 100, n = 12, 100 iterations, residual target 1e-2 m), CUDA events
+    between L2 flushes, about target_s of steps."""
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc
+    sc, params = workload(seed=0, kind="scene")
+    B, m, n = len(sc.goals), sc.obst.shape[0], params["n"]
+    solver = mmpc.Solver(params, m)
+    meta = mmpc.make_meta(**sc.meta)
+    f32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).contiguous()  # noqa: E731
+    ego, obst, goals = f32(sc.ego), f32(sc.obst), f32(sc.goals)
+    coef = torch.empty((B, 3 * n), device=dev)
+    resid = torch.empty((B, 4), device=dev)
+    iters = torch.empty((B,), dtype=torch.int32, device=dev)
+    cost = torch.empty((B,), device=dev)
+    am = torch.empty((1,), dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    for i in range(5 + int(target_s / 4e-4)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mmpc.mmpc_solve(solver.ctx, ego, obst, goals, coef, None, None, None, resid, iters, stream)
+        mmpc.mmpc_score(solver.ctx, meta, coef, cost, am, stream)
+        b.record(stream)
+        if i >= 5:
+            ms.append((a, b))
+    torch.cuda.synchronize(dev)
+    solver.status()
+    t = [a.elapsed_time(b) for a, b in ms]
+    conv = int((resid[:, :3].max(dim=1).values <= TOL).sum().item())
+    solver.close()
+    avg = sum(t) / len(t)
+    return dict(workload=workload_name(params, B, m), steps=len(t), ms_per_step=avg, trajectories_per_s=B / (avg * 1e-3),
+                converged=conv, converged_per_s=conv / (avg * 1e-3))
 
 
 def _oracle_run(sc, params, idx, threads):
@@ -627,10 +819,92 @@ def cpu_baseline(sc, params, sample_stride=4, single_sample=16):
                               "sample": f"the first {min(single_sample, len(idx))} goals of that sample"}}
 
 
+def _warm_eval_scenes(params, S, B, m, x_range, seed):
+    """The evaluation scenes of the warm workload as the GPU receives them
+    (the same seeded stack, rounded to float32), scene-major."""
+    from paper_2109_10392_gb300 import scenes
+    ego, obst, goals = scenes.scene_stack(seed, S, B, m, x_range, goals="grid" if B % 8 == 0 else "random")
+    f = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)  # noqa: E731
+    return f(ego), f(obst), f(goals)
+
+
+def _oracle_scenes(params, ego, obst, goals, idx, threads):
+    """The FP64 oracle, cold start, on scenes idx (all goals of each, OpenMP
+    over goals); returns (seconds, trajectories, converged)."""
+    import oracle
+    p = oracle.params(**dict(params, tol=TOL, check_every=CHECK_EVERY))
+    t0 = time.perf_counter()
+    units = conv = 0
+    for i in idx:
+        r = oracle.solve(p, ego[i], obst[i], goals[i], nthreads=threads)
+        units += goals.shape[1]
+        conv += int((r["resid"][:, :3].max(axis=1) <= TOL).sum())
+    return time.perf_counter() - t0, units, conv
+
+
+def cpu_baseline_warm(params, S, B, m, x_range, seed, budget_s=15.0):
+    """The FP64 oracle as it stands (the plain cold-started method) on the
+    host cores, on the first evaluation scenes of the warm workload, as many
+    as fit in about budget_s; converged trajectories per second."""
+    threads = os.cpu_count() or 1
+    ego, obst, goals = _warm_eval_scenes(params, S, B, m, x_range, seed)
+    dt1, _, _ = _oracle_scenes(params, ego, obst, goals, [0], threads)
+    k = int(max(1, min(S, budget_s / max(dt1, 1e-3))))
+    dt, units, conv = _oracle_scenes(params, ego, obst, goals, range(k), threads)
+    return {"value": conv / dt, "unit": UNIT_CONV, "cores": threads, "kind": "oracle",
+            "sample": f"the first {k} of the {S} evaluation scenes, all {B} goals each ({units} trajectories), "
+                      "cold start, same stopping rule", "trajectories_per_s": units / dt, "converged": conv,
+            "seconds": dt}
+
+
 def run_reference(args):
     rank, world, _ = rank_env()
     if rank != 0:
         return None
+    threads = os.cpu_count() or 1
+    if args.workload != "warm":
+        return run_reference_scene(args)
+    from paper_2109_10392_gb300 import warmstart
+    cfg = warmstart.WarmConfig(seed=0)
+    p = cfg.params
+    S, B, m = args.warm_eval_scenes, 256, cfg.obstacles
+    ego, obst, goals = _warm_eval_scenes(p, S, B, m, cfg.x_range, 10**6)
+    # size one step so that warmup + steps take about a minute in total
+    dt1, _, _ = _oracle_scenes(p, ego, obst, goals, [0], threads)
+    per_step = 60.0 / max(1, args.steps + args.warmup)
+    k = int(max(1, min(S // max(1, args.steps + args.warmup), per_step / max(dt1, 1e-3))))
+    pos = 1
+    for _ in range(args.warmup):
+        _oracle_scenes(p, ego, obst, goals, range(pos, pos + k), threads)
+        pos += k
+    units = conv = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        dt, u, c = _oracle_scenes(p, ego, obst, goals, range(pos, pos + k), threads)
+        pos += k
+        units += u
+        conv += c
+        secs += dt
+    value = conv / secs
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT_CONV, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"highway_warm_S{S}_B{B}_m{m}_N{p['N']}_n{p['n']}_K{p['iters']}_tol{TOL:g}",
+                   "form": "the FP64 oracle (plain method, cold start) on consecutive evaluation scenes",
+                   "scenes_per_step": k, "trajectories_per_step": k * B},
+        "cpu_baseline": {"value": value, "unit": UNIT_CONV, "cores": threads, "kind": "oracle",
+                         "sample": f"{k} evaluation scenes x {B} goals per step, cold start, same stopping rule",
+                         "trajectories_per_s": units / secs, "converged": conv},
+        "e2e": {"value": value, "unit": UNIT_CONV, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def run_reference_scene(args):
+    """The oracle on a bounded sample of the 1024-goal scene per step (the
+    reference arm of the single-scene workloads)."""
     sc, params = workload(seed=0)
     threads = os.cpu_count() or 1
     # size one step so that warmup + steps take about a minute in total
@@ -651,7 +925,7 @@ def run_reference(args):
     value = units / secs
     return {
         "impl": "reference",
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(params, len(sc.goals), sc.obst.shape[0]),
@@ -763,7 +1037,7 @@ def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default per workload: scene 2000, precision 20, batch 100, warm 3; "
+                    help="timed steps (default per workload: warm 5, scene 2000, precision 20, batch 100; "
                          "--impl reference: 3); a warm step replays the whole 1M-trajectory evaluation")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
@@ -772,9 +1046,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-cull", action="store_true", help="evaluate every obstacle-sample pair (no culling)")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                     help="solve kernel: 1 one sample per thread, 2 two samples per thread, 0 automatic")
-    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "warm", "precision", "sweep"],
-                    help="scene: one 1024-goal scene per GPU; batch: 256 uneven scenes per GPU in one graph; "
-                         "warm: learned warm start (trained in the run) against the cold start; precision: "
+    ap.add_argument("--workload", default="warm", choices=["warm", "scene", "batch", "precision", "sweep"],
+                    help="warm (default, the metric): learned warm start (trained in the run), batched, with cold "
+                         "fallback and stall stop, against the plain cold-started method on 4096 fresh scenes x "
+                         "256 goals; scene: one 1024-goal scene per GPU; batch: 256 uneven scenes per GPU in one "
+                         "graph; precision: "
                          "one 16384-goal scene, 30 obstacles, N = 200, n = 16; sweep: trajectories/s against the "
                          "batch size (11 to 65536 goals) and one MPC cycle of the paper's 11-goal setting")
     ap.add_argument("--stall", action="store_true",
@@ -787,7 +1063,7 @@ def parse_args(argv=None):
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = (3 if args.impl == "reference" else
-                      {"precision": 20, "batch": 100, "warm": 3}.get(args.workload, 2000))
+                      {"precision": 20, "batch": 100, "warm": 5}.get(args.workload, 2000))
     if args.steps < 1:
         ap.error("--steps must be >= 1")
     if args.warmup < 3:

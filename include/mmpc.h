@@ -272,9 +272,25 @@ int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen);
  * (coef, lam, resid, iters) are those of the cold solve. */
 int mmpc_batch_run(mmpc_batch* b, void* stream);
 
-/* Fallback to the cold start (see mmpc_batch_run) on (on != 0) or off
- * (the default).  Needs resid_out of the warm-started scenes. */
+/* Fallback to the cold start (see mmpc_batch_run): mode 0 off (the
+ * default), 1 every warm-started trajectory that missed tol, 2 only the
+ * misses that ran the whole iteration budget -- a miss that the opt-in stall
+ * rule (mmpc_params.stall_tol / stall_ratio) stopped earlier is kept as it
+ * is, because its residual trace showed it far from the target and no longer
+ * closing in (mode 2 is not in the paper; without the stall rule it equals
+ * mode 1).  Needs resid_out (and, for mode 2, iters_out) of the warm-started
+ * scenes.  Other modes -> MMPC_ERR_INVALID_ARG. */
 int mmpc_batch_set_fallback(mmpc_batch* b, int on);
+
+/* Optional timing of the solve launches inside mmpc_batch_run: events[0..3]
+ * (cudaEvent_t, created by the caller with timing enabled) are recorded on
+ * the run's stream before and after the persistent solve launch(es) (with
+ * schedule 4: before the fork and after the join of the horizon-group
+ * streams) and before and after the fallback solve launch.  NULL turns
+ * timing off (the default).  The events are the caller's; set NULL before
+ * destroying them.  Recording inside a graph capture is not supported:
+ * turn timing off before capturing. */
+int mmpc_batch_set_timing(mmpc_batch* b, void* const* events);
 
 /* After a run (synchronises the device): the number of trajectories the
  * last run solved again from the cold start. */

@@ -1879,9 +1879,12 @@ __global__ void batch_reset_kernel(unsigned long long* scratch, int S, int G, in
 // NaN, goes to the fallback list, to be solved again from the cold start.
 // The list order depends on timing; each trajectory's solve does not.  Also
 // rewinds the work queue for the next persistent launch.
+// With budget_only set, a miss that the stall rule stopped before the
+// iteration budget (iters_out < iters) is not solved again: its residual
+// trace already showed it far from the target and no longer closing in.
 __global__ void fallback_compact_kernel(const SolveArgs* __restrict__ warm, const int2* __restrict__ items, int total,
                                         int2* __restrict__ fb_items, int* __restrict__ fb_count,
-                                        unsigned long long* scratch)
+                                        unsigned long long* scratch, int budget_only)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) scratch[0] = 0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -1891,7 +1894,9 @@ __global__ void fallback_compact_kernel(const SolveArgs* __restrict__ warm, cons
         const float* r = A.resid_out + (size_t)sl.y * 4;
         const float conv = fmaxf(fmaxf(r[0], r[1]), r[2]);
         const bool nan = isnan(r[0]) || isnan(r[1]) || isnan(r[2]);
-        if (nan || !(conv <= A.tol)) fb_items[atomicAdd(fb_count, 1)] = sl;
+        if (!nan && conv <= A.tol) continue;
+        if (budget_only && !nan && A.iters_out && A.iters_out[sl.y] < A.iters) continue;
+        fb_items[atomicAdd(fb_count, 1)] = sl;
     }
 }
 
@@ -2525,8 +2530,9 @@ struct mmpc_batch {
     int2* d_items = nullptr;
     int2* d_fb_items = nullptr;               // fallback list
     int* d_counts = nullptr;                  // [0] items, [1] fallback items, [2 + g] items of group g
-    bool fallback = false;
+    int fallback = 0;  // 0 off, 1 every miss, 2 misses that ran the whole budget
     bool any_warm = false;
+    cudaEvent_t timing[4] = {};  // optional: around the solve launch(es) and the fallback launch
     // horizon groups (schedule 4): scenes with the same pair-thread count,
     // one right-sized persistent launch each, on forked streams
     struct Group {
@@ -2798,6 +2804,7 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
     const int G = (int)b->groups.size();
     batch_reset_kernel<<<1, 256, 0, st>>>(b->d_scratch, b->S, G, b->d_counts + 1);
     if (b->total > 0) {
+        if (b->timing[0]) cudaEventRecord(b->timing[0], st);
         using KernT = void (*)(const SolveArgs*, const int2*, const int*, unsigned long long*, unsigned long long*);
         if (b->schedule == 4) {
             // one right-sized persistent launch per horizon group, on forked
@@ -2816,12 +2823,15 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
             reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args, b->d_items, b->d_counts,
                                                                                 b->d_scratch, b->d_scratch);
         }
+        if (b->timing[1]) cudaEventRecord(b->timing[1], st);
         if (b->fallback && b->any_warm) {
             fallback_compact_kernel<<<std::min(1024, (b->total + 255) / 256), 256, 0, st>>>(
-                b->d_args, b->d_items, b->total, b->d_fb_items, b->d_counts + 1, b->d_scratch);
+                b->d_args, b->d_items, b->total, b->d_fb_items, b->d_counts + 1, b->d_scratch, b->fallback == 2);
+            if (b->timing[2]) cudaEventRecord(b->timing[2], st);
             reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args_cold, b->d_fb_items,
                                                                                 b->d_counts + 1, b->d_scratch,
                                                                                 b->d_scratch);
+            if (b->timing[3]) cudaEventRecord(b->timing[3], st);
         }
         const int wpb = 8;
         const int sgrid = (b->total + wpb - 1) / wpb;
@@ -2887,7 +2897,15 @@ extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
 extern "C" int mmpc_batch_set_fallback(mmpc_batch* b, int on)
 {
     if (!b) return batch_fail("mmpc_batch_set_fallback: NULL batch", MMPC_ERR_NOT_SETUP);
-    b->fallback = on != 0;
+    if (on < 0 || on > 2) return batch_fail("mmpc_batch_set_fallback: mode must be 0, 1 or 2", MMPC_ERR_INVALID_ARG);
+    b->fallback = on;
+    return MMPC_OK;
+}
+
+extern "C" int mmpc_batch_set_timing(mmpc_batch* b, void* const* events)
+{
+    if (!b) return batch_fail("mmpc_batch_set_timing: NULL batch", MMPC_ERR_NOT_SETUP);
+    for (int i = 0; i < 4; ++i) b->timing[i] = events ? reinterpret_cast<cudaEvent_t>(events[i]) : nullptr;
     return MMPC_OK;
 }
 

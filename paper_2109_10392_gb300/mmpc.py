@@ -31,7 +31,7 @@ MMPC_META_ABS = 2
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
             "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
             "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
-            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_fallbacks", "mmpc_step_host",
+            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_set_timing", "mmpc_batch_fallbacks", "mmpc_step_host",
             "mmpc_measure_peaks", "mmpc_status", "mmpc_batch_status", "mmpc_debug_expire_wait")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
@@ -152,6 +152,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_step_host.restype = ctypes.c_int
     L.mmpc_batch_set_fallback.argtypes = [vp, ctypes.c_int]
     L.mmpc_batch_set_fallback.restype = ctypes.c_int
+    L.mmpc_batch_set_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
+    L.mmpc_batch_set_timing.restype = ctypes.c_int
     L.mmpc_batch_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.mmpc_batch_fallbacks.restype = ctypes.c_int
     L.mmpc_measure_peaks.argtypes = [ctypes.POINTER(MmpcPeaks), ctypes.c_int, vp]
@@ -574,8 +576,25 @@ class Batch:
         out.S = S
         return out
 
-    def set_fallback(self, on: bool) -> None:
-        rc = lib().mmpc_batch_set_fallback(self.handle, 1 if on else 0)
+    def set_fallback(self, on) -> None:
+        """False / 0: off; True / 1: every warm-started miss; 2: only the misses
+        that ran the whole iteration budget (not stopped by the stall rule)."""
+        mode = int(on) if not isinstance(on, bool) else (1 if on else 0)
+        rc = lib().mmpc_batch_set_fallback(self.handle, mode)
+        if rc != MMPC_OK:
+            _err(None, rc)
+
+    def set_timing(self, events) -> None:
+        """Four torch.cuda.Event(enable_timing=True) recorded around the solve
+        launch(es) and the fallback launch of every run, or None (off)."""
+        if events is None:
+            rc = lib().mmpc_batch_set_timing(self.handle, None)
+        else:
+            if len(events) != 4:
+                raise ValueError("set_timing needs four events")
+            arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+            self._timing_events = events  # kept alive while the library holds them
+            rc = lib().mmpc_batch_set_timing(self.handle, arr)
         if rc != MMPC_OK:
             _err(None, rc)
 

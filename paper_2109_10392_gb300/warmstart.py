@@ -232,10 +232,15 @@ def validation_loss(ws: WarmStart, X, T):
 
 def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256, seed: int = 10**6,
              reps: int = 3, tol: float = 1e-2, obstacles=None, x_range=None, plain: bool = False,
-             stall: tuple | None = None):
+             stall: tuple | None = None, keep: bool = False):
     """Cold start against warm start (+ cold fallback) on S fresh scenes x B
     goals, each timed as one CUDA graph replay (warm: features, network,
-    decode, solve, fallback solve, score).  Returns a dict of results."""
+    decode, solve, fallback solve, score).  Returns a dict of results.  With
+    the stall stop, a fourth variant falls back only the misses that ran the
+    whole budget (`warm_fallback_budget`, mmpc_batch_set_fallback mode 2).
+    With keep, out["_keep"] holds the warm-started batch, its step function,
+    the graphs per variant and the inputs, for the caller to time further and
+    close."""
     import torch
     m = cfg.obstacles if obstacles is None else obstacles
     xr = cfg.x_range if x_range is None else x_range
@@ -322,6 +327,17 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
     warm_iters = warm.flat["iters"].clone()
     out["warm"]["misses"] = int((~warm_conv).sum().item())
     del g_w
+    g_fb2 = None
+    if stall is not None:
+        # only the misses that ran the whole budget go to the cold fallback
+        warm.set_fallback(2)
+        g_fb2, ms = timed(warm_step)
+        stats(warm, ms, "warm_fallback_budget")
+        out["warm_fallback_budget"]["fallbacks"] = warm.fallbacks()
+        budget_miss = (~warm_conv) & (warm_iters == int(pb["iters"]))
+        out["warm_fallback_budget"]["budget_misses"] = int(budget_miss.sum().item())
+        out["warm_fallback_budget"]["passes"] = int((warm_iters.to(torch.int64) + 1).sum().item() +
+                                                    (cold.flat["iters"].to(torch.int64) + 1)[budget_miss].sum().item())
     warm.set_fallback(True)
     g_f, ms = timed(warm_step)
     stats(warm, ms, "warm_fallback")
@@ -353,7 +369,12 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
         out["batched_warm_vs_plain"] = out["warm"]["trajectories_per_s"] / out["plain"]["trajectories_per_s"]
     if out["cold"]["converged"] > 0:
         out["speedup_converged_per_s"] = out["warm_fallback"]["converged_per_s"] / out["cold"]["converged_per_s"]
-    del g_cold, g_f
+    if keep:
+        out["_keep"] = dict(warm=warm, cold=cold, step=warm_step, stream=stream, table=table, buf=buf,
+                            graphs=dict(cold=g_cold, warm_fallback=g_f, warm_fallback_budget=g_fb2),
+                            inputs=dict(ego=ego, obst=obst, goals=goals))
+        return out
+    del g_cold, g_f, g_fb2
     cold.close()
     warm.close()
     return out

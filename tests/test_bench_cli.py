@@ -7,18 +7,20 @@ import pytest
 
 def test_default_steps_per_workload():
     import bench
-    assert bench.parse_args([]).steps == 2000
+    assert bench.parse_args([]).workload == "warm"
+    assert bench.parse_args([]).steps == 5
+    assert bench.parse_args(["--workload", "scene"]).steps == 2000
     assert bench.parse_args(["--workload", "precision"]).steps == 20
     assert bench.parse_args(["--workload", "batch"]).steps == 100
-    assert bench.parse_args(["--workload", "warm"]).steps == 3
+    assert bench.parse_args(["--workload", "warm"]).steps == 5
     assert bench.parse_args(["--workload", "sweep"]).steps == 2000
     assert bench.parse_args(["--impl", "reference"]).steps == 3
 
 
 def test_explicit_values_and_limits():
     import bench
-    a = bench.parse_args(["--workload", "warm", "--steps", "5", "--warmup", "4"])
-    assert (a.steps, a.warmup) == (5, 4)
+    a = bench.parse_args(["--workload", "warm", "--steps", "7", "--warmup", "4"])
+    assert (a.steps, a.warmup) == (7, 4)
     for bad in (["--warmup", "2"], ["--steps", "0"]):
         with pytest.raises(SystemExit):
             bench.parse_args(bad)

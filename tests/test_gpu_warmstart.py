@@ -30,3 +30,22 @@ def test_warm_start_gains_over_cold_start():
     assert r["converged_both"] > 1000, r
     it = r["iters_both_converged"]
     assert it["warm"] < 0.85 * it["cold"], r
+
+
+def test_budget_only_fallback_with_stall_stop():
+    """Fallback mode 2 (not in the paper): with the stall stop on, only the
+    warm-started misses that ran the whole iteration budget are solved again
+    from the cold start; the stalled ones keep their warm-started result."""
+    import torch
+    dev = torch.device("cuda:0")
+    cfg = warmstart.WarmConfig(train_scenes=20000, goals_per_scene=8, obstacles=50, steps=800, batch=4096, seed=4)
+    X, T = warmstart.build_dataset(cfg, dev)
+    ws, _ = warmstart.train(cfg, X, T, dev, log_every=400)
+    r = warmstart.evaluate(ws, cfg, dev, S=64, B=128, reps=1, stall=(1.0, 0.5))
+    ws.close()
+    fb2, fb1 = r["warm_fallback_budget"], r["warm_fallback"]
+    assert fb2["fallbacks"] == fb2["budget_misses"]
+    assert fb1["fallbacks"] == r["warm"]["misses"]
+    assert fb2["fallbacks"] <= fb1["fallbacks"]
+    assert r["warm"]["converged"] <= fb2["converged"] <= fb1["converged"]
+    assert fb2["passes"] <= fb1["passes"]
