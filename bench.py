@@ -636,6 +636,9 @@ def run_warm(args):
     p = cfg.params
     N, n, m = int(p["N"]), int(p["n"]), cfg.obstacles
     tev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in tev:  # torch creates the CUDA event at its first record
+        e.record(stream)
+    torch.cuda.synchronize(dev)
     warm.set_fallback(1)
     warm.set_timing(tev)
     warm.take_work_count()

@@ -592,6 +592,8 @@ class Batch:
         else:
             if len(events) != 4:
                 raise ValueError("set_timing needs four events")
+            if any(not e.cuda_event for e in events):
+                raise ValueError("set_timing: record each event once before passing it (torch creates it lazily)")
             arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
             self._timing_events = events  # kept alive while the library holds them
             rc = lib().mmpc_batch_set_timing(self.handle, arr)
