@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libmmpc.so")
 SOURCES = ["mmpc_solve.cu", "mmpc_build.cpp", "mmpc_mlp.cu", "mmpc_peaks.cu"]
-HEADERS = ["mmpc_internal.h", os.path.join("..", "..", "include", "mmpc.h"),
+HEADERS = ["mmpc_internal.h", "mmpc_tc.cuh", os.path.join("..", "..", "include", "mmpc.h"),
            os.path.join("..", "..", "include", "mmpc_mlp.h"), os.path.join("..", "..", "include", "mmpc_peaks.h")]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -149,12 +149,16 @@ std::string check_params(const mmpc_params* p)
     if (p->iters < 0) return "iters must be >= 0";
     if (p->check_every < 1) return "check_every must be >= 1";
     if (std::isnan(p->tol)) return "tol is NaN";
-    if (p->variant < 0 || p->variant > 2) return "variant must be 0, 1 or 2";
+    if (p->variant < 0 || p->variant > 3) return "variant must be 0, 1, 2 or 3";
     if (std::isnan(p->stall_tol)) return "stall_tol is NaN";
     if (p->stall_tol > 0.f && !(p->stall_ratio > 0.f && p->stall_ratio <= 1.f)) return "stall_ratio must be in (0, 1]";
     if (p->precision < MMPC_PREC_FP32 || p->precision > MMPC_PREC_BF16_SPLIT) return "unknown precision";
-    if (p->precision != MMPC_PREC_FP32 && (p->N < 129 || p->N > 256 || p->n < 13 || p->variant == 1))
+    if (p->variant == 3) {
+        if (p->precision == MMPC_PREC_FP32) return "variant 3 (tensor cores) needs a TF32 or BF16 precision";
+        if (p->N > 256) return "variant 3 needs N <= 256";
+    } else if (p->precision != MMPC_PREC_FP32 && (p->N < 129 || p->N > 256 || p->n < 13 || p->variant == 1)) {
         return "precision variants need N in 129..256, n in 13..16 and the pair kernel";
+    }
     if (p->variant == 1 && p->N > 256) return "variant 1 needs N <= 256";
     return "";
 }

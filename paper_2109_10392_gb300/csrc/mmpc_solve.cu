@@ -33,6 +33,7 @@
 //    obstacles in that moving frame; velocity rows add v0 back.  This keeps
 //    the carried coefficients small; outputs are in the road frame.
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <functional>
@@ -1727,6 +1728,8 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
     if (lane == 0 && A.work) atomicAdd(A.work, work);
 }
 
+#include "mmpc_tc.cuh"
+
 // ---------------------------------------------------------------------------
 // Meta cost (Sec. III-F) and batch argmin.  One warp per trajectory, lanes
 // over samples; the argmin is a packed 64-bit atomicMin of (cost bits << 32 |
@@ -1921,6 +1924,8 @@ struct mmpc_ctx {
     int sm_count = -1;                        // SMs of the device (queried on the first solve)
     int last_variant = 0;
     int debug_missing = 0;  // mmpc_debug_expire_wait: bytes the staging wait expects beyond the copy
+    mmpc::TcLayout tc{};             // variant 3: layout of the tensor-core operand blob
+    unsigned char* d_tc = nullptr;   // variant 3: the blob (device)
     std::string err = "no error";
     // device buffers of mmpc_step_host, grown on demand: inputs (ego, obstacles,
     // goals) and outputs (coef, resid, iters, cost, argmin) for up to host_cap goals
@@ -1953,6 +1958,55 @@ int launch_kernel(mmpc_ctx* ctx, K kern, const SolveArgs& a, int threads, size_t
     kern<<<a.B, threads, smem, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve launch");
+    return MMPC_OK;
+}
+
+// Variant 3, the tensor-core kernel: tiles of TT = min(128, ceil(B / SMs))
+// trajectories, one CTA (384 threads, all 512 tensor-memory columns) per tile.
+template <int NC>
+void* tc_kernel(int prec)
+{
+    switch (prec) {
+    case MMPC_PREC_TF32: return (void*)am_solve_tc_kernel<NC, MMPC_PREC_TF32>;
+    case MMPC_PREC_TF32_SPLIT: return (void*)am_solve_tc_kernel<NC, MMPC_PREC_TF32_SPLIT>;
+    case MMPC_PREC_BF16: return (void*)am_solve_tc_kernel<NC, MMPC_PREC_BF16>;
+    default: return (void*)am_solve_tc_kernel<NC, MMPC_PREC_BF16_SPLIT>;
+    }
+}
+
+size_t tc_smem(const mmpc_ctx* ctx, int m)
+{
+    const int nmat = ctx->L.init - ctx->L.Q;
+    return (size_t)ctx->tc.bytes + sizeof(float) * (size_t)((nmat + 3) & ~3) + 16 * (size_t)m +
+           sizeof(int) * (size_t)(TC_THREADS / 32) * m + sizeof(float) * 3 * 128 * 4;
+}
+
+int launch_tc(mmpc_ctx* ctx, const SolveArgs& a, int B, cudaStream_t st)
+{
+    if (ctx->sm_count < 0) {
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "device query");
+        ctx->sm_count = sms;
+    }
+    TcArgs T{};
+    T.blob = ctx->d_tc;
+    T.L = ctx->tc;
+    T.TT = std::min(128, std::max(1, (B + ctx->sm_count - 1) / ctx->sm_count));
+    // at least 116 KB, so that one CTA holds an SM (it allocates all of the
+    // SM's tensor memory; a second CTA would only wait in tcgen05.alloc)
+    const size_t smem = std::max<size_t>(tc_smem(ctx, a.m), 116 * 1024);
+    if (smem > 227 * 1024) return fail(ctx, MMPC_ERR_SHAPE, "scene does not fit in shared memory");
+    using K = void (*)(const SolveArgs, const TcArgs);
+    K kern = reinterpret_cast<K>(ctx->NC == 12 ? tc_kernel<12>(ctx->p.precision) : tc_kernel<16>(ctx->p.precision));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    const int grid = (B + T.TT - 1) / T.TT;
+    kern<<<grid, TC_THREADS, smem, st>>>(a, T);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core solve launch");
+    ctx->last_variant = 3;
     return MMPC_OK;
 }
 
@@ -2031,6 +2085,7 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
     for (size_t i = 0; i < PL.total; ++i)
         if (!std::isfinite(buf[i])) return fail(nullptr, MMPC_ERR_INVALID_ARG, "problem buffer holds a non-finite value");
 
+    if (p->variant == 3 && m > TC_MAX_M) return fail(nullptr, MMPC_ERR_SHAPE, "variant 3 takes at most 128 obstacles");
     const int NC = n <= 12 ? 12 : 16;
     const int prec = p->precision;
     const BlobLayout L = blob_layout(N, NC, prec_split(prec));
@@ -2088,12 +2143,49 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
     mat(PL.C0y, L.C0y, n, MMPC_NEQ_Y, 8, false);
     mat(PL.C0p, L.C0p, n, MMPC_NEQ_PSI, 4, false);
 
+    // variant 3: the basis blocks as the tensor cores' B operands (layouts at
+    // TcLayout), rounded to the precision's type, hi and (split) lo
+    std::vector<unsigned char> htc;
+    TcLayout TL{};
+    if (p->variant == 3) {
+        const bool bf = prec == MMPC_PREC_BF16 || prec == MMPC_PREC_BF16_SPLIT;
+        const int esz = bf ? 2 : 4, per = 16 / esz;
+        TL = tc_layout(N, esz, prec_split(prec) ? 2 : 1);
+        htc.assign(TL.bytes, 0);
+        const size_t src[3] = {PL.P, PL.Pd, PL.Pdd};
+        auto put = [&](int off, float v) {
+            if (bf) {
+                unsigned u;
+                memcpy(&u, &v, 4);
+                const uint16_t hbits = (uint16_t)(u >> 16);  // v is already rounded to BF16
+                memcpy(&htc[off], &hbits, 2);
+            } else {
+                memcpy(&htc[off], &v, 4);
+            }
+        };
+        for (int b = 0; b < 3; ++b)
+            for (int smp = 0; smp < N; ++smp)
+                for (int k = 0; k < n; ++k) {
+                    const double v = buf[src[b] + (size_t)smp * n + k];
+                    const float hi = round_operand((float)v, prec);
+                    const float lo = round_operand((float)(v - (double)hi), prec);
+                    for (int part = 0; part < TL.parts; ++part) {
+                        const float x = part == 0 ? hi : lo;
+                        put(TL.eb[b][part] + (k / per) * TL.NSP * 16 + 16 * smp + (k % per) * esz, x);
+                        put(TL.cb[b][part] + (smp / per) * 256 + 16 * k + (smp % per) * esz, x);
+                    }
+                }
+    }
+
     mmpc_ctx* ctx = new mmpc_ctx();
     ctx->p = *p;
     ctx->m = m;
     ctx->NC = NC;
     ctx->L = L;
+    ctx->tc = TL;
     cudaError_t e = cudaMalloc(&ctx->d_blob, sizeof(float) * L.total);
+    if (e == cudaSuccess && !htc.empty()) e = cudaMalloc(&ctx->d_tc, htc.size());
+    if (e == cudaSuccess && !htc.empty()) e = cudaMemcpy(ctx->d_tc, htc.data(), htc.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, 3 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_blob, h.data(), sizeof(float) * L.total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -2104,6 +2196,7 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
         std::string msg = std::string("mmpc_setup: ") + cudaGetErrorString(e);
         cudaFree(ctx->d_blob);
         cudaFree(ctx->d_scratch);
+        cudaFree(ctx->d_tc);
         delete ctx;
         return fail(nullptr, MMPC_ERR_CUDA, msg);
     }
@@ -2153,7 +2246,8 @@ extern "C" int mmpc_solve(mmpc_ctx* ctx, const float* ego, const float* obst, in
             if (B <= ctx->sm_count) variant = 1;
         }
     }
-    if (p.precision != MMPC_PREC_FP32) variant = 2;  // the precision modes exist in the pair kernel only
+    if (variant == 3) return launch_tc(ctx, a, B, reinterpret_cast<cudaStream_t>(stream));
+    if (p.precision != MMPC_PREC_FP32) variant = 2;  // the emulated precision modes exist in the pair kernel only
     LaunchShape sh = shape_for(ctx, variant, m);
     if (p.precision != MMPC_PREC_FP32) {  // NC = 16, 128 threads (checked at setup)
         using K = void (*)(const SolveArgs);
@@ -2317,6 +2411,7 @@ extern "C" void mmpc_destroy(mmpc_ctx* ctx)
     cudaDeviceSynchronize();
     cudaFree(ctx->d_blob);
     cudaFree(ctx->d_scratch);
+    cudaFree(ctx->d_tc);
     cudaFree(ctx->h_in);
     cudaFree(ctx->h_out);
     delete ctx;

@@ -1,0 +1,843 @@
+// Trajectory-tiled tensor-core form of Algorithm 1 (Sec. III-E) for large
+// batches: the shared-matrix products -- the evaluations P c of x, y, psi and
+// their derivatives (Eq. param) and the contractions P^T e of Eqs.
+// lin_solve_xy_2 / lin_solve_psi_2 -- run as tcgen05.mma on the tensor
+// cores, in TF32 (kind::tf32) or BF16 (kind::f16) with FP32 accumulation in
+// tensor memory, optionally as hi + lo splits; the projections of Eqs.
+// split_v, split_alpha_o, split_alpha_a, the QP increments (K11 as FP32
+// hi + lo) and the multipliers stay FP32 on the CUDA cores.
+//
+// One CTA holds a tile of up to 128 trajectories of one scene: tensor-memory
+// lane t is trajectory slot t for every matrix.
+//  * Evaluation, per chunk of 16 samples and channel (x, y, psi, xdot, ydot,
+//    xddot, yddot): D[t][s] = sum_k C[t][k] B[k][s], M = 128 trajectories,
+//    N = 16 samples, K = 16 coefficients; A = the coefficient rows C in
+//    tensor memory (written by the thread that owns the trajectory's axis),
+//    B = the basis block (P, Pdot or Pddot) from shared memory.
+//  * Contraction: D[t][k] += sum_s E[t][s] B[s][k], N = 16 coefficients,
+//    K = the chunk's samples; A = the residual rows E written in place over
+//    the evaluated chunk in tensor memory, B = the transposed basis block.
+//    The three blocks of F^T (F c - g) per axis (obstacles with P,
+//    non-holonomic with Pdot, acceleration with Pddot) accumulate into one
+//    16-column accumulator, so no reduction over samples runs on the CUDA
+//    cores.
+// Threads: three groups of four warps; group g owns axis g (x, y, psi) for the
+// QP steps and processes the chunks c with c % 3 == g, one thread per
+// trajectory (warp 4 g + q serves lanes 32 q .. 32 q + 31, the tensor-memory
+// sub-partition it may access).  Per round of three chunks one thread issues
+// the evaluation MMAs and commits them to an mbarrier; the groups read their
+// chunk (tcgen05.ld), project every sample on the CUDA cores and write the
+// residuals back (tcgen05.st); after a CTA barrier the same thread issues
+// the contraction MMAs.  tcgen05.mma from one thread execute in issue order,
+// so the next round's evaluations never overwrite residuals not yet read.
+//
+// Tensor memory (512 columns, 32-bit): [0, 64) the contraction accumulators
+// (x, y, psi - theta, theta), [64, 160) the coefficient operands (axis x, y,
+// psi; hi, lo), [160, 496) three chunk buffers of 7 channels x 16 samples.
+
+// Precision of the tensor-core operands (MMPC_PREC_*): element size and the
+// K extent of one MMA (32 bytes of K).
+template <int PREC>
+struct TcType {
+    static constexpr bool BF16 = PREC == MMPC_PREC_BF16 || PREC == MMPC_PREC_BF16_SPLIT;
+    static constexpr bool SPLIT = PREC == MMPC_PREC_TF32_SPLIT || PREC == MMPC_PREC_BF16_SPLIT;
+    static constexpr int ESZ = BF16 ? 2 : 4;       // bytes per element
+    static constexpr int PER = 16 / ESZ;            // elements per 16-byte core row
+    static constexpr int KMMA = 2 * PER;            // K of one MMA (two core-row groups)
+    static constexpr int KSTEPS = 16 / KMMA;        // MMAs over the 16 coefficients
+    static constexpr int CSTEPS = 16 / KMMA;        // MMAs over a chunk of 16 samples
+    static constexpr int PARTS = SPLIT ? 2 : 1;     // hi (+ lo)
+    static constexpr int ACOLS = BF16 ? 8 : 16;     // tensor-memory columns of 16 coefficients
+    static constexpr uint32_t FMT = BF16 ? 1u : 2u; // instruction-descriptor operand format
+};
+
+constexpr int TC_THREADS = 384;
+constexpr int TC_GROUPS = 3;
+constexpr int TC_CS = 16;         // samples per chunk
+constexpr int TC_CH = 7;          // channels per chunk
+constexpr uint32_t TC_COLS = 512; // tensor-memory allocation
+constexpr uint32_t TC_DC = 0;     // contraction accumulators: x, y, psi - theta, theta (16 columns each)
+constexpr uint32_t TC_AC = 64;    // coefficient operands
+constexpr uint32_t TC_BUF = 160;  // chunk buffers
+constexpr int TC_MAX_M = 128;     // obstacles
+
+// Layout of the tensor-core constant blob (bytes): per basis block (P, Pdot,
+// Pddot) and part (hi, lo) the evaluation operand EB (16 coefficients x NSP
+// samples, K-major over the coefficients: element (k, s) at
+// (k / PER) NSP 16 + 16 s + (k % PER) ESZ) and the contraction operand CB
+// (NSP samples x 16 coefficients, K-major over the samples: element (s, k) at
+// (s / PER) 256 + 16 k + (s % PER) ESZ).  NSP = N rounded up to 16; rows of
+// samples >= N and of coefficients >= n are zero.
+struct TcLayout {
+    int NSP, esz, parts;
+    int eb[3][2], cb[3][2];
+    int bytes;
+};
+
+static TcLayout tc_layout(int N, int esz, int parts)
+{
+    TcLayout T{};
+    T.NSP = (N + TC_CS - 1) / TC_CS * TC_CS;
+    T.esz = esz;
+    T.parts = parts;
+    const int blk = T.NSP * 16 * esz;
+    int o = 0;
+    for (int b = 0; b < 3; ++b)
+        for (int p = 0; p < parts; ++p) {
+            T.eb[b][p] = o; o += blk;
+            T.cb[b][p] = o; o += blk;
+        }
+    for (int b = 0; b < 3; ++b)
+        for (int p = parts; p < 2; ++p) { T.eb[b][p] = T.eb[b][0]; T.cb[b][p] = T.cb[b][0]; }
+    T.bytes = o;
+    return T;
+}
+
+struct TcArgs {
+    const unsigned char* blob;  // device, tc_layout bytes
+    TcLayout L;
+    int TT;                     // trajectories per tile (<= 128)
+};
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    // shared-memory matrix descriptor: start, leading (K) and stride (8-row)
+    // byte offsets in 16-byte units, descriptor version 1, no swizzle
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// tcgen05.mma with A in tensor memory: D (+)= A B
+template <bool BF16>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    if (BF16)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+                     "r"(a), "l"(b), "r"(idesc), "r"(acc)
+                     : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+                     "r"(a), "l"(b), "r"(idesc), "r"(acc)
+                     : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 8 or 16 consecutive 32-bit columns (warp-collective).  The
+// wait is inside the same asm statement, so no use of the loaded registers
+// can be scheduled before the load has completed.
+__device__ __forceinline__ void tc_ld8(uint32_t addr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t addr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(addr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_st4(uint32_t addr, const uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_st8(uint32_t addr, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(addr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+// Round to TF32 (10-bit significand, to nearest, ties away from zero) -- the
+// operand the tensor core takes, so nothing is left to its own truncation.
+__device__ __forceinline__ uint32_t tf32_bits(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float lo_elem, float hi_elem)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ float bf16_val(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// Bounded wait on an mbarrier phase (device global timer, a poll count as a
+// backstop); false when it expired.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done = 0;
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < WAIT_MAX_POLLS && !done; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (!done && (it & 63) == 63 && global_ns() - t0 > WAIT_LIMIT_NS) break;
+    }
+    return done != 0;
+}
+
+// Instruction descriptor: D float32, A and B of the precision's format, both
+// K-major, N = 16, M = 128.
+template <int PREC>
+__device__ __forceinline__ uint32_t tc_idesc()
+{
+    return (1u << 4) | (TcType<PREC>::FMT << 7) | (TcType<PREC>::FMT << 10) | ((uint32_t)(16 >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
+// Channels of a chunk buffer: evaluated value (basis block, coefficient
+// axis), and, written in place, the residual whose contraction uses the same
+// block: 0 x (P, x) -> obstacle x; 1 y (P, y) -> obstacle y; 2 psi (P, psi)
+// -> psi - theta; 3 xdot (Pdot, x) -> non-holonomic x (theta in the heading
+// phase); 4 ydot (Pdot, y) -> non-holonomic y; 5 xddot (Pddot, x) ->
+// acceleration x; 6 yddot (Pddot, y) -> acceleration y.
+__device__ __forceinline__ int tc_ch_blk(int ch) { return ch < 3 ? 0 : (ch < 5 ? 1 : 2); }
+__device__ __forceinline__ int tc_ch_axis(int ch) { return ch < 3 ? ch : ((ch - 3) & 1); }
+// contraction target of a channel: accumulator 0 x, 1 y, 2 psi - theta (the axis)
+
+// Evaluation MMAs of one chunk (samples s0 .. s0 + 15) into buffer `buf`
+// for channels [ch0, ch1): D = C B with C = hi (+ lo) coefficient rows, B =
+// the block's hi (+ lo) rows; split products a b ~ a_hi b_hi + a_hi b_lo +
+// a_lo b_hi.
+template <int PREC>
+__device__ __forceinline__ void tc_issue_eval(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0, uint32_t buf,
+                                              int ch0, int ch1)
+{
+    using TY = TcType<PREC>;
+    const uint32_t idesc = tc_idesc<PREC>();
+    const uint32_t lbo = (uint32_t)(L.NSP * 16);
+    for (int ch = ch0; ch < ch1; ++ch) {
+        const int blk = tc_ch_blk(ch), ax = tc_ch_axis(ch);
+        const uint32_t d = tmem + buf + (uint32_t)(ch * TC_CS);
+        int first = 1;
+#pragma unroll
+        for (int ks = 0; ks < TY::KSTEPS; ++ks) {
+#pragma unroll
+            for (int pr = 0; pr < (TY::SPLIT ? 3 : 1); ++pr) {
+                const int pa = pr == 2 ? 1 : 0;  // coefficient part: hi, hi, lo
+                const int pb = pr == 1 ? 1 : 0;  // basis part: hi, lo, hi
+                const uint32_t a = tmem + TC_AC + (uint32_t)((2 * ax + pa) * TY::ACOLS + ks * 8);
+                const uint64_t b = tc_desc(sm_base + (uint32_t)L.eb[blk][pb] + (uint32_t)(s0 * 16) +
+                                               (uint32_t)(ks * 2) * lbo,
+                                           lbo, 128u);
+                tc_mma<TY::BF16>(d, a, b, idesc, first ? 0u : 1u);
+                first = 0;
+            }
+        }
+    }
+}
+
+// Contraction MMAs of one chunk: for channels [ch0, ch1) the residual rows E
+// (in place in buffer `buf`) times the transposed block, accumulated into
+// the channel's target (or into `dst_override` when >= 0); `fresh` marks the
+// targets not yet written in this phase (bit per target), cleared as they
+// are written.
+template <int PREC>
+__device__ __forceinline__ void tc_issue_contr(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0,
+                                               uint32_t buf, int ch0, int ch1, int dst_override, unsigned& fresh)
+{
+    using TY = TcType<PREC>;
+    const uint32_t idesc = tc_idesc<PREC>();
+    for (int ch = ch0; ch < ch1; ++ch) {
+        // theta (over the xdot channel, target 3) contracts with P (Eq. lin_solve_psi_2)
+        const int blk = dst_override == 3 ? 0 : tc_ch_blk(ch);
+        const int dst = dst_override >= 0 ? dst_override : tc_ch_axis(ch);
+        const uint32_t d = tmem + TC_DC + (uint32_t)(dst * 16);
+#pragma unroll
+        for (int ks = 0; ks < TY::CSTEPS; ++ks) {
+            const uint32_t a = tmem + buf + (uint32_t)(ch * TC_CS + ks * 8);
+#pragma unroll
+            for (int pb = 0; pb < TY::PARTS; ++pb) {
+                const uint64_t b = tc_desc(sm_base + (uint32_t)L.cb[blk][pb] +
+                                               (uint32_t)((s0 / TY::PER + 2 * ks) * 256),
+                                           256u, 128u);
+                const uint32_t acc = (fresh >> dst) & 1u ? 0u : 1u;
+                tc_mma<TY::BF16>(d, a, b, idesc, acc);
+                fresh &= ~(1u << dst);
+            }
+        }
+    }
+}
+
+// Culling list of one warp for one chunk, rebuilt every time (the exact test
+// of cull_update, with no growth of the box: the list holds every obstacle
+// not provably apart from the box of the warp's samples over the chunk's time
+// window, in increasing index order).
+__device__ __forceinline__ int tc_cull(int m, float xlo, float xhi, float ylo, float yhi, bool any_bad, float tw_lo,
+                                       float tw_hi, int* list, int lane, const float4* __restrict__ obs)
+{
+    const unsigned below = (1u << lane) - 1u;
+    int count = 0;
+    for (int j0 = 0; j0 < m; j0 += 32) {
+        const int j = j0 + lane;
+        bool keep = false;
+        if (j < m) {
+            const float4 o = obs[j];
+            const float e1 = -fmaf(o.z, tw_lo, o.x), e2 = -fmaf(o.z, tw_hi, o.x);
+            const float f1 = -fmaf(o.w, tw_lo, o.y), g1 = -fmaf(o.w, tw_hi, o.y);
+            const bool apart = (xlo - fmaxf(e1, e2) >= CULL_MARGIN) || (fminf(e1, e2) - xhi >= CULL_MARGIN) ||
+                               (ylo - fmaxf(f1, g1) >= CULL_MARGIN) || (fminf(f1, g1) - yhi >= CULL_MARGIN);
+            keep = any_bad || !apart;
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) list[count + __popc(bal & below)] = j;
+        count += __popc(bal);
+    }
+    __syncwarp();
+    return count;
+}
+
+// Residuals of one sample (Eqs. split_v, split_alpha_o, split_alpha_a in the
+// trigonometry-free forms of the pair kernel; x and the obstacles in the frame
+// moving with v0): e = (obstacle x, obstacle y, psi - theta, non-holonomic x,
+// y, acceleration x, y), and the squared residual norms.
+struct TcSample {
+    float x, y, ps, xd, yd, xdd, ydd;  // evaluated (x, xd relative to v0 t)
+};
+
+template <bool LIST>
+__device__ __forceinline__ void tc_residuals(const SolveArgs& A, const TcSample& v, float tt, float v0,
+                                             const float4* __restrict__ obs, const int* __restrict__ list, int cnt,
+                                             float (&e)[7], float (&r)[4])
+{
+    const float xd = v.xd + v0, yd = v.yd;
+    const float theta = atan2_own(yd, xd);
+    const float vel = fminf(fmaxf(sqrtf(fmaf(xd, xd, yd * yd)), A.v_min), A.v_max);
+    float sn, cs;
+    heading_sincos(v.ps, &sn, &cs);
+    const float evx = fmaf(-vel, cs, xd);
+    const float evy = fmaf(-vel, sn, yd);
+    const float an2 = fmaf(v.xdd, v.xdd, v.ydd * v.ydd);
+    const float fr = 1.f - fminf(1.f, A.a_max * rsqrtf(an2));
+    const float eax = v.xdd * fr, eay = v.ydd * fr;
+    const float Xn = v.x * A.inv_a, Yn = v.y * A.inv_b;
+    const float a2 = A.a * A.a, b2 = A.b * A.b;
+    float Sx, Sy, R2;
+    obstacle_sum1<true, LIST>(obs, list, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+    if (isnan(Sx) || isnan(Sy)) obstacle_sum1_exact(obs, A.m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+    const float dpsi = v.ps - theta;
+    e[0] = -A.a * Sx;
+    e[1] = -A.b * Sy;
+    e[2] = dpsi;
+    e[3] = evx;
+    e[4] = evy;
+    e[5] = eax;
+    e[6] = eay;
+    r[0] += R2;
+    r[1] += fmaf(eax, eax, eay * eay);
+    r[2] += fmaf(evx, evx, evy * evy);
+    r[3] += dpsi * dpsi;
+}
+
+// 8 values of one channel into tensor memory as the MMA's A operand: TF32
+// bits (8 columns) or BF16 pairs (4 columns).
+template <int PREC>
+__device__ __forceinline__ void tc_store8(uint32_t addr_tf32, uint32_t addr_bf16, const float (&v)[8])
+{
+    if (TcType<PREC>::BF16) {
+        uint32_t r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = bf16_pair(v[2 * j], v[2 * j + 1]);
+        tc_st4(addr_bf16, r);
+    } else {
+        uint32_t r[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) r[j] = tf32_bits(v[j]);
+        tc_st8(addr_tf32, r);
+    }
+}
+
+// The coefficient rows of one axis (hi and, split, lo) into tensor memory.
+template <int PREC>
+__device__ __forceinline__ void tc_write_coef(uint32_t lane_tmem, int axis, const float (&c)[16])
+{
+    using TY = TcType<PREC>;
+    const uint32_t base = lane_tmem + TC_AC + (uint32_t)(2 * axis * TY::ACOLS);
+    float hi[16], lo[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        hi[k] = TY::BF16 ? bf16_val(c[k]) : __uint_as_float(tf32_bits(c[k]));
+        lo[k] = c[k] - hi[k];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = hi[8 * h + j];
+        tc_store8<PREC>(base + 8 * h, base + 4 * h, v);
+    }
+    if (TY::SPLIT) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lo[8 * h + j];
+            tc_store8<PREC>(base + TY::ACOLS + 8 * h, base + TY::ACOLS + 4 * h, v);
+        }
+    }
+}
+
+// 16-wide dot product of a shared-memory row with a register vector; four
+// partial sums.
+template <int NC>
+__device__ __forceinline__ float tc_dot(const float* __restrict__ row, const float (&v)[16])
+{
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NC; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(row + j);
+        acc[0] = fmaf(x.x, v[j], acc[0]);
+        acc[1] = fmaf(x.y, v[j + 1], acc[1]);
+        acc[2] = fmaf(x.z, v[j + 2], acc[2]);
+        acc[3] = fmaf(x.w, v[j + 3], acc[3]);
+    }
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+__device__ __forceinline__ void tc_sync()
+{
+    tc_wait_st();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+template <int NC, int PREC>
+__global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid_constant__ SolveArgs A,
+                                                                    const __grid_constant__ TcArgs T)
+{
+    using TY = TcType<PREC>;
+    constexpr int KS = k_stride(NC);
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ __align__(8) unsigned long long s_stage;
+    __shared__ __align__(8) unsigned long long s_mma;
+    __shared__ uint32_t s_tmem;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = warp >> 2, q = warp & 3;  // axis group, tensor-memory sub-partition
+    const int t = 32 * q + lane;            // trajectory slot
+    const int l = blockIdx.x * T.TT + t;
+    const bool slot = t < T.TT && l < A.B;
+    const int N = A.N, m = A.m;
+    const BlobLayout& L = A.L;
+    const TcLayout& TL = T.L;
+
+    // shared memory: [tensor-core blob | Q, K11 x hi, lo, y hi, lo, K11_psi |
+    // obstacles | culling lists | residual partial sums]
+    float* mats = reinterpret_cast<float*>(tsm + TL.bytes);
+    const int nmat = L.init - L.Q;
+    float4* obs = reinterpret_cast<float4*>(mats + ((nmat + 3) & ~3));
+    int* lists = reinterpret_cast<int*>(obs + m);
+    float* part = reinterpret_cast<float*>(lists + 12 * m);  // [3][128][4]
+    int* olist = lists + warp * m;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    const float y0 = __ldg(A.ego + 0), v0 = __ldg(A.ego + 1), psi0 = __ldg(A.ego + 2), acc0 = __ldg(A.ego + 3);
+    for (int j = tid; j < m; j += TC_THREADS) {
+        const float* o = A.obst + 4 * j;
+        obs[j] = make_float4(-__ldg(o + 0) * A.inv_a, -__ldg(o + 1) * A.inv_b, -(__ldg(o + 2) - v0) * A.inv_a,
+                             -__ldg(o + 3) * A.inv_b);
+    }
+    for (int i = tid; i < nmat; i += TC_THREADS) mats[i] = __ldg(A.blob + L.Q + i);
+    const bool staged = stage_blob(reinterpret_cast<float*>(tsm), reinterpret_cast<const float*>(T.blob), TL.bytes,
+                                   &s_stage, A.err_flag, A.missing_tx);
+    const uint32_t bar = smem_u32(&s_mma);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);  // this warp's lanes
+    const uint32_t sm_base = smem_u32(tsm);
+    uint32_t mma_phase = 0;
+    bool ok = staged;
+
+    // ---- state of this thread's axis (g: 0 x, 1 y, 2 psi) for slot t ----
+    float c[16], e[16], lam[16];  // e: compensation (x, y); K12_psi b_psi (psi)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) c[k] = e[k] = lam[k] = 0.f;
+    const int n = A.n;
+    if (slot) {
+        const float* gl = A.goals + 3 * l;
+        const float yg = __ldg(gl + 0), vg = __ldg(gl + 1), ag = __ldg(gl + 2);
+        float cpsi, spsi;
+        sincosf(psi0, &spsi, &cpsi);
+        const size_t wo = (size_t)l * 3 * n;
+        if (g < 2) {
+            const bool isy = g == 1;
+            const float bx[6] = {0.f, v0 * cpsi - v0, acc0 * cpsi, vg - v0, ag, 0.f};
+            const float by[6] = {y0, v0 * spsi, acc0 * spsi, yg, 0.f, 0.f};
+            const int nb = isy ? 6 : 5;
+            const float* C0 = A.blob + (isy ? L.C0y : L.C0x);
+            const float* K12 = A.blob + (isy ? L.K12y : L.K12x);
+            if (A.warm_c) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < n)
+                        c[k] = __ldg(A.warm_c + wo + (isy ? n : 0) + k) - (isy ? 0.f : v0 * __ldg(A.blob + L.lin + k));
+            } else {
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int r = 0; r < 6; ++r)
+                        if (r < nb) s = fmaf(__ldg(C0 + k * 8 + r), isy ? by[r] : bx[r], s);
+                    c[k] = s;
+                }
+            }
+            // K12 (b - A c^0): added by the first step (the start's boundary rows)
+            const int rx[6] = {0, 1, 2, 4, 5, 5};
+            float res[6];
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                const int row = isy ? r : rx[r];
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s = fmaf(__ldg(A.blob + L.brow + row * NC + k), c[k], s);
+                res[r] = (isy ? by[r] : bx[r]) - s;
+            }
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int r = 0; r < 6; ++r)
+                    if (r < nb) s = fmaf(__ldg(K12 + k * 8 + r), res[r], s);
+                e[k] = s;
+            }
+            if (A.warm_l) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < n) lam[k] = __ldg(A.warm_l + wo + (isy ? n : 0) + k);
+            }
+        } else {
+            const float bp[4] = {psi0, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                float s = 0.f, s0 = 0.f;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    s = fmaf(__ldg(A.blob + L.Kp12 + k * 4 + r), bp[r], s);
+                    s0 = fmaf(__ldg(A.blob + L.C0p + k * 4 + r), bp[r], s0);
+                }
+                e[k] = s;
+                c[k] = s0;
+            }
+            if (A.warm_c) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < n) c[k] = __ldg(A.warm_c + wo + 2 * n + k);
+            }
+            if (A.warm_l) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < n) lam[k] = __ldg(A.warm_l + wo + 2 * n + k);
+            }
+        }
+    }
+
+    bool done = !slot;
+    int kit = 0, it = 0;
+    float rsum[4] = {0.f, 0.f, 0.f, 0.f};
+    float rh1 = INFINITY, rh2 = INFINITY;  // convergence residuals of the last two checks
+    unsigned long long work = 0;
+    const float* tgrid = A.blob + L.t;
+    const int nch = TL.NSP / TC_CS;
+    const uint32_t buf = TC_BUF + (uint32_t)(g * TC_CH * TC_CS);  // this group's chunk buffer
+
+    // projections of one chunk (samples s0 .. s0 + 15) of this group's buffer:
+    // evaluated channels in, residual rows out (in place)
+    auto chunk_project = [&](int cidx, float (&r4)[4]) {
+        const int s0 = cidx * TC_CS;
+        const bool act = !done;
+        const unsigned amask = __ballot_sync(FULL, act);
+        if (!amask) return;
+        const uint32_t ba = tl + buf;
+        const int nval = min(TC_CS, N - s0);
+        int cnt = m;
+        if (A.cull && m > 0) {
+            float X[16], Y[16];
+            tc_ld16(ba + 0, X);
+            tc_ld16(ba + TC_CS, Y);
+            const float inf = __int_as_float(0x7f800000);
+            float xlo = inf, xhi = -inf, ylo = inf, yhi = -inf;
+            bool bad = false;
+            if (act) {
+#pragma unroll
+                for (int i = 0; i < TC_CS; ++i)
+                    if (i < nval) {
+                        const float Xn = X[i] * A.inv_a, Yn = Y[i] * A.inv_b;
+                        xlo = fminf(xlo, Xn); xhi = fmaxf(xhi, Xn);
+                        ylo = fminf(ylo, Yn); yhi = fmaxf(yhi, Yn);
+                        bad = bad || !(isfinite(Xn) && isfinite(Yn));
+                    }
+            }
+            xlo = warp_min(xlo); xhi = warp_max(xhi);
+            ylo = warp_min(ylo); yhi = warp_max(yhi);
+            const bool any_bad = __any_sync(FULL, bad);
+            cnt = tc_cull(m, xlo, xhi, ylo, yhi, any_bad, __ldg(tgrid + s0), __ldg(tgrid + s0 + nval - 1), olist, lane,
+                          obs);
+        }
+        if (lane == 0) work += (unsigned long long)cnt * (unsigned)nval * (unsigned)__popc(amask);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            float v[TC_CH][8];
+#pragma unroll
+            for (int ch = 0; ch < TC_CH; ++ch) tc_ld8(ba + ch * TC_CS + 8 * h, v[ch]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int s = s0 + 8 * h + i;
+                float ev[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (act && s < N) {
+                    const TcSample smp{v[0][i], v[1][i], v[2][i], v[3][i], v[4][i], v[5][i], v[6][i]};
+                    if (A.cull) tc_residuals<true>(A, smp, __ldg(tgrid + s), v0, obs, olist, cnt, ev, r4);
+                    else tc_residuals<false>(A, smp, __ldg(tgrid + s), v0, obs, nullptr, m, ev, r4);
+                }
+#pragma unroll
+                for (int ch = 0; ch < TC_CH; ++ch) v[ch][i] = ev[ch];
+            }
+#pragma unroll
+            for (int ch = 0; ch < TC_CH; ++ch)
+                tc_store8<PREC>(ba + ch * TC_CS + 8 * h, ba + ch * TC_CS + 4 * h, v[ch]);
+        }
+    };
+
+    // heading of one chunk: theta = atan2(ydot, xdot) written over the xdot channel
+    auto chunk_heading = [&](int cidx) {
+        const int s0 = cidx * TC_CS;
+        const bool act = !done;
+        if (!__any_sync(FULL, act)) return;
+        const uint32_t ba = tl + buf;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            float vx[8], vy[8];
+            tc_ld8(ba + 3 * TC_CS + 8 * h, vx);
+            tc_ld8(ba + 4 * TC_CS + 8 * h, vy);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int s = s0 + 8 * h + i;
+                vx[i] = (act && s < N) ? atan2_own(vy[i], vx[i] + v0) : 0.f;
+            }
+            tc_store8<PREC>(ba + 3 * TC_CS + 8 * h, ba + 3 * TC_CS + 4 * h, vx);
+        }
+    };
+
+    // one pass over the samples: rounds of three chunks (evaluation MMAs,
+    // projections on the CUDA cores, contraction MMAs); heading: the
+    // channels xdot, ydot only and the contraction P^T theta
+    auto phase = [&](bool heading, float (&r4)[4]) -> bool {
+        unsigned fresh = heading ? 0x8u : 0x7u;
+        const int rounds = (nch + TC_GROUPS - 1) / TC_GROUPS;
+        for (int r = 0; r < rounds; ++r) {
+            if (tid == 0) {
+                for (int gg = 0; gg < TC_GROUPS; ++gg) {
+                    const int ci = TC_GROUPS * r + gg;
+                    if (ci < nch)
+                        tc_issue_eval<PREC>(tmem, sm_base, TL, ci * TC_CS, TC_BUF + (uint32_t)(gg * TC_CH * TC_CS),
+                                            heading ? 3 : 0, heading ? 5 : TC_CH);
+                }
+                tc_commit(bar);
+            }
+            const bool w = __syncthreads_and(tc_wait(bar, mma_phase)) != 0;
+            mma_phase ^= 1u;
+            if (!w) return false;
+            tc_fence_after();
+            const int ci = TC_GROUPS * r + g;
+            if (ci < nch) {
+                if (heading) chunk_heading(ci);
+                else chunk_project(ci, r4);
+            }
+            tc_sync();
+            if (tid == 0)
+                for (int gg = 0; gg < TC_GROUPS; ++gg) {
+                    const int cj = TC_GROUPS * r + gg;
+                    if (cj < nch)
+                        tc_issue_contr<PREC>(tmem, sm_base, TL, cj * TC_CS, TC_BUF + (uint32_t)(gg * TC_CH * TC_CS),
+                                             heading ? 3 : 0, heading ? 4 : TC_CH, heading ? 3 : -1, fresh);
+                }
+        }
+        if (tid == 0) tc_commit(bar);
+        const bool w = __syncthreads_and(tc_wait(bar, mma_phase)) != 0;
+        mma_phase ^= 1u;
+        tc_fence_after();
+        return w;
+    };
+
+    // residual sums of the three groups, added in a fixed order
+    auto exchange = [&](const float (&r4)[4]) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) part[(g * 128 + t) * 4 + r] = r4[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            rsum[r] = (part[(0 * 128 + t) * 4 + r] + part[(1 * 128 + t) * 4 + r]) + part[(2 * 128 + t) * 4 + r];
+        __syncthreads();
+    };
+
+    // multiplier update, convergence check and the xy QP increment (Sec.
+    // III-E), from the contraction accumulators of the pass just run
+    auto finish = [&](bool first, bool check) {
+        float ftd[16];
+        tc_ld16(tl + TC_DC + (uint32_t)(16 * g), ftd);  // x, y: F^T (F c - g); psi: P^T (P c_psi - theta)
+        if (done) return;
+        const float rho = A.rho;
+        float u[16];
+        if (!first) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) lam[k] = k < NC ? fmaf(-rho, ftd[k], lam[k]) : 0.f;
+        }
+        if (g < 2) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                u[k] = k < NC ? lam[k] - tc_dot<NC>(mats + k * KS, c) - rho * ftd[k] : 0.f;
+        }
+        bool dn = kit >= A.iters;
+        if (check && kit % A.check_every == 0 && (A.tol > 0.f || A.stall_tol > 0.f)) {
+            const float conv = fmaxf(sqrtf(rsum[0]), fmaxf(sqrtf(rsum[1]), sqrtf(rsum[2])));
+            if (!first) {
+                if (A.tol > 0.f) dn = dn || conv <= A.tol;
+                // stall stop: far from the target and not closing in over two checks
+                if (A.stall_tol > 0.f && kit >= 2 * A.check_every && conv > A.stall_tol && conv > A.stall_ratio * rh2)
+                    dn = true;
+            }
+            rh2 = rh1;
+            rh1 = conv;
+        }
+        if (dn) {
+            done = true;
+            return;
+        }
+        if (g < 2) {
+            const float* Kh = mats + (L.Q - L.Q) + (1 + 2 * g) * NC * KS;  // K11 hi of this axis
+            const float* Kl = Kh + NC * KS;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                const float d0 = tc_dot<NC>(Kh + k * KS, u);
+                const float d1 = tc_dot<NC>(Kl + k * KS, u);
+                const float dd = (d0 + d1) + e[k];
+                const float snew = c[k] + dd;
+                e[k] = dd - (snew - c[k]);
+                c[k] = snew;
+            }
+        }
+    };
+
+    // heading QP (Eq. lin_solve_psi_2): c_psi = K12_psi b_psi + K11_psi (rho P^T theta + lambda_psi)
+    auto psi_step = [&]() {
+        float pth[16];
+        tc_ld16(tl + TC_DC + 48u, pth);
+        if (done || g != 2) return;
+        float vec[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) vec[k] = k < NC ? fmaf(A.rho, pth[k], lam[k]) : 0.f;
+        const float* Kp = mats + 5 * NC * KS;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) c[k] = e[k] + tc_dot<NC>(Kp + k * KS, vec);
+    };
+
+    if (ok) {
+        // initial pass (iterate 0): auxiliaries and F^T (F c^0 - g^0), then the first step
+        tc_write_coef<PREC>(tl, g, c);
+        tc_sync();
+        float r4[4] = {0.f, 0.f, 0.f, 0.f};
+        ok = phase(false, r4);
+        if (ok) {
+            exchange(r4);
+            finish(true, true);
+        }
+        while (ok) {
+            if (g < 2) tc_write_coef<PREC>(tl, g, c);
+            tc_sync();
+            if (!__syncthreads_or(!done)) break;
+            ++it;  // the tile's iteration; a slot's own count stops when it is done
+            if (!done) kit = it;
+            const bool check = (it % A.check_every == 0) || it >= A.iters;
+            float rz[4] = {0.f, 0.f, 0.f, 0.f};
+            ok = phase(true, rz);
+            if (!ok) break;
+            psi_step();
+            if (g == 2) tc_write_coef<PREC>(tl, g, c);
+            tc_sync();
+            float rr[4] = {0.f, 0.f, 0.f, 0.f};
+            ok = phase(false, rr);
+            if (!ok) break;
+            if (check) exchange(rr);
+            finish(false, check);
+        }
+    }
+    if (!ok) {
+        // an expired wait: record it, then let the tensor core finish what was
+        // issued (bounded) before the tensor memory is released
+        if (tid == 0) atomicOr(A.err_flag, ERR_TMA_TIMEOUT);
+        if (staged) {
+            if (tid == 0) tc_commit(bar);
+            tc_wait(bar, mma_phase);
+        }
+    } else if (slot) {
+        const size_t o = (size_t)l * 3 * n;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < n) {
+                const float v =
+                    g == 0 ? (c[k] + e[k]) + v0 * __ldg(A.blob + L.lin + k) : (g == 1 ? c[k] + e[k] : c[k]);
+                A.coef_out[o + g * n + k] = v;
+                if (A.lam_out) A.lam_out[o + g * n + k] = lam[k];
+            }
+        }
+        if (g == 0) {
+            if (A.resid_out) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) A.resid_out[(size_t)l * 4 + r] = sqrtf(rsum[r]);
+            }
+            if (A.iters_out) A.iters_out[l] = kit;
+        }
+    }
+    if (lane == 0 && A.work && work) atomicAdd(A.work, work);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
+}
