@@ -1978,7 +1978,8 @@ size_t tc_smem(const mmpc_ctx* ctx, int m)
 {
     const int nmat = ctx->L.init - ctx->L.Q;
     return (size_t)ctx->tc.bytes + sizeof(float) * (size_t)((nmat + 3) & ~3) + 16 * (size_t)m +
-           sizeof(int) * (size_t)(TC_THREADS / 32) * m + sizeof(float) * 3 * 128 * 4;
+           sizeof(int) * (size_t)(TC_THREADS / 32) * m + sizeof(float) * 3 * 128 * 4 +
+           sizeof(float) * (size_t)ctx->tc.NSP;
 }
 
 int launch_tc(mmpc_ctx* ctx, const SolveArgs& a, int B, cudaStream_t st)

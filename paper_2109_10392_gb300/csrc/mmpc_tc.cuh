@@ -58,7 +58,8 @@ constexpr int TC_CH = 7;          // channels per chunk
 constexpr uint32_t TC_COLS = 512; // tensor-memory allocation
 constexpr uint32_t TC_DC = 0;     // contraction accumulators: x, y, psi - theta, theta (16 columns each)
 constexpr uint32_t TC_AC = 64;    // coefficient operands
-constexpr uint32_t TC_BUF = 160;  // chunk buffers
+constexpr uint32_t TC_BUF = 160;  // round buffer: 7 channels x TC_RW columns
+constexpr int TC_RW = 48;         // columns per channel: the three chunks of a round
 constexpr int TC_MAX_M = 128;     // obstacles
 
 // Layout of the tensor-core constant blob (bytes): per basis block (P, Pdot,
@@ -162,6 +163,53 @@ __device__ __forceinline__ void tc_ld16(uint32_t addr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Two consecutive columns of each of the 7 channels of a round buffer slot
+// (channel stride TC_RW columns), one wait for all seven loads.
+__device__ __forceinline__ void tc_ld7x2(uint32_t addr, float (&v)[TC_CH][2])
+{
+    uint32_t r[14];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%14];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%15];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%16];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%17];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%18];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%19];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%20];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13])
+                 : "r"(addr), "r"(addr + TC_RW), "r"(addr + 2 * TC_RW), "r"(addr + 3 * TC_RW), "r"(addr + 4 * TC_RW),
+                   "r"(addr + 5 * TC_RW), "r"(addr + 6 * TC_RW)
+                 : "memory");
+#pragma unroll
+    for (int ch = 0; ch < TC_CH; ++ch) {
+        v[ch][0] = __uint_as_float(r[2 * ch]);
+        v[ch][1] = __uint_as_float(r[2 * ch + 1]);
+    }
+}
+
+__device__ __forceinline__ void tc_ld2(uint32_t addr, float (&v)[2])
+{
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr)
+                 : "memory");
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+}
+
+__device__ __forceinline__ void tc_st1(uint32_t addr, uint32_t r0)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(addr), "r"(r0) : "memory");
+}
+
+__device__ __forceinline__ void tc_st2(uint32_t addr, uint32_t r0, uint32_t r1)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(r0), "r"(r1) : "memory");
+}
+
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_st4(uint32_t addr, const uint32_t (&r)[4])
@@ -213,38 +261,39 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity)
 }
 
 // Instruction descriptor: D float32, A and B of the precision's format, both
-// K-major, N = 16, M = 128.
+// K-major, M = 128, N = n_cols.
 template <int PREC>
-__device__ __forceinline__ uint32_t tc_idesc()
+__device__ __forceinline__ uint32_t tc_idesc(int n_cols)
 {
-    return (1u << 4) | (TcType<PREC>::FMT << 7) | (TcType<PREC>::FMT << 10) | ((uint32_t)(16 >> 3) << 17) |
+    return (1u << 4) | (TcType<PREC>::FMT << 7) | (TcType<PREC>::FMT << 10) | ((uint32_t)(n_cols >> 3) << 17) |
            ((uint32_t)(128 >> 4) << 24);
 }
 
-// Channels of a chunk buffer: evaluated value (basis block, coefficient
+// Channels of the round buffer: evaluated value (basis block, coefficient
 // axis), and, written in place, the residual whose contraction uses the same
 // block: 0 x (P, x) -> obstacle x; 1 y (P, y) -> obstacle y; 2 psi (P, psi)
 // -> psi - theta; 3 xdot (Pdot, x) -> non-holonomic x (theta in the heading
 // phase); 4 ydot (Pdot, y) -> non-holonomic y; 5 xddot (Pddot, x) ->
-// acceleration x; 6 yddot (Pddot, y) -> acceleration y.
+// acceleration x; 6 yddot (Pddot, y) -> acceleration y.  Each channel holds
+// the round's three chunks side by side (TC_RW columns; chunk g of the round
+// at column 16 g), so one MMA evaluates a channel for the whole round.
 __device__ __forceinline__ int tc_ch_blk(int ch) { return ch < 3 ? 0 : (ch < 5 ? 1 : 2); }
 __device__ __forceinline__ int tc_ch_axis(int ch) { return ch < 3 ? ch : ((ch - 3) & 1); }
 // contraction target of a channel: accumulator 0 x, 1 y, 2 psi - theta (the axis)
 
-// Evaluation MMAs of one chunk (samples s0 .. s0 + 15) into buffer `buf`
-// for channels [ch0, ch1): D = C B with C = hi (+ lo) coefficient rows, B =
-// the block's hi (+ lo) rows; split products a b ~ a_hi b_hi + a_hi b_lo +
-// a_lo b_hi.
+// Evaluation MMAs of one round (samples s0 .. s0 + 16 nc - 1) for channels
+// [ch0, ch1): D = C B with C = hi (+ lo) coefficient rows, B = the block's
+// hi (+ lo) rows; split products a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
 template <int PREC>
-__device__ __forceinline__ void tc_issue_eval(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0, uint32_t buf,
+__device__ __forceinline__ void tc_issue_eval(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0, int nc,
                                               int ch0, int ch1)
 {
     using TY = TcType<PREC>;
-    const uint32_t idesc = tc_idesc<PREC>();
+    const uint32_t idesc = tc_idesc<PREC>(TC_CS * nc);
     const uint32_t lbo = (uint32_t)(L.NSP * 16);
     for (int ch = ch0; ch < ch1; ++ch) {
         const int blk = tc_ch_blk(ch), ax = tc_ch_axis(ch);
-        const uint32_t d = tmem + buf + (uint32_t)(ch * TC_CS);
+        const uint32_t d = tmem + TC_BUF + (uint32_t)(ch * TC_RW);
         int first = 1;
 #pragma unroll
         for (int ks = 0; ks < TY::KSTEPS; ++ks) {
@@ -263,17 +312,17 @@ __device__ __forceinline__ void tc_issue_eval(uint32_t tmem, uint32_t sm_base, c
     }
 }
 
-// Contraction MMAs of one chunk: for channels [ch0, ch1) the residual rows E
-// (in place in buffer `buf`) times the transposed block, accumulated into
-// the channel's target (or into `dst_override` when >= 0); `fresh` marks the
-// targets not yet written in this phase (bit per target), cleared as they
-// are written.
+// Contraction MMAs of one chunk (samples s0 .. s0 + 15, columns `col` +
+// 16-column slot of each channel): for channels [ch0, ch1) the residual rows
+// E (in place) times the transposed block, accumulated into the channel's
+// target (or into `dst_override` when >= 0); `fresh` marks the targets not
+// yet written in this phase (bit per target), cleared as they are written.
 template <int PREC>
 __device__ __forceinline__ void tc_issue_contr(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0,
-                                               uint32_t buf, int ch0, int ch1, int dst_override, unsigned& fresh)
+                                               uint32_t col, int ch0, int ch1, int dst_override, unsigned& fresh)
 {
     using TY = TcType<PREC>;
-    const uint32_t idesc = tc_idesc<PREC>();
+    const uint32_t idesc = tc_idesc<PREC>(16);
     for (int ch = ch0; ch < ch1; ++ch) {
         // theta (over the xdot channel, target 3) contracts with P (Eq. lin_solve_psi_2)
         const int blk = dst_override == 3 ? 0 : tc_ch_blk(ch);
@@ -281,7 +330,7 @@ __device__ __forceinline__ void tc_issue_contr(uint32_t tmem, uint32_t sm_base, 
         const uint32_t d = tmem + TC_DC + (uint32_t)(dst * 16);
 #pragma unroll
         for (int ks = 0; ks < TY::CSTEPS; ++ks) {
-            const uint32_t a = tmem + buf + (uint32_t)(ch * TC_CS + ks * 8);
+            const uint32_t a = tmem + col + (uint32_t)(ch * TC_RW + ks * 8);
 #pragma unroll
             for (int pb = 0; pb < TY::PARTS; ++pb) {
                 const uint64_t b = tc_desc(sm_base + (uint32_t)L.cb[blk][pb] +
@@ -383,6 +432,15 @@ __device__ __forceinline__ void tc_store8(uint32_t addr_tf32, uint32_t addr_bf16
     }
 }
 
+// The values of samples 2j, 2j + 1 of one channel slot as the MMA's A
+// operand: TF32 bits in columns 2j, 2j + 1, or one BF16 pair in column j.
+template <int PREC>
+__device__ __forceinline__ void tc_store_pair(uint32_t slot, int j, float a, float b)
+{
+    if (TcType<PREC>::BF16) tc_st1(slot + (uint32_t)j, bf16_pair(a, b));
+    else tc_st2(slot + (uint32_t)(2 * j), tf32_bits(a), tf32_bits(b));
+}
+
 // The coefficient rows of one axis (hi and, split, lo) into tensor memory.
 template <int PREC>
 __device__ __forceinline__ void tc_write_coef(uint32_t lane_tmem, int axis, const float (&c)[16])
@@ -459,12 +517,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     const TcLayout& TL = T.L;
 
     // shared memory: [tensor-core blob | Q, K11 x hi, lo, y hi, lo, K11_psi |
-    // obstacles | culling lists | residual partial sums]
+    // obstacles | culling lists | residual partial sums | sample times]
     float* mats = reinterpret_cast<float*>(tsm + TL.bytes);
     const int nmat = L.init - L.Q;
     float4* obs = reinterpret_cast<float4*>(mats + ((nmat + 3) & ~3));
     int* lists = reinterpret_cast<int*>(obs + m);
     float* part = reinterpret_cast<float*>(lists + 12 * m);  // [3][128][4]
+    float* tgrid = part + 3 * 128 * 4;                       // sample times [NSP]
     int* olist = lists + warp * m;
 
     if (warp == 0) {
@@ -480,6 +539,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
                              -__ldg(o + 3) * A.inv_b);
     }
     for (int i = tid; i < nmat; i += TC_THREADS) mats[i] = __ldg(A.blob + L.Q + i);
+    for (int i = tid; i < TL.NSP; i += TC_THREADS) tgrid[i] = i < N ? __ldg(A.blob + L.t + i) : 0.f;
     const bool staged = stage_blob(reinterpret_cast<float*>(tsm), reinterpret_cast<const float*>(T.blob), TL.bytes,
                                    &s_stage, A.err_flag, A.missing_tx);
     const uint32_t bar = smem_u32(&s_mma);
@@ -584,64 +644,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
     float rh1 = INFINITY, rh2 = INFINITY;  // convergence residuals of the last two checks
     unsigned long long work = 0;
-    const float* tgrid = A.blob + L.t;
     const int nch = TL.NSP / TC_CS;
-    const uint32_t buf = TC_BUF + (uint32_t)(g * TC_CH * TC_CS);  // this group's chunk buffer
+    const uint32_t gslot = TC_BUF + (uint32_t)(g * TC_CS);  // this group's 16 columns of each channel
 
-    // projections of one chunk (samples s0 .. s0 + 15) of this group's buffer:
+    // projections of one chunk (samples s0 .. s0 + 15) of this group's slot:
     // evaluated channels in, residual rows out (in place)
     auto chunk_project = [&](int cidx, float (&r4)[4]) {
         const int s0 = cidx * TC_CS;
         const bool act = !done;
         const unsigned amask = __ballot_sync(FULL, act);
         if (!amask) return;
-        const uint32_t ba = tl + buf;
+        const uint32_t ba = tl + gslot;
         const int nval = min(TC_CS, N - s0);
         int cnt = m;
         if (A.cull && m > 0) {
-            float X[16], Y[16];
-            tc_ld16(ba + 0, X);
-            tc_ld16(ba + TC_CS, Y);
             const float inf = __int_as_float(0x7f800000);
             float xlo = inf, xhi = -inf, ylo = inf, yhi = -inf;
             bool bad = false;
-            if (act) {
+            {
+                float X[16], Y[16];
+                tc_ld16(ba + 0, X);
+                tc_ld16(ba + TC_RW, Y);
+                if (act) {
 #pragma unroll
-                for (int i = 0; i < TC_CS; ++i)
-                    if (i < nval) {
-                        const float Xn = X[i] * A.inv_a, Yn = Y[i] * A.inv_b;
-                        xlo = fminf(xlo, Xn); xhi = fmaxf(xhi, Xn);
-                        ylo = fminf(ylo, Yn); yhi = fmaxf(yhi, Yn);
-                        bad = bad || !(isfinite(Xn) && isfinite(Yn));
-                    }
+                    for (int i = 0; i < TC_CS; ++i)
+                        if (i < nval) {
+                            const float Xn = X[i] * A.inv_a, Yn = Y[i] * A.inv_b;
+                            xlo = fminf(xlo, Xn); xhi = fmaxf(xhi, Xn);
+                            ylo = fminf(ylo, Yn); yhi = fmaxf(yhi, Yn);
+                            bad = bad || !(isfinite(Xn) && isfinite(Yn));
+                        }
+                }
             }
             xlo = warp_min(xlo); xhi = warp_max(xhi);
             ylo = warp_min(ylo); yhi = warp_max(yhi);
             const bool any_bad = __any_sync(FULL, bad);
-            cnt = tc_cull(m, xlo, xhi, ylo, yhi, any_bad, __ldg(tgrid + s0), __ldg(tgrid + s0 + nval - 1), olist, lane,
-                          obs);
+            cnt = tc_cull(m, xlo, xhi, ylo, yhi, any_bad, tgrid[s0], tgrid[s0 + nval - 1], olist, lane, obs);
         }
         if (lane == 0) work += (unsigned long long)cnt * (unsigned)nval * (unsigned)__popc(amask);
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            float v[TC_CH][8];
+        for (int j = 0; j < TC_CS / 2; ++j) {
+            float v[TC_CH][2];
+            tc_ld7x2(ba + 2 * j, v);
+            float ev[2][7];
 #pragma unroll
-            for (int ch = 0; ch < TC_CH; ++ch) tc_ld8(ba + ch * TC_CS + 8 * h, v[ch]);
+            for (int h = 0; h < 2; ++h) {
+                const int s = s0 + 2 * j + h;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int s = s0 + 8 * h + i;
-                float ev[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int ch = 0; ch < TC_CH; ++ch) ev[h][ch] = 0.f;
                 if (act && s < N) {
-                    const TcSample smp{v[0][i], v[1][i], v[2][i], v[3][i], v[4][i], v[5][i], v[6][i]};
-                    if (A.cull) tc_residuals<true>(A, smp, __ldg(tgrid + s), v0, obs, olist, cnt, ev, r4);
-                    else tc_residuals<false>(A, smp, __ldg(tgrid + s), v0, obs, nullptr, m, ev, r4);
+                    const TcSample smp{v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h]};
+                    if (A.cull) tc_residuals<true>(A, smp, tgrid[s], v0, obs, olist, cnt, ev[h], r4);
+                    else tc_residuals<false>(A, smp, tgrid[s], v0, obs, nullptr, m, ev[h], r4);
                 }
-#pragma unroll
-                for (int ch = 0; ch < TC_CH; ++ch) v[ch][i] = ev[ch];
             }
 #pragma unroll
-            for (int ch = 0; ch < TC_CH; ++ch)
-                tc_store8<PREC>(ba + ch * TC_CS + 8 * h, ba + ch * TC_CS + 4 * h, v[ch]);
+            for (int ch = 0; ch < TC_CH; ++ch) tc_store_pair<PREC>(ba + ch * TC_RW, j, ev[0][ch], ev[1][ch]);
         }
     };
 
@@ -650,18 +708,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
         const int s0 = cidx * TC_CS;
         const bool act = !done;
         if (!__any_sync(FULL, act)) return;
-        const uint32_t ba = tl + buf;
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            float vx[8], vy[8];
-            tc_ld8(ba + 3 * TC_CS + 8 * h, vx);
-            tc_ld8(ba + 4 * TC_CS + 8 * h, vy);
+        const uint32_t ba = tl + gslot;
+#pragma unroll 2
+        for (int j = 0; j < TC_CS / 2; ++j) {
+            float vx[2], vy[2];
+            tc_ld2(ba + 3 * TC_RW + 2 * j, vx);
+            tc_ld2(ba + 4 * TC_RW + 2 * j, vy);
+            float th[2];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int s = s0 + 8 * h + i;
-                vx[i] = (act && s < N) ? atan2_own(vy[i], vx[i] + v0) : 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int s = s0 + 2 * j + h;
+                th[h] = (act && s < N) ? atan2_own(vy[h], vx[h] + v0) : 0.f;
             }
-            tc_store8<PREC>(ba + 3 * TC_CS + 8 * h, ba + 3 * TC_CS + 4 * h, vx);
+            tc_store_pair<PREC>(ba + 3 * TC_RW, j, th[0], th[1]);
         }
     };
 
@@ -672,13 +731,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
         unsigned fresh = heading ? 0x8u : 0x7u;
         const int rounds = (nch + TC_GROUPS - 1) / TC_GROUPS;
         for (int r = 0; r < rounds; ++r) {
+            const int nc = min(TC_GROUPS, nch - TC_GROUPS * r);
             if (tid == 0) {
-                for (int gg = 0; gg < TC_GROUPS; ++gg) {
-                    const int ci = TC_GROUPS * r + gg;
-                    if (ci < nch)
-                        tc_issue_eval<PREC>(tmem, sm_base, TL, ci * TC_CS, TC_BUF + (uint32_t)(gg * TC_CH * TC_CS),
-                                            heading ? 3 : 0, heading ? 5 : TC_CH);
-                }
+                tc_issue_eval<PREC>(tmem, sm_base, TL, r * TC_RW, nc, heading ? 3 : 0, heading ? 5 : TC_CH);
                 tc_commit(bar);
             }
             const bool w = __syncthreads_and(tc_wait(bar, mma_phase)) != 0;
@@ -686,18 +741,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             if (!w) return false;
             tc_fence_after();
             const int ci = TC_GROUPS * r + g;
-            if (ci < nch) {
+            if (g < nc) {
                 if (heading) chunk_heading(ci);
                 else chunk_project(ci, r4);
             }
             tc_sync();
             if (tid == 0)
-                for (int gg = 0; gg < TC_GROUPS; ++gg) {
-                    const int cj = TC_GROUPS * r + gg;
-                    if (cj < nch)
-                        tc_issue_contr<PREC>(tmem, sm_base, TL, cj * TC_CS, TC_BUF + (uint32_t)(gg * TC_CH * TC_CS),
-                                             heading ? 3 : 0, heading ? 4 : TC_CH, heading ? 3 : -1, fresh);
-                }
+                for (int gg = 0; gg < nc; ++gg)
+                    tc_issue_contr<PREC>(tmem, sm_base, TL, (TC_GROUPS * r + gg) * TC_CS,
+                                         TC_BUF + (uint32_t)(gg * TC_CS), heading ? 3 : 0, heading ? 4 : TC_CH,
+                                         heading ? 3 : -1, fresh);
         }
         if (tid == 0) tc_commit(bar);
         const bool w = __syncthreads_and(tc_wait(bar, mma_phase)) != 0;
