@@ -1926,6 +1926,8 @@ struct mmpc_ctx {
     int debug_missing = 0;  // mmpc_debug_expire_wait: bytes the staging wait expects beyond the copy
     mmpc::TcLayout tc{};             // variant 3: layout of the tensor-core operand blob
     unsigned char* d_tc = nullptr;   // variant 3: the blob (device)
+    int* d_order = nullptr;          // variant 3: bucket counts [TC_BUCKETS], then the slot order [order_cap]
+    int order_cap = 0;
     std::string err = "no error";
     // device buffers of mmpc_step_host, grown on demand: inputs (ego, obstacles,
     // goals) and outputs (coef, resid, iters, cost, argmin) for up to host_cap goals
@@ -1977,7 +1979,7 @@ void* tc_kernel(int prec)
 size_t tc_smem(const mmpc_ctx* ctx, int m)
 {
     const int nmat = ctx->L.init - ctx->L.Q;
-    return (size_t)ctx->tc.bytes + sizeof(float) * (size_t)((nmat + 3) & ~3) + 16 * (size_t)m +
+    return (size_t)ctx->tc.bytes + sizeof(float) * (size_t)((nmat + 3) & ~3) + 32 * (size_t)m +
            sizeof(int) * (size_t)(TC_THREADS / 32) * m + sizeof(float) * 3 * 128 * 4 +
            sizeof(float) * (size_t)ctx->tc.NSP;
 }
@@ -1991,10 +1993,31 @@ int launch_tc(mmpc_ctx* ctx, const SolveArgs& a, int B, cudaStream_t st)
         if (e != cudaSuccess) return cuda_fail(ctx, e, "device query");
         ctx->sm_count = sms;
     }
+    if (B > ctx->order_cap) {  // grown on demand (a first solve of a larger batch, outside graph capture)
+        const int cap = std::max(B, 2 * ctx->order_cap);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            cudaFree(ctx->d_order);
+            ctx->d_order = nullptr;
+            ctx->order_cap = 0;
+            e = cudaMalloc(&ctx->d_order, sizeof(int) * ((size_t)TC_BUCKETS + cap));
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "variant 3 order buffer");
+        ctx->order_cap = cap;
+    }
+    int* count = ctx->d_order;
+    int* order = ctx->d_order + TC_BUCKETS;
+    const int og = std::min(1024, (B + 255) / 256);
+    cudaError_t e0 = cudaMemsetAsync(count, 0, sizeof(int) * TC_BUCKETS, st);
+    if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "cudaMemsetAsync");
+    tc_order_count<<<og, 256, 0, st>>>(a.goals, B, count);
+    tc_order_scan<<<1, 1024, 0, st>>>(count);
+    tc_order_scatter<<<og, 256, 0, st>>>(a.goals, B, count, order);
     TcArgs T{};
     T.blob = ctx->d_tc;
     T.L = ctx->tc;
     T.TT = std::min(128, std::max(1, (B + ctx->sm_count - 1) / ctx->sm_count));
+    T.order = order;
     // at least 116 KB, so that one CTA holds an SM (it allocates all of the
     // SM's tensor memory; a second CTA would only wait in tcgen05.alloc)
     const size_t smem = std::max<size_t>(tc_smem(ctx, a.m), 116 * 1024);
@@ -2413,6 +2436,7 @@ extern "C" void mmpc_destroy(mmpc_ctx* ctx)
     cudaFree(ctx->d_blob);
     cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_tc);
+    cudaFree(ctx->d_order);
     cudaFree(ctx->h_in);
     cudaFree(ctx->h_out);
     delete ctx;

@@ -98,7 +98,66 @@ struct TcArgs {
     const unsigned char* blob;  // device, tc_layout bytes
     TcLayout L;
     int TT;                     // trajectories per tile (<= 128)
+    const int* order;           // trajectory of each slot position (tile-major), or NULL (identity)
 };
+
+// Slot order: trajectories with similar goals share a warp, so that the
+// warp's culling box (the union over its 32 trajectories) stays tight.  A
+// counting sort over buckets of the goal's terminal lateral offset (0.5 m
+// bins over [-8, 8) m) and speed (0.5 m/s bins over [0, 32) m/s); the order
+// inside a bucket is arbitrary.  Each trajectory's arithmetic is independent
+// of its slot (the MMA rows are independent, and culling only skips exact
+// zero terms), so the order changes no result.
+constexpr int TC_YBINS = 32, TC_VBINS = 64, TC_BUCKETS = TC_YBINS * TC_VBINS;
+
+__device__ __forceinline__ int tc_bucket(const float* __restrict__ goal)
+{
+    const float y = __ldg(goal + 0), v = __ldg(goal + 1);
+    const float fy = (y + 8.f) * 2.f, fv = v * 2.f;
+    const int by = fy >= 0.f ? min(TC_YBINS - 1, (int)fy) : 0;  // NaN -> 0
+    const int bv = fv >= 0.f ? min(TC_VBINS - 1, (int)fv) : 0;
+    return by * TC_VBINS + bv;
+}
+
+__global__ void tc_order_count(const float* __restrict__ goals, int B, int* __restrict__ count)
+{
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < B; l += gridDim.x * blockDim.x)
+        atomicAdd(count + tc_bucket(goals + 3 * l), 1);
+}
+
+// exclusive scan of the bucket counts in place (one CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) tc_order_scan(int* __restrict__ count)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    constexpr int PER = TC_BUCKETS / 1024;
+    int v[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        v[i] = count[t * PER + i];
+        sum += v[i];
+    }
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int add = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += add;
+        __syncthreads();
+    }
+    int run = part[t] - sum;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        count[t * PER + i] = run;
+        run += v[i];
+    }
+}
+
+__global__ void tc_order_scatter(const float* __restrict__ goals, int B, int* __restrict__ next, int* __restrict__ order)
+{
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < B; l += gridDim.x * blockDim.x)
+        order[atomicAdd(next + tc_bucket(goals + 3 * l), 1)] = l;
+}
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
@@ -186,6 +245,34 @@ __device__ __forceinline__ void tc_ld7x2(uint32_t addr, float (&v)[TC_CH][2])
         v[ch][0] = __uint_as_float(r[2 * ch]);
         v[ch][1] = __uint_as_float(r[2 * ch + 1]);
     }
+}
+
+// The same loads without the wait, for prefetching: the registers may be
+// used only after tc_ld_wait14 on them (whose "+r" operands keep every use
+// after the wait).
+__device__ __forceinline__ void tc_ld7x2_issue(uint32_t addr, uint32_t (&r)[14])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%14];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%15];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%16];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%17];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%18];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%19];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%20];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13])
+                 : "r"(addr), "r"(addr + TC_RW), "r"(addr + 2 * TC_RW), "r"(addr + 3 * TC_RW), "r"(addr + 4 * TC_RW),
+                   "r"(addr + 5 * TC_RW), "r"(addr + 6 * TC_RW)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld_wait14(uint32_t (&r)[14])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13])
+                 :
+                 : "memory");
 }
 
 __device__ __forceinline__ void tc_ld2(uint32_t addr, float (&v)[2])
@@ -357,9 +444,9 @@ __device__ __forceinline__ int tc_cull(int m, float xlo, float xhi, float ylo, f
         const int j = j0 + lane;
         bool keep = false;
         if (j < m) {
-            const float4 o = obs[j];
-            const float e1 = -fmaf(o.z, tw_lo, o.x), e2 = -fmaf(o.z, tw_hi, o.x);
-            const float f1 = -fmaf(o.w, tw_lo, o.y), g1 = -fmaf(o.w, tw_hi, o.y);
+            const float4 ox = obs[2 * j], oy = obs[2 * j + 1];  // (p, p, pv, pv) per axis
+            const float e1 = -fmaf(ox.z, tw_lo, ox.x), e2 = -fmaf(ox.z, tw_hi, ox.x);
+            const float f1 = -fmaf(oy.z, tw_lo, oy.x), g1 = -fmaf(oy.z, tw_hi, oy.x);
             const bool apart = (xlo - fmaxf(e1, e2) >= CULL_MARGIN) || (fminf(e1, e2) - xhi >= CULL_MARGIN) ||
                                (ylo - fmaxf(f1, g1) >= CULL_MARGIN) || (fminf(f1, g1) - yhi >= CULL_MARGIN);
             keep = any_bad || !apart;
@@ -372,46 +459,52 @@ __device__ __forceinline__ int tc_cull(int m, float xlo, float xhi, float ylo, f
     return count;
 }
 
-// Residuals of one sample (Eqs. split_v, split_alpha_o, split_alpha_a in the
-// trigonometry-free forms of the pair kernel; x and the obstacles in the frame
-// moving with v0): e = (obstacle x, obstacle y, psi - theta, non-holonomic x,
-// y, acceleration x, y), and the squared residual norms.
-struct TcSample {
-    float x, y, ps, xd, yd, xdd, ydd;  // evaluated (x, xd relative to v0 t)
-};
-
-template <bool LIST>
-__device__ __forceinline__ void tc_residuals(const SolveArgs& A, const TcSample& v, float tt, float v0,
-                                             const float4* __restrict__ obs, const int* __restrict__ list, int cnt,
-                                             float (&e)[7], float (&r)[4])
+// Residuals of a pair of samples, as packed f32x2 arithmetic (Eqs. split_v,
+// split_alpha_o, split_alpha_a in the trigonometry-free forms of the pair
+// kernel; x and the obstacles in the frame moving with v0): e = (obstacle x,
+// obstacle y, psi - theta, non-holonomic x, y, acceleration x, y), and the
+// squared residual norms of the valid samples.
+template <bool LIST, bool RESID>
+__device__ __forceinline__ void tc_pair(const SolveArgs& A, const float (&v)[TC_CH][2], float2 tt, float2 valid,
+                                        float v0, const float4* __restrict__ obs, const int* __restrict__ list, int cnt,
+                                        float2 (&e)[TC_CH], float (&r)[4])
 {
-    const float xd = v.xd + v0, yd = v.yd;
-    const float theta = atan2_own(yd, xd);
-    const float vel = fminf(fmaxf(sqrtf(fmaf(xd, xd, yd * yd)), A.v_min), A.v_max);
-    float sn, cs;
-    heading_sincos(v.ps, &sn, &cs);
-    const float evx = fmaf(-vel, cs, xd);
-    const float evy = fmaf(-vel, sn, yd);
-    const float an2 = fmaf(v.xdd, v.xdd, v.ydd * v.ydd);
-    const float fr = 1.f - fminf(1.f, A.a_max * rsqrtf(an2));
-    const float eax = v.xdd * fr, eay = v.ydd * fr;
-    const float Xn = v.x * A.inv_a, Yn = v.y * A.inv_b;
+    const float2 x = f2(v[0][0], v[0][1]), y = f2(v[1][0], v[1][1]), ps = f2(v[2][0], v[2][1]);
+    const float2 xd = __fadd2_rn(f2(v[3][0], v[3][1]), f2(v0)), yd = f2(v[4][0], v[4][1]);
+    const float2 xdd = f2(v[5][0], v[5][1]), ydd = f2(v[6][0], v[6][1]);
+    const float2 theta = atan2_pair(yd, xd);
+    const float2 sp2 = __ffma2_rn(xd, xd, __fmul2_rn(yd, yd));
+    const float2 nvel = f2(-fminf(fmaxf(sqrtf(sp2.x), A.v_min), A.v_max), -fminf(fmaxf(sqrtf(sp2.y), A.v_min), A.v_max));
+    float2 sn, cs;
+    sincos_pair(ps, sn, cs);
+    const float2 evx = __ffma2_rn(nvel, cs, xd);
+    const float2 evy = __ffma2_rn(nvel, sn, yd);
+    const float2 an2 = __ffma2_rn(xdd, xdd, __fmul2_rn(ydd, ydd));
+    const float2 fr = f2(1.f - fminf(1.f, A.a_max * rsqrtf(an2.x)), 1.f - fminf(1.f, A.a_max * rsqrtf(an2.y)));
+    const float2 eax = __fmul2_rn(xdd, fr);
+    const float2 eay = __fmul2_rn(ydd, fr);
+    const float2 Xn = __fmul2_rn(x, f2(A.inv_a)), Yn = __fmul2_rn(y, f2(A.inv_b));
     const float a2 = A.a * A.a, b2 = A.b * A.b;
-    float Sx, Sy, R2;
-    obstacle_sum1<true, LIST>(obs, list, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-    if (isnan(Sx) || isnan(Sy)) obstacle_sum1_exact(obs, A.m, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-    const float dpsi = v.ps - theta;
-    e[0] = -A.a * Sx;
-    e[1] = -A.b * Sy;
-    e[2] = dpsi;
+    float2 Sx, Sy, R2;
+    obstacle_sum2<RESID, LIST>(obs, list, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
+    if (isnan(Sx.x) || isnan(Sy.x)) obstacle_sum_exact(obs, A.m, Xn.x, Yn.x, tt.x, a2, b2, Sx.x, Sy.x, R2.x);
+    if (isnan(Sx.y) || isnan(Sy.y)) obstacle_sum_exact(obs, A.m, Xn.y, Yn.y, tt.y, a2, b2, Sx.y, Sy.y, R2.y);
+    e[0] = __fmul2_rn(Sx, f2(-A.a));
+    e[1] = __fmul2_rn(Sy, f2(-A.b));
+    e[2] = __fadd2_rn(ps, f2(-theta.x, -theta.y));
     e[3] = evx;
     e[4] = evy;
     e[5] = eax;
     e[6] = eay;
-    r[0] += R2;
-    r[1] += fmaf(eax, eax, eay * eay);
-    r[2] += fmaf(evx, evx, evy * evy);
-    r[3] += dpsi * dpsi;
+    if (RESID) {
+        const float2 ra = __ffma2_rn(eax, eax, __fmul2_rn(eay, eay));
+        const float2 rv = __ffma2_rn(evx, evx, __fmul2_rn(evy, evy));
+        const float2 rp = __fmul2_rn(e[2], e[2]);
+        r[0] = fmaf(R2.y, valid.y, fmaf(R2.x, valid.x, r[0]));
+        r[1] = fmaf(ra.y, valid.y, fmaf(ra.x, valid.x, r[1]));
+        r[2] = fmaf(rv.y, valid.y, fmaf(rv.x, valid.x, r[2]));
+        r[3] = fmaf(rp.y, valid.y, fmaf(rp.x, valid.x, r[3]));
+    }
 }
 
 // 8 values of one channel into tensor memory as the MMA's A operand: TF32
@@ -510,8 +603,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = warp >> 2, q = warp & 3;  // axis group, tensor-memory sub-partition
     const int t = 32 * q + lane;            // trajectory slot
-    const int l = blockIdx.x * T.TT + t;
-    const bool slot = t < T.TT && l < A.B;
+    const int pos = blockIdx.x * T.TT + t;
+    const bool slot = t < T.TT && pos < A.B;
+    const int l = slot && T.order ? T.order[pos] : pos;
     const int N = A.N, m = A.m;
     const BlobLayout& L = A.L;
     const TcLayout& TL = T.L;
@@ -521,7 +615,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     float* mats = reinterpret_cast<float*>(tsm + TL.bytes);
     const int nmat = L.init - L.Q;
     float4* obs = reinterpret_cast<float4*>(mats + ((nmat + 3) & ~3));
-    int* lists = reinterpret_cast<int*>(obs + m);
+    int* lists = reinterpret_cast<int*>(obs + 2 * m);
     float* part = reinterpret_cast<float*>(lists + 12 * m);  // [3][128][4]
     float* tgrid = part + 3 * 128 * 4;                       // sample times [NSP]
     int* olist = lists + warp * m;
@@ -535,8 +629,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     const float y0 = __ldg(A.ego + 0), v0 = __ldg(A.ego + 1), psi0 = __ldg(A.ego + 2), acc0 = __ldg(A.ego + 3);
     for (int j = tid; j < m; j += TC_THREADS) {
         const float* o = A.obst + 4 * j;
-        obs[j] = make_float4(-__ldg(o + 0) * A.inv_a, -__ldg(o + 1) * A.inv_b, -(__ldg(o + 2) - v0) * A.inv_a,
-                             -__ldg(o + 3) * A.inv_b);
+        const float px = -__ldg(o + 0) * A.inv_a, py = -__ldg(o + 1) * A.inv_b;
+        const float pvx = -(__ldg(o + 2) - v0) * A.inv_a, pvy = -__ldg(o + 3) * A.inv_b;
+        obs[2 * j] = make_float4(px, px, pvx, pvx);
+        obs[2 * j + 1] = make_float4(py, py, pvy, pvy);
     }
     for (int i = tid; i < nmat; i += TC_THREADS) mats[i] = __ldg(A.blob + L.Q + i);
     for (int i = tid; i < TL.NSP; i += TC_THREADS) tgrid[i] = i < N ? __ldg(A.blob + L.t + i) : 0.f;
@@ -649,7 +745,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
 
     // projections of one chunk (samples s0 .. s0 + 15) of this group's slot:
     // evaluated channels in, residual rows out (in place)
-    auto chunk_project = [&](int cidx, float (&r4)[4]) {
+    auto chunk_project = [&](int cidx, bool check, float (&r4)[4]) {
         const int s0 = cidx * TC_CS;
         const bool act = !done;
         const unsigned amask = __ballot_sync(FULL, act);
@@ -682,21 +778,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             cnt = tc_cull(m, xlo, xhi, ylo, yhi, any_bad, tgrid[s0], tgrid[s0 + nval - 1], olist, lane, obs);
         }
         if (lane == 0) work += (unsigned long long)cnt * (unsigned)nval * (unsigned)__popc(amask);
+        uint32_t rn[14];
+        tc_ld7x2_issue(ba, rn);
 #pragma unroll 1
         for (int j = 0; j < TC_CS / 2; ++j) {
+            tc_ld_wait14(rn);
             float v[TC_CH][2];
-            tc_ld7x2(ba + 2 * j, v);
+#pragma unroll
+            for (int ch = 0; ch < TC_CH; ++ch) {
+                v[ch][0] = __uint_as_float(rn[2 * ch]);
+                v[ch][1] = __uint_as_float(rn[2 * ch + 1]);
+            }
+            if (j + 1 < TC_CS / 2) tc_ld7x2_issue(ba + 2 * (j + 1), rn);  // the next pair, while this one runs
+            const int sa = s0 + 2 * j;
+            const float2 valid = f2(act && sa < N ? 1.f : 0.f, act && sa + 1 < N ? 1.f : 0.f);
+            const float2 tt = f2(tgrid[sa], tgrid[sa + 1]);
+            float2 e2[TC_CH];
+            if (check) {
+                if (A.cull) tc_pair<true, true>(A, v, tt, valid, v0, obs, olist, cnt, e2, r4);
+                else tc_pair<false, true>(A, v, tt, valid, v0, obs, nullptr, m, e2, r4);
+            } else {
+                if (A.cull) tc_pair<true, false>(A, v, tt, valid, v0, obs, olist, cnt, e2, r4);
+                else tc_pair<false, false>(A, v, tt, valid, v0, obs, nullptr, m, e2, r4);
+            }
             float ev[2][7];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int s = s0 + 2 * j + h;
-#pragma unroll
-                for (int ch = 0; ch < TC_CH; ++ch) ev[h][ch] = 0.f;
-                if (act && s < N) {
-                    const TcSample smp{v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h]};
-                    if (A.cull) tc_residuals<true>(A, smp, tgrid[s], v0, obs, olist, cnt, ev[h], r4);
-                    else tc_residuals<false>(A, smp, tgrid[s], v0, obs, nullptr, m, ev[h], r4);
-                }
+            for (int ch = 0; ch < TC_CH; ++ch) {
+                ev[0][ch] = e2[ch].x;
+                ev[1][ch] = e2[ch].y;
             }
 #pragma unroll
             for (int ch = 0; ch < TC_CH; ++ch) tc_store_pair<PREC>(ba + ch * TC_RW, j, ev[0][ch], ev[1][ch]);
@@ -714,20 +823,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             float vx[2], vy[2];
             tc_ld2(ba + 3 * TC_RW + 2 * j, vx);
             tc_ld2(ba + 4 * TC_RW + 2 * j, vy);
-            float th[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int s = s0 + 2 * j + h;
-                th[h] = (act && s < N) ? atan2_own(vy[h], vx[h] + v0) : 0.f;
-            }
-            tc_store_pair<PREC>(ba + 3 * TC_RW, j, th[0], th[1]);
+            const float2 th = atan2_pair(f2(vy[0], vy[1]), __fadd2_rn(f2(vx[0], vx[1]), f2(v0)));
+            tc_store_pair<PREC>(ba + 3 * TC_RW, j, th.x, th.y);
         }
     };
 
     // one pass over the samples: rounds of three chunks (evaluation MMAs,
     // projections on the CUDA cores, contraction MMAs); heading: the
     // channels xdot, ydot only and the contraction P^T theta
-    auto phase = [&](bool heading, float (&r4)[4]) -> bool {
+    auto phase = [&](bool heading, bool check, float (&r4)[4]) -> bool {
         unsigned fresh = heading ? 0x8u : 0x7u;
         const int rounds = (nch + TC_GROUPS - 1) / TC_GROUPS;
         for (int r = 0; r < rounds; ++r) {
@@ -743,7 +847,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             const int ci = TC_GROUPS * r + g;
             if (g < nc) {
                 if (heading) chunk_heading(ci);
-                else chunk_project(ci, r4);
+                else chunk_project(ci, check, r4);
             }
             tc_sync();
             if (tid == 0)
@@ -836,7 +940,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
         tc_write_coef<PREC>(tl, g, c);
         tc_sync();
         float r4[4] = {0.f, 0.f, 0.f, 0.f};
-        ok = phase(false, r4);
+        ok = phase(false, true, r4);
         if (ok) {
             exchange(r4);
             finish(true, true);
@@ -849,13 +953,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             if (!done) kit = it;
             const bool check = (it % A.check_every == 0) || it >= A.iters;
             float rz[4] = {0.f, 0.f, 0.f, 0.f};
-            ok = phase(true, rz);
+            ok = phase(true, false, rz);
             if (!ok) break;
             psi_step();
             if (g == 2) tc_write_coef<PREC>(tl, g, c);
             tc_sync();
             float rr[4] = {0.f, 0.f, 0.f, 0.f};
-            ok = phase(false, rr);
+            ok = phase(false, check, rr);
             if (!ok) break;
             if (check) exchange(rr);
             finish(false, check);
