@@ -364,68 +364,68 @@ __device__ __forceinline__ uint32_t tc_idesc(int n_cols)
 // acceleration x; 6 yddot (Pddot, y) -> acceleration y.  Each channel holds
 // the round's three chunks side by side (TC_RW columns; chunk g of the round
 // at column 16 g), so one MMA evaluates a channel for the whole round.
-__device__ __forceinline__ int tc_ch_blk(int ch) { return ch < 3 ? 0 : (ch < 5 ? 1 : 2); }
-__device__ __forceinline__ int tc_ch_axis(int ch) { return ch < 3 ? ch : ((ch - 3) & 1); }
-// contraction target of a channel: accumulator 0 x, 1 y, 2 psi - theta (the axis)
+// (block of channel ch: ch < 3 ? P : ch < 5 ? Pdot : Pddot; coefficient axis
+// and contraction target: ch < 3 ? ch : (ch - 3) & 1)
 
 // Evaluation MMAs of one round (samples s0 .. s0 + 16 nc - 1) for channels
-// [ch0, ch1): D = C B with C = hi (+ lo) coefficient rows, B = the block's
+// [CH0, CH1): D = C B with C = hi (+ lo) coefficient rows, B = the block's
 // hi (+ lo) rows; split products a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
-template <int PREC>
-__device__ __forceinline__ void tc_issue_eval(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0, int nc,
-                                              int ch0, int ch1)
+// The shared-memory descriptors differ only in their start address, so each
+// is a constant or'ed with (address >> 4) (addresses stay below 256 KB).
+template <int PREC, int CH0, int CH1>
+__device__ __forceinline__ void tc_issue_eval(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0, int nc)
 {
     using TY = TcType<PREC>;
     const uint32_t idesc = tc_idesc<PREC>(TC_CS * nc);
-    const uint32_t lbo = (uint32_t)(L.NSP * 16);
-    for (int ch = ch0; ch < ch1; ++ch) {
-        const int blk = tc_ch_blk(ch), ax = tc_ch_axis(ch);
+    const uint32_t lbo4 = (uint32_t)L.NSP;  // NSP 16 bytes in 16-byte units
+    const uint64_t hi = ((uint64_t)(lbo4 & 0x3FFFu) << 16) | ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+    const uint32_t row4 = (sm_base >> 4) + (uint32_t)s0;  // s0 rows of 16 bytes
+#pragma unroll
+    for (int ch = CH0; ch < CH1; ++ch) {
+        const int blk = ch < 3 ? 0 : (ch < 5 ? 1 : 2), ax = ch < 3 ? ch : ((ch - 3) & 1);
         const uint32_t d = tmem + TC_BUF + (uint32_t)(ch * TC_RW);
-        int first = 1;
+        const uint32_t b_hi = row4 + ((uint32_t)L.eb[blk][0] >> 4);
+        const uint32_t b_lo = row4 + ((uint32_t)L.eb[blk][1] >> 4);
 #pragma unroll
         for (int ks = 0; ks < TY::KSTEPS; ++ks) {
 #pragma unroll
             for (int pr = 0; pr < (TY::SPLIT ? 3 : 1); ++pr) {
                 const int pa = pr == 2 ? 1 : 0;  // coefficient part: hi, hi, lo
-                const int pb = pr == 1 ? 1 : 0;  // basis part: hi, lo, hi
                 const uint32_t a = tmem + TC_AC + (uint32_t)((2 * ax + pa) * TY::ACOLS + ks * 8);
-                const uint64_t b = tc_desc(sm_base + (uint32_t)L.eb[blk][pb] + (uint32_t)(s0 * 16) +
-                                               (uint32_t)(ks * 2) * lbo,
-                                           lbo, 128u);
-                tc_mma<TY::BF16>(d, a, b, idesc, first ? 0u : 1u);
-                first = 0;
+                const uint64_t b = hi | (uint64_t)((pr == 1 ? b_lo : b_hi) + (uint32_t)(2 * ks) * lbo4);
+                tc_mma<TY::BF16>(d, a, b, idesc, (ks == 0 && pr == 0) ? 0u : 1u);
             }
         }
     }
 }
 
-// Contraction MMAs of one chunk (samples s0 .. s0 + 15, columns `col` +
-// 16-column slot of each channel): for channels [ch0, ch1) the residual rows
-// E (in place) times the transposed block, accumulated into the channel's
-// target (or into `dst_override` when >= 0); `fresh` marks the targets not
-// yet written in this phase (bit per target), cleared as they are written.
-template <int PREC>
+// Contraction MMAs of one chunk (samples s0 .. s0 + 15, column `col` of each
+// channel): for channels [CH0, CH1) the residual rows E (in place) times the
+// transposed block, accumulated into the channel's target (THETA: theta in
+// the xdot channel, with P, into target 3).  `first`: the round's first
+// chunk of the phase, whose first product per target overwrites it.
+template <int PREC, int CH0, int CH1, bool THETA>
 __device__ __forceinline__ void tc_issue_contr(uint32_t tmem, uint32_t sm_base, const TcLayout& L, int s0,
-                                               uint32_t col, int ch0, int ch1, int dst_override, unsigned& fresh)
+                                               uint32_t col, bool first)
 {
     using TY = TcType<PREC>;
     const uint32_t idesc = tc_idesc<PREC>(16);
-    for (int ch = ch0; ch < ch1; ++ch) {
-        // theta (over the xdot channel, target 3) contracts with P (Eq. lin_solve_psi_2)
-        const int blk = dst_override == 3 ? 0 : tc_ch_blk(ch);
-        const int dst = dst_override >= 0 ? dst_override : tc_ch_axis(ch);
+    const uint64_t hi = ((uint64_t)(256u >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+    const uint32_t grp4 = (sm_base >> 4) + (uint32_t)(s0 / TY::PER) * 16u;  // 256-byte K groups
+#pragma unroll
+    for (int ch = CH0; ch < CH1; ++ch) {
+        const int blk = THETA ? 0 : (ch < 3 ? 0 : (ch < 5 ? 1 : 2));
+        const int dst = THETA ? 3 : (ch < 3 ? ch : ((ch - 3) & 1));
+        const bool lead = THETA || ch < 3;  // the target's first channel
         const uint32_t d = tmem + TC_DC + (uint32_t)(dst * 16);
 #pragma unroll
         for (int ks = 0; ks < TY::CSTEPS; ++ks) {
             const uint32_t a = tmem + col + (uint32_t)(ch * TC_RW + ks * 8);
 #pragma unroll
             for (int pb = 0; pb < TY::PARTS; ++pb) {
-                const uint64_t b = tc_desc(sm_base + (uint32_t)L.cb[blk][pb] +
-                                               (uint32_t)((s0 / TY::PER + 2 * ks) * 256),
-                                           256u, 128u);
-                const uint32_t acc = (fresh >> dst) & 1u ? 0u : 1u;
+                const uint64_t b = hi | (uint64_t)(grp4 + ((uint32_t)L.cb[blk][pb] >> 4) + (uint32_t)(32 * ks));
+                const uint32_t acc = (first && lead && ks == 0 && pb == 0) ? 0u : 1u;
                 tc_mma<TY::BF16>(d, a, b, idesc, acc);
-                fresh &= ~(1u << dst);
             }
         }
     }
@@ -832,12 +832,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     // projections on the CUDA cores, contraction MMAs); heading: the
     // channels xdot, ydot only and the contraction P^T theta
     auto phase = [&](bool heading, bool check, float (&r4)[4]) -> bool {
-        unsigned fresh = heading ? 0x8u : 0x7u;
         const int rounds = (nch + TC_GROUPS - 1) / TC_GROUPS;
         for (int r = 0; r < rounds; ++r) {
             const int nc = min(TC_GROUPS, nch - TC_GROUPS * r);
             if (tid == 0) {
-                tc_issue_eval<PREC>(tmem, sm_base, TL, r * TC_RW, nc, heading ? 3 : 0, heading ? 5 : TC_CH);
+                if (heading) tc_issue_eval<PREC, 3, 5>(tmem, sm_base, TL, r * TC_RW, nc);
+                else tc_issue_eval<PREC, 0, TC_CH>(tmem, sm_base, TL, r * TC_RW, nc);
                 tc_commit(bar);
             }
             const bool w = __syncthreads_and(tc_wait(bar, mma_phase)) != 0;
@@ -851,10 +851,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             }
             tc_sync();
             if (tid == 0)
-                for (int gg = 0; gg < nc; ++gg)
-                    tc_issue_contr<PREC>(tmem, sm_base, TL, (TC_GROUPS * r + gg) * TC_CS,
-                                         TC_BUF + (uint32_t)(gg * TC_CS), heading ? 3 : 0, heading ? 4 : TC_CH,
-                                         heading ? 3 : -1, fresh);
+                for (int gg = 0; gg < nc; ++gg) {
+                    const int sc = (TC_GROUPS * r + gg) * TC_CS;
+                    const uint32_t col = TC_BUF + (uint32_t)(gg * TC_CS);
+                    const bool first = r == 0 && gg == 0;
+                    if (heading) tc_issue_contr<PREC, 3, 4, true>(tmem, sm_base, TL, sc, col, first);
+                    else tc_issue_contr<PREC, 0, TC_CH, false>(tmem, sm_base, TL, sc, col, first);
+                }
         }
         if (tid == 0) tc_commit(bar);
         const bool w = __syncthreads_and(tc_wait(bar, mma_phase)) != 0;
