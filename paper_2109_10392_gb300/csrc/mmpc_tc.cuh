@@ -487,8 +487,18 @@ __device__ __forceinline__ void tc_pair(const SolveArgs& A, const float (&v)[TC_
     const float a2 = A.a * A.a, b2 = A.b * A.b;
     float2 Sx, Sy, R2;
     obstacle_sum2<RESID, LIST>(obs, list, cnt, Xn, Yn, tt, a2, b2, Sx, Sy, R2);
-    if (isnan(Sx.x) || isnan(Sy.x)) obstacle_sum_exact(obs, A.m, Xn.x, Yn.x, tt.x, a2, b2, Sx.x, Sy.x, R2.x);
-    if (isnan(Sx.y) || isnan(Sy.y)) obstacle_sum_exact(obs, A.m, Xn.y, Yn.y, tt.y, a2, b2, Sx.y, Sy.y, R2.y);
+    // a sample exactly at an obstacle centre (rare): the exact sum, through
+    // temporaries so that the common path keeps its values in registers
+    if (isnan(Sx.x) || isnan(Sy.x)) {
+        float sx, sy, r2;
+        obstacle_sum_exact(obs, A.m, Xn.x, Yn.x, tt.x, a2, b2, sx, sy, r2);
+        Sx.x = sx; Sy.x = sy; R2.x = r2;
+    }
+    if (isnan(Sx.y) || isnan(Sy.y)) {
+        float sx, sy, r2;
+        obstacle_sum_exact(obs, A.m, Xn.y, Yn.y, tt.y, a2, b2, sx, sy, r2);
+        Sx.y = sx; Sy.y = sy; R2.y = r2;
+    }
     e[0] = __fmul2_rn(Sx, f2(-A.a));
     e[1] = __fmul2_rn(Sy, f2(-A.b));
     e[2] = __fadd2_rn(ps, f2(-theta.x, -theta.y));
@@ -871,9 +881,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
 #pragma unroll
         for (int r = 0; r < 4; ++r) part[(g * 128 + t) * 4 + r] = r4[r];
         __syncthreads();
+        if (!done) {  // a finished trajectory keeps the residuals of its last check
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            rsum[r] = (part[(0 * 128 + t) * 4 + r] + part[(1 * 128 + t) * 4 + r]) + part[(2 * 128 + t) * 4 + r];
+            for (int r = 0; r < 4; ++r)
+                rsum[r] = (part[(0 * 128 + t) * 4 + r] + part[(1 * 128 + t) * 4 + r]) + part[(2 * 128 + t) * 4 + r];
+        }
         __syncthreads();
     };
 

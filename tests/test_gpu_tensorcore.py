@@ -1,0 +1,147 @@
+"""The tensor-core solve kernel (variant 3): the shared-matrix products of
+Algorithm 1 (the evaluations P c and the contractions P^T e of Eqs.
+lin_solve_xy_2 / lin_solve_psi_2) as tcgen05.mma in TF32 or BF16 with FP32
+accumulation, optionally as hi + lo splits; projections, QP steps and
+multipliers FP32.  Checked against the FP64 oracle:
+
+* ragged shapes (N not a multiple of the 16-sample chunk, n < 12 and n = 16,
+  no obstacles, B smaller than a tile): TF32 hi + lo to the FP32 parity bars,
+  BF16 hi + lo (16 significant bits per product) to 1e-2 m;
+* the precision workload (16384 goals, 30 obstacles, N = 200, n = 16) at its
+  full size, every 256th trajectory: the error table of the four modes, with
+  both split modes keeping FP32-class positions and the unsplit BF16 mode
+  missing the 1e-3 m bar;
+* a trajectory's result does not depend on its slot in the tile (the goals
+  are bucket-sorted into warps; permuting the goals permutes the results bit
+  for bit);
+* arguments the kernel cannot take are refused at setup.
+"""
+import numpy as np
+import pytest
+
+import parity_utils as U
+from paper_2109_10392_gb300 import mmpc, scenes
+
+pytestmark = pytest.mark.gpu
+
+NAMES = {mmpc.MMPC_PREC_TF32: "tf32", mmpc.MMPC_PREC_TF32_SPLIT: "tf32 hi+lo", mmpc.MMPC_PREC_BF16: "bf16",
+         mmpc.MMPC_PREC_BF16_SPLIT: "bf16 hi+lo"}
+
+BF16_TOL = 1e-2  # [m] positions of the BF16 hi + lo mode on the parity set
+
+# (N, n, m, B, iters): ragged chunk tails, both coefficient paddings, no obstacles
+SHAPES = [
+    (16, 7, 0, 3, 30),
+    (37, 10, 3, 5, 25),
+    (100, 12, 4, 40, 40),
+    (130, 12, 5, 3, 20),
+    (200, 16, 8, 4, 20),
+    (64, 13, 2, 3, 15),
+]
+
+
+@pytest.mark.parametrize("prec", [mmpc.MMPC_PREC_TF32_SPLIT, mmpc.MMPC_PREC_BF16_SPLIT])
+@pytest.mark.parametrize("N,n,m,B,iters", SHAPES)
+def test_shapes_split_modes(N, n, m, B, iters, prec):
+    sc = scenes.scene_custom(seed=N + n + m, B=B, m=m, N=N, n=n, x_range=(10.0, 150.0))
+    params = dict(sc.params, iters=iters)
+    ego, obst, goals = U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    gpu = U.gpu_solve(dict(params, variant=3, precision=prec), ego, obst, goals)
+    assert np.array_equal(gpu["iters"], orc["iters"])
+    if prec == mmpc.MMPC_PREC_TF32_SPLIT:
+        # 22 significant bits per product: the FP32 parity bars
+        U.check_parity(params, ego, obst, goals, gpu, orc)
+    else:
+        # BF16 hi + lo carries 16 significant bits: a 100 m position term
+        # keeps about 1e-3 m, so the bar is BF16_TOL on the parity set
+        err = U.pos_err(params, gpu["coef"], orc["coef"])
+        sens = U.sensitivity(params, ego, obst, goals, orc["coef"])
+        good = sens < U.SENS_TOL
+        assert good.mean() >= 0.3
+        assert np.all(err[good] <= BF16_TOL), err
+        assert np.all(np.isfinite(gpu["coef"]))
+        assert np.all(U.boundary_error(params, ego, goals, gpu["coef"]) < 1e-2)
+
+
+def test_eleven_goal_scene_tf32_split():
+    sc = scenes.scene_small(0)
+    ego, obst, goals = U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
+    params = dict(sc.params, tol=0.0)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    gpu = U.gpu_solve(dict(params, variant=3, precision=mmpc.MMPC_PREC_TF32_SPLIT), ego, obst, goals)
+    U.check_parity(params, ego, obst, goals, gpu, orc)
+    rel = np.abs(gpu["resid"] - orc["resid"]) / np.maximum(np.abs(orc["resid"]), 1e-3)
+    assert np.median(rel) < 1e-2
+
+
+def test_precision_workload_error_table(capsys):
+    sc = scenes.scene_custom(31, 16384, 30, N=200, n=16)
+    params = dict(sc.params, tol=0.0)
+    ego, obst, goals = U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
+    sel = np.arange(0, len(goals), 256)
+    orc = U.oracle_solve(params, ego, obst, goals[sel])
+    sens = U.sensitivity(params, ego, obst, goals[sel], orc["coef"], trials=1)
+    good = sens < U.SENS_TOL
+    fp32 = U.gpu_solve(params, ego, obst, goals)
+    err32 = U.pos_err(params, fp32["coef"][sel], orc["coef"])
+    rows = [f"  {'fp32 (CUDA cores)':>18}: parity set ({good.sum()}) median {np.median(err32[good]):.2e} max "
+            f"{err32[good].max():.2e} m, share <= 1e-3 m {np.mean(err32[good] <= U.POS_TOL):.2f}"]
+    med, share = {}, {}
+    for mode in NAMES:
+        gpu = U.gpu_solve(dict(params, variant=3, precision=mode), ego, obst, goals)
+        assert np.all(np.isfinite(gpu["coef"])), NAMES[mode]
+        err = U.pos_err(params, gpu["coef"][sel], orc["coef"])
+        med[mode] = float(np.median(err[good]))
+        share[mode] = float(np.mean(err[good] <= U.POS_TOL))
+        rows.append(f"  {NAMES[mode] + ' (tensor)':>18}: parity set ({good.sum()}) median {med[mode]:.2e} max "
+                    f"{err[good].max():.2e} m, share <= 1e-3 m {share[mode]:.2f}; all sampled median "
+                    f"{np.median(err):.2e} m")
+    with capsys.disabled():
+        print(f"\n[tensor-core modes, N = 200, n = 16, m = 30, sample {len(sel)} of 16384]")
+        print("\n".join(rows))
+    tf32, tf32s, bf16, bf16s = (mmpc.MMPC_PREC_TF32, mmpc.MMPC_PREC_TF32_SPLIT, mmpc.MMPC_PREC_BF16,
+                                mmpc.MMPC_PREC_BF16_SPLIT)
+    m32 = float(np.median(err32[good]))
+    # the splits keep FP32-class positions; the plain types do not
+    assert share[tf32s] >= 0.9 and share[bf16s] >= 0.9
+    assert med[tf32s] <= 2 * m32 and med[bf16s] <= 2 * m32
+    assert med[tf32s] <= med[tf32] and med[bf16s] <= med[bf16]
+    assert share[bf16] < 0.5 and med[bf16] > 1e-3
+
+
+def test_result_independent_of_slot():
+    """Permuting the goals permutes the results bit for bit (slot order,
+    tile and warp membership do not enter a trajectory's arithmetic)."""
+    sc = scenes.scene_custom(7, 700, 12, N=100, n=12)
+    params = dict(sc.params, tol=1e-2, variant=3, precision=mmpc.MMPC_PREC_BF16_SPLIT)
+    ego, obst, goals = U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
+    a = U.gpu_solve(params, ego, obst, goals)
+    perm = np.random.default_rng(3).permutation(len(goals))
+    b = U.gpu_solve(params, ego, obst, goals[perm])
+    for k in ("coef", "lam", "resid", "iters"):
+        assert np.array_equal(a[k][perm], b[k]), k
+
+
+def test_early_exit_matches_oracle_iterations():
+    sc = scenes.scene_custom(11, 48, 3, N=100, n=12, x_range=(30.0, 200.0))
+    params = dict(sc.params, tol=1e-2, check_every=10)
+    ego, obst, goals = U.f32(sc.ego), U.f32(sc.obst), U.f32(sc.goals)
+    gpu = U.gpu_solve(dict(params, variant=3, precision=mmpc.MMPC_PREC_TF32_SPLIT), ego, obst, goals)
+    orc = U.oracle_solve(params, ego, obst, goals)
+    conv = orc["iters"] < params["iters"]
+    assert conv.sum() >= 10
+    # converging trajectories stop at the same check as the oracle (or the next)
+    assert np.all(np.abs(gpu["iters"][conv] - orc["iters"][conv]) <= params["check_every"])
+
+
+def test_arguments():
+    base = dict(scenes.scene_custom(1, 4, 3, N=100, n=12).params)
+    for bad in (dict(base, variant=3, precision=0), dict(base, variant=3, precision=2, N=300),
+                dict(base, variant=4, precision=2)):
+        with pytest.raises(mmpc.MmpcError):
+            mmpc.Solver(bad, 3)
+    with pytest.raises(mmpc.MmpcError):
+        mmpc.Solver(dict(base, variant=3, precision=2), 129)
+    s = mmpc.Solver(dict(base, variant=3, precision=4), 128)
+    s.close()
