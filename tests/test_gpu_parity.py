@@ -80,19 +80,35 @@ def test_shapes(N, n, m, B, iters, variant):
 
 
 @pytest.mark.parametrize("variant", [0, 2])
-def test_full_size_sampled(variant):
+def test_full_size_sampled(variant, capsys):
     """The 1024-goal, 50-obstacle scene in the launch configuration the
-    benchmark times (variant 0: automatic, as the benchmark runs it); the
-    oracle runs on every 8th trajectory, with the conditioning probe."""
+    benchmark times (variant 0: automatic, as the benchmark runs it).  The
+    oracle solves all 1024 goals: meta costs within 1e-4 relative on the
+    parity set and the batch argmin over all goals, unconditionally (the GPU's
+    choice is the oracle's, or the two costs are within the cost tolerance of
+    each other); positions with the conditioning probe on every 8th goal,
+    whose parity-set share is printed and held to 0.45 (measured 0.484)."""
     sc = scenes.scene_large(0)
     sc.params["variant"] = variant
     ego, obst, goals = _scene_arrays(sc)
     gpu = U.gpu_solve(sc.params, ego, obst, goals)
+    orc_all = U.oracle_solve(sc.params, ego, obst, goals)
     sel = np.arange(0, len(goals), 8)
-    orc = U.oracle_solve(sc.params, ego, obst, goals[sel])
+    orc = {k: v[sel] for k, v in orc_all.items()}
     sens = U.sensitivity(sc.params, ego, obst, goals[sel], orc["coef"])
     gs = {k: v[sel] for k, v in gpu.items()}
-    _check_parity(sc.params, ego, obst, goals[sel], gs, orc, sens=sens)
+    err, good = _check_parity(sc.params, ego, obst, goals[sel], gs, orc, sens=sens, min_frac=0.45)
+    cg, ag = U.gpu_score(sc.params, obst.shape[0], gpu["coef"], sc.meta)
+    co, ao = U.meta_oracle(sc.params, orc_all["coef"], sc.meta)
+    fin = np.isfinite(co[sel]) & good
+    rel = np.abs(cg[sel][fin] - co[sel][fin]) / np.maximum(np.abs(co[sel][fin]), 1e-9)
+    with capsys.disabled():
+        print(f"\n[1024 goals, variant {variant}] parity set {good.mean():.3f} of {len(sel)}; position error "
+              f"max {err[good].max():.2e} m; meta cost rel error max {rel.max():.2e}; argmin gpu {ag} "
+              f"oracle {ao} (costs {co[ag]:.6g} / {co[ao]:.6g})")
+    assert np.all(rel <= U.COST_RTOL)
+    assert ao >= 0 and ag >= 0
+    assert ag == ao or abs(co[ag] - co[ao]) <= U.COST_RTOL * abs(co[ao])
 
 
 def test_cold_start_only():
