@@ -1963,8 +1963,8 @@ int launch_kernel(mmpc_ctx* ctx, K kern, const SolveArgs& a, int threads, size_t
     return MMPC_OK;
 }
 
-// Variant 3, the tensor-core kernel: tiles of TT = min(128, ceil(B / SMs))
-// trajectories, one CTA (384 threads, all 512 tensor-memory columns) per tile.
+// Variant 3, the tensor-core kernel: persistent CTAs (384 threads, all 512
+// tensor-memory columns, one per SM) taking items of 32 goals from a queue.
 template <int NC>
 void* tc_kernel(int prec)
 {
@@ -1979,7 +1979,7 @@ void* tc_kernel(int prec)
 size_t tc_smem(const mmpc_ctx* ctx, int m)
 {
     const int nmat = ctx->L.init - ctx->L.Q;
-    return (size_t)ctx->tc.bytes + sizeof(float) * (size_t)((nmat + 3) & ~3) + 32 * (size_t)m +
+    return (size_t)ctx->tc.bytes + sizeof(float) * (size_t)((nmat + 3) & ~3) + 128 * (size_t)m +
            sizeof(int) * (size_t)(TC_THREADS / 32) * m + sizeof(float) * 3 * 128 * 4 +
            sizeof(float) * (size_t)ctx->tc.NSP;
 }
@@ -2000,15 +2000,16 @@ int launch_tc(mmpc_ctx* ctx, const SolveArgs& a, int B, cudaStream_t st)
             cudaFree(ctx->d_order);
             ctx->d_order = nullptr;
             ctx->order_cap = 0;
-            e = cudaMalloc(&ctx->d_order, sizeof(int) * ((size_t)TC_BUCKETS + cap));
+            e = cudaMalloc(&ctx->d_order, sizeof(int) * ((size_t)4 + TC_BUCKETS + cap));
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "variant 3 order buffer");
         ctx->order_cap = cap;
     }
-    int* count = ctx->d_order;
-    int* order = ctx->d_order + TC_BUCKETS;
+    int* queue = ctx->d_order;  // [queue | pad to 4 | bucket counts | order]
+    int* count = ctx->d_order + 4;
+    int* order = ctx->d_order + 4 + TC_BUCKETS;
     const int og = std::min(1024, (B + 255) / 256);
-    cudaError_t e0 = cudaMemsetAsync(count, 0, sizeof(int) * TC_BUCKETS, st);
+    cudaError_t e0 = cudaMemsetAsync(ctx->d_order, 0, sizeof(int) * (4 + TC_BUCKETS), st);
     if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "cudaMemsetAsync");
     tc_order_count<<<og, 256, 0, st>>>(a.goals, B, count);
     tc_order_scan<<<1, 1024, 0, st>>>(count);
@@ -2016,8 +2017,11 @@ int launch_tc(mmpc_ctx* ctx, const SolveArgs& a, int B, cudaStream_t st)
     TcArgs T{};
     T.blob = ctx->d_tc;
     T.L = ctx->tc;
-    T.TT = std::min(128, std::max(1, (B + ctx->sm_count - 1) / ctx->sm_count));
+    T.scenes = nullptr;
+    T.items = nullptr;
+    T.n_items = (B + 31) / 32;
     T.order = order;
+    T.queue = queue;
     // at least 116 KB, so that one CTA holds an SM (it allocates all of the
     // SM's tensor memory; a second CTA would only wait in tcgen05.alloc)
     const size_t smem = std::max<size_t>(tc_smem(ctx, a.m), 116 * 1024);
@@ -2026,7 +2030,8 @@ int launch_tc(mmpc_ctx* ctx, const SolveArgs& a, int B, cudaStream_t st)
     K kern = reinterpret_cast<K>(ctx->NC == 12 ? tc_kernel<12>(ctx->p.precision) : tc_kernel<16>(ctx->p.precision));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
-    const int grid = (B + T.TT - 1) / T.TT;
+    // persistent: one CTA per SM (or fewer, four items each to start)
+    const int grid = std::max(1, std::min(ctx->sm_count, (T.n_items + 3) / 4));
     kern<<<grid, TC_THREADS, smem, st>>>(a, T);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core solve launch");

@@ -94,11 +94,17 @@ static TcLayout tc_layout(int N, int esz, int parts)
     return T;
 }
 
+// Work of the persistent kernel: items of up to 32 trajectories of one scene
+// (one warp's lanes), taken from a queue.  An item is (scene, first position
+// in the scene's slot order, count, offset of the scene's order entries).
 struct TcArgs {
     const unsigned char* blob;  // device, tc_layout bytes
     TcLayout L;
-    int TT;                     // trajectories per tile (<= 128)
-    const int* order;           // trajectory of each slot position (tile-major), or NULL (identity)
+    const SolveArgs* scenes;    // per-scene arguments (device), or NULL: one scene, the kernel's own
+    const int4* items;          // device, or NULL: one scene, items of 32 consecutive positions
+    int n_items;
+    const int* order;           // goal index (within its scene) of each position
+    int* queue;                 // item counter, zero at the launch
 };
 
 // Slot order: trajectories with similar goals share a warp, so that the
@@ -157,6 +163,31 @@ __global__ void tc_order_scatter(const float* __restrict__ goals, int B, int* __
 {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < B; l += gridDim.x * blockDim.x)
         order[atomicAdd(next + tc_bucket(goals + 3 * l), 1)] = l;
+}
+
+// The same order for every scene of a batch (one CTA per scene, at most
+// TC_RANK_MAX goals): goal i goes to position rank(i) = #{j : (bucket_j, j) <
+// (bucket_i, i)}, a stable, deterministic sort.
+constexpr int TC_RANK_MAX = 8192;
+
+__global__ void __launch_bounds__(256) tc_order_rank(const SolveArgs* __restrict__ sc, const int* __restrict__ scene_off,
+                                                     int* __restrict__ order)
+{
+    __shared__ short key[TC_RANK_MAX];
+    const SolveArgs& A = sc[blockIdx.x];
+    const int B = A.B;
+    const int off = scene_off[blockIdx.x];
+    for (int i = threadIdx.x; i < B; i += blockDim.x) key[i] = (short)tc_bucket(A.goals + 3 * i);
+    __syncthreads();
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        const int ki = key[i];
+        int r = 0;
+        for (int j = 0; j < B; ++j) {
+            const int kj = key[j];
+            r += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+        }
+        order[off + r] = i;
+    }
 }
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
@@ -613,22 +644,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = warp >> 2, q = warp & 3;  // axis group, tensor-memory sub-partition
     const int t = 32 * q + lane;            // trajectory slot
-    const int pos = blockIdx.x * T.TT + t;
-    const bool slot = t < T.TT && pos < A.B;
-    const int l = slot && T.order ? T.order[pos] : pos;
     const int N = A.N, m = A.m;
     const BlobLayout& L = A.L;
     const TcLayout& TL = T.L;
 
     // shared memory: [tensor-core blob | Q, K11 x hi, lo, y hi, lo, K11_psi |
-    // obstacles | culling lists | residual partial sums | sample times]
+    // obstacles of each sub-partition's scene [4][m][2] | culling lists |
+    // residual partial sums | sample times]
     float* mats = reinterpret_cast<float*>(tsm + TL.bytes);
     const int nmat = L.init - L.Q;
-    float4* obs = reinterpret_cast<float4*>(mats + ((nmat + 3) & ~3));
-    int* lists = reinterpret_cast<int*>(obs + 2 * m);
+    float4* obs_all = reinterpret_cast<float4*>(mats + ((nmat + 3) & ~3));
+    int* lists = reinterpret_cast<int*>(obs_all + 8 * m);
     float* part = reinterpret_cast<float*>(lists + 12 * m);  // [3][128][4]
     float* tgrid = part + 3 * 128 * 4;                       // sample times [NSP]
     int* olist = lists + warp * m;
+    const float4* obs = obs_all + q * 2 * m;                 // this warp's scene
+    __shared__ int4 s_item[4];     // current item of each sub-partition
+    __shared__ int s_new[4];       // whether it was taken at this refill
+    __shared__ float4 s_ego[4];    // (y0, v0, psi0, acc0) of its scene
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -636,16 +669,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    const float y0 = __ldg(A.ego + 0), v0 = __ldg(A.ego + 1), psi0 = __ldg(A.ego + 2), acc0 = __ldg(A.ego + 3);
-    for (int j = tid; j < m; j += TC_THREADS) {
-        const float* o = A.obst + 4 * j;
-        const float px = -__ldg(o + 0) * A.inv_a, py = -__ldg(o + 1) * A.inv_b;
-        const float pvx = -(__ldg(o + 2) - v0) * A.inv_a, pvy = -__ldg(o + 3) * A.inv_b;
-        obs[2 * j] = make_float4(px, px, pvx, pvx);
-        obs[2 * j + 1] = make_float4(py, py, pvy, pvy);
-    }
     for (int i = tid; i < nmat; i += TC_THREADS) mats[i] = __ldg(A.blob + L.Q + i);
     for (int i = tid; i < TL.NSP; i += TC_THREADS) tgrid[i] = i < N ? __ldg(A.blob + L.t + i) : 0.f;
+    if (tid < 4) s_item[tid] = make_int4(-1, 0, 0, 0);
     const bool staged = stage_blob(reinterpret_cast<float*>(tsm), reinterpret_cast<const float*>(T.blob), TL.bytes,
                                    &s_stage, A.err_flag, A.missing_tx);
     const uint32_t bar = smem_u32(&s_mma);
@@ -661,14 +687,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     const uint32_t sm_base = smem_u32(tsm);
     uint32_t mma_phase = 0;
     bool ok = staged;
+    const int n = A.n;
 
     // ---- state of this thread's axis (g: 0 x, 1 y, 2 psi) for slot t ----
     float c[16], e[16], lam[16];  // e: compensation (x, y); K12_psi b_psi (psi)
 #pragma unroll
     for (int k = 0; k < 16; ++k) c[k] = e[k] = lam[k] = 0.f;
-    const int n = A.n;
-    if (slot) {
-        const float* gl = A.goals + 3 * l;
+    int l = 0;            // the slot's goal within its scene
+    float v0 = 0.f;       // speed of the sub-partition's ego (the moving frame)
+
+    // initial iterate of goal l of scene As (cold start, or warm start
+    // projected onto the boundary rows by the first step)
+    auto init_slot = [&](const SolveArgs& As, float4 ego) {
+        const float y0 = ego.x, psi0 = ego.z, acc0 = ego.w;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = e[k] = lam[k] = 0.f;
+        const float* gl = As.goals + 3 * l;
         const float yg = __ldg(gl + 0), vg = __ldg(gl + 1), ag = __ldg(gl + 2);
         float cpsi, spsi;
         sincosf(psi0, &spsi, &cpsi);
@@ -680,19 +714,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             const int nb = isy ? 6 : 5;
             const float* C0 = A.blob + (isy ? L.C0y : L.C0x);
             const float* K12 = A.blob + (isy ? L.K12y : L.K12x);
-            if (A.warm_c) {
+            if (As.warm_c) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
                     if (k < n)
-                        c[k] = __ldg(A.warm_c + wo + (isy ? n : 0) + k) - (isy ? 0.f : v0 * __ldg(A.blob + L.lin + k));
+                        c[k] = __ldg(As.warm_c + wo + (isy ? n : 0) + k) - (isy ? 0.f : v0 * __ldg(A.blob + L.lin + k));
             } else {
 #pragma unroll
                 for (int k = 0; k < NC; ++k) {
-                    float s = 0.f;
+                    float sacc = 0.f;
 #pragma unroll
                     for (int r = 0; r < 6; ++r)
-                        if (r < nb) s = fmaf(__ldg(C0 + k * 8 + r), isy ? by[r] : bx[r], s);
-                    c[k] = s;
+                        if (r < nb) sacc = fmaf(__ldg(C0 + k * 8 + r), isy ? by[r] : bx[r], sacc);
+                    c[k] = sacc;
                 }
             }
             // K12 (b - A c^0): added by the first step (the start's boundary rows)
@@ -701,55 +735,134 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
 #pragma unroll
             for (int r = 0; r < 6; ++r) {
                 const int row = isy ? r : rx[r];
-                float s = 0.f;
+                float sacc = 0.f;
 #pragma unroll
-                for (int k = 0; k < NC; ++k) s = fmaf(__ldg(A.blob + L.brow + row * NC + k), c[k], s);
-                res[r] = (isy ? by[r] : bx[r]) - s;
+                for (int k = 0; k < NC; ++k) sacc = fmaf(__ldg(A.blob + L.brow + row * NC + k), c[k], sacc);
+                res[r] = (isy ? by[r] : bx[r]) - sacc;
             }
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
-                float s = 0.f;
+                float sacc = 0.f;
 #pragma unroll
                 for (int r = 0; r < 6; ++r)
-                    if (r < nb) s = fmaf(__ldg(K12 + k * 8 + r), res[r], s);
-                e[k] = s;
+                    if (r < nb) sacc = fmaf(__ldg(K12 + k * 8 + r), res[r], sacc);
+                e[k] = sacc;
             }
-            if (A.warm_l) {
+            if (As.warm_l) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < n) lam[k] = __ldg(A.warm_l + wo + (isy ? n : 0) + k);
+                    if (k < n) lam[k] = __ldg(As.warm_l + wo + (isy ? n : 0) + k);
             }
         } else {
             const float bp[4] = {psi0, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
-                float s = 0.f, s0 = 0.f;
+                float sacc = 0.f, s0 = 0.f;
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    s = fmaf(__ldg(A.blob + L.Kp12 + k * 4 + r), bp[r], s);
+                    sacc = fmaf(__ldg(A.blob + L.Kp12 + k * 4 + r), bp[r], sacc);
                     s0 = fmaf(__ldg(A.blob + L.C0p + k * 4 + r), bp[r], s0);
                 }
-                e[k] = s;
+                e[k] = sacc;
                 c[k] = s0;
             }
-            if (A.warm_c) {
+            if (As.warm_c) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < n) c[k] = __ldg(A.warm_c + wo + 2 * n + k);
+                    if (k < n) c[k] = __ldg(As.warm_c + wo + 2 * n + k);
             }
-            if (A.warm_l) {
+            if (As.warm_l) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < n) lam[k] = __ldg(A.warm_l + wo + 2 * n + k);
+                    if (k < n) lam[k] = __ldg(As.warm_l + wo + 2 * n + k);
             }
         }
-    }
+    };
 
-    bool done = !slot;
+    bool done = true;    // the slot holds no active trajectory
+    bool fresh = false;  // its trajectory was placed at this iteration (its pass 0)
     int kit = 0, it = 0;
     float rsum[4] = {0.f, 0.f, 0.f, 0.f};
     float rh1 = INFINITY, rh2 = INFINITY;  // convergence residuals of the last two checks
     unsigned long long work = 0;
+    auto scene = [&](int sidx) -> const SolveArgs& { return T.scenes ? T.scenes[sidx] : A; };
+
+    // Refill, at iterations that are multiples of check_every (so that every
+    // trajectory's checks fall on the same iterations): a sub-partition whose
+    // 32 slots are all done takes the next item from the queue; its scene's
+    // obstacles (moving frame of its ego speed) go to the sub-partition's
+    // shared-memory block, and its slots are initialised.
+    auto refill = [&]() {
+        if (g == 0) {
+            const bool empty = __all_sync(FULL, done);
+            if (lane == 0) {
+                int take = 0;
+                if (empty && s_item[q].x != -2) {
+                    const int k = atomicAdd(T.queue, 1);
+                    if (k < T.n_items) {
+                        s_item[q] = T.items ? T.items[k] : make_int4(0, 32 * k, min(32, A.B - 32 * k), 0);
+                        take = 1;
+                    } else {
+                        s_item[q] = make_int4(-2, 0, 0, 0);  // drained
+                    }
+                }
+                s_new[q] = take;
+            }
+        }
+        __syncthreads();
+        if (g == 0 && s_new[q]) {
+            const SolveArgs& As = scene(s_item[q].x);
+            const float4 eg = make_float4(__ldg(As.ego + 0), __ldg(As.ego + 1), __ldg(As.ego + 2), __ldg(As.ego + 3));
+            if (lane == 0) s_ego[q] = eg;
+            float4* ob = obs_all + q * 2 * m;
+            for (int j = lane; j < m; j += 32) {
+                const float* o = As.obst + 4 * j;
+                const float px = -__ldg(o + 0) * A.inv_a, py = -__ldg(o + 1) * A.inv_b;
+                const float pvx = -(__ldg(o + 2) - eg.y) * A.inv_a, pvy = -__ldg(o + 3) * A.inv_b;
+                ob[2 * j] = make_float4(px, px, pvx, pvx);
+                ob[2 * j + 1] = make_float4(py, py, pvy, pvy);
+            }
+        }
+        __syncthreads();
+        if (s_new[q]) {
+            const int4 item = s_item[q];
+            const float4 eg = s_ego[q];
+            v0 = eg.y;
+            if (lane < item.z) {
+                const int posn = item.y + lane;
+                l = T.order ? T.order[item.w + posn] : posn;
+                init_slot(scene(item.x), eg);
+                done = false;
+                fresh = true;
+                kit = 0;
+                rh1 = rh2 = INFINITY;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) rsum[r] = 0.f;
+            }
+        }
+    };
+
+    // this slot's outputs (its axis; group 0 also residuals and iterations)
+    auto write_out = [&]() {
+        const SolveArgs& As = scene(s_item[q].x);
+        const size_t o = (size_t)l * 3 * n;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < n) {
+                const float v =
+                    g == 0 ? (c[k] + e[k]) + v0 * __ldg(A.blob + L.lin + k) : (g == 1 ? c[k] + e[k] : c[k]);
+                As.coef_out[o + g * n + k] = v;
+                if (As.lam_out) As.lam_out[o + g * n + k] = lam[k];
+            }
+        }
+        if (g == 0) {
+            if (As.resid_out) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) As.resid_out[(size_t)l * 4 + r] = sqrtf(rsum[r]);
+            }
+            if (As.iters_out) As.iters_out[l] = kit;
+        }
+    };
     const int nch = TL.NSP / TC_CS;
     const uint32_t gslot = TC_BUF + (uint32_t)(g * TC_CS);  // this group's 16 columns of each channel
 
@@ -919,6 +1032,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
             rh1 = conv;
         }
         if (dn) {
+            write_out();
             done = true;
             return;
         }
@@ -941,7 +1055,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     auto psi_step = [&]() {
         float pth[16];
         tc_ld16(tl + TC_DC + 48u, pth);
-        if (done || g != 2) return;
+        if (done || fresh || g != 2) return;
         float vec[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) vec[k] = k < NC ? fmaf(A.rho, pth[k], lam[k]) : 0.f;
@@ -950,35 +1064,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
         for (int k = 0; k < NC; ++k) c[k] = e[k] + tc_dot<NC>(Kp + k * KS, vec);
     };
 
-    if (ok) {
-        // initial pass (iterate 0): auxiliaries and F^T (F c^0 - g^0), then the first step
-        tc_write_coef<PREC>(tl, g, c);
-        tc_sync();
-        float r4[4] = {0.f, 0.f, 0.f, 0.f};
-        ok = phase(false, true, r4);
-        if (ok) {
-            exchange(r4);
-            finish(true, true);
-        }
-        while (ok) {
+    // One iteration of every slot per pass of the loop; a slot placed at
+    // this iteration runs its initial pass (iterate 0: auxiliaries and
+    // F^T (F c^0 - g^0), then the first step) while the others run Algorithm
+    // 1's iteration (heading QP, projections, multipliers, xy QP).
+    while (ok) {
+        if (it % A.check_every == 0) refill();
+        if (!__syncthreads_or(!done)) break;
+        if (!done) kit = fresh ? 0 : kit + 1;
+        const bool need = !done && (fresh || kit % A.check_every == 0 || kit >= A.iters);
+        const bool check = __syncthreads_or(need) != 0;
+        if (__syncthreads_or(!done && !fresh)) {
             if (g < 2) tc_write_coef<PREC>(tl, g, c);
             tc_sync();
-            if (!__syncthreads_or(!done)) break;
-            ++it;  // the tile's iteration; a slot's own count stops when it is done
-            if (!done) kit = it;
-            const bool check = (it % A.check_every == 0) || it >= A.iters;
             float rz[4] = {0.f, 0.f, 0.f, 0.f};
             ok = phase(true, false, rz);
             if (!ok) break;
             psi_step();
-            if (g == 2) tc_write_coef<PREC>(tl, g, c);
-            tc_sync();
-            float rr[4] = {0.f, 0.f, 0.f, 0.f};
-            ok = phase(false, check, rr);
-            if (!ok) break;
-            if (check) exchange(rr);
-            finish(false, check);
         }
+        tc_write_coef<PREC>(tl, g, c);
+        tc_sync();
+        float rr[4] = {0.f, 0.f, 0.f, 0.f};
+        ok = phase(false, check, rr);
+        if (!ok) break;
+        if (check) exchange(rr);
+        finish(fresh, need);
+        fresh = false;
+        ++it;
     }
     if (!ok) {
         // an expired wait: record it, then let the tensor core finish what was
@@ -987,24 +1099,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
         if (staged) {
             if (tid == 0) tc_commit(bar);
             tc_wait(bar, mma_phase);
-        }
-    } else if (slot) {
-        const size_t o = (size_t)l * 3 * n;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (k < n) {
-                const float v =
-                    g == 0 ? (c[k] + e[k]) + v0 * __ldg(A.blob + L.lin + k) : (g == 1 ? c[k] + e[k] : c[k]);
-                A.coef_out[o + g * n + k] = v;
-                if (A.lam_out) A.lam_out[o + g * n + k] = lam[k];
-            }
-        }
-        if (g == 0) {
-            if (A.resid_out) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) A.resid_out[(size_t)l * 4 + r] = sqrtf(rsum[r]);
-            }
-            if (A.iters_out) A.iters_out[l] = kit;
         }
     }
     if (lane == 0 && A.work && work) atomicAdd(A.work, work);
