@@ -1976,6 +1976,11 @@ void* tc_kernel(int prec)
     }
 }
 
+void* tc_kernel_of(const mmpc_ctx* ctx)
+{
+    return ctx->NC == 12 ? tc_kernel<12>(ctx->p.precision) : tc_kernel<16>(ctx->p.precision);
+}
+
 size_t tc_smem(const mmpc_ctx* ctx, int m)
 {
     const int nmat = ctx->L.init - ctx->L.Q;
@@ -2116,7 +2121,10 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
 
     if (p->variant == 3 && m > TC_MAX_M) return fail(nullptr, MMPC_ERR_SHAPE, "variant 3 takes at most 128 obstacles");
     const int NC = n <= 12 ? 12 : 16;
-    const int prec = p->precision;
+    // the CUDA-core rows carry the emulated precision modes (variants 0 and
+    // 2); with variant 3 the tensor cores take the precision and these rows
+    // (used by the FP32 fallback and scoring) stay FP32
+    const int prec = p->variant == 3 ? MMPC_PREC_FP32 : p->precision;
     const BlobLayout L = blob_layout(N, NC, prec_split(prec));
     std::vector<float> h(L.total, 0.f);
     auto h_set = [&](int i, float v) { h[i] = v; };
@@ -2177,9 +2185,10 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
     std::vector<unsigned char> htc;
     TcLayout TL{};
     if (p->variant == 3) {
-        const bool bf = prec == MMPC_PREC_BF16 || prec == MMPC_PREC_BF16_SPLIT;
+        const int tprec = p->precision;
+        const bool bf = tprec == MMPC_PREC_BF16 || tprec == MMPC_PREC_BF16_SPLIT;
         const int esz = bf ? 2 : 4, per = 16 / esz;
-        TL = tc_layout(N, esz, prec_split(prec) ? 2 : 1);
+        TL = tc_layout(N, esz, prec_split(tprec) ? 2 : 1);
         htc.assign(TL.bytes, 0);
         const size_t src[3] = {PL.P, PL.Pd, PL.Pdd};
         auto put = [&](int off, float v) {
@@ -2196,8 +2205,8 @@ extern "C" int mmpc_setup(const mmpc_params* p, int m, const double* buf, size_t
             for (int smp = 0; smp < N; ++smp)
                 for (int k = 0; k < n; ++k) {
                     const double v = buf[src[b] + (size_t)smp * n + k];
-                    const float hi = round_operand((float)v, prec);
-                    const float lo = round_operand((float)(v - (double)hi), prec);
+                    const float hi = round_operand((float)v, tprec);
+                    const float lo = round_operand((float)(v - (double)hi), tprec);
                     for (int part = 0; part < TL.parts; ++part) {
                         const float x = part == 0 ? hi : lo;
                         put(TL.eb[b][part] + (k / per) * TL.NSP * 16 + 16 * smp + (k % per) * esz, x);
@@ -2656,6 +2665,14 @@ struct mmpc_batch {
     int2* d_fb_items = nullptr;               // fallback list
     int* d_counts = nullptr;                  // [0] items, [1] fallback items, [2 + g] items of group g
     int fallback = 0;  // 0 off, 1 every miss, 2 misses that ran the whole budget
+    // one context of variant 3 for every scene: the solve runs on the
+    // tensor-core kernel over items of 32 goals (the fallback stays FP32)
+    bool tc = false;
+    int tc_items = 0;
+    size_t tc_smem_bytes = 0;
+    int4* d_tc_items = nullptr;  // (scene, first position, count, order offset)
+    int* d_tc_off = nullptr;     // order offset of each scene
+    int* d_tc_order = nullptr;   // [queue | pad to 4 | goal index of each position]
     bool any_warm = false;
     cudaEvent_t timing[4] = {};  // optional: around the solve launch(es) and the fallback launch
     // horizon groups (schedule 4): scenes with the same pair-thread count,
@@ -2687,6 +2704,9 @@ void batch_free(mmpc_batch* b)
     if (!b) return;
     cudaFree(b->d_args);
     cudaFree(b->d_args_cold);
+    cudaFree(b->d_tc_items);
+    cudaFree(b->d_tc_off);
+    cudaFree(b->d_tc_order);
     cudaFree(b->d_sargs);
     cudaFree(b->d_items);
     cudaFree(b->d_fb_items);
@@ -2770,9 +2790,19 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         if (!c || !c->d_blob) { batch_free(b); return batch_fail("mmpc_batch_create: scene without a set-up context", MMPC_ERR_NOT_SETUP); }
         if (s == 0) b->NC = c->NC;
         if (c->NC != b->NC) { batch_free(b); return batch_fail("mmpc_batch_create: scenes mix n <= 12 and n > 12", MMPC_ERR_SHAPE); }
-        if (c->p.precision != MMPC_PREC_FP32) {
+        if (s == 0) b->tc = c->p.variant == 3;
+        if (c->p.precision != MMPC_PREC_FP32 && !(b->tc && c == scenes[0].ctx)) {
             batch_free(b);
-            return batch_fail("mmpc_batch_create: precision modes run through mmpc_solve only", MMPC_ERR_INVALID_ARG);
+            return batch_fail("mmpc_batch_create: precision modes run in batches only as variant 3 with one context "
+                              "for every scene", MMPC_ERR_INVALID_ARG);
+        }
+        if (b->tc && c != scenes[0].ctx) {
+            batch_free(b);
+            return batch_fail("mmpc_batch_create: a variant 3 batch takes one context for every scene", MMPC_ERR_INVALID_ARG);
+        }
+        if (b->tc && sc.B > TC_RANK_MAX) {
+            batch_free(b);
+            return batch_fail("mmpc_batch_create: variant 3 batches take at most 8192 goals per scene", MMPC_ERR_SHAPE);
         }
         if (sc.B < 0 || !sc.ego || (c->m > 0 && !sc.obst) || (sc.B > 0 && (!sc.goals || !sc.coef_out || !sc.cost_out)) || !sc.argmin_out) {
             batch_free(b);
@@ -2900,6 +2930,33 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
     }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_sargs, b->sargs.data(), sizeof(ScoreArgs) * S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_scratch, 0, sizeof(unsigned long long) * nscratch);
+    if (e == cudaSuccess && b->tc) {
+        // items of 32 goals in each scene's slot order (the order itself is
+        // computed on the device by every run, from the current goals)
+        std::vector<int4> items;
+        std::vector<int> off(S);
+        int o = 0;
+        for (int s = 0; s < S; ++s) {
+            off[s] = o;
+            for (int p0 = 0; p0 < scenes[s].B; p0 += 32) items.push_back(make_int4(s, p0, std::min(32, scenes[s].B - p0), o));
+            o += scenes[s].B;
+        }
+        b->tc_items = (int)items.size();
+        const mmpc_ctx* c = scenes[0].ctx;
+        b->tc_smem_bytes = std::max<size_t>(tc_smem(c, c->m), 116 * 1024);
+        if (b->tc_smem_bytes > 227 * 1024) {
+            batch_free(b);
+            return batch_fail("mmpc_batch_create: scenes do not fit in shared memory", MMPC_ERR_SHAPE);
+        }
+        e = cudaMalloc(&b->d_tc_items, sizeof(int4) * std::max<size_t>(1, items.size()));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_tc_off, sizeof(int) * S);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_tc_order, sizeof(int) * (4 + (size_t)std::max(1, o)));
+        if (e == cudaSuccess && !items.empty())
+            e = cudaMemcpy(b->d_tc_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_tc_off, off.data(), sizeof(int) * S, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tc_kernel_of(c), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->tc_smem_bytes);
+    }
     if (e != cudaSuccess) {
         batch_free(b);
         return batch_fail(std::string("mmpc_batch_create: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
@@ -2931,7 +2988,30 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
     if (b->total > 0) {
         if (b->timing[0]) cudaEventRecord(b->timing[0], st);
         using KernT = void (*)(const SolveArgs*, const int2*, const int*, unsigned long long*, unsigned long long*);
-        if (b->schedule == 4) {
+        if (b->tc) {
+            // tensor-core kernel over every scene: each scene's goals ordered
+            // (one CTA per scene), then persistent CTAs over the item queue
+            const mmpc_ctx* c = b->scenes[0].ctx;
+            cudaMemsetAsync(b->d_tc_order, 0, sizeof(int) * 4, st);
+            tc_order_rank<<<b->S, 256, 0, st>>>(b->d_args, b->d_tc_off, b->d_tc_order + 4);
+            TcArgs T{};
+            T.blob = c->d_tc;
+            T.L = c->tc;
+            T.scenes = b->d_args;
+            T.items = b->d_tc_items;
+            T.n_items = b->tc_items;
+            T.order = b->d_tc_order + 4;
+            T.queue = b->d_tc_order;
+            int sms = c->sm_count;
+            if (sms < 0) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            }
+            const int grid = std::max(1, std::min(sms, (b->tc_items + 3) / 4));
+            using K3 = void (*)(const SolveArgs, const TcArgs);
+            reinterpret_cast<K3>(tc_kernel_of(c))<<<grid, TC_THREADS, b->tc_smem_bytes, st>>>(b->args[0], T);
+        } else if (b->schedule == 4) {
             // one right-sized persistent launch per horizon group, on forked
             // streams joined back before scoring (capturable in a graph)
             cudaEventRecord(b->fork, st);

@@ -145,3 +145,82 @@ def test_arguments():
         mmpc.Solver(dict(base, variant=3, precision=2), 129)
     s = mmpc.Solver(dict(base, variant=3, precision=4), 128)
     s.close()
+
+
+def _batch(params, ego, obst, goals, warm_coef=None, warm_lam=None):
+    import torch
+    t = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda:0").contiguous()  # noqa: E731
+    return mmpc.Batch.from_uniform(params, t(ego), t(obst), t(goals), scenes.META_ABS, want_lam=True,
+                                   warm_coef=warm_coef, warm_lam=warm_lam)
+
+
+def test_batch_matches_single_scene_solves():
+    """A batch of scenes on the tensor-core kernel (one persistent launch over
+    all scenes' 32-goal items, uneven last items) reproduces each scene
+    solved alone, bit for bit, and the same again when replayed from a CUDA
+    graph."""
+    import torch
+    S, B, m = 6, 70, 8
+    ego, obst, goals = scenes.scene_stack(5, S, B, m, (10.0, 150.0))
+    ego, obst, goals = U.f32(ego), U.f32(obst), U.f32(goals)
+    params = dict(scenes.BASE_PARAMS, tol=1e-2, variant=3, precision=mmpc.MMPC_PREC_TF32_SPLIT)
+    bt = _batch(params, ego, obst, goals)
+    bt.run()
+    torch.cuda.synchronize()
+    first = {k: bt.flat[k].clone() for k in ("coef", "lam", "resid", "iters", "cost")}
+    n = params["n"]
+    for s in range(S):
+        one = U.gpu_solve(params, ego[s], obst[s], goals[s])
+        sl = slice(s * B, (s + 1) * B)
+        assert np.array_equal(first["coef"].view(-1, 3 * n)[sl].double().cpu().numpy(), one["coef"])
+        assert np.array_equal(first["lam"].view(-1, 3 * n)[sl].double().cpu().numpy(), one["lam"])
+        assert np.array_equal(first["resid"].view(-1, 4)[sl].double().cpu().numpy(), one["resid"])
+        assert np.array_equal(first["iters"][sl].cpu().numpy(), one["iters"])
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        bt.run()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=st):
+        bt.run()
+    g.replay()
+    torch.cuda.synchronize()
+    for k, v in first.items():
+        assert torch.equal(bt.flat[k], v), k
+    bt.status()
+    bt.close()
+
+
+def test_batch_against_oracle_with_warm_start_and_fallback():
+    """Warm-started tensor-core batch with the FP32 cold fallback of the
+    misses: converged trajectories and the re-solved misses both match the
+    oracle (positions on the parity set)."""
+    import torch
+    S, B, m = 3, 40, 6
+    ego, obst, goals = scenes.scene_stack(9, S, B, m, (10.0, 150.0))
+    ego, obst, goals = U.f32(ego), U.f32(obst), U.f32(goals)
+    params = dict(scenes.BASE_PARAMS, tol=1e-2, variant=3, precision=mmpc.MMPC_PREC_TF32_SPLIT)
+    # warm starts: the oracle's own solutions at 10 iterations (a start off the
+    # boundary rows' exact values is projected by the first step)
+    p10 = dict(params, iters=10, tol=0.0)
+    n = params["n"]
+    wc = np.zeros((S, B, 3 * n)); wl = np.zeros((S, B, 3 * n))
+    for s in range(S):
+        r = U.oracle_solve(p10, ego[s], obst[s], goals[s])
+        wc[s], wl[s] = r["coef"], r["lam"]
+    t = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda:0").contiguous()  # noqa: E731
+    bt = _batch(params, ego, obst, goals, warm_coef=t(wc), warm_lam=t(wl))
+    bt.set_fallback(True)
+    bt.run()
+    torch.cuda.synchronize()
+    coef = bt.flat["coef"].view(S, B, 3 * n).double().cpu().numpy()
+    for s in range(S):
+        orc_w = U.oracle_solve(params, ego[s], obst[s], goals[s], init=U.f32(wc[s]), init_lam=U.f32(wl[s]))
+        orc_c = U.oracle_solve(params, ego[s], obst[s], goals[s])
+        conv = orc_w["resid"][:, :3].max(axis=1) <= params["tol"]
+        ref = np.where(conv[:, None], orc_w["coef"], orc_c["coef"])  # misses were solved again cold
+        err = U.pos_err(params, coef[s], ref)
+        sens = U.sensitivity(params, ego[s], obst[s], goals[s], orc_c["coef"], trials=1)
+        good = (sens < U.SENS_TOL) & conv
+        assert np.all(err[good] <= U.POS_TOL), err[good]
+    bt.close()
