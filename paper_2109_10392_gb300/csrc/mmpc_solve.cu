@@ -2933,13 +2933,19 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
     if (e == cudaSuccess && b->tc) {
         // items of 32 goals in each scene's slot order (the order itself is
         // computed on the device by every run, from the current goals)
+        // item size: a whole scene when there are enough scenes to keep every
+        // sub-partition busy (about 8 items per SM), else blocks of whole warps
         std::vector<int4> items;
         std::vector<int> off(S);
         int o = 0;
+        const double target = 8.0 * std::max(1, sms);
         for (int s = 0; s < S; ++s) {
             off[s] = o;
-            for (int p0 = 0; p0 < scenes[s].B; p0 += 32) items.push_back(make_int4(s, p0, std::min(32, scenes[s].B - p0), o));
-            o += scenes[s].B;
+            const int Bs = scenes[s].B;
+            const int ks = std::max(1, (int)std::ceil((double)Bs * target / std::max(1, b->total)));
+            const int block = 32 * std::max(1, (int)std::ceil((double)Bs / (32.0 * ks)));
+            for (int p0 = 0; p0 < Bs; p0 += block) items.push_back(make_int4(s, p0, std::min(block, Bs - p0), o));
+            o += Bs;
         }
         b->tc_items = (int)items.size();
         const mmpc_ctx* c = scenes[0].ctx;

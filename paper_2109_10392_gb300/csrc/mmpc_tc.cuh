@@ -661,6 +661,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     const float4* obs = obs_all + q * 2 * m;                 // this warp's scene
     __shared__ int4 s_item[4];     // current item of each sub-partition
     __shared__ int s_new[4];       // whether it was taken at this refill
+    __shared__ int s_next[4];      // next goal of the item
+    __shared__ int s_pos[128];     // goal (position within the item) each slot takes at this refill
     __shared__ float4 s_ego[4];    // (y0, v0, psi0, acc0) of its scene
 
     if (warp == 0) {
@@ -671,7 +673,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     }
     for (int i = tid; i < nmat; i += TC_THREADS) mats[i] = __ldg(A.blob + L.Q + i);
     for (int i = tid; i < TL.NSP; i += TC_THREADS) tgrid[i] = i < N ? __ldg(A.blob + L.t + i) : 0.f;
-    if (tid < 4) s_item[tid] = make_int4(-1, 0, 0, 0);
+    if (tid < 4) {
+        s_item[tid] = make_int4(-1, 0, 0, 0);
+        s_next[tid] = 0;
+    }
     const bool staged = stage_blob(reinterpret_cast<float*>(tsm), reinterpret_cast<const float*>(T.blob), TL.bytes,
                                    &s_stage, A.err_flag, A.missing_tx);
     const uint32_t bar = smem_u32(&s_mma);
@@ -787,20 +792,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     unsigned long long work = 0;
     auto scene = [&](int sidx) -> const SolveArgs& { return T.scenes ? T.scenes[sidx] : A; };
 
-    // Refill, at iterations that are multiples of check_every (so that every
-    // trajectory's checks fall on the same iterations): a sub-partition whose
-    // 32 slots are all done takes the next item from the queue; its scene's
-    // obstacles (moving frame of its ego speed) go to the sub-partition's
-    // shared-memory block, and its slots are initialised.
+    // Refill, at the start of every iteration.  A sub-partition holds one
+    // item (goals of one scene) at a time: each free slot takes the item's
+    // next goal; when the item is exhausted and every slot of the
+    // sub-partition is free, it takes the next item from the queue, and its
+    // scene's obstacles (moving frame of its ego speed) go to the
+    // sub-partition's shared-memory block.  Slots run their own iteration
+    // counts; a pass forms the residual sums when any slot checks.
     auto refill = [&]() {
         if (g == 0) {
             const bool empty = __all_sync(FULL, done);
             if (lane == 0) {
                 int take = 0;
-                if (empty && s_item[q].x != -2) {
+                const int4 cur = s_item[q];
+                if (empty && cur.x != -2 && s_next[q] >= cur.z) {
                     const int k = atomicAdd(T.queue, 1);
                     if (k < T.n_items) {
                         s_item[q] = T.items ? T.items[k] : make_int4(0, 32 * k, min(32, A.B - 32 * k), 0);
+                        s_next[q] = 0;
                         take = 1;
                     } else {
                         s_item[q] = make_int4(-2, 0, 0, 0);  // drained
@@ -823,22 +832,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
                 ob[2 * j + 1] = make_float4(py, py, pvy, pvy);
             }
         }
-        __syncthreads();
-        if (s_new[q]) {
-            const int4 item = s_item[q];
-            const float4 eg = s_ego[q];
-            v0 = eg.y;
-            if (lane < item.z) {
-                const int posn = item.y + lane;
-                l = T.order ? T.order[item.w + posn] : posn;
-                init_slot(scene(item.x), eg);
-                done = false;
-                fresh = true;
-                kit = 0;
-                rh1 = rh2 = INFINITY;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) rsum[r] = 0.f;
+        if (g == 0) {  // free slots take the item's next goals
+            int pos = -1;
+            const int4 cur = s_item[q];
+            if (done && cur.x >= 0 && s_next[q] < cur.z) {
+                pos = atomicAdd(&s_next[q], 1);
+                if (pos >= cur.z) pos = -1;
             }
+            s_pos[t] = pos;
+        }
+        __syncthreads();
+        if (s_new[q]) v0 = s_ego[q].y;
+        const int pos = s_pos[t];
+        if (pos >= 0) {
+            const int4 item = s_item[q];
+            const int posn = item.y + pos;
+            l = T.order ? T.order[item.w + posn] : posn;
+            init_slot(scene(item.x), s_ego[q]);
+            done = false;
+            fresh = true;
+            kit = 0;
+            rh1 = rh2 = INFINITY;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) rsum[r] = 0.f;
         }
     };
 
@@ -1069,8 +1085,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
     // F^T (F c^0 - g^0), then the first step) while the others run Algorithm
     // 1's iteration (heading QP, projections, multipliers, xy QP).
     while (ok) {
-        if (it % A.check_every == 0) refill();
-        if (!__syncthreads_or(!done)) break;
+        refill();
+        if (!__syncthreads_or(!done)) break;  // every slot done and the queue drained
         if (!done) kit = fresh ? 0 : kit + 1;
         const bool need = !done && (fresh || kit % A.check_every == 0 || kit >= A.iters);
         const bool check = __syncthreads_or(need) != 0;

@@ -232,13 +232,15 @@ def validation_loss(ws: WarmStart, X, T):
 
 def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256, seed: int = 10**6,
              reps: int = 3, tol: float = 1e-2, obstacles=None, x_range=None, plain: bool = False,
-             stall: tuple | None = None, keep: bool = False):
+             stall: tuple | None = None, keep: bool = False, precision: int = 0):
     """Cold start against warm start (+ cold fallback) on S fresh scenes x B
     goals, each timed as one CUDA graph replay (warm: features, network,
     decode, solve, fallback solve, score).  Returns a dict of results.  With
     the stall stop, a fourth variant falls back only the misses that ran the
     whole budget (`warm_fallback_budget`, mmpc_batch_set_fallback mode 2).
-    With keep, out["_keep"] holds the warm-started batch, its step function,
+    With precision (an MMPC_PREC_* other than FP32), the batched solves run on
+    the tensor-core kernel (variant 3); the plain method and the cold fallback
+    stay FP32.  With keep, out["_keep"] holds the warm-started batch, its step function,
     the graphs per variant and the inputs, for the caller to time further and
     close."""
     import torch
@@ -251,6 +253,8 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
     pb = dict(p)  # the batched variants: with the opt-in stall stop when given
     if stall is not None:
         pb.update(stall_tol=float(stall[0]), stall_ratio=float(stall[1]))
+    if precision:  # the batched solves on the tensor cores (variant 3) in that precision
+        pb.update(variant=3, precision=int(precision))
     meta = mmpc.make_meta(**scenes.META_ABS)
     stream = torch.cuda.Stream(device)
     out = {}
@@ -361,6 +365,7 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
                                            warm=float(warm_iters[both].double().mean().item()))
     out["scenes"], out["goals"], out["obstacles"], out["x_range"] = S, B, m, list(xr)
     out["stall"] = None if stall is None else list(stall)
+    out["precision"] = int(precision)
     out["speedup_trajectories_per_s"] = out["warm_fallback"]["trajectories_per_s"] / out["cold"]["trajectories_per_s"]
     if plain:
         out["batched_cold_vs_plain"] = out["cold"]["trajectories_per_s"] / out["plain"]["trajectories_per_s"]
