@@ -116,6 +116,23 @@ def alu_ops(N, n, passes, elements):
     return elements * OPS_PER_ELEMENT + passes * (14 * N * n + 7 * n * n + 60 * N)
 
 
+def tensor_peak_tflops(kind: str):
+    """Dense tensor peak for `kind` from MEASURED_PEAKS.json's BF16 burst
+    figure times the nominal ratio (TF32 1.1 / BF16 2.25 PFLOP/s); the
+    recipe's fallback 1.9 PFLOP/s BF16 when the file is absent."""
+    bf16 = 1900.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        for k in ("bf16_tflops", "bf16_dense_tflops"):
+            if k in d:
+                bf16 = float(d[k])
+                break
+    except (OSError, ValueError):
+        pass
+    return bf16 * (1.1 / 2.25 if kind == "tf32" else 1.0)
+
+
 def rank_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -588,15 +605,22 @@ def run_warm(args):
     seed = 10**6 + rank
     fwd = warmstart.time_forward(ws, S * B, dev)
     reps = 3
+    from paper_2109_10392_gb300 import mmpc as _m
     dense = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=seed, plain=True)
-    ev = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=seed, stall=STALL, keep=True)
+    ev32 = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=seed, stall=STALL)
+    evbf = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=seed, stall=STALL,
+                              precision=_m.MMPC_PREC_BF16_SPLIT)
+    # the target form: tensor-core solves in TF32 hi + lo (FP32-class positions)
+    ev = warmstart.evaluate(ws, cfg, dev, S=S, B=B, reps=reps, seed=seed, stall=STALL, keep=True,
+                            precision=_m.MMPC_PREC_TF32_SPLIT)
     keep = ev.pop("_keep")
     plain = dense["plain"]
-    for k in ("cold", "warm", "warm_fallback", "warm_fallback_budget"):
-        ev[f"{k}_vs_plain"] = ev[k]["trajectories_per_s"] / plain["trajectories_per_s"]
-        ev[f"{k}_converged_vs_plain"] = ev[k]["converged_per_s"] / plain["converged_per_s"]
-        ev[f"{k}_converged_vs_batched_cold"] = ev[k]["converged_per_s"] / dense["cold"]["converged_per_s"]
-        ev[f"{k}_converged_vs_batched_cold_stall"] = ev[k]["converged_per_s"] / ev["cold"]["converged_per_s"]
+    for e_ in (ev, ev32, evbf):
+        for k in ("cold", "warm", "warm_fallback", "warm_fallback_budget"):
+            e_[f"{k}_vs_plain"] = e_[k]["trajectories_per_s"] / plain["trajectories_per_s"]
+            e_[f"{k}_converged_vs_plain"] = e_[k]["converged_per_s"] / plain["converged_per_s"]
+            e_[f"{k}_converged_vs_batched_cold"] = e_[k]["converged_per_s"] / dense["cold"]["converged_per_s"]
+            e_[f"{k}_converged_vs_batched_cold_stall"] = e_[k]["converged_per_s"] / ev32["cold"]["converged_per_s"]
     warm, stream = keep["warm"], keep["stream"]
     graph = keep["graphs"][HEADLINE]
     converged = ev[HEADLINE]["converged"]
@@ -652,12 +676,20 @@ def run_warm(args):
     warm.set_timing(None)
     elements = warm.take_work_count() / R
     passes = ev[HEADLINE]["passes"]
-    ops = _warm_ops(N, n, m, passes)  # two launches per step
-    exec_ops = alu_ops(N, n, passes, elements)
     launch_ms = (solve_ms + fb_ms) / 2
+    # am_solve_tc_kernel (both launches of a step): the basis products on the
+    # tensor cores, the rest -- projections, element-wise work, QP products --
+    # on the FP32 pipes, which bound it (issue-bound; the tensor pipe is a few
+    # percent busy).  ALU roofline over the FP32-pipe part of the count; the
+    # tensor part against the TF32 peak beside it.
+    alu = passes * (7 * n * n + 60 * N) + OPS_PER_ELEMENT * passes * N * m
+    alu_exec = passes * (7 * n * n + 60 * N) + OPS_PER_ELEMENT * elements
+    ops = _warm_ops(N, n, m, passes)  # the per-unit count of every AM pass (both launches)
     achieved = ops / 2 / (launch_ms * 1e-3) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = measured_traffic("am_solve_batch_kernel", f"highway_warm_S{S}_B{B}_m{m}_N{N}_n{n}")
+    mma_flops = 2.0 * 14 * N * n * passes  # the algorithm's basis products, as tensor FLOPs
+    tf32_peak = tensor_peak_tflops("tf32")
+    traffic = measured_traffic("am_solve_tc_kernel", f"highway_warm_S{S}_B{B}_m{m}_N{N}_n{n}")
 
     # end to end through the library's public calls with host buffers: the
     # step's inputs copied in from pinned memory, the graph replayed, every
@@ -704,30 +736,42 @@ def run_warm(args):
     out = {
         "metric": METRIC, "value": agg["units"] / (agg["ms"] * 1e-3), "unit": UNIT_CONV, "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": agg["ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32 hi+lo (tensor) + f32", "data": "synthetic",
         "config": {"workload": f"highway_warm_S{S}_B{B}_m{m}_N{N}_n{n}_K{p['iters']}_tol{TOL:g}",
-                   "form": "batched (one persistent launch over all scenes), learned warm start (lambda0 = Q c0), "
-                           "cold fallback of every miss, stall stop (residual > 1 m and not halved over two "
-                           "checks)", "scenes_per_gpu": S, "goals_per_scene": B, "obstacles": m,
+                   "form": "batched (one persistent tensor-core launch over all scenes), learned warm start "
+                           "(lambda0 = Q c0), cold fallback of every miss, stall stop (residual > 1 m and not "
+                           "halved over two checks); basis products TF32 hi + lo on tcgen05 with FP32 "
+                           "accumulation, projections and QP steps FP32", "scenes_per_gpu": S, "goals_per_scene": B,
+                   "obstacles": m,
                    "samples": N, "coefficients": n, "max_iters": int(p["iters"]), "tol_m": TOL,
                    "check_every": CHECK_EVERY, "stall_stop": list(STALL),
                    "train_scenes": cfg.train_scenes, "train_rows": train_rows, "train_steps": cfg.steps,
                    "network": list(cfg.widths), "graph": "one CUDA graph replay per step",
                    "l2": "inputs larger than L2: each step reads 4096 scenes and writes 1M trajectories' "
                          "outputs (>150 MB)"},
-        "roofline": {"bound": "alu", "kernel": "am_solve_batch_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": "am_solve_tc_kernel", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak, "traffic": traffic,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum), "
                                      "null when not measured for this kernel source",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz",
-                     "ops_basis": "per trajectory-iteration 14 N n + 7 n^2 (basis and QP products) + 10 m N "
-                                  "(obstacle projections) + 60 N (element-wise), over every AM pass the two "
-                                  "launches of a step ran (warm solve, cold fallback)",
+                     "ops_basis": "per trajectory-iteration 14 N n (basis products, here on the tensor cores) + "
+                                  "7 n^2 (QP products) + 10 m N (obstacle projections) + 60 N (element-wise), over "
+                                  "every AM pass the two launches of a step ran (warm solve, cold fallback)",
                      "ops_per_launch": ops / 2, "launch_ms": launch_ms, "launches_per_step": 2,
                      "solve_launch_ms": solve_ms, "fallback_launch_ms": fb_ms,
+                     "fp32_pipe_part": {"ops_per_launch": alu / 2,
+                                        "achieved": alu / 2 / (launch_ms * 1e-3) / 1e12,
+                                        "frac": alu / 2 / (launch_ms * 1e-3) / 1e12 / peak,
+                                        "basis": "the count without the 14 N n basis products (the work the FP32 "
+                                                 "pipes carry)"},
                      "evaluated_pairs_per_step": elements, "dense_pairs_per_step": passes * N * m,
-                     "executed_ops_per_launch": exec_ops / 2,
-                     "executed_frac": exec_ops / 2 / (launch_ms * 1e-3) / 1e12 / peak},
+                     "executed_ops_per_launch": alu_exec / 2,
+                     "executed_frac": alu_exec / 2 / (launch_ms * 1e-3) / 1e12 / peak,
+                     "tensor": {"achieved": mma_flops / 2 / (launch_ms * 1e-3) / 1e12, "peak": tf32_peak,
+                                "unit": "TFLOP/s", "frac": mma_flops / 2 / (launch_ms * 1e-3) / 1e12 / tf32_peak,
+                                "basis": "2 x 14 N n FLOPs per trajectory-iteration (the algorithm's basis "
+                                         "products; the hi + lo split issues three times as many) against the "
+                                         "TF32 dense peak = measured BF16 burst x 1.1 / 2.25 (nominal ratio)"}},
         "e2e": {"value": agg["e2e_units"] / (agg["e2e_ms"] * 1e-3), "unit": UNIT_CONV,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": agg["e2e_ms"], "steps": Ke,
                 "trajectories_per_s": tagg["e2e_units"] / (tagg["e2e_ms"] * 1e-3),
@@ -741,8 +785,10 @@ def run_warm(args):
                    "plain_converged_per_s": plain["converged_per_s"],
                    "ratio_vs_plain": ev[HEADLINE]["converged_per_s"] / plain["converged_per_s"],
                    "ratio_vs_batched_cold": ev[HEADLINE]["converged_per_s"] / dense["cold"]["converged_per_s"],
-                   "ratio_vs_batched_cold_stall": ev[HEADLINE]["converged_per_s"] / ev["cold"]["converged_per_s"],
-                   "variants_no_stall": dense, "variants_stall_stop": ev, "sparse_10_obstacles": sparse,
+                   "ratio_vs_batched_cold_stall": ev[HEADLINE]["converged_per_s"] / ev32["cold"]["converged_per_s"],
+                   "variants_no_stall": dense, "variants_stall_stop_tensor_tf32x2": ev,
+                   "variants_stall_stop_fp32": ev32, "variants_stall_stop_tensor_bf16x2": evbf,
+                   "sparse_10_obstacles": sparse,
                    "scene_1024_goals_plain_cold": scene, "val_loss": val, "network_forward": fwd,
                    "loss_first_last": [losses[0][1], losses[-1][1]], "dataset_s": t1 - t0, "train_s": t2 - t1,
                    "wall_s": wall, "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)},

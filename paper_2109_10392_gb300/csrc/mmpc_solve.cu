@@ -2673,6 +2673,8 @@ struct mmpc_batch {
     int4* d_tc_items = nullptr;  // (scene, first position, count, order offset)
     int* d_tc_off = nullptr;     // order offset of each scene
     int* d_tc_order = nullptr;   // [queue | pad to 4 | goal index of each position]
+    int* d_tc_fb = nullptr;      // fallback: [queue | pad to 4 | the misses of each scene, in its segment]
+    int4* d_tc_fb_items = nullptr;  // fallback: one item per scene
     bool any_warm = false;
     cudaEvent_t timing[4] = {};  // optional: around the solve launch(es) and the fallback launch
     // horizon groups (schedule 4): scenes with the same pair-thread count,
@@ -2707,6 +2709,8 @@ void batch_free(mmpc_batch* b)
     cudaFree(b->d_tc_items);
     cudaFree(b->d_tc_off);
     cudaFree(b->d_tc_order);
+    cudaFree(b->d_tc_fb);
+    cudaFree(b->d_tc_fb_items);
     cudaFree(b->d_sargs);
     cudaFree(b->d_items);
     cudaFree(b->d_fb_items);
@@ -2957,6 +2961,8 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         e = cudaMalloc(&b->d_tc_items, sizeof(int4) * std::max<size_t>(1, items.size()));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_tc_off, sizeof(int) * S);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_tc_order, sizeof(int) * (4 + (size_t)std::max(1, o)));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_tc_fb, sizeof(int) * (4 + (size_t)std::max(1, o)));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_tc_fb_items, sizeof(int4) * S);
         if (e == cudaSuccess && !items.empty())
             e = cudaMemcpy(b->d_tc_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(b->d_tc_off, off.data(), sizeof(int) * S, cudaMemcpyHostToDevice);
@@ -3035,7 +3041,36 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
                                                                                 b->d_scratch, b->d_scratch);
         }
         if (b->timing[1]) cudaEventRecord(b->timing[1], st);
-        if (b->fallback && b->any_warm) {
+        if (b->fallback && b->any_warm && b->tc) {
+            // the misses of each scene, in its slot order, solved again from
+            // the cold start on the tensor-core kernel (one item per scene)
+            const mmpc_ctx* c = b->scenes[0].ctx;
+            cudaMemsetAsync(b->d_tc_fb, 0, sizeof(int) * 4, st);
+            tc_fallback_compact<<<b->S, 256, 0, st>>>(b->d_args, b->d_tc_off, b->d_tc_order + 4, b->fallback == 2,
+                                                     b->d_tc_fb + 4, b->d_tc_fb_items, b->d_counts + 1);
+            if (b->timing[2]) cudaEventRecord(b->timing[2], st);
+            TcArgs T{};
+            T.blob = c->d_tc;
+            T.L = c->tc;
+            T.scenes = b->d_args_cold;
+            T.items = b->d_tc_fb_items;
+            T.n_items = b->S;
+            T.order = b->d_tc_fb + 4;
+            T.queue = b->d_tc_fb;
+            int sms = c->sm_count;
+            if (sms < 0) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            }
+            const int grid = std::max(1, std::min(sms, (b->S + 3) / 4));
+            using K3 = void (*)(const SolveArgs, const TcArgs);
+            SolveArgs a0 = b->args[0];
+            a0.warm_c = nullptr;
+            a0.warm_l = nullptr;
+            reinterpret_cast<K3>(tc_kernel_of(c))<<<grid, TC_THREADS, b->tc_smem_bytes, st>>>(a0, T);
+            if (b->timing[3]) cudaEventRecord(b->timing[3], st);
+        } else if (b->fallback && b->any_warm) {
             fallback_compact_kernel<<<std::min(1024, (b->total + 255) / 256), 256, 0, st>>>(
                 b->d_args, b->d_items, b->total, b->d_fb_items, b->d_counts + 1, b->d_scratch, b->fallback == 2);
             if (b->timing[2]) cudaEventRecord(b->timing[2], st);

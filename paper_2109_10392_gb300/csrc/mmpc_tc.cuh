@@ -165,6 +165,56 @@ __global__ void tc_order_scatter(const float* __restrict__ goals, int B, int* __
         order[atomicAdd(next + tc_bucket(goals + 3 * l), 1)] = l;
 }
 
+// Misses of a warm-started scene for the cold fallback on the tensor cores
+// (one CTA per scene): the trajectories whose convergence residual missed
+// tol (or is NaN) -- with budget_only, those that also ran the whole budget
+// -- written in the scene's slot order to its segment of `list`, and the
+// scene's item (scene, 0, count, segment offset); counts added to *total.
+__global__ void __launch_bounds__(256) tc_fallback_compact(const SolveArgs* __restrict__ sc,
+                                                           const int* __restrict__ scene_off,
+                                                           const int* __restrict__ order, int budget_only,
+                                                           int* __restrict__ list, int4* __restrict__ items,
+                                                           int* __restrict__ total)
+{
+    __shared__ int warp_cnt[8];
+    __shared__ int base;
+    const SolveArgs& A = sc[blockIdx.x];
+    const int off = scene_off[blockIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const bool warm = A.warm_c && A.resid_out && A.tol > 0.f;
+    for (int p0 = 0; p0 < A.B; p0 += 256) {
+        const int pp = p0 + threadIdx.x;
+        const int i = pp < A.B ? order[off + pp] : 0;  // in the scene's slot order
+        bool miss = false;
+        if (warm && pp < A.B) {
+            const float* r = A.resid_out + (size_t)i * 4;
+            const bool nan = isnan(r[0]) || isnan(r[1]) || isnan(r[2]);
+            const float conv = fmaxf(fmaxf(r[0], r[1]), r[2]);
+            miss = nan || !(conv <= A.tol);
+            if (miss && budget_only && !nan && A.iters_out && A.iters_out[i] < A.iters) miss = false;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, miss);
+        if (lane == 0) warp_cnt[w] = __popc(bal);
+        __syncthreads();
+        int before = base;
+        for (int v = 0; v < w; ++v) before += warp_cnt[v];
+        if (miss) list[off + before + __popc(bal & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int add = 0;
+            for (int v = 0; v < 8; ++v) add += warp_cnt[v];
+            base += add;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        items[blockIdx.x] = make_int4(blockIdx.x, 0, base, off);
+        if (base) atomicAdd(total, base);
+    }
+}
+
 // The same order for every scene of a batch (one CTA per scene, at most
 // TC_RANK_MAX goals): goal i goes to position rank(i) = #{j : (bucket_j, j) <
 // (bucket_i, i)}, a stable, deterministic sort.
@@ -806,13 +856,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
                 int take = 0;
                 const int4 cur = s_item[q];
                 if (empty && cur.x != -2 && s_next[q] >= cur.z) {
-                    const int k = atomicAdd(T.queue, 1);
-                    if (k < T.n_items) {
-                        s_item[q] = T.items ? T.items[k] : make_int4(0, 32 * k, min(32, A.B - 32 * k), 0);
-                        s_next[q] = 0;
-                        take = 1;
-                    } else {
-                        s_item[q] = make_int4(-2, 0, 0, 0);  // drained
+                    for (;;) {  // the next item with goals (a fallback item may hold none)
+                        const int k = atomicAdd(T.queue, 1);
+                        if (k >= T.n_items) {
+                            s_item[q] = make_int4(-2, 0, 0, 0);  // drained
+                            break;
+                        }
+                        const int4 it4 = T.items ? T.items[k] : make_int4(0, 32 * k, min(32, A.B - 32 * k), 0);
+                        if (it4.z > 0) {
+                            s_item[q] = it4;
+                            s_next[q] = 0;
+                            take = 1;
+                            break;
+                        }
                     }
                 }
                 s_new[q] = take;
