@@ -659,14 +659,16 @@ class Batch:
             pass
 
 
-def _time_scene(goals: int, obstacles: int, N: int, n: int, iters: int, reps: int, seed: int) -> dict:
+def _time_scene(goals: int, obstacles: int, N: int, n: int, iters: int, reps: int, seed: int, tol: float = 1e-2,
+                variant: int = 0, precision: int = 0) -> dict:
     """Times solve + score of one seeded highway scene (goals, obstacles, N, n)
-    with CUDA events between L2 flushes: median of `reps` steps."""
+    with CUDA events between L2 flushes: median of `reps` steps (after three
+    untimed ones)."""
     import torch
 
     from . import scenes
     sc = scenes.scene_custom(seed, goals, obstacles, N=N, n=n, x_range=(-50.0, 250.0))
-    params = dict(sc.params, iters=iters, tol=1e-2, check_every=10)
+    params = dict(sc.params, iters=iters, tol=tol, check_every=10, variant=variant, precision=precision)
     s = Solver(params, obstacles)
     meta = make_meta(**sc.meta)
     dev = torch.device("cuda:0")
@@ -691,7 +693,8 @@ def _time_scene(goals: int, obstacles: int, N: int, n: int, iters: int, reps: in
     s.status()
     s.close()
     ms.sort()
-    return dict(goals=goals, obstacles=obstacles, N=N, n=n, iters=iters, reps=reps, ms_median=ms[len(ms) // 2],
+    return dict(goals=goals, obstacles=obstacles, N=N, n=n, iters=iters, tol=tol, variant=variant,
+                precision=precision, reps=reps, ms_median=ms[len(ms) // 2],
                 trajectories_per_s=goals / (ms[len(ms) // 2] * 1e-3), best_goal=int(am.item()))
 
 
@@ -706,5 +709,9 @@ if __name__ == "__main__":
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--reps", type=int, default=100)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-2)
+    ap.add_argument("--variant", type=int, default=0, help="solve kernel (3: tensor cores, needs --precision)")
+    ap.add_argument("--precision", type=int, default=0, help="MMPC_PREC_*: 1 TF32, 2 TF32 hi+lo, 3 BF16, 4 BF16 hi+lo")
     a = ap.parse_args()
-    print(json.dumps(_time_scene(a.goals, a.obstacles, a.N, a.n, a.iters, a.reps, a.seed)))
+    print(json.dumps(_time_scene(a.goals, a.obstacles, a.N, a.n, a.iters, a.reps, a.seed, a.tol, a.variant,
+                                 a.precision)))
