@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
         if (lane == 0) work += (unsigned long long)cnt * (unsigned)nval * (unsigned)__popc(amask);
         uint32_t rn[14];
         tc_ld7x2_issue(ba, rn);
-#pragma unroll 1
+#pragma unroll 2
         for (int j = 0; j < TC_CS / 2; ++j) {
             tc_ld_wait14(rn);
             float v[TC_CH][2];
