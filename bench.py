@@ -998,6 +998,83 @@ def run_reference_scene(args):
     }
 
 
+PRECISION_MODES = ((0, 0, "fp32 (CUDA cores)"), (3, 1, "tf32 (tensor)"), (3, 2, "tf32 hi+lo (tensor)"),
+                   (3, 3, "bf16 (tensor)"), (3, 4, "bf16 hi+lo (tensor)"))
+
+
+def run_precision(args):
+    """The precision workload (16384 goals, 30 obstacles, N = 200, n = 16):
+    solve + score per step under the metric's stopping rule, for the FP32
+    kernel and the tensor-core kernel in each precision; the headline is the
+    tensor-core TF32 hi + lo mode.  The error of each mode against the FP64
+    oracle is measured by the GPU tests, not here."""
+    import torch
+
+    from paper_2109_10392_gb300 import mmpc
+    rank, world, _ = rank_env()
+    if world > 1:
+        raise SystemExit("--workload precision runs on one GPU")
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sc, params = workload(seed=0, kind="precision")
+    B, m, n, N = len(sc.goals), sc.obst.shape[0], params["n"], params["N"]
+    f32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).contiguous()  # noqa: E731
+    ego, obst, goals = f32(sc.ego), f32(sc.obst), f32(sc.goals)
+    meta = mmpc.make_meta(**sc.meta)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows, coefs = {}, {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for variant, prec, name in PRECISION_MODES:
+        p = dict(params, variant=variant, precision=prec)
+        solver = mmpc.Solver(p, m)
+        coef = torch.empty((B, 3 * n), device=dev)
+        resid = torch.empty((B, 4), device=dev)
+        iters = torch.empty((B,), dtype=torch.int32, device=dev)
+        cost = torch.empty((B,), device=dev)
+        am = torch.empty((1,), dtype=torch.int32, device=dev)
+
+        def step():
+            mmpc.mmpc_solve(solver.ctx, ego, obst, goals, coef, None, None, None, resid, iters, stream)
+            mmpc.mmpc_score(solver.ctx, meta, coef, cost, am, stream)
+
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        solver.status()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+        conv = int((resid[:, :3].max(dim=1).values <= TOL).sum().item())
+        rows[name] = dict(ms_per_step=ms, trajectories_per_s=B / (ms * 1e-3), converged=conv,
+                          converged_per_s=conv / (ms * 1e-3), mean_iters=float(iters.double().mean().item()),
+                          argmin=int(am.item()))
+        coefs[name] = (coef.double().cpu().numpy(), cost.double().cpu().numpy())
+        solver.close()
+    clocks = sampler.stop()
+    head = rows["tf32 hi+lo (tensor)"]
+    return {
+        "metric": METRIC, "value": head["converged_per_s"], "unit": UNIT_CONV, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32 hi+lo (tensor) + f32", "data": "synthetic",
+        "config": {"workload": workload_name(params, B, m), "goals_per_scene": B, "obstacles": m, "samples": N,
+                   "coefficients": n, "max_iters": params["iters"], "tol_m": TOL, "check_every": CHECK_EVERY,
+                   "l2": "flushed between timed steps (256 MiB memset outside the event brackets)",
+                   "form": "tensor-core kernel (variant 3), TF32 hi + lo basis products; the other modes in detail"},
+        "clocks": clocks,
+        "detail": {"modes": rows,
+                   "error_vs_fp64_oracle": "tests/test_gpu_tensorcore.py::test_precision_workload_error_table",
+                   "speedup_tf32x2_vs_fp32": rows["fp32 (CUDA cores)"]["ms_per_step"] / head["ms_per_step"]},
+    }
+
+
 SWEEP_B = (11, 32, 128, 512, 1024, 2048, 4096, 16384, 65536)
 
 
@@ -1136,7 +1213,8 @@ def main():
     if args.impl == "reference":
         out = run_reference(args)
     else:
-        out = {"batch": run_batch, "warm": run_warm, "sweep": run_sweep}.get(args.workload, run_mine)(args)
+        out = {"batch": run_batch, "warm": run_warm, "sweep": run_sweep,
+               "precision": run_precision}.get(args.workload, run_mine)(args)
         if out is not None and out.get("roofline", {}).get("bound") == "alu":
             add_measured_peak(out["roofline"])
     if out is not None:
