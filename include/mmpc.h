@@ -257,11 +257,20 @@ int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_meta* meta, mm
  * 4 groups the scenes by horizon (the CTA size ceil(N / 2) rounded up to
  * whole warps) and runs one right-sized persistent launch per group, on
  * streams forked from and joined back to the run's stream, so that no warp
- * idles through a shorter horizon.  Synchronous. */
+ * idles through a shorter horizon.  5 runs the tensor-core kernel (one
+ * persistent launch over 32-goal items of every scene; also the fallback) and
+ * needs one context of variant 3 for every scene; such a batch starts with 5,
+ * any other with 1.  Schedules 1-4 run the FP32 kernel (for a variant 3
+ * context its rows are FP32).  Other values -> MMPC_ERR_INVALID_ARG.
+ * Synchronous. */
 int mmpc_batch_set_schedule(mmpc_batch* b, int schedule);
 
-/* Times the four schedules (a warm-up and two timed runs each, on `stream`),
- * keeps the fastest and writes it to *chosen (may be NULL).  Synchronous. */
+/* Times the schedules the batch can run (1-4, and 5 when it can run on the
+ * tensor cores; a warm-up and two timed runs each, on `stream`), keeps the
+ * fastest and writes it to *chosen (may be NULL).  The choice is cached per
+ * batch signature (each scene's goal count, N, n, m and warm start, in
+ * order, and the kernel family) for the life of the process: a later batch
+ * of the same signature takes it without timing.  Synchronous. */
 int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen);
 
 /* Solves and scores every scene of the batch on `stream` (asynchronous).

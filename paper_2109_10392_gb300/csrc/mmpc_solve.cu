@@ -2667,7 +2667,9 @@ struct mmpc_batch {
     int fallback = 0;  // 0 off, 1 every miss, 2 misses that ran the whole budget
     // one context of variant 3 for every scene: the solve runs on the
     // tensor-core kernel over items of 32 goals (the fallback stays FP32)
-    bool tc = false;
+    bool tc = false;     // the batch can run on the tensor-core kernel
+    bool use_tc = false;  // and does (schedule 5; 1-4 run the FP32 kernel)
+    std::string signature;  // the autotuner's cache key
     int tc_items = 0;
     size_t tc_smem_bytes = 0;
     int4* d_tc_items = nullptr;  // (scene, first position, count, order offset)
@@ -2974,13 +2976,37 @@ extern "C" int mmpc_batch_create(const mmpc_scene* scenes, int S, const mmpc_met
         return batch_fail(std::string("mmpc_batch_create: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
     }
     *out = b;
-    return mmpc_batch_set_schedule(b, 1);
+    {   // the autotuner's key: the shapes of the scenes, in order, and the kernel family
+        std::string key = std::to_string(S) + (b->tc ? "/tc" + std::to_string(scenes[0].ctx->p.precision) : "");
+        for (int s = 0; s < S; ++s) {
+            const mmpc_ctx* c = scenes[s].ctx;
+            key += ";" + std::to_string(scenes[s].B) + "," + std::to_string(c->p.N) + "," + std::to_string(c->p.n) +
+                   "," + std::to_string(c->m) + "," + std::to_string(scenes[s].warm_coef ? 1 : 0);
+        }
+        b->signature = key;
+    }
+    return mmpc_batch_set_schedule(b, b->tc ? 5 : 1);
 }
 
 extern "C" int mmpc_batch_set_schedule(mmpc_batch* b, int schedule)
 {
     if (!b) return batch_fail("mmpc_batch_set_schedule: NULL batch", MMPC_ERR_NOT_SETUP);
-    if (schedule < 1 || schedule > 4) return batch_fail("mmpc_batch_set_schedule: schedule must be 1 to 4", MMPC_ERR_INVALID_ARG);
+    if (schedule == 5) {
+        if (!b->tc)
+            return batch_fail("mmpc_batch_set_schedule: schedule 5 needs one context of variant 3 for every scene",
+                              MMPC_ERR_INVALID_ARG);
+        // the (scene, trajectory) items of scene order still serve the scoring
+        std::vector<int2> items = batch_items(b, 1);
+        if (b->total > 0) {
+            cudaError_t e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return batch_fail(std::string("mmpc_batch_set_schedule: ") + cudaGetErrorString(e), MMPC_ERR_CUDA);
+        }
+        b->use_tc = true;
+        b->schedule = 5;
+        return MMPC_OK;
+    }
+    b->use_tc = false;
+    if (schedule < 1 || schedule > 4) return batch_fail("mmpc_batch_set_schedule: schedule must be 1 to 5", MMPC_ERR_INVALID_ARG);
     std::vector<int2> items = batch_items(b, schedule == 4 ? 2 : schedule);
     if (b->total > 0) {
         cudaError_t e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
@@ -3000,7 +3026,7 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
     if (b->total > 0) {
         if (b->timing[0]) cudaEventRecord(b->timing[0], st);
         using KernT = void (*)(const SolveArgs*, const int2*, const int*, unsigned long long*, unsigned long long*);
-        if (b->tc) {
+        if (b->use_tc) {
             // tensor-core kernel over every scene: each scene's goals ordered
             // (one CTA per scene), then persistent CTAs over the item queue
             const mmpc_ctx* c = b->scenes[0].ctx;
@@ -3041,7 +3067,7 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
                                                                                 b->d_scratch, b->d_scratch);
         }
         if (b->timing[1]) cudaEventRecord(b->timing[1], st);
-        if (b->fallback && b->any_warm && b->tc) {
+        if (b->fallback && b->any_warm && b->use_tc) {
             // the misses of each scene, in its slot order, solved again from
             // the cold start on the tensor-core kernel (one item per scene)
             const mmpc_ctx* c = b->scenes[0].ctx;
@@ -3107,9 +3133,22 @@ extern "C" int mmpc_batch_times(mmpc_batch* b, float* scene_ms, float* makespan_
     return MMPC_OK;
 }
 
+namespace {
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, int>> g_tune_cache;  // batch signature -> chosen schedule
+}  // namespace
+
 extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
 {
     if (!b) return batch_fail("mmpc_batch_autotune: NULL batch", MMPC_ERR_NOT_SETUP);
+    {   // a batch of the same signature was tuned before: take its choice
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto& kv : g_tune_cache)
+            if (kv.first == b->signature) {
+                if (chosen) *chosen = kv.second;
+                return mmpc_batch_set_schedule(b, kv.second);
+            }
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -3117,7 +3156,8 @@ extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
     int best = 1;
     float best_ms = 1e30f;
     int rc = MMPC_OK;
-    for (int sch = 1; sch <= 4 && rc == MMPC_OK; ++sch) {
+    const int last = b->tc ? 5 : 4;
+    for (int sch = 1; sch <= last && rc == MMPC_OK; ++sch) {
         rc = mmpc_batch_set_schedule(b, sch);
         if (rc == MMPC_OK) rc = mmpc_batch_run(b, stream);  // warm-up
         float total = 0.f;
@@ -3137,6 +3177,10 @@ extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
     if (rc != MMPC_OK) return rc;
     rc = mmpc_batch_set_schedule(b, best);
     if (chosen) *chosen = best;
+    if (rc == MMPC_OK) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.emplace_back(b->signature, best);
+    }
     return rc;
 }
 

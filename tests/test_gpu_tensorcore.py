@@ -224,3 +224,39 @@ def test_batch_against_oracle_with_warm_start_and_fallback():
         good = (sens < U.SENS_TOL) & conv
         assert np.all(err[good] <= U.POS_TOL), err[good]
     bt.close()
+
+
+def test_batch_schedules_and_autotune():
+    """A batch of one variant-3 context runs on the tensor cores (schedule 5)
+    or on the FP32 kernel (1-4, the same results as a context of variant 0);
+    the autotuner times all five, and a second batch of the same signature
+    takes the cached choice."""
+    import torch
+    S, B, m = 4, 64, 6
+    ego, obst, goals = scenes.scene_stack(21, S, B, m, (10.0, 150.0))
+    ego, obst, goals = U.f32(ego), U.f32(obst), U.f32(goals)
+    p3 = dict(scenes.BASE_PARAMS, tol=1e-2, variant=3, precision=mmpc.MMPC_PREC_TF32_SPLIT)
+    p0 = dict(scenes.BASE_PARAMS, tol=1e-2)
+    ref = _batch(p0, ego, obst, goals)
+    ref.run()
+    bt = _batch(p3, ego, obst, goals)
+    for sch in (1, 4):
+        bt.set_schedule(sch)
+        bt.run()
+        torch.cuda.synchronize()
+        for k in ("coef", "resid", "iters", "cost", "argmin"):
+            assert torch.equal(bt.flat[k], ref.flat[k]), (sch, k)
+    bt.set_schedule(5)
+    bt.run()
+    torch.cuda.synchronize()
+    n = p3["n"]
+    one = U.gpu_solve(p3, ego[0], obst[0], goals[0])
+    assert np.array_equal(bt.flat["coef"].view(-1, 3 * n)[:B].double().cpu().numpy(), one["coef"])
+    with pytest.raises(mmpc.MmpcError):
+        ref.set_schedule(5)
+    chosen = bt.autotune()
+    assert chosen in (1, 2, 3, 4, 5)
+    again = _batch(p3, ego, obst, goals)
+    assert again.autotune() == chosen
+    for b_ in (ref, bt, again):
+        b_.close()
