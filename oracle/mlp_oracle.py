@@ -17,7 +17,9 @@ float64:
   each hidden layer, weights rounded to bfloat16 (round to nearest even) and
   every product and sum in float64;
 * the mean-squared-error loss over standardised targets and its gradients by
-  the chain rule (pinned against central finite differences);
+  the chain rule (pinned against central finite differences), optionally
+  with every operand of every product rounded to bfloat16 as the tensor
+  cores take it (``op_bf16``; pinned by a hand-worked one-unit case);
 * AdamW with bias correction and decoupled weight decay on the weight
   matrices (Loshchilov & Hutter, "Decoupled Weight Decay Regularization",
   2019);
@@ -188,23 +190,31 @@ def forward(Ws, bs, X, bf16=True, act_bf16=False):
     return h, (acts, pres)
 
 
-def loss_and_grads(Ws, bs, X, Z, bf16=True):
+def loss_and_grads(Ws, bs, X, Z, bf16=True, op_bf16=False):
     """Mean squared error over all outputs, L = sum (y - Z)^2 / (B * outs),
     and its gradients with respect to every weight matrix and bias (the
-    gradient of a bfloat16-rounded weight is passed to its master copy)."""
-    y, (acts, pres) = forward(Ws, bs, X, bf16)
+    gradient of a bfloat16-rounded weight is passed to its master copy).
+
+    op_bf16: every operand of every matrix product is rounded to bfloat16
+    (held as float32 first), as the tensor cores take them -- the layer
+    inputs of the forward products (act_bf16), and in the backward pass the
+    output gradient d of each layer and that layer's input, in both
+    d W^T and H^T d.  The bias gradients sum the unrounded d."""
+    y, (acts, pres) = forward(Ws, bs, X, bf16, act_bf16=op_bf16)
     Z = np.asarray(Z, dtype=np.float64)
     cnt = y.size
     r = y - Z
     L = float(np.sum(r * r) / cnt)
     d = 2.0 * r / cnt
+    rnd = (lambda a: bf16_round(np.asarray(a).astype(np.float32))) if op_bf16 else (lambda a: a)
     gW, gb = [None] * len(Ws), [None] * len(Ws)
     for i in range(len(Ws) - 1, -1, -1):
-        gW[i] = acts[i].T @ d
+        dq = rnd(d)
+        gW[i] = rnd(acts[i]).T @ dq
         gb[i] = d.sum(axis=0)
         if i > 0:
             Wq = bf16_round(Ws[i]) if bf16 else np.asarray(Ws[i], dtype=np.float64)
-            d = (d @ Wq.T) * gelu_grad(pres[i - 1])
+            d = (dq @ Wq.T) * gelu_grad(pres[i - 1])
     return L, gW, gb
 
 

@@ -198,3 +198,49 @@ def test_bf16_activations_round_every_layer_input():
     assert np.array_equal(y, h)
     y0, _ = M.forward(Ws, bs, X, bf16=True)
     assert 0 < np.max(np.abs(y - y0)) < 0.05 * np.abs(y0).max()
+
+
+def test_bf16_operand_gradients_hand_case():
+    """op_bf16 on a 1 -> 1 -> 1 network worked by hand: the input 1 + 2^-9
+    rounds to 1, the output gelu(1) = 0.84134... to 0.83984375 (215 / 256),
+    the output gradient 2 y = 1.6796875 is exact in bfloat16, the hidden
+    gradient 2 y gelu'(1) = 1.81961... rounds to 1.8203125 (233 / 128) for
+    the weight gradient while the bias gradient keeps it unrounded."""
+    Ws = [np.array([[1.0]], dtype=np.float32), np.array([[1.0]], dtype=np.float32)]
+    bs = [np.zeros(1, dtype=np.float32), np.zeros(1, dtype=np.float32)]
+    X = np.array([[1.0 + 2.0 ** -9]])
+    Z = np.zeros((1, 1))
+    L, gW, gb = M.loss_and_grads(Ws, bs, X, Z, bf16=True, op_bf16=True)
+    y = 215.0 / 256.0
+    assert L == y * y
+    d1 = 2.0 * y
+    assert gb[1][0] == d1 and gW[1][0, 0] == y * d1
+    phi1 = 0.5 * (1.0 + math.erf(1.0 / math.sqrt(2.0)))
+    dens1 = math.exp(-0.5) / math.sqrt(2.0 * math.pi)
+    d0 = d1 * (phi1 + dens1)
+    assert abs(d0 - 1.8196) < 1e-4
+    assert abs(gb[0][0] - d0) < 1e-15
+    assert gW[0][0, 0] == 233.0 / 128.0
+    # without the operand rounding: y = gelu(x) at the exact input x, and
+    # gW0 = x * 2 y gelu'(x)
+    x = 1.0 + 2.0 ** -9
+    _, gW2, _ = M.loss_and_grads(Ws, bs, X, Z, bf16=True)
+    yx = x * 0.5 * (1.0 + math.erf(x / math.sqrt(2.0)))
+    gx = 0.5 * (1.0 + math.erf(x / math.sqrt(2.0))) + x * math.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    assert abs(gW2[0][0, 0] - x * 2.0 * yx * gx) < 1e-14
+
+
+def test_bf16_operand_gradients_near_the_plain_ones():
+    """The roundings move every gradient by a bfloat16-sized relative amount
+    (nonzero, well under 5 %) on a random network; the loss moves only by the
+    rounding of the forward inputs."""
+    Ws, bs = _tiny_net(11)
+    rng = np.random.default_rng(12)
+    X = rng.normal(size=(40, 5))
+    Z = rng.normal(size=(40, Ws[-1].shape[1]))
+    L0, gW0, gb0 = M.loss_and_grads(Ws, bs, X, Z, bf16=True)
+    L1, gW1, gb1 = M.loss_and_grads(Ws, bs, X, Z, bf16=True, op_bf16=True)
+    assert 0 < abs(L1 - L0) < 1e-2 * L0
+    for a, b in zip(gW0 + gb0, gW1 + gb1):
+        rel = np.abs(a - b).max() / np.abs(a).max()
+        assert 0 < rel < 5e-2, rel
