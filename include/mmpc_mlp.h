@@ -144,8 +144,25 @@ int mmpc_mlp_write(mmpc_mlp* net, int what, int layer, const float* host, size_t
  * hidden activation) is rounded to bfloat16 (nearest even), where the SIMT
  * path keeps it in float32; the two give the same result up to the order of
  * the float32 sums.  Other values of on: MMPC_ERR_INVALID_ARG.  Training
- * always uses the SIMT kernels. */
+ * is set separately (mmpc_mlp_set_train_tensor_cores). */
 int mmpc_mlp_set_tensor_cores(mmpc_mlp* net, int on);
+
+/* Training (mmpc_mlp_loss_grad) on the tensor cores (on = 1) or the FP32
+ * SIMT kernels (on = 0, the default).  With on = 1 the three products of
+ * every layer -- forward H W, backward D W^T and weight gradient H^T D --
+ * run on the pipelined tcgen05 GEMM with bfloat16 operands and float32
+ * accumulation: the layer inputs (features, hidden activations) and the
+ * output gradients D are rounded to bfloat16 (nearest even) where the SIMT
+ * path keeps them in float32; the pre-activations, the GELU derivative, the
+ * loss and the bias gradients (column sums of the float32 D) stay float32.
+ * The weight gradient's sum over the M rows is split into ranges whose
+ * float32 partial sums are added in a fixed order, so results are
+ * deterministic.  Enabling allocates the bfloat16 operand buffers
+ * (synchronous, ~ max_batch x (sum of widths) x 4 bytes) and needs every
+ * layer input width (width[0 .. layers-1]) to be a multiple of 8 and
+ * max_batch <= 2,097,120: otherwise MMPC_ERR_INVALID_ARG and the mode is
+ * unchanged.  Other values of on: MMPC_ERR_INVALID_ARG. */
+int mmpc_mlp_set_train_tensor_cores(mmpc_mlp* net, int on);
 
 /* Synchronises the device and reports MMPC_ERR_TIMEOUT if a bounded wait of
  * a tensor-core kernel expired since the network was created. */

@@ -737,47 +737,128 @@ __device__ __forceinline__ void load_bias16(const float* __restrict__ bias, int 
     }
 }
 
-// accumulators + bias (+ GELU) of columns j0 .. j0 + 16 of row gi, stored
-template <typename TC, bool GELU>
+// What the pipelined kernel's epilogue makes of a 128 x BN accumulator tile.
+enum : int {
+    TE_HID = 0,    // inference, hidden layer: GELU(acc + bias) -> bfloat16 rows
+    TE_OUT = 1,    // last layer: acc + bias -> float32 rows
+    TE_TRAIN = 2,  // training, hidden layer: pre = acc + bias -> float32 rows (kept for the
+                   // backward pass); GELU(pre) -> bfloat16 rows (the next layer's input) and
+                   // bfloat16 columns (its input transposed, for the weight gradient)
+    TE_DX = 3,     // backward product: acc * gelu'(pre) -> float32 rows (bias gradient),
+                   // bfloat16 rows and columns (the operands of the next two products)
+    TE_WGRAD = 4,  // weight gradient: acc -> float32 rows of split z's partial sum
+};
+
+// Destinations of the epilogue (row i, column j of the tile's product).
+struct Epi {
+    const float* bias;   // [N]: TE_HID, TE_OUT, TE_TRAIN
+    float* f32;          // float32 rows, f32[z * zstride + i * ld32 + j]
+    int ld32;
+    __nv_bfloat16* r16;  // bfloat16 rows, r16[i * ld16 + j]
+    int ld16;
+    __nv_bfloat16* t16;  // bfloat16 columns, t16[j * ldT + i]
+    int ldT;
+    const float* pre;    // TE_DX: pre-activations pre[i * ldp + j]
+    int ldp;
+    size_t zstride;      // TE_WGRAD: elements between consecutive splits' partials
+};
+
+__device__ __forceinline__ void store_f32_16(float* o, const float2 (&v)[8], int cnt, bool vec)
+{
+    if (cnt >= 16 && vec) {
+        float4* o4 = reinterpret_cast<float4*>(o);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o4[c] = make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < cnt) o[c] = (c & 1) ? v[c >> 1].y : v[c >> 1].x;
+    }
+}
+
+__device__ __forceinline__ void store_bf16_16(__nv_bfloat16* o, const float2 (&v)[8], int cnt, bool vec)
+{
+    if (cnt >= 16 && vec) {
+        uint4* o4 = reinterpret_cast<uint4*>(o);
+        o4[0] = make_uint4(pack_bf16(v[0].x, v[0].y), pack_bf16(v[1].x, v[1].y), pack_bf16(v[2].x, v[2].y),
+                           pack_bf16(v[3].x, v[3].y));
+        o4[1] = make_uint4(pack_bf16(v[4].x, v[4].y), pack_bf16(v[5].x, v[5].y), pack_bf16(v[6].x, v[6].y),
+                           pack_bf16(v[7].x, v[7].y));
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < cnt) o[c] = __float2bfloat16_rn((c & 1) ? v[c >> 1].y : v[c >> 1].x);
+    }
+}
+
+// column j0 + c of row gi at t[(j0 + c) * ldT + gi]: the 32 lanes of a warp
+// (consecutive rows) write 64 contiguous bytes per column
+__device__ __forceinline__ void store_bf16_cols(__nv_bfloat16* t, int ldT, int gi, int j0, const float2 (&v)[8],
+                                                int cnt)
+{
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        if (c < cnt) t[(size_t)(j0 + c) * ldT + gi] = __float2bfloat16_rn((c & 1) ? v[c >> 1].y : v[c >> 1].x);
+}
+
+// the epilogue of columns j0 .. j0 + 16 of row gi (bv: the bias there, or zeros)
+template <int MODE>
 __device__ __forceinline__ void epilogue16(const uint32_t (&r)[16], const float (&bv)[16], int gi, int M, int j0, int N,
-                                           TC* __restrict__ C, int ldc)
+                                           int z, const Epi& e)
 {
     float2 v[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        v[c] = __fadd2_rn(make_float2(__uint_as_float(r[2 * c]), __uint_as_float(r[2 * c + 1])),
-                          make_float2(bv[2 * c], bv[2 * c + 1]));
-        if (GELU) v[c] = gelu_poly2(v[c]);
+        v[c] = make_float2(__uint_as_float(r[2 * c]), __uint_as_float(r[2 * c + 1]));
+        if (MODE == TE_HID || MODE == TE_OUT || MODE == TE_TRAIN)
+            v[c] = __fadd2_rn(v[c], make_float2(bv[2 * c], bv[2 * c + 1]));
+        if (MODE == TE_HID) v[c] = gelu_poly2(v[c]);
     }
     if (gi >= M) return;
-    TC* out = C + (size_t)gi * ldc + j0;
-    const bool full = j0 + 16 <= N;
-    if (sizeof(TC) == 2 && full && (ldc & 7) == 0) {
-        uint4* o = reinterpret_cast<uint4*>(out);
-        o[0] = make_uint4(pack_bf16(v[0].x, v[0].y), pack_bf16(v[1].x, v[1].y), pack_bf16(v[2].x, v[2].y),
-                          pack_bf16(v[3].x, v[3].y));
-        o[1] = make_uint4(pack_bf16(v[4].x, v[4].y), pack_bf16(v[5].x, v[5].y), pack_bf16(v[6].x, v[6].y),
-                          pack_bf16(v[7].x, v[7].y));
-    } else if (sizeof(TC) == 4 && full && (ldc & 3) == 0) {
-        float4* o = reinterpret_cast<float4*>(out);
+    const int cnt = min(16, N - j0);
+    if (MODE == TE_HID) {
+        store_bf16_16(e.r16 + (size_t)gi * e.ld16 + j0, v, cnt, (e.ld16 & 7) == 0);
+    } else if (MODE == TE_OUT) {
+        store_f32_16(e.f32 + (size_t)gi * e.ld32 + j0, v, cnt, (e.ld32 & 3) == 0);
+    } else if (MODE == TE_TRAIN) {
+        store_f32_16(e.f32 + (size_t)gi * e.ld32 + j0, v, cnt, (e.ld32 & 3) == 0);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) o[c] = make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
-    } else {
+        for (int c = 0; c < 8; ++c) v[c] = gelu_poly2(v[c]);
+        store_bf16_16(e.r16 + (size_t)gi * e.ld16 + j0, v, cnt, (e.ld16 & 7) == 0);
+        store_bf16_cols(e.t16, e.ldT, gi, j0, v, cnt);
+    } else if (MODE == TE_DX) {
+        const float* p = e.pre + (size_t)gi * e.ldp + j0;
+        float pv[16];
+        if (cnt >= 16 && (e.ldp & 3) == 0) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-            if (j0 + c < N) {
-                const float val = (c & 1) ? v[c >> 1].y : v[c >> 1].x;
-                if (sizeof(TC) == 2) reinterpret_cast<__nv_bfloat16*>(out)[c] = __float2bfloat16_rn(val);
-                else reinterpret_cast<float*>(out)[c] = val;
+            for (int c = 0; c < 16; c += 4) {
+                const float4 t4 = *reinterpret_cast<const float4*>(p + c);
+                pv[c] = t4.x; pv[c + 1] = t4.y; pv[c + 2] = t4.z; pv[c + 3] = t4.w;
             }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) pv[c] = c < cnt ? p[c] : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = make_float2(v[c].x * gelu_grad(pv[2 * c]), v[c].y * gelu_grad(pv[2 * c + 1]));
+        store_f32_16(e.f32 + (size_t)gi * e.ld32 + j0, v, cnt, (e.ld32 & 3) == 0);
+        store_bf16_16(e.r16 + (size_t)gi * e.ld16 + j0, v, cnt, (e.ld16 & 7) == 0);
+        store_bf16_cols(e.t16, e.ldT, gi, j0, v, cnt);
+    } else {
+        store_f32_16(e.f32 + (size_t)z * e.zstride + (size_t)gi * e.ld32 + j0, v, cnt, (e.ld32 & 3) == 0);
     }
 }
 
-template <typename TC, bool GELU>
+// The pipelined product C = A Bt^T over work units: a unit is one output
+// tile and one of Z splits of the reduction (Z > 1 only for the weight
+// gradients, whose reduction runs over the batch rows); split z covers the
+// KS steps of BK from z KS BK, and steps past the operands' extent read the
+// tensor maps' zero fill.  Unit u is tile u mod tiles, split u / tiles; the
+// CTAs take units blockIdx.x, + gridDim.x, ...
+template <int MODE>
 __global__ void __launch_bounds__(TMA_THREADS, 1)
     umma_tma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
-                         int N, int K, const float* __restrict__ bias, TC* __restrict__ C, int ldc, int BN,
-                         uint32_t ncols, unsigned* err)
+                         int N, int KS, int Z, const Epi epi, int BN, uint32_t ncols, unsigned* err)
 {
     extern __shared__ __align__(1024) unsigned char tsm_raw[];
     // the ring starts on a 1024-byte boundary (the request carries 1 KB of slack)
@@ -786,7 +867,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     __shared__ __align__(8) unsigned long long s_full[TMA_STAGES], s_empty[TMA_STAGES], s_tfull[2], s_tempty[2];
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN, tiles = mt * nt, KS = (K + BK - 1) / BK;
+    const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN, tiles = mt * nt, units = tiles * Z;
     if (warp == TMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
                      "r"(ncols)
@@ -811,9 +892,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     const uint32_t half = ncols / 2;  // columns per accumulator buffer
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     bool ok = true;
-    // local tiles of this CTA: blockIdx.x, + gridDim.x, ...
-    const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int total = my_tiles * KS;  // K steps of this CTA, over its tiles in order
+    // local units of this CTA: blockIdx.x, + gridDim.x, ...
+    const int my_units = blockIdx.x < units ? (units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_units * KS;  // K steps of this CTA, over its units in order
     if (warp == TMA_WARP) {
         // producer: fill stage g % S with the A and B tiles of K step g once
         // the MMAs of step g - S have released it
@@ -822,9 +903,10 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 const int s = g % TMA_STAGES;
                 if (g >= TMA_STAGES) ok = mbar_wait(saddr(&s_empty[s]), (uint32_t)(((g / TMA_STAGES) - 1) & 1), err);
                 if (!ok) break;
-                const int ti = g / KS, ks = g % KS;
-                const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
-                const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN, k0 = ks * BK;
+                const int ui = g / KS, ks = g % KS;
+                const int unit = (int)blockIdx.x + ui * (int)gridDim.x;
+                const int tile = unit % tiles, z = unit / tiles;
+                const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN, k0 = (z * KS + ks) * BK;
                 const uint32_t full = saddr(&s_full[s]);
                 const uint32_t base = saddr(tsm + (size_t)s * st_bytes);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(st_bytes)
@@ -835,17 +917,17 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         }
         __syncwarp();
     } else if (warp == MMA_WARP) {
-        // MMA issuer: step g once its stage has landed (and, at a tile's
+        // MMA issuer: step g once its stage has landed (and, at a unit's
         // first step, once the epilogue has drained the TMEM buffer of two
-        // tiles back); each step's commit frees its stage, a tile's last
+        // units back); each step's commit frees its stage, a unit's last
         // commit hands the accumulator to the epilogue
         if (lane == 0) {
             int g = 0;
             for (; g < total && ok; ++g) {
                 const int s = g % TMA_STAGES;
-                const int ti = g / KS, ks = g % KS, b = ti & 1;
-                if (ks == 0 && ti >= 2) {
-                    ok = mbar_wait(saddr(&s_tempty[b]), (uint32_t)(((ti - 2) >> 1) & 1), err);
+                const int ui = g / KS, ks = g % KS, b = ui & 1;
+                if (ks == 0 && ui >= 2) {
+                    ok = mbar_wait(saddr(&s_tempty[b]), (uint32_t)(((ui - 2) >> 1) & 1), err);
                     if (!ok) break;
                 }
                 ok = mbar_wait(saddr(&s_full[s]), (uint32_t)((g / TMA_STAGES) & 1), err);
@@ -883,13 +965,15 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         // warp: TMEM sub-partition q (its 32 rows of the tile), and every
         // fourth 16-column chunk starting at `part`
         const int q = warp & 3, part = warp >> 2, chunks = BN / 16;
-        for (int ti = 0; ti < my_tiles && ok; ++ti) {
-            const int b = ti & 1;
-            const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
+        constexpr bool has_bias = MODE == TE_HID || MODE == TE_OUT || MODE == TE_TRAIN;
+        for (int ui = 0; ui < my_units && ok; ++ui) {
+            const int b = ui & 1;
+            const int unit = (int)blockIdx.x + ui * (int)gridDim.x;
+            const int tile = unit % tiles, z = unit / tiles;
             const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
             const int gi = m0 + q * 32 + lane;
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * half;
-            ok = mbar_wait(saddr(&s_tfull[b]), (uint32_t)((ti >> 1) & 1), err);
+            ok = mbar_wait(saddr(&s_tfull[b]), (uint32_t)((ui >> 1) & 1), err);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // this warp's chunks part, part + 4, ...: the TMEM load and the
@@ -899,34 +983,34 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             uint32_t ra[16], rb[16];
             float ba[16], bb[16];
             if (nch > 0) {
-                load_bias16(bias, n0 + part * 16, N, ba);
+                if (has_bias) load_bias16(epi.bias, n0 + part * 16, N, ba);
                 tmem_ld16(trow + (uint32_t)(part * 16), ra);
             }
             for (int i = 0; i < nch; i += 2) {
                 const int ca = part + 4 * i, cb = ca + 4;
                 tmem_wait_ld();
                 if (i + 1 < nch) {
-                    load_bias16(bias, n0 + cb * 16, N, bb);
+                    if (has_bias) load_bias16(epi.bias, n0 + cb * 16, N, bb);
                     tmem_ld16(trow + (uint32_t)(cb * 16), rb);
                 }
-                epilogue16<TC, GELU>(ra, ba, gi, M, n0 + ca * 16, N, C, ldc);
+                epilogue16<MODE>(ra, ba, gi, M, n0 + ca * 16, N, z, epi);
                 if (i + 1 < nch) {
                     tmem_wait_ld();
                     if (i + 2 < nch) {
-                        load_bias16(bias, n0 + (cb + 4) * 16, N, ba);
+                        if (has_bias) load_bias16(epi.bias, n0 + (cb + 4) * 16, N, ba);
                         tmem_ld16(trow + (uint32_t)((cb + 4) * 16), ra);
                     }
-                    epilogue16<TC, GELU>(rb, bb, gi, M, n0 + cb * 16, N, C, ldc);
+                    epilogue16<MODE>(rb, bb, gi, M, n0 + cb * 16, N, z, epi);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(saddr(&s_tempty[b]));
         }
     }
-    // the last MMAs are complete once the epilogue has drained the last tile;
+    // the last MMAs are complete once the epilogue has drained the last unit;
     // a CTA that gave up waits (bounded) for its outstanding commits first
-    if (!ok && warp == MMA_WARP && lane == 0 && my_tiles > 0) {
-        const int last = my_tiles - 1;
+    if (!ok && warp == MMA_WARP && lane == 0 && my_units > 0) {
+        const int last = my_units - 1;
         mbar_wait(saddr(&s_tfull[last & 1]), (uint32_t)((last >> 1) & 1), err);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -942,6 +1026,33 @@ __global__ void rows_to_bf16_kernel(const float* __restrict__ X, size_t count, _
         Y[e] = __float2bfloat16_rn(X[e]);
 }
 
+// float32 rows X [M][cols] (row stride ldx) -> bfloat16 rows R [M][ldr] and
+// bfloat16 columns T [cols][ldT] (T[j ldT + i] = X[i][j]): the operands of a
+// layer's two training products.  32 x 32 tiles pass through shared memory,
+// so that the reads and both writes are coalesced.
+__global__ void __launch_bounds__(256) rows_cols_bf16_kernel(const float* __restrict__ X, int M, int cols, int ldx,
+                                                             __nv_bfloat16* __restrict__ R, int ldr,
+                                                             __nv_bfloat16* __restrict__ T, int ldT)
+{
+    __shared__ float tile[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, j = j0 + tx;
+        float v = 0.f;
+        if (i < M && j < cols) {
+            v = X[(size_t)i * ldx + j];
+            R[(size_t)i * ldr + j] = __float2bfloat16_rn(v);
+        }
+        tile[r][tx] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = j0 + r, i = i0 + tx;
+        if (j < cols && i < M) T[(size_t)j * ldT + i] = __float2bfloat16_rn(tile[tx][r]);
+    }
+}
+
 // bfloat16 copy of W [K][N] transposed: Wt [N][K]
 __global__ void to_bf16_t_kernel(const float* __restrict__ W, int K, int N, __nv_bfloat16* __restrict__ Wt)
 {
@@ -949,6 +1060,17 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ W, int K, int N, __nv
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const int n = (int)(e / K), k = (int)(e % K);
         Wt[e] = __float2bfloat16_rn(W[(size_t)k * N + n]);
+    }
+}
+
+// bfloat16 copy of W [K][N] with rows padded to ldp >= N elements (16-byte
+// rows for the tensor maps; the padding is never read)
+__global__ void to_bf16_padded_kernel(const float* __restrict__ W, int K, int N, int ldp, __nv_bfloat16* __restrict__ Wp)
+{
+    const size_t total = (size_t)K * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / N), j = (int)(e % N);
+        Wp[(size_t)k * ldp + j] = __float2bfloat16_rn(W[e]);
     }
 }
 
@@ -985,6 +1107,19 @@ struct mmpc_mlp {
     float* I0 = nullptr;      // inference ping-pong [inf_rows][maxw]
     float* I1 = nullptr;
     long long step = 0;
+    // training on the tensor cores (mmpc_mlp_set_train_tensor_cores): the
+    // bfloat16 operands of the three products of every layer, allocated on
+    // first use
+    int train_tensor = 0;
+    int ldT = 0;                         // row stride of the column (transposed) buffers: max_batch rounded up to 8
+    __nv_bfloat16* X16 = nullptr;        // features as bfloat16 rows [max_batch][width[0]]
+    std::vector<__nv_bfloat16*> H16;     // H16[i] (i >= 1): layer i's input as bfloat16 rows [max_batch][width[i]]
+    std::vector<__nv_bfloat16*> HT;      // HT[i]: layer i's input as bfloat16 columns [width[i]][ldT] (HT[0]: features)
+    __nv_bfloat16* G16[2] = {nullptr, nullptr};  // output gradients, bfloat16 rows [max_batch][ld8(maxw)]
+    __nv_bfloat16* GT[2] = {nullptr, nullptr};   // and columns [maxw][ldT]
+    std::vector<__nv_bfloat16*> W16P;    // W16P[i]: bfloat16 W[i] with rows padded to ld8(width[i+1]) (only where width[i+1] % 8 != 0)
+    float* tpart = nullptr;              // split partial sums of a weight gradient
+    size_t tpart_count = 0;
 };
 
 namespace {
@@ -999,6 +1134,10 @@ void mlp_free(mmpc_mlp* n)
         for (float* p : *v) f(p);
     for (auto* p : n->W16) f(p);
     for (auto* p : n->W16T) f(p);
+    for (auto* p : n->H16) f(p);
+    for (auto* p : n->HT) f(p);
+    for (auto* p : n->W16P) f(p);
+    f(n->X16); f(n->G16[0]); f(n->G16[1]); f(n->GT[0]); f(n->GT[1]); f(n->tpart);
     f(n->d_err);
     f(n->Yb); f(n->D0); f(n->D1); f(n->part); f(n->I0); f(n->I1); f(n->Xb);
     delete n;
@@ -1016,10 +1155,17 @@ void gemm(int M, int N, int K, int splits, const float* A, int lda, const TBt* B
 
 int splits_for(const mmpc_mlp* n, int rows) { return std::max(1, (rows + n->ksplit_rows - 1) / n->ksplit_rows); }
 
+int ld8(int c) { return (c + 7) / 8 * 8; }
+
+constexpr int MAX_WGRAD_SPLITS = 64;  // split partial sums of a weight gradient
+
 void refresh_bf16(mmpc_mlp* n, int i, cudaStream_t st)
 {
     const size_t wc = wcount(n, i);
     tc::to_bf16_t_kernel<<<grid_for(wc), 256, 0, st>>>(n->W[i], n->cfg.width[i], n->cfg.width[i + 1], n->W16T[i]);
+    if (i < (int)n->W16P.size() && n->W16P[i])
+        tc::to_bf16_padded_kernel<<<grid_for(wc), 256, 0, st>>>(n->W[i], n->cfg.width[i], n->cfg.width[i + 1],
+                                                                 ld8(n->cfg.width[i + 1]), n->W16P[i]);
 }
 
 // Launch shape of the tensor-core GEMM for N outputs: BN columns per CTA
@@ -1076,19 +1222,20 @@ EncodeTiledFn tensor_map_encoder()
     return fn;
 }
 
-// Row-major bfloat16 matrix [rows][cols] (cols a multiple of 8, base 16-byte
-// aligned) as a 2-D tensor map with boxes of {64 columns, box_rows rows} in
-// the 128-byte swizzle: one K step (64 elements = 128 B per row) of box_rows
-// rows per copy, landing in the layout the MMA descriptors read; outside the
-// matrix the box reads zeros.
-bool encode_rows(CUtensorMap* map, const void* base, int cols, int rows, int box_rows)
+// Row-major bfloat16 matrix [rows][cols] with a row stride of ld elements
+// (a multiple of 8: 16-byte rows; base 16-byte aligned) as a 2-D tensor map
+// with boxes of {64 columns, box_rows rows} in the 128-byte swizzle: one K
+// step (64 elements = 128 B per row) of box_rows rows per copy, landing in the
+// layout the MMA descriptors read; outside the matrix (columns >= cols, rows
+// >= rows) the box reads zeros.
+bool encode_rows(CUtensorMap* map, const void* base, int cols, int ld, int rows, int box_rows)
 {
     const EncodeTiledFn fn = tensor_map_encoder();
-    if (!fn || cols % 8 != 0 || rows < 1 || box_rows < 1 || box_rows > 256 ||
+    if (!fn || ld % 8 != 0 || cols < 1 || cols > ld || rows < 1 || box_rows < 1 || box_rows > 256 ||
         (reinterpret_cast<uintptr_t>(base) & 15) != 0)
         return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1u, 1u};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
@@ -1107,28 +1254,55 @@ size_t tma_smem(int BN)
     return (size_t)tc::TMA_STAGES * ((size_t)tc::BM * tc::BK * 2 + (size_t)BN * tc::BK * 2) + 1024;
 }
 
-template <typename TC, bool GELU>
-bool tma_launch(const mmpc_mlp* n, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
-                const float* bias, TC* C, cudaStream_t st)
+// C = A Bt^T through the pipelined kernel: A [M][K] (row stride lda), Bt
+// [N][K] (row stride ldb), both bfloat16; the epilogue `epi` of MODE.  Z > 1
+// splits the reduction into Z ranges of whole K steps, each unit writing its
+// partial sum (TE_WGRAD); *splits_out (if given) receives the number of
+// splits launched (ranges past K are dropped).  False when a tensor map
+// cannot be made (nothing launched).
+template <int MODE>
+bool tma_run(const mmpc_mlp* n, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt,
+             int ldb, int Z, const tc::Epi& epi, cudaStream_t st, int* splits_out = nullptr)
 {
     const int BN = tma_bn(N);
     CUtensorMap ma, mb;
-    if (!encode_rows(&ma, A, K, M, tc::BM) || !encode_rows(&mb, Bt, K, N, BN)) return false;
+    if (!encode_rows(&ma, A, K, lda, M, tc::BM) || !encode_rows(&mb, Bt, K, ldb, N, BN)) return false;
     uint32_t ncols = 32;
     while ((int)ncols < 2 * BN) ncols <<= 1;
     const size_t smem = tma_smem(BN);
-    const int tiles = ((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN);
+    const int ks_total = (K + tc::BK - 1) / tc::BK;
+    Z = std::max(1, std::min(Z, ks_total));
+    const int KS = (ks_total + Z - 1) / Z;
+    Z = (ks_total + KS - 1) / KS;
+    const int units = ((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN) * Z;
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::umma_tma_gemm_kernel<TC, GELU>, tc::TMA_THREADS,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::umma_tma_gemm_kernel<MODE>, tc::TMA_THREADS,
                                                       smem) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         return false;
     }
-    const int grid = std::max(1, std::min(tiles, n->sms * per_sm));
-    tc::umma_tma_gemm_kernel<TC, GELU>
-        <<<grid, tc::TMA_THREADS, smem, st>>>(ma, mb, M, N, K, bias, C, N, BN, ncols, n->d_err);
+    const int grid = std::max(1, std::min(units, n->sms * per_sm));
+    tc::umma_tma_gemm_kernel<MODE><<<grid, tc::TMA_THREADS, smem, st>>>(ma, mb, M, N, KS, Z, epi, BN, ncols, n->d_err);
+    if (splits_out) *splits_out = Z;
     return true;
+}
+
+// one inference layer: GELU + bfloat16 rows (hidden) or float32 rows (last)
+template <typename TC, bool GELU>
+bool tma_launch(const mmpc_mlp* n, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
+                const float* bias, TC* C, cudaStream_t st)
+{
+    tc::Epi e{};
+    e.bias = bias;
+    if (GELU) {
+        e.r16 = reinterpret_cast<__nv_bfloat16*>(C);
+        e.ld16 = N;
+        return tma_run<tc::TE_HID>(n, M, N, K, A, K, Bt, K, 1, e, st);
+    }
+    e.f32 = reinterpret_cast<float*>(C);
+    e.ld32 = N;
+    return tma_run<tc::TE_OUT>(n, M, N, K, A, K, Bt, K, 1, e, st);
 }
 
 // Inference on the tensor cores: hidden activations travel as bfloat16, the
@@ -1187,6 +1361,130 @@ void forward_rows(mmpc_mlp* n, const float* X, int M, float* Y, bool keep, float
                                                              keep ? n->P[i] : nullptr, nullptr, st);
         in = out;
     }
+}
+
+// Buffers of tensor-core training (first use); false on an allocation error.
+bool ensure_train_buffers(mmpc_mlp* n)
+{
+    if (n->X16) return true;
+    const int L = n->L;
+    const int* w = n->cfg.width;
+    const size_t mb = (size_t)n->cfg.max_batch;
+    n->ldT = ld8(n->cfg.max_batch);
+    cudaError_t e = cudaSuccess;
+    auto bf = [&](__nv_bfloat16** p, size_t cnt) {
+        if (e == cudaSuccess) e = cudaMalloc(p, sizeof(__nv_bfloat16) * std::max<size_t>(cnt, 1));
+    };
+    n->H16.assign(L, nullptr);
+    n->HT.assign(L, nullptr);
+    n->W16P.assign(L, nullptr);
+    bf(&n->X16, mb * w[0]);
+    for (int i = 0; i < L; ++i) {
+        if (i >= 1) bf(&n->H16[i], mb * w[i]);
+        bf(&n->HT[i], (size_t)w[i] * n->ldT);
+        if (w[i + 1] % 8 != 0) bf(&n->W16P[i], (size_t)w[i] * ld8(w[i + 1]));
+    }
+    for (int k = 0; k < 2; ++k) {
+        bf(&n->G16[k], mb * ld8(n->maxw));
+        bf(&n->GT[k], (size_t)n->maxw * n->ldT);
+    }
+    size_t maxw_count = 0;
+    for (int i = 0; i < L; ++i) maxw_count = std::max(maxw_count, wcount(n, i));
+    n->tpart_count = maxw_count * MAX_WGRAD_SPLITS;
+    if (e == cudaSuccess) e = cudaMalloc(&n->tpart, sizeof(float) * n->tpart_count);
+    for (int i = 0; i < L && e == cudaSuccess; ++i) {
+        refresh_bf16(n, i, 0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        // leave no half-made set behind: the next call retries from scratch
+        auto f = [](void* p) { if (p) cudaFree(p); };
+        for (auto* p : n->H16) f(p);
+        for (auto* p : n->HT) f(p);
+        for (auto* p : n->W16P) f(p);
+        f(n->X16); f(n->G16[0]); f(n->G16[1]); f(n->GT[0]); f(n->GT[1]); f(n->tpart);
+        n->H16.clear(); n->HT.clear(); n->W16P.clear();
+        n->X16 = nullptr; n->G16[0] = n->G16[1] = n->GT[0] = n->GT[1] = nullptr; n->tpart = nullptr;
+        cuda_fail(e, "tensor-core training buffers");
+        return false;
+    }
+    return true;
+}
+
+void rows_cols(const float* X, int M, int cols, __nv_bfloat16* R, int ldr, __nv_bfloat16* T, int ldT, cudaStream_t st)
+{
+    dim3 grid((cols + 31) / 32, (M + 31) / 32);
+    tc::rows_cols_bf16_kernel<<<grid, 256, 0, st>>>(X, M, cols, cols, R, ldr, T, ldT);
+}
+
+// Splits of a weight gradient's reduction over M rows: enough units to cover
+// the SMs, at least two K steps (128 rows) per split.
+int wgrad_splits(const mmpc_mlp* n, int K_out, int N_out, int M)
+{
+    const int tiles = ((K_out + tc::BM - 1) / tc::BM) * ((N_out + tma_bn(N_out) - 1) / tma_bn(N_out));
+    const int ks = (M + tc::BK - 1) / tc::BK;
+    return std::max(1, std::min({(n->sms + tiles - 1) / tiles, ks / 2, MAX_WGRAD_SPLITS}));
+}
+
+// Loss and gradients with the three products of every layer on the tensor
+// cores (bfloat16 operands, float32 accumulation):
+//   forward    P_i = H_i W_i + b_i, H_{i+1} = GELU(P_i)     A = H_i rows, Bt = W_i^T
+//   backward   D_{i-1} = (D_i W_i^T) * GELU'(P_{i-1})       A = D_i rows, Bt = W_i
+//   gradient   dW_i = H_i^T D_i, split over the rows        A = H_i columns, Bt = D_i columns
+// with db_i the column sums of the float32 D_i.  Every epilogue writes the
+// bfloat16 operands the later products read (rows and columns), so no
+// separate rounding or transposition pass runs except for the features and
+// the loss gradient.  Returns false if a tensor map could not be made.
+bool loss_grad_tensor(mmpc_mlp* n, const float* X, const float* Z, int M, float* loss_out, cudaStream_t st)
+{
+    const int L = n->L;
+    const int* w = n->cfg.width;
+    rows_cols(X, M, w[0], n->X16, w[0], n->HT[0], n->ldT, st);
+    for (int i = 0; i < L; ++i) {
+        const __nv_bfloat16* in = i == 0 ? n->X16 : n->H16[i];
+        tc::Epi e{};
+        e.bias = n->b[i];
+        if (i < L - 1) {
+            e.f32 = n->P[i]; e.ld32 = w[i + 1];
+            e.r16 = n->H16[i + 1]; e.ld16 = w[i + 1];
+            e.t16 = n->HT[i + 1]; e.ldT = n->ldT;
+            if (!tma_run<tc::TE_TRAIN>(n, M, w[i + 1], w[i], in, w[i], n->W16T[i], w[i], 1, e, st)) return false;
+        } else {
+            e.f32 = n->Yb; e.ld32 = w[L];
+            if (!tma_run<tc::TE_OUT>(n, M, w[L], w[i], in, w[i], n->W16T[i], w[i], 1, e, st)) return false;
+        }
+    }
+    const size_t cnt = (size_t)M * w[L];
+    if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(float), st);
+    mse_kernel<<<grid_for(cnt), 256, 0, st>>>(n->Yb, Z, cnt, n->D0, loss_out);
+    rows_cols(n->D0, M, w[L], n->G16[0], ld8(w[L]), n->GT[0], n->ldT, st);
+    float* Df = n->D0;
+    float* Dn = n->D1;
+    int cur = 0;
+    for (int i = L - 1; i >= 0; --i) {
+        const int K = w[i], N = w[i + 1];
+        tc::Epi g{};
+        g.f32 = n->tpart; g.ld32 = N; g.zstride = (size_t)K * N;
+        int z = 1;
+        if (!tma_run<tc::TE_WGRAD>(n, K, N, M, n->HT[i], n->ldT, n->GT[cur], n->ldT, wgrad_splits(n, K, N, M), g, st,
+                                   &z))
+            return false;
+        reduce_partials_kernel<<<grid_for((size_t)K * N), 256, 0, st>>>(n->tpart, z, (size_t)K * N, n->gW[i]);
+        colsum_kernel<<<(N + 7) / 8, 256, 0, st>>>(Df, M, N, n->gb[i]);
+        if (i > 0) {
+            tc::Epi d{};
+            d.f32 = Dn; d.ld32 = K;
+            d.r16 = n->G16[cur ^ 1]; d.ld16 = ld8(K);
+            d.t16 = n->GT[cur ^ 1]; d.ldT = n->ldT;
+            d.pre = n->P[i - 1]; d.ldp = K;
+            const __nv_bfloat16* Wb = n->W16P[i] ? n->W16P[i] : n->W16[i];
+            if (!tma_run<tc::TE_DX>(n, M, K, N, n->G16[cur], ld8(N), Wb, ld8(N), 1, d, st)) return false;
+            std::swap(Df, Dn);
+            cur ^= 1;
+        }
+    }
+    return true;
 }
 
 bool valid_cfg(const mmpc_mlp_config* c)
@@ -1353,9 +1651,12 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
     for (const void* kf : tc_kernels)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
     size_t tma_max = 0;
-    for (int i = 0; i < L; ++i) tma_max = std::max(tma_max, tma_smem(tma_bn(cfg->width[i + 1])));
-    const void* tma_kernels[] = {(const void*)tc::umma_tma_gemm_kernel<float, false>,
-                                 (const void*)tc::umma_tma_gemm_kernel<__nv_bfloat16, true>};
+    for (int i = 0; i <= L; ++i) tma_max = std::max(tma_max, tma_smem(tma_bn(cfg->width[i])));
+    const void* tma_kernels[] = {(const void*)tc::umma_tma_gemm_kernel<tc::TE_HID>,
+                                 (const void*)tc::umma_tma_gemm_kernel<tc::TE_OUT>,
+                                 (const void*)tc::umma_tma_gemm_kernel<tc::TE_TRAIN>,
+                                 (const void*)tc::umma_tma_gemm_kernel<tc::TE_DX>,
+                                 (const void*)tc::umma_tma_gemm_kernel<tc::TE_WGRAD>};
     for (const void* kf : tma_kernels)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_max);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -1389,6 +1690,12 @@ int mmpc_mlp_loss_grad(mmpc_mlp* n, const float* X, const float* Z, int M, float
     if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
     if (!X || !Z || M < 1 || M > n->cfg.max_batch) return fail(MMPC_ERR_INVALID_ARG, "bad loss_grad arguments");
     cudaStream_t st = (cudaStream_t)stream;
+    if (n->train_tensor) {
+        if (!loss_grad_tensor(n, X, Z, M, loss_out, st))
+            return fail(MMPC_ERR_CUDA, "mmpc_mlp_loss_grad: a tensor map could not be made");
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_loss_grad");
+    }
     const int L = n->L;
     forward_rows(n, X, M, n->Yb, true, nullptr, nullptr, st);
     const size_t cnt = (size_t)M * n->cfg.width[L];
@@ -1480,6 +1787,20 @@ int mmpc_mlp_set_tensor_cores(mmpc_mlp* n, int on)
     if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
     if (on < 0 || on > 2) return fail(MMPC_ERR_INVALID_ARG, "tensor-core mode must be 0, 1 or 2");
     n->tensor = on;
+    return MMPC_OK;
+}
+
+int mmpc_mlp_set_train_tensor_cores(mmpc_mlp* n, int on)
+{
+    if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");
+    if (on != 0 && on != 1) return fail(MMPC_ERR_INVALID_ARG, "training mode must be 0 or 1");
+    if (on) {
+        if (!n->tma_widths || !tensor_map_encoder())
+            return fail(MMPC_ERR_INVALID_ARG, "tensor-core training needs every layer input width a multiple of 8");
+        if (n->cfg.max_batch > 65535 * 32) return fail(MMPC_ERR_INVALID_ARG, "max_batch too large for tensor-core training");
+        if (!ensure_train_buffers(n)) return MMPC_ERR_CUDA;
+    }
+    n->train_tensor = on;
     return MMPC_OK;
 }
 

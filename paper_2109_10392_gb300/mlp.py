@@ -19,7 +19,7 @@ EXPORTED = ("mmpc_features", "mmpc_warm_decode", "mmpc_warm_encode", "mmpc_colum
             "mmpc_standardize",
             "mmpc_mlp_create", "mmpc_mlp_forward", "mmpc_mlp_loss_grad", "mmpc_mlp_adamw", "mmpc_mlp_read",
             "mmpc_mlp_write", "mmpc_mlp_destroy", "mmpc_mlp_last_error", "mmpc_mlp_set_tensor_cores",
-            "mmpc_mlp_status")
+            "mmpc_mlp_set_train_tensor_cores", "mmpc_mlp_status")
 READ_W, READ_B, READ_DW, READ_DB, READ_MW, READ_VW, READ_MB, READ_VB = range(8)
 
 
@@ -72,6 +72,7 @@ def lib():
     L.mmpc_mlp_read.argtypes = [vp, ip, ip, vp, ctypes.c_size_t]
     L.mmpc_mlp_write.argtypes = [vp, ip, ip, vp, ctypes.c_size_t]
     L.mmpc_mlp_set_tensor_cores.argtypes = [vp, ip]
+    L.mmpc_mlp_set_train_tensor_cores.argtypes = [vp, ip]
     L.mmpc_mlp_status.argtypes = [vp]
     L.mmpc_mlp_destroy.argtypes = [vp]
     L.mmpc_mlp_destroy.restype = None
@@ -226,6 +227,11 @@ class Mlp:
         """False/0: SIMT; True/1: the TMA-fed tcgen05 pipeline; 2: the single-stage tcgen05 GEMM."""
         _check(lib().mmpc_mlp_set_tensor_cores(self.handle, int(on)))
 
+    def set_train_tensor_cores(self, on):
+        """False/0: training on the FP32 SIMT kernels; True/1: its three
+        products per layer on the tcgen05 pipeline (bfloat16 operands)."""
+        _check(lib().mmpc_mlp_set_train_tensor_cores(self.handle, int(on)))
+
     def status(self):
         _check(lib().mmpc_mlp_status(self.handle))
 
@@ -293,13 +299,57 @@ def _time_forward(rows: int, reps: int = 10, seed: int = 0) -> list:
     return out
 
 
+def _time_train(batch: int = 4096, reps: int = 50, seed: int = 0) -> list:
+    """Times one training step (loss and gradients, then AdamW) of the
+    warm-start network (64 -> 256 x 3 -> 72, seeded random weights) on a
+    random batch: FP32 SIMT kernels, then the tensor-core products; CUDA
+    events over `reps` consecutive steps.  FLOPs: the forward products, the
+    weight gradients and the backward products of every layer but the first."""
+    import torch
+
+    from . import scenes
+    widths = (64, 256, 256, 256, 72)
+    Ws, bs = scenes.mlp_init(seed, widths)
+    net = Mlp(widths, Ws, bs, max_batch=batch)
+    prods = [i * o for i, o in zip(widths[:-1], widths[1:])]
+    flops = 2.0 * batch * (2 * sum(prods) + sum(prods[1:]))
+    g = torch.Generator("cuda:0").manual_seed(seed)
+    X = torch.randn((batch, widths[0]), device="cuda:0", generator=g)
+    Z = torch.randn((batch, widths[-1]), device="cuda:0", generator=g)
+    loss = torch.zeros((1,), device="cuda:0")
+    out = []
+    for on in (0, 1):
+        net.set_train_tensor_cores(on)
+        for _ in range(3):
+            net.loss_grad(X, Z, loss)
+            net.adamw(1e-4)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            net.loss_grad(X, Z, loss)
+            net.adamw(1e-4)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out.append(dict(batch=batch, train_tensor_cores=on, ms_per_step=ms, tflops=flops / (ms * 1e-3) / 1e12))
+    net.status()
+    net.close()
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     import json
-    ap = argparse.ArgumentParser(description="time the warm-start network's forward pass")
+    ap = argparse.ArgumentParser(description="time the warm-start network's forward pass and training step")
     ap.add_argument("--rows", type=int, nargs="+", default=[65536, 1 << 20])
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--train-batch", type=int, nargs="*", default=[],
+                    help="also time one training step at these batch sizes")
     a = ap.parse_args()
     for r in a.rows:
         for line in _time_forward(r, a.reps):
+            print(json.dumps(line), flush=True)
+    for bsz in a.train_batch:
+        for line in _time_train(bsz):
             print(json.dumps(line), flush=True)

@@ -328,3 +328,108 @@ def test_tensor_core_mode_checked():
         with pytest.raises(RuntimeError):
             net.set_tensor_cores(bad)
     net.close()
+
+
+@pytest.mark.parametrize("widths", [(64, 256, 256, 256, 72), (64, 256, 256, 256, 36), (64, 320, 40),
+                                    (8, 16, 8, 24), (16, 32, 13)])
+def test_tensor_core_gradients_match_oracle(widths):
+    """Training on the tensor cores (forward H W, backward D W^T and weight
+    gradient H^T D on the tcgen05 pipeline, bfloat16 operands, float32
+    accumulation) against the oracle with the same operand roundings
+    (op_bf16): ragged row counts (one row, the 128-row tile's tail, several
+    tiles, splits of the weight gradient's row sum), an output width that is
+    not a multiple of 8 (padded operand rows), a layer wider than one
+    256-column tile.  The bfloat16 rounding of an activation or gradient
+    can fall the other way where float32 and float64 pre-activations differ
+    in the last bits, which moves single terms by 2^-8: hence max 1e-2 and
+    RMS 2e-3 of each array's scale."""
+    import torch
+    Ws, bs = scenes.mlp_init(31, widths)
+    rng = np.random.default_rng(32)
+    bs = [rng.normal(0, 0.1, b.shape).astype(np.float32) for b in bs]
+    net = mlp.Mlp(widths, Ws, bs, max_batch=2100)
+    net.set_train_tensor_cores(True)
+    loss = torch.zeros((1,), device="cuda:0")
+    for M_rows in (1, 127, 300, 2100):
+        X = rng.normal(size=(M_rows, widths[0])).astype(np.float32)
+        Z = rng.normal(size=(M_rows, widths[-1])).astype(np.float32)
+        net.loss_grad(_dev(X), _dev(Z), loss)
+        net.status()
+        L, gW, gb = M.loss_and_grads(Ws, bs, X.astype(np.float64), Z.astype(np.float64), bf16=True, op_bf16=True)
+        assert abs(float(loss.item()) - L) <= 1e-3 * L, (M_rows, float(loss.item()), L)
+        for i in range(len(Ws)):
+            for got, want, tag in ((net.read(mlp.READ_DW, i), gW[i], "dW"), (net.read(mlp.READ_DB, i), gb[i], "db")):
+                scale = np.abs(want).max()
+                err = np.abs(got - want)
+                assert err.max() <= 1e-2 * scale, (widths, M_rows, i, tag, err.max(), scale)
+                assert np.sqrt(np.mean(err ** 2)) <= 2e-3 * scale, (widths, M_rows, i, tag)
+    net.close()
+
+
+def test_tensor_core_training_against_simt():
+    """Same network, same batch: the tensor-core gradients differ from the
+    float32 SIMT ones only by the bfloat16 operand rounding (nonzero, a few
+    per mille of the scale), are bit-identical over repeated calls (fixed
+    order of the split partial sums), and switching back restores the SIMT
+    results exactly."""
+    import torch
+    widths = (64, 256, 256, 256, 72)
+    Ws, bs = scenes.mlp_init(41, widths)
+    net = mlp.Mlp(widths, Ws, bs, max_batch=4096)
+    rng = np.random.default_rng(42)
+    X, Z = _dev(rng.normal(size=(4096, 64))), _dev(rng.normal(size=(4096, 72)))
+    net.loss_grad(X, Z)
+    simt = [net.read(mlp.READ_DW, i) for i in range(4)]
+    net.set_train_tensor_cores(True)
+    net.loss_grad(X, Z)
+    a = [net.read(mlp.READ_DW, i) for i in range(4)]
+    net.loss_grad(X, Z)
+    net.status()
+    b = [net.read(mlp.READ_DW, i) for i in range(4)]
+    for x, y, s in zip(a, b, simt):
+        assert np.array_equal(x, y)
+        d = np.abs(x - s).max() / np.abs(s).max()
+        assert 0 < d < 3e-2, d
+    net.set_train_tensor_cores(False)
+    net.loss_grad(X, Z)
+    torch.cuda.synchronize()
+    for i in range(4):
+        assert np.array_equal(net.read(mlp.READ_DW, i), simt[i])
+    net.close()
+
+
+def test_tensor_core_training_fits_a_smooth_map():
+    """Behaviour: the tensor-core training loop fits the smooth synthetic map
+    of the SIMT test as well."""
+    import torch
+    Ws, bs = scenes.mlp_init(9, (64, 128, 128, 8))
+    net = mlp.Mlp((64, 128, 128, 8), Ws, bs, max_batch=1024, weight_decay=0.0)
+    net.set_train_tensor_cores(True)
+    rng = np.random.default_rng(10)
+    A = rng.normal(size=(64, 8)) / 8
+    X = rng.normal(size=(1024, 64))
+    Z = np.tanh(X @ A) + 0.1 * (X[:, :8] ** 2)
+    Xd, Zd = _dev(X), _dev(Z)
+    loss = torch.zeros((1,), device="cuda:0")
+    first = None
+    for it in range(400):
+        net.loss_grad(Xd, Zd, loss)
+        if it == 0:
+            first = float(loss.item())
+        net.adamw(3e-3)
+    net.loss_grad(Xd, Zd, loss)
+    net.status()
+    last = float(loss.item())
+    assert last < 0.05 * first, (first, last)
+    net.close()
+
+
+def test_tensor_core_training_mode_checked():
+    Ws, bs = scenes.mlp_init(1, (60, 256, 36))
+    net = mlp.Mlp((60, 256, 36), Ws, bs, max_batch=16)
+    with pytest.raises(RuntimeError):
+        net.set_train_tensor_cores(True)  # input width 60: rows of 120 bytes
+    for bad in (-1, 2):
+        with pytest.raises(RuntimeError):
+            net.set_train_tensor_cores(bad)
+    net.close()
