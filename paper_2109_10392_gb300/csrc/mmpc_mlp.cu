@@ -653,30 +653,31 @@ __global__ void __launch_bounds__(THREADS, 1) umma_gemm_kernel(int M, int N, int
 // ---------------------------------------------------------------------------
 constexpr int TMA_STAGES = 4;
 constexpr int EPI_WARPS = 16;
+constexpr int EPI_PARTS = EPI_WARPS / 4;  // epilogue warps per TMEM sub-partition
 constexpr int TMA_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
 constexpr int TMA_THREADS = 32 * (EPI_WARPS + 2);
 
-// GELU of two lanes with fused multiply-adds only: x / 2 + g(x), where
-// g(x) = x (Phi(x) - 1/2) is even and entire in t = x^2; for |x| <= 5 a
-// degree-12 polynomial in u = 2 t / 25 - 1 (coefficients from
-// csrc/fit_gelu.py: least squares on Chebyshev nodes refined towards the
-// minimax), beyond it g = |x| / 2.  |error| < 2e-6 in float32 -- far below
-// the bfloat16 rounding the activations then undergo.
+// GELU of two lanes with fused multiply-adds only: x Phi(x) with
+// Phi(x) = sat(1/2 + x k(x^2)), k a degree-12 polynomial in
+// u = 2 min(x^2, 25) / 25 - 1 (coefficients from csrc/fit_gelu.py: least
+// squares on Chebyshev nodes, weighted by x^2, refined towards the minimax)
+// and sat the clamp to [0, 1], which also gives the limits x and 0 beyond
+// |x| = 5 without a branch.  |error| < 1.5e-6 in float32 -- far below the
+// bfloat16 rounding the activations then undergo.
 __device__ __forceinline__ float2 gelu_poly2(float2 x)
 {
-    constexpr float P[13] = {-1.302992459e-02f, 2.610467188e-02f, -1.061521657e-02f, 1.563348621e-02f,
-                             -6.101960689e-02f, 8.403629065e-02f, -8.500314504e-02f, 9.675235301e-02f,
-                             -1.126994267e-01f, 1.391513944e-01f,  -2.346803546e-01f, 8.883196115e-01f,
-                             1.767047167e+00f};
+    constexpr float P[13] = {4.817027657e-04f,  -1.503391657e-03f, 2.027839655e-03f,  -2.940212376e-03f,
+                             6.143897772e-03f,  -1.095324289e-02f, 1.650539227e-02f,  -2.334370278e-02f,
+                             3.142509237e-02f,  -4.043198377e-02f, 5.152147263e-02f,  -7.029668987e-02f,
+                             1.413637847e-01f};
     const float2 t = __fmul2_rn(x, x);
     const float2 u = __ffma2_rn(make_float2(fminf(t.x, 25.f), fminf(t.y, 25.f)), make_float2(0.08f, 0.08f),
                                 make_float2(-1.f, -1.f));
     float2 p = make_float2(P[0], P[0]);
 #pragma unroll
     for (int i = 1; i < 13; ++i) p = __ffma2_rn(p, u, make_float2(P[i], P[i]));
-    const float ax = fabsf(x.x), ay = fabsf(x.y);
-    const float2 g = make_float2(ax > 5.f ? 0.5f * ax : p.x, ay > 5.f ? 0.5f * ay : p.y);
-    return __ffma2_rn(make_float2(0.5f, 0.5f), x, g);
+    const float2 phi = make_float2(__saturatef(__fmaf_rn(x.x, p.x, 0.5f)), __saturatef(__fmaf_rn(x.y, p.y, 0.5f)));
+    return __fmul2_rn(x, phi);
 }
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte
@@ -721,21 +722,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// bias[j0 .. j0 + 16) (zeros past N); j0 is a multiple of 16
-__device__ __forceinline__ void load_bias16(const float* __restrict__ bias, int j0, int N, float (&bv)[16])
-{
-    if (j0 + 16 <= N) {
-#pragma unroll
-        for (int c = 0; c < 16; c += 4) {
-            const float4 t4 = __ldg(reinterpret_cast<const float4*>(bias + j0 + c));
-            bv[c] = t4.x; bv[c + 1] = t4.y; bv[c + 2] = t4.z; bv[c + 3] = t4.w;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 16; ++c) bv[c] = j0 + c < N ? bias[j0 + c] : 0.f;
-    }
-}
 
 // What the pipelined kernel's epilogue makes of a 128 x BN accumulator tile.
 enum : int {
@@ -801,18 +787,26 @@ __device__ __forceinline__ void store_bf16_cols(__nv_bfloat16* t, int ldT, int g
         if (c < cnt) t[(size_t)(j0 + c) * ldT + gi] = __float2bfloat16_rn((c & 1) ? v[c >> 1].y : v[c >> 1].x);
 }
 
-// the epilogue of columns j0 .. j0 + 16 of row gi (bv: the bias there, or zeros)
+// the epilogue of columns j0 .. j0 + 16 of row gi (sb: the bias of those
+// columns in shared memory, 16-byte aligned; read only by the modes with a bias)
 template <int MODE>
-__device__ __forceinline__ void epilogue16(const uint32_t (&r)[16], const float (&bv)[16], int gi, int M, int j0, int N,
+__device__ __forceinline__ void epilogue16(const uint32_t (&r)[16], const float* sb, int gi, int M, int j0, int N,
                                            int z, const Epi& e)
 {
     float2 v[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        v[c] = make_float2(__uint_as_float(r[2 * c]), __uint_as_float(r[2 * c + 1]));
-        if (MODE == TE_HID || MODE == TE_OUT || MODE == TE_TRAIN)
-            v[c] = __fadd2_rn(v[c], make_float2(bv[2 * c], bv[2 * c + 1]));
-        if (MODE == TE_HID) v[c] = gelu_poly2(v[c]);
+    for (int c = 0; c < 8; ++c) v[c] = make_float2(__uint_as_float(r[2 * c]), __uint_as_float(r[2 * c + 1]));
+    if (MODE == TE_HID || MODE == TE_OUT || MODE == TE_TRAIN) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float4 b4 = reinterpret_cast<const float4*>(sb)[c];
+            v[2 * c] = __fadd2_rn(v[2 * c], make_float2(b4.x, b4.y));
+            v[2 * c + 1] = __fadd2_rn(v[2 * c + 1], make_float2(b4.z, b4.w));
+        }
+    }
+    if (MODE == TE_HID) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = gelu_poly2(v[c]);
     }
     if (gi >= M) return;
     const int cnt = min(16, N - j0);
@@ -866,8 +860,12 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     const int a_bytes = BM * BK * 2, b_bytes = BN * BK * 2, st_bytes = a_bytes + b_bytes;
     __shared__ __align__(8) unsigned long long s_full[TMA_STAGES], s_empty[TMA_STAGES], s_tfull[2], s_tempty[2];
     __shared__ uint32_t s_tmem;
+    __shared__ __align__(16) float s_bias[MMPC_MLP_MAX_WIDTH];  // the layer's bias (N <= MMPC_MLP_MAX_WIDTH)
+    constexpr bool has_bias = MODE == TE_HID || MODE == TE_OUT || MODE == TE_TRAIN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN, tiles = mt * nt, units = tiles * Z;
+    if (has_bias)
+        for (int j = tid; j < MMPC_MLP_MAX_WIDTH; j += blockDim.x) s_bias[j] = j < N ? epi.bias[j] : 0.f;
     if (warp == TMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
                      "r"(ncols)
@@ -963,9 +961,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         __syncwarp();
     } else {
         // warp: TMEM sub-partition q (its 32 rows of the tile), and every
-        // fourth 16-column chunk starting at `part`
+        // EPI_PARTS-th 16-column chunk starting at `part`
         const int q = warp & 3, part = warp >> 2, chunks = BN / 16;
-        constexpr bool has_bias = MODE == TE_HID || MODE == TE_OUT || MODE == TE_TRAIN;
         for (int ui = 0; ui < my_units && ok; ++ui) {
             const int b = ui & 1;
             const int unit = (int)blockIdx.x + ui * (int)gridDim.x;
@@ -976,31 +973,21 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             ok = mbar_wait(saddr(&s_tfull[b]), (uint32_t)((ui >> 1) & 1), err);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // this warp's chunks part, part + 4, ...: the TMEM load and the
-            // bias of the next chunk are issued before the current one is
-            // processed (a wait::ld covers every load issued so far)
-            const int nch = chunks > part ? (chunks - part + 3) / 4 : 0;
+            // this warp's chunks part, part + EPI_PARTS, ...: the TMEM load of
+            // the next chunk is issued before the current one is processed (a
+            // wait::ld covers every load issued so far)
+            const int nch = chunks > part ? (chunks - part + EPI_PARTS - 1) / EPI_PARTS : 0;
             uint32_t ra[16], rb[16];
-            float ba[16], bb[16];
-            if (nch > 0) {
-                if (has_bias) load_bias16(epi.bias, n0 + part * 16, N, ba);
-                tmem_ld16(trow + (uint32_t)(part * 16), ra);
-            }
+            if (nch > 0) tmem_ld16(trow + (uint32_t)(part * 16), ra);
             for (int i = 0; i < nch; i += 2) {
-                const int ca = part + 4 * i, cb = ca + 4;
+                const int ca = part + EPI_PARTS * i, cb = ca + EPI_PARTS;
                 tmem_wait_ld();
-                if (i + 1 < nch) {
-                    if (has_bias) load_bias16(epi.bias, n0 + cb * 16, N, bb);
-                    tmem_ld16(trow + (uint32_t)(cb * 16), rb);
-                }
-                epilogue16<MODE>(ra, ba, gi, M, n0 + ca * 16, N, z, epi);
+                if (i + 1 < nch) tmem_ld16(trow + (uint32_t)(cb * 16), rb);
+                epilogue16<MODE>(ra, s_bias + n0 + ca * 16, gi, M, n0 + ca * 16, N, z, epi);
                 if (i + 1 < nch) {
                     tmem_wait_ld();
-                    if (i + 2 < nch) {
-                        if (has_bias) load_bias16(epi.bias, n0 + (cb + 4) * 16, N, ba);
-                        tmem_ld16(trow + (uint32_t)((cb + 4) * 16), ra);
-                    }
-                    epilogue16<MODE>(rb, bb, gi, M, n0 + cb * 16, N, z, epi);
+                    if (i + 2 < nch) tmem_ld16(trow + (uint32_t)((cb + EPI_PARTS) * 16), ra);
+                    epilogue16<MODE>(rb, s_bias + n0 + cb * 16, gi, M, n0 + cb * 16, N, z, epi);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1017,6 +1004,299 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     __syncthreads();
     if (warp == TMA_WARP)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// The whole network in one persistent kernel (inference).  A CTA takes pairs
+// of 128-row tiles; each tile's layer input lives in shared memory (the
+// 128-byte-swizzled K-major layout the MMA descriptors read, 16 KB per 64
+// columns), so hidden activations never leave the SM: the epilogue of layer l
+// writes layer l + 1's input in place of layer l's, which the MMAs of layer
+// l have finished reading.  The weights stream from L2 by TMA through a ring
+// of boxes {64 K, 128 N} (16 KB), each box feeding the MMAs of both tiles, in
+// the order (pair, layer, K block, N half) that the producer can run ahead in
+// without waiting for activations.  Accumulators: tile t in TMEM columns
+// [256 t, 256 t + 256).  Warp roles: 16 epilogue warps (tile t = warp / 8;
+// TMEM sub-partition warp % 4; column chunks alternate between the two warps
+// of a sub-partition), warp 16 the weight TMA, warp 17 the MMAs.  The
+// features are read (float32, coalesced) and rounded to bfloat16 by the
+// epilogue warps; the last layer's float32 outputs are staged in the tile's
+// buffer and copied out in contiguous rows.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int FUSED_MAX_RING = 6;
+
+struct FusedArgs {
+    CUtensorMap wmap[MMPC_MLP_MAX_LAYERS];  // transposed bfloat16 weights [N_l][K_l], boxes {64, 128}
+    const float* bias[MMPC_MLP_MAX_LAYERS];
+    int width[MMPC_MLP_MAX_LAYERS + 1];
+    int L, M, stages, bias_total;
+    uint32_t h_bytes;                       // one tile's buffer (a multiple of 1024)
+    const float* X;                         // [M][width[0]]
+    float* Y;                               // [M][width[L]]
+    unsigned* err;
+};
+
+// 16 bytes into the tile buffer: row r, 16-byte chunk j (8 bfloat16 columns)
+// of 64-column block kb, at (j ^ (r mod 8)) within the row (the 128-byte
+// swizzle of 8-row, 1024-byte atoms)
+__device__ __forceinline__ void st_sw128(uint32_t hbase, int r, int kb, int j, uint4 v)
+{
+    const uint32_t a = hbase + (uint32_t)kb * 16384u + (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u +
+                       ((uint32_t)(j ^ (r & 7)) << 4);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// bounded wait on an mbarrier completed by `count` arrivals of a group of
+// warps (tile-local synchronisation of the epilogue warps)
+__device__ __forceinline__ bool group_sync(uint32_t bar, uint32_t parity, unsigned* err)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+    return mbar_wait(bar, parity, err);
+}
+
+__global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __grid_constant__ FusedArgs args)
+{
+    extern __shared__ __align__(1024) unsigned char fsm_raw[];
+    unsigned char* fsm = fsm_raw + ((1024u - (saddr(fsm_raw) & 1023u)) & 1023u);
+    // [tile 0 buffer | tile 1 buffer | ring of stages x 16 KB | biases]
+    const uint32_t hb = args.h_bytes;
+    const uint32_t h0 = saddr(fsm), ring = h0 + 2 * hb;
+    float* s_bias = reinterpret_cast<float*>(fsm + 2 * hb + (size_t)args.stages * 16384);
+    __shared__ __align__(8) unsigned long long s_full[FUSED_MAX_RING], s_empty[FUSED_MAX_RING];
+    __shared__ __align__(8) unsigned long long s_acc, s_ready, s_tile[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_boff[MMPC_MLP_MAX_LAYERS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = args.L, M = args.M, S = args.stages;
+    unsigned* err = args.err;
+    if (tid == 0) {
+        int o = 0;
+        for (int l = 0; l < L; ++l) {
+            s_boff[l] = o;
+            o += (args.width[l + 1] + 15) / 16 * 16;
+        }
+    }
+    if (warp == TMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(saddr(&s_full[i]), 1);
+            mbar_init(saddr(&s_empty[i]), 1);
+        }
+        mbar_init(saddr(&s_acc), 1);
+        mbar_init(saddr(&s_ready), EPI_WARPS);
+        mbar_init(saddr(&s_tile[0]), EPI_WARPS / 2);
+        mbar_init(saddr(&s_tile[1]), EPI_WARPS / 2);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    for (int l = 0; l < L; ++l) {
+        const int nl = args.width[l + 1], off = s_boff[l];
+        for (int j = tid; j < (nl + 15) / 16 * 16; j += blockDim.x) s_bias[off + j] = j < nl ? args.bias[l][j] : 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const int pairs = (M + 255) / 256;
+    const int my_pairs = blockIdx.x < pairs ? (pairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    bool ok = true;
+    if (warp == TMA_WARP) {
+        if (lane == 0) {
+            int g = 0;
+            for (int pi = 0; pi < my_pairs && ok; ++pi)
+                for (int l = 0; l < L && ok; ++l) {
+                    const int KB = (args.width[l] + 63) / 64, NH = (args.width[l + 1] + 127) / 128;
+                    for (int kb = 0; kb < KB && ok; ++kb)
+                        for (int h = 0; h < NH && ok; ++h, ++g) {
+                            const int s = g % S;
+                            if (g >= S) ok = mbar_wait(saddr(&s_empty[s]), (uint32_t)(((g / S) - 1) & 1), err);
+                            if (!ok) break;
+                            const uint32_t full = saddr(&s_full[s]);
+                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full),
+                                         "r"(16384)
+                                         : "memory");
+                            tma_load_2d(ring + (uint32_t)s * 16384u, &args.wmap[l], kb * 64, h * 128, full);
+                        }
+                }
+        }
+        __syncwarp();
+    } else if (warp == MMA_WARP) {
+        if (lane == 0) {
+            int g = 0, issued = 0;
+            for (int pi = 0; pi < my_pairs && ok; ++pi)
+                for (int l = 0; l < L && ok; ++l) {
+                    const int e = pi * L + l;
+                    ok = mbar_wait(saddr(&s_ready), (uint32_t)(e & 1), err);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int N = args.width[l + 1];
+                    const int KB = (args.width[l] + 63) / 64, NH = (N + 127) / 128;
+                    for (int kb = 0; kb < KB && ok; ++kb)
+                        for (int h = 0; h < NH && ok; ++h, ++g) {
+                            const int s = g % S;
+                            ok = mbar_wait(saddr(&s_full[s]), (uint32_t)((g / S) & 1), err);
+                            if (!ok) break;
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const int nh = (min(128, N - 128 * h) + 15) / 16 * 16;
+                            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nh >> 3) << 17) |
+                                                   ((uint32_t)(BM >> 4) << 24);
+                            const uint32_t bst = ring + (uint32_t)s * 16384u;
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                const uint32_t dtm = tmem + (uint32_t)(256 * t + 128 * h);
+                                const uint32_t ast = h0 + (uint32_t)t * hb + (uint32_t)kb * 16384u;
+#pragma unroll
+                                for (int kk = 0; kk < BK / 16; ++kk) {
+                                    const uint64_t ad = sw128_desc(ast + (uint32_t)(kk * 32));
+                                    const uint64_t bd = sw128_desc(bst + (uint32_t)(kk * 32));
+                                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                                    asm volatile(
+                                        "{\n\t.reg .pred p;\n\t"
+                                        "setp.ne.b32 p, %4, 0;\n\t"
+                                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+                                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                        : "memory");
+                                }
+                            }
+                            asm volatile(
+                                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                    saddr(&s_empty[s]))
+                                : "memory");
+                        }
+                    if (!ok) break;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     saddr(&s_acc))
+                                 : "memory");
+                    issued = e + 1;
+                }
+            // after an expired wait: the copies issued by the producer land,
+            // and the last committed layer's MMAs complete, before the CTA
+            // exits (bounded as well)
+            if (!ok) {
+                for (int gg = g; gg < g + S; ++gg) mbar_wait(saddr(&s_full[gg % S]), (uint32_t)((gg / S) & 1), err);
+                if (issued > 0) mbar_wait(saddr(&s_acc), (uint32_t)((issued - 1) & 1), err);
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps: tile t, TMEM sub-partition q (rows 32 q .. 32 q + 31),
+        // chunks part, part + 2, ... of 16 columns
+        const int t = warp >> 3, q = warp & 3, part = (warp >> 2) & 1;
+        const int r = q * 32 + lane;           // this thread's row in the tile
+        const int tt = tid & 255;              // index among the tile's 256 threads
+        const uint32_t hbase = h0 + (uint32_t)t * hb;
+        float* stage = reinterpret_cast<float*>(fsm + (size_t)t * hb);
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(256 * t);
+        const int w0 = args.width[0];
+        int tsync = 0;  // completed phases of this tile's group barrier
+        for (int pi = 0; pi < my_pairs && ok; ++pi) {
+            const int m0 = ((int)blockIdx.x + pi * (int)gridDim.x) * 256 + t * 128;
+            // the features: 8 float32 per thread and step, coalesced rows,
+            // rounded to bfloat16 into block 0.. of the buffer; zeros past
+            // width[0] (up to the 64-column block) and past M
+            const int kb0 = (w0 + 63) / 64;
+            for (int e8 = tt; e8 < 128 * kb0 * 8; e8 += 256) {
+                const int rr = e8 / (kb0 * 8), cj = e8 % (kb0 * 8);  // row, 8-column group
+                const int gr = m0 + rr, c0 = cj * 8;
+                float v[8];
+                if (gr < M && c0 + 8 <= w0) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(args.X + (size_t)gr * w0 + c0));
+                    const float4 b = __ldg(reinterpret_cast<const float4*>(args.X + (size_t)gr * w0 + c0 + 4));
+                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = (gr < M && c0 + k < w0) ? args.X[(size_t)gr * w0 + c0 + k] : 0.f;
+                }
+                st_sw128(hbase, rr, cj >> 3, cj & 7,
+                         make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                    pack_bf16(v[6], v[7])));
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(saddr(&s_ready));
+            for (int l = 0; l < L && ok; ++l) {
+                const int e = pi * L + l;
+                ok = mbar_wait(saddr(&s_acc), (uint32_t)(e & 1), err);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int N = args.width[l + 1];
+                const float* bl = s_bias + s_boff[l];
+                if (l < L - 1) {
+                    // hidden layer: GELU(acc + b) as bfloat16 into the buffer
+                    // (the next layer's input), zeros up to the 64-column block
+                    const int nch = (N + 63) / 64 * 4;
+                    for (int c = part; c < nch; c += 2) {
+                        uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+                        if (c * 16 < N) {
+                            uint32_t rv[16];
+                            tmem_ld16(trow + (uint32_t)(c * 16), rv);
+                            tmem_wait_ld();
+                            float2 v[8];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const float4 b4 = reinterpret_cast<const float4*>(bl + c * 16)[k];
+                                v[2 * k] = gelu_poly2(__fadd2_rn(
+                                    make_float2(__uint_as_float(rv[4 * k]), __uint_as_float(rv[4 * k + 1])),
+                                    make_float2(b4.x, b4.y)));
+                                v[2 * k + 1] = gelu_poly2(__fadd2_rn(
+                                    make_float2(__uint_as_float(rv[4 * k + 2]), __uint_as_float(rv[4 * k + 3])),
+                                    make_float2(b4.z, b4.w)));
+                            }
+                            lo = make_uint4(pack_bf16(v[0].x, v[0].y), pack_bf16(v[1].x, v[1].y),
+                                            pack_bf16(v[2].x, v[2].y), pack_bf16(v[3].x, v[3].y));
+                            hi = make_uint4(pack_bf16(v[4].x, v[4].y), pack_bf16(v[5].x, v[5].y),
+                                            pack_bf16(v[6].x, v[6].y), pack_bf16(v[7].x, v[7].y));
+                        }
+                        st_sw128(hbase, r, c >> 2, (c & 3) * 2, lo);
+                        st_sw128(hbase, r, c >> 2, (c & 3) * 2 + 1, hi);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(saddr(&s_ready));
+                } else {
+                    // last layer: acc + b (float32) staged as rows of N in the
+                    // tile's buffer, then copied out as one contiguous range
+                    for (int c = part; c * 16 < N; c += 2) {
+                        uint32_t rv[16];
+                        tmem_ld16(trow + (uint32_t)(c * 16), rv);
+                        tmem_wait_ld();
+                        const int cnt = min(16, N - c * 16);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (k < cnt) stage[r * N + c * 16 + k] = __uint_as_float(rv[k]) + bl[c * 16 + k];
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    ok = group_sync(saddr(&s_tile[t]), (uint32_t)(tsync & 1), err);
+                    ++tsync;
+                    if (!ok) break;
+                    const int rows = max(0, min(128, M - m0));
+                    const size_t total = (size_t)rows * N;
+                    float* dst = args.Y + (size_t)min(m0, M) * N;
+                    if ((N & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                        for (size_t i4 = tt; i4 < total / 4; i4 += 256)
+                            reinterpret_cast<float4*>(dst)[i4] = reinterpret_cast<const float4*>(stage)[i4];
+                    } else {
+                        for (size_t i = tt; i < total; i += 256) dst[i] = stage[i];
+                    }
+                    // the buffer is free for the next pair's features
+                    ok = group_sync(saddr(&s_tile[t]), (uint32_t)(tsync & 1), err);
+                    ++tsync;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == TMA_WARP)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // features (float32) -> bfloat16 rows, the first layer's TMA operand
@@ -1120,6 +1400,12 @@ struct mmpc_mlp {
     std::vector<__nv_bfloat16*> W16P;    // W16P[i]: bfloat16 W[i] with rows padded to ld8(width[i+1]) (only where width[i+1] % 8 != 0)
     float* tpart = nullptr;              // split partial sums of a weight gradient
     size_t tpart_count = 0;
+    // the whole network in one kernel (inference, mode 1): shapes that fit,
+    // its tensor maps of the transposed weights (made once: the buffers are
+    // refreshed in place), and its launch shape
+    bool fused_ok = false;
+    tc::FusedArgs fused{};
+    size_t fused_smem = 0;
 };
 
 namespace {
@@ -1487,6 +1773,58 @@ bool loss_grad_tensor(mmpc_mlp* n, const float* X, const float* Z, int M, float*
     return true;
 }
 
+// Shapes the single-kernel network takes: TMA rows of the weights (every
+// layer input width a multiple of 8), inputs and hidden widths of at most
+// 256 (four 64-column blocks per tile buffer, one 256-column accumulator per
+// tile), an output of at most 128 columns (staged in a tile buffer), and a
+// ring of at least two weight boxes beside the two tile buffers.  Makes the
+// weights' tensor maps; false (and the layer-by-layer path) otherwise.
+bool fused_setup(mmpc_mlp* n)
+{
+    const int L = n->L;
+    const int* w = n->cfg.width;
+    if (!n->tma_widths || !tensor_map_encoder() || L > MMPC_MLP_MAX_LAYERS || w[L] > 128) return false;
+    int kbmax = 1, bias = 0;
+    for (int l = 0; l < L; ++l) {
+        if (w[l] > 256) return false;
+        kbmax = std::max(kbmax, (w[l] + 63) / 64);
+        bias += (w[l + 1] + 15) / 16 * 16;
+    }
+    tc::FusedArgs& f = n->fused;
+    f = tc::FusedArgs{};
+    const size_t stage = (size_t)tc::BM * w[L] * 4;
+    f.h_bytes = (uint32_t)std::max<size_t>((size_t)kbmax * 16384, (stage + 1023) / 1024 * 1024);
+    const size_t fixed = 2 * (size_t)f.h_bytes + (size_t)bias * 4 + 1024;
+    const size_t cap = 227 * 1024;
+    if (fixed + 2 * 16384 > cap) return false;
+    f.stages = (int)std::min<size_t>(tc::FUSED_MAX_RING, (cap - fixed) / 16384);
+    f.L = L;
+    f.bias_total = bias;
+    for (int l = 0; l <= L; ++l) f.width[l] = w[l];
+    for (int l = 0; l < L; ++l) {
+        f.bias[l] = n->b[l];
+        if (!encode_rows(&f.wmap[l], n->W16T[l], w[l], w[l], w[l + 1], 128)) return false;
+    }
+    f.err = n->d_err;
+    n->fused_smem = fixed + (size_t)f.stages * 16384;
+    return cudaFuncSetAttribute(tc::umma_mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)n->fused_smem) == cudaSuccess;
+}
+
+// Y [M][width[L]] = network(X [M][width[0]]) in one launch: one CTA per SM
+// (the kernel takes all 512 TMEM columns), pairs of 128-row tiles.
+bool fused_launch(mmpc_mlp* n, const float* X, int M, float* Y, cudaStream_t st)
+{
+    tc::FusedArgs f = n->fused;
+    f.M = M;
+    f.X = X;
+    f.Y = Y;
+    const int pairs = (M + 255) / 256;
+    const int grid = std::max(1, std::min(pairs, n->sms));
+    tc::umma_mlp_fused_kernel<<<grid, tc::TMA_THREADS, n->fused_smem, st>>>(f);
+    return true;
+}
+
 bool valid_cfg(const mmpc_mlp_config* c)
 {
     if (!c || c->layers < 1 || c->layers > MMPC_MLP_MAX_LAYERS || c->max_batch < 1) return false;
@@ -1660,6 +1998,10 @@ int mmpc_mlp_create(const mmpc_mlp_config* cfg, const float* const* W, const flo
     for (const void* kf : tma_kernels)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_max);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) {
+        n->fused_ok = fused_setup(n);
+        cudaGetLastError();  // a refused shape leaves the layer-by-layer path
+    }
     if (e != cudaSuccess) {
         mlp_free(n);
         return cuda_fail(e, "mmpc_mlp_create");
@@ -1674,6 +2016,10 @@ int mmpc_mlp_forward(mmpc_mlp* n, const float* X, int M, float* Y, void* stream)
     if (M < 0 || (M > 0 && (!X || !Y))) return fail(MMPC_ERR_INVALID_ARG, "bad forward arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const int in = n->cfg.width[0], outw = n->cfg.width[n->L];
+    if (n->tensor == 1 && n->fused_ok && M > 0 && fused_launch(n, X, M, Y, st)) {
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_forward");
+    }
     for (int r0 = 0; r0 < M; r0 += n->inf_rows) {
         const int rows = std::min(n->inf_rows, M - r0);
         if (n->tensor)

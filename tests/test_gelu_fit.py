@@ -1,7 +1,8 @@
-"""The tensor-core epilogue's GELU (fitted polynomial in x^2, no special
-functions): the constants in the kernel are the output of csrc/fit_gelu.py,
-and a float32 emulation of its steps stays within 2e-6 of the exact
-x Phi(x) everywhere, with the exact limits (0 and x) beyond |x| = 5."""
+"""The tensor-core epilogues' GELU (x times a saturated polynomial in x^2
+for Phi, no special functions): the constants in the kernel are the output
+of csrc/fit_gelu.py, and a float32 emulation of its steps stays within 1.5e-6
+of the exact x Phi(x) everywhere, with the exact limits (0 and x) beyond
+|x| = 5."""
 import importlib.util
 import math
 import os
@@ -47,7 +48,7 @@ def test_error_bound():
     x = np.concatenate([rng.uniform(-10, 10, 200000), rng.normal(0, 1.5, 200000),
                         np.float32([4.999999, 5.0, 5.000001, -5.0, -4.999999])]).astype(np.float32)
     got = mod.gelu32(x, P).astype(np.float64)
-    assert np.max(np.abs(got - _exact(x))) < 2e-6
+    assert np.max(np.abs(got - _exact(x))) < 1.5e-6
 
 
 def test_limits_and_special_values():
@@ -55,6 +56,6 @@ def test_limits_and_special_values():
     P = np.float32(mod.fit())
     x = np.float32([0.0, -0.0, 6.0, 100.0, 1e30, -6.0, -100.0, -1e30])
     got = mod.gelu32(x, P)
-    assert abs(float(got[0])) < 2e-6 and abs(float(got[1])) < 2e-6
+    assert float(got[0]) == 0.0 and float(got[1]) == 0.0
     assert np.array_equal(got[2:5], x[2:5])          # GELU(x) = x beyond 5
     assert np.all(got[5:] == 0.0)                    # GELU(x) = 0 below -5
