@@ -1056,6 +1056,49 @@ __device__ __forceinline__ bool group_sync(uint32_t bar, uint32_t parity, unsign
     return mbar_wait(bar, parity, err);
 }
 
+// 32 accumulator columns of this thread's TMEM lane, loaded and waited for in
+// one statement (the registers are defined only once the wait returns)
+__device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// one 16-column chunk c of a hidden layer's epilogue for row r (accumulators
+// rv[o .. o + 16)): GELU(acc + b) as bfloat16 into the tile buffer (zeros for
+// a chunk past N)
+__device__ __forceinline__ void hidden_chunk(const uint32_t (&rv)[32], int o, const float* bl, uint32_t hbase, int r,
+                                             int c, int N)
+{
+    uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+    if (c * 16 < N) {
+        float2 v[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 b4 = reinterpret_cast<const float4*>(bl + c * 16)[k];
+            v[2 * k] = gelu_poly2(__fadd2_rn(
+                make_float2(__uint_as_float(rv[o + 4 * k]), __uint_as_float(rv[o + 4 * k + 1])), make_float2(b4.x, b4.y)));
+            v[2 * k + 1] = gelu_poly2(__fadd2_rn(
+                make_float2(__uint_as_float(rv[o + 4 * k + 2]), __uint_as_float(rv[o + 4 * k + 3])),
+                make_float2(b4.z, b4.w)));
+        }
+        lo = make_uint4(pack_bf16(v[0].x, v[0].y), pack_bf16(v[1].x, v[1].y), pack_bf16(v[2].x, v[2].y),
+                        pack_bf16(v[3].x, v[3].y));
+        hi = make_uint4(pack_bf16(v[4].x, v[4].y), pack_bf16(v[5].x, v[5].y), pack_bf16(v[6].x, v[6].y),
+                        pack_bf16(v[7].x, v[7].y));
+    }
+    st_sw128(hbase, r, c >> 2, (c & 3) * 2, lo);
+    st_sw128(hbase, r, c >> 2, (c & 3) * 2 + 1, hi);
+}
+
 __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __grid_constant__ FusedArgs args)
 {
     extern __shared__ __align__(1024) unsigned char fsm_raw[];
@@ -1065,7 +1108,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
     const uint32_t h0 = saddr(fsm), ring = h0 + 2 * hb;
     float* s_bias = reinterpret_cast<float*>(fsm + 2 * hb + (size_t)args.stages * 16384);
     __shared__ __align__(8) unsigned long long s_full[FUSED_MAX_RING], s_empty[FUSED_MAX_RING];
-    __shared__ __align__(8) unsigned long long s_acc, s_ready, s_tile[2];
+    __shared__ __align__(8) unsigned long long s_acc[2], s_ready[2], s_tile[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_boff[MMPC_MLP_MAX_LAYERS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1089,10 +1132,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
             mbar_init(saddr(&s_full[i]), 1);
             mbar_init(saddr(&s_empty[i]), 1);
         }
-        mbar_init(saddr(&s_acc), 1);
-        mbar_init(saddr(&s_ready), EPI_WARPS);
-        mbar_init(saddr(&s_tile[0]), EPI_WARPS / 2);
-        mbar_init(saddr(&s_tile[1]), EPI_WARPS / 2);
+        for (int t = 0; t < 2; ++t) {
+            mbar_init(saddr(&s_acc[t]), 1);
+            mbar_init(saddr(&s_ready[t]), EPI_WARPS / 2);
+            mbar_init(saddr(&s_tile[t]), EPI_WARPS / 2);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -1111,7 +1155,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
         if (lane == 0) {
             int g = 0;
             for (int pi = 0; pi < my_pairs && ok; ++pi)
-                for (int l = 0; l < L && ok; ++l) {
+                for (int lt = 0; lt < 2 * L && ok; ++lt) {
+                    const int l = lt >> 1;
                     const int KB = (args.width[l] + 63) / 64, NH = (args.width[l + 1] + 127) / 128;
                     for (int kb = 0; kb < KB && ok; ++kb)
                         for (int h = 0; h < NH && ok; ++h, ++g) {
@@ -1129,11 +1174,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
         __syncwarp();
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
-            int g = 0, issued = 0;
+            int g = 0, issued0 = 0, issued1 = 0;  // layers committed per tile
             for (int pi = 0; pi < my_pairs && ok; ++pi)
-                for (int l = 0; l < L && ok; ++l) {
-                    const int e = pi * L + l;
-                    ok = mbar_wait(saddr(&s_ready), (uint32_t)(e & 1), err);
+                for (int lt = 0; lt < 2 * L && ok; ++lt) {
+                    const int l = lt >> 1, t = lt & 1, e = pi * L + l;
+                    ok = mbar_wait(saddr(&s_ready[t]), (uint32_t)(e & 1), err);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const int N = args.width[l + 1];
@@ -1148,22 +1193,19 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
                             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nh >> 3) << 17) |
                                                    ((uint32_t)(BM >> 4) << 24);
                             const uint32_t bst = ring + (uint32_t)s * 16384u;
+                            const uint32_t dtm = tmem + (uint32_t)(256 * t + 128 * h);
+                            const uint32_t ast = h0 + (uint32_t)t * hb + (uint32_t)kb * 16384u;
 #pragma unroll
-                            for (int t = 0; t < 2; ++t) {
-                                const uint32_t dtm = tmem + (uint32_t)(256 * t + 128 * h);
-                                const uint32_t ast = h0 + (uint32_t)t * hb + (uint32_t)kb * 16384u;
-#pragma unroll
-                                for (int kk = 0; kk < BK / 16; ++kk) {
-                                    const uint64_t ad = sw128_desc(ast + (uint32_t)(kk * 32));
-                                    const uint64_t bd = sw128_desc(bst + (uint32_t)(kk * 32));
-                                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                                    asm volatile(
-                                        "{\n\t.reg .pred p;\n\t"
-                                        "setp.ne.b32 p, %4, 0;\n\t"
-                                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
-                                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                                        : "memory");
-                                }
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                const uint64_t ad = sw128_desc(ast + (uint32_t)(kk * 32));
+                                const uint64_t bd = sw128_desc(bst + (uint32_t)(kk * 32));
+                                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n\t.reg .pred p;\n\t"
+                                    "setp.ne.b32 p, %4, 0;\n\t"
+                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+                                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                    : "memory");
                             }
                             asm volatile(
                                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -1172,16 +1214,17 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
                         }
                     if (!ok) break;
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     saddr(&s_acc))
+                                     saddr(&s_acc[t]))
                                  : "memory");
-                    issued = e + 1;
+                    (t ? issued1 : issued0) = e + 1;
                 }
             // after an expired wait: the copies issued by the producer land,
             // and the last committed layer's MMAs complete, before the CTA
             // exits (bounded as well)
             if (!ok) {
                 for (int gg = g; gg < g + S; ++gg) mbar_wait(saddr(&s_full[gg % S]), (uint32_t)((gg / S) & 1), err);
-                if (issued > 0) mbar_wait(saddr(&s_acc), (uint32_t)((issued - 1) & 1), err);
+                if (issued0 > 0) mbar_wait(saddr(&s_acc[0]), (uint32_t)((issued0 - 1) & 1), err);
+                if (issued1 > 0) mbar_wait(saddr(&s_acc[1]), (uint32_t)((issued1 - 1) & 1), err);
             }
         }
         __syncwarp();
@@ -1198,32 +1241,48 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
         int tsync = 0;  // completed phases of this tile's group barrier
         for (int pi = 0; pi < my_pairs && ok; ++pi) {
             const int m0 = ((int)blockIdx.x + pi * (int)gridDim.x) * 256 + t * 128;
-            // the features: 8 float32 per thread and step, coalesced rows,
+            // the features: 8 float32 per thread and group, coalesced rows,
             // rounded to bfloat16 into block 0.. of the buffer; zeros past
-            // width[0] (up to the 64-column block) and past M
-            const int kb0 = (w0 + 63) / 64;
-            for (int e8 = tt; e8 < 128 * kb0 * 8; e8 += 256) {
-                const int rr = e8 / (kb0 * 8), cj = e8 % (kb0 * 8);  // row, 8-column group
-                const int gr = m0 + rr, c0 = cj * 8;
-                float v[8];
-                if (gr < M && c0 + 8 <= w0) {
-                    const float4 a = __ldg(reinterpret_cast<const float4*>(args.X + (size_t)gr * w0 + c0));
-                    const float4 b = __ldg(reinterpret_cast<const float4*>(args.X + (size_t)gr * w0 + c0 + 4));
-                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-                } else {
+            // width[0] (up to the 64-column block) and past M.  Two groups'
+            // loads are in flight before the first is stored.
+            const int kb0 = (w0 + 63) / 64, groups = 128 * kb0 * 8;
+            for (int e0 = tt; e0 < groups; e0 += 2 * 256) {
+                float4 va[2], vb[2];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) v[k] = (gr < M && c0 + k < w0) ? args.X[(size_t)gr * w0 + c0 + k] : 0.f;
+                for (int u = 0; u < 2; ++u) {
+                    const int e8 = e0 + u * 256;
+                    const int rr = e8 / (kb0 * 8), c0 = (e8 % (kb0 * 8)) * 8, gr = m0 + rr;
+                    va[u] = vb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e8 < groups && gr < M) {
+                        const float* src = args.X + (size_t)gr * w0 + c0;
+                        if (c0 + 8 <= w0) {
+                            va[u] = __ldg(reinterpret_cast<const float4*>(src));
+                            vb[u] = __ldg(reinterpret_cast<const float4*>(src + 4));
+                        } else if (c0 < w0) {
+                            float v[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) v[k] = c0 + k < w0 ? src[k] : 0.f;
+                            va[u] = make_float4(v[0], v[1], v[2], v[3]);
+                            vb[u] = make_float4(v[4], v[5], v[6], v[7]);
+                        }
+                    }
                 }
-                st_sw128(hbase, rr, cj >> 3, cj & 7,
-                         make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                                    pack_bf16(v[6], v[7])));
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e8 = e0 + u * 256;
+                    if (e8 >= groups) break;
+                    const int rr = e8 / (kb0 * 8), cj = e8 % (kb0 * 8);
+                    st_sw128(hbase, rr, cj >> 3, cj & 7,
+                             make_uint4(pack_bf16(va[u].x, va[u].y), pack_bf16(va[u].z, va[u].w),
+                                        pack_bf16(vb[u].x, vb[u].y), pack_bf16(vb[u].z, vb[u].w)));
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&s_ready));
+            if (lane == 0) mbar_arrive(saddr(&s_ready[t]));
             for (int l = 0; l < L && ok; ++l) {
                 const int e = pi * L + l;
-                ok = mbar_wait(saddr(&s_acc), (uint32_t)(e & 1), err);
+                ok = mbar_wait(saddr(&s_acc[t]), (uint32_t)(e & 1), err);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int N = args.width[l + 1];
@@ -1231,47 +1290,29 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) umma_mlp_fused_kernel(const __
                 if (l < L - 1) {
                     // hidden layer: GELU(acc + b) as bfloat16 into the buffer
                     // (the next layer's input), zeros up to the 64-column block
-                    const int nch = (N + 63) / 64 * 4;
-                    for (int c = part; c < nch; c += 2) {
-                        uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-                        if (c * 16 < N) {
-                            uint32_t rv[16];
-                            tmem_ld16(trow + (uint32_t)(c * 16), rv);
-                            tmem_wait_ld();
-                            float2 v[8];
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const float4 b4 = reinterpret_cast<const float4*>(bl + c * 16)[k];
-                                v[2 * k] = gelu_poly2(__fadd2_rn(
-                                    make_float2(__uint_as_float(rv[4 * k]), __uint_as_float(rv[4 * k + 1])),
-                                    make_float2(b4.x, b4.y)));
-                                v[2 * k + 1] = gelu_poly2(__fadd2_rn(
-                                    make_float2(__uint_as_float(rv[4 * k + 2]), __uint_as_float(rv[4 * k + 3])),
-                                    make_float2(b4.z, b4.w)));
-                            }
-                            lo = make_uint4(pack_bf16(v[0].x, v[0].y), pack_bf16(v[1].x, v[1].y),
-                                            pack_bf16(v[2].x, v[2].y), pack_bf16(v[3].x, v[3].y));
-                            hi = make_uint4(pack_bf16(v[4].x, v[4].y), pack_bf16(v[5].x, v[5].y),
-                                            pack_bf16(v[6].x, v[6].y), pack_bf16(v[7].x, v[7].y));
-                        }
-                        st_sw128(hbase, r, c >> 2, (c & 3) * 2, lo);
-                        st_sw128(hbase, r, c >> 2, (c & 3) * 2 + 1, hi);
+                    // column groups of 32 (chunks 2 g, 2 g + 1), alternating
+                    // between the two warps of the sub-partition
+                    const int ngr = (N + 63) / 64 * 2;
+                    for (int gq = part; gq < ngr; gq += 2) {
+                        uint32_t rv[32];
+                        if (gq * 32 < N) tmem_ld32_wait(trow + (uint32_t)(gq * 32), rv);
+                        hidden_chunk(rv, 0, bl, hbase, r, 2 * gq, N);
+                        hidden_chunk(rv, 16, bl, hbase, r, 2 * gq + 1, N);
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(saddr(&s_ready));
+                    if (lane == 0) mbar_arrive(saddr(&s_ready[t]));
                 } else {
                     // last layer: acc + b (float32) staged as rows of N in the
                     // tile's buffer, then copied out as one contiguous range
-                    for (int c = part; c * 16 < N; c += 2) {
-                        uint32_t rv[16];
-                        tmem_ld16(trow + (uint32_t)(c * 16), rv);
-                        tmem_wait_ld();
-                        const int cnt = min(16, N - c * 16);
+                    for (int gq = part; gq * 32 < N; gq += 2) {
+                        uint32_t rv[32];
+                        tmem_ld32_wait(trow + (uint32_t)(gq * 32), rv);
+                        const int cnt = min(32, N - gq * 32);
 #pragma unroll
-                        for (int k = 0; k < 16; ++k)
-                            if (k < cnt) stage[r * N + c * 16 + k] = __uint_as_float(rv[k]) + bl[c * 16 + k];
+                        for (int k = 0; k < 32; ++k)
+                            if (k < cnt) stage[r * N + gq * 32 + k] = __uint_as_float(rv[k]) + bl[gq * 32 + k];
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     ok = group_sync(saddr(&s_tile[t]), (uint32_t)(tsync & 1), err);
