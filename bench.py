@@ -802,6 +802,7 @@ def run_warm(args):
                    "sparse_10_obstacles": sparse,
                    "scene_1024_goals_plain_cold": scene, "val_loss": val, "network_forward": fwd,
                    "loss_first_last": [losses[0][1], losses[-1][1]], "dataset_s": t1 - t0, "train_s": t2 - t1,
+                   "train_step_ms": ws.train_step_ms, "train_tensor_cores": cfg.tensor_training,
                    "wall_s": wall, "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)},
     }
     if cpu is not None:
@@ -1174,7 +1175,7 @@ def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default per workload: warm 5, scene 2000, precision 20, batch 100; "
+                    help="timed steps (default per workload: warm 10, scene 2000, precision 20, batch 100; "
                          "--impl reference: 3); a warm step replays the whole 1M-trajectory evaluation")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
@@ -1200,7 +1201,7 @@ def parse_args(argv=None):
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = (3 if args.impl == "reference" else
-                      {"precision": 20, "batch": 100, "warm": 5}.get(args.workload, 2000))
+                      {"precision": 20, "batch": 100, "warm": 10}.get(args.workload, 2000))
     if args.steps < 1:
         ap.error("--steps must be >= 1")
     if args.warmup < 3:

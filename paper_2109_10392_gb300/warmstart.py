@@ -52,6 +52,7 @@ class WarmConfig:
     lam_from_q: bool = True
     converged_only: bool = True   # train on the trajectories that reached tol only
     tensor_inference: bool = True  # inference on the tensor cores (tcgen05, bfloat16 layer inputs)
+    tensor_training: bool = True   # training products on the tensor cores (bfloat16 operands)
     tol: float = 1e-2
     seed: int = 0
     params: dict = field(default_factory=lambda: dict(scenes.BASE_PARAMS))
@@ -165,12 +166,15 @@ def train(cfg: WarmConfig, X, T, device, log_every: int = 250):
     mlp.standardize(T, mu, sigma, Z)
     Ws, bs = scenes.mlp_init(cfg.seed, cfg.widths)
     net = mlp.Mlp(cfg.widths, Ws, bs, max_batch=cfg.batch, weight_decay=cfg.weight_decay)
+    net.set_train_tensor_cores(cfg.tensor_training)
     rng = np.random.default_rng(cfg.seed + 7)
     Xb = torch.zeros((cfg.batch, 64), device=device)
     Zb = torch.zeros((cfg.batch, W), device=device)
     loss = torch.zeros((1,), device=device)
     perm, pos = None, R
     log = []
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record()
     for step in range(cfg.steps):
         if pos + cfg.batch > R:
             perm = torch.tensor(rng.permutation(R).astype(np.int32), device=device)
@@ -184,9 +188,14 @@ def train(cfg: WarmConfig, X, T, device, log_every: int = 250):
         net.adamw(lr)
         if step % log_every == 0 or step == cfg.steps - 1:
             log.append((step, float(loss.item())))
+    t_end.record()
+    torch.cuda.synchronize(device)
     Q = q_matrix(cfg.params, device) if (not cfg.predict_lam and cfg.lam_from_q) else None
     net.set_tensor_cores(cfg.tensor_inference)
-    return WarmStart(net, mu, sigma, cfg.params, Q), log
+    ws = WarmStart(net, mu, sigma, cfg.params, Q)
+    # device time per training step (row gathers, loss and gradients, AdamW)
+    ws.train_step_ms = t_start.elapsed_time(t_end) / max(1, cfg.steps)
+    return ws, log
 
 
 def time_forward(ws: WarmStart, rows: int, device, reps: int = 5):

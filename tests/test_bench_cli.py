@@ -8,11 +8,11 @@ import pytest
 def test_default_steps_per_workload():
     import bench
     assert bench.parse_args([]).workload == "warm"
-    assert bench.parse_args([]).steps == 5
+    assert bench.parse_args([]).steps == 10
     assert bench.parse_args(["--workload", "scene"]).steps == 2000
     assert bench.parse_args(["--workload", "precision"]).steps == 20
     assert bench.parse_args(["--workload", "batch"]).steps == 100
-    assert bench.parse_args(["--workload", "warm"]).steps == 5
+    assert bench.parse_args(["--workload", "warm"]).steps == 10
     assert bench.parse_args(["--workload", "sweep"]).steps == 2000
     assert bench.parse_args(["--impl", "reference"]).steps == 3
 
