@@ -323,6 +323,54 @@ __device__ __forceinline__ float2 lo2(float4 v) { return f2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return f2(v.z, v.w); }
 __device__ __forceinline__ float2 hsum2(float2 a, float2 b) { return f2(a.x + a.y, b.x + b.y); }
 
+// Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
+// Intrinsics, so that no contraction or reassociation can change the steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// Compensated dot product of NC floats (algorithm Dot2 of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005): the
+// rounding error of each product (by FMA) and of each sum (by TwoSum) is
+// carried and added at the end, so the result is as accurate as a dot
+// product in twice the working precision, rounded once; four interleaved
+// partial sums for ILP, themselves added by TwoSum.  Used for K11 u, where
+// the terms (K11 entries of ~1e3 with alternating signs times multipliers of
+// up to ~1e3) cancel by five orders of magnitude: the plain FP32 sum of such
+// terms loses ~1e-2 of the increment per iteration.
+// The columns j < J0 are skipped: for K11 the first three (the coefficients
+// fixed by the initial position, speed and acceleration) are zero.
+template <int NC, int J0 = 0>
+__device__ __forceinline__ float dot2(const float* __restrict__ row, const float* __restrict__ v)
+{
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = J0 & ~3; j < NC; j += 4) {
+        const float4 r4 = *reinterpret_cast<const float4*>(row + j), w4 = *reinterpret_cast<const float4*>(v + j);
+        const float rr[4] = {r4.x, r4.y, r4.z, r4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (j + q < J0) continue;
+            const float pq = __fmul_rn(rr[q], ww[q]);
+            const float pe = __fmaf_rn(rr[q], ww[q], -pq);
+            float t;
+            two_sum(s[q], pq, s[q], t);
+            c[q] = __fadd_rn(c[q], __fadd_rn(pe, t));
+        }
+    }
+    float S = s[0], E = __fadd_rn(__fadd_rn(c[0], c[1]), __fadd_rn(c[2], c[3]));
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+        float t;
+        two_sum(S, s[q], S, t);
+        E = __fadd_rn(E, t);
+    }
+    return __fadd_rn(S, E);
+}
+
 // Basis evaluations at a sample pair.  A pair row holds, for each coefficient
 // pair (2j, 2j + 1), the 16-byte block (P[s0][2j], P[s0][2j+1], P[s1][2j],
 // P[s1][2j+1]) of its two samples s0 = 2i, s1 = 2i + 1; coefficient vectors
@@ -1226,7 +1274,7 @@ __device__ __forceinline__ bool pair_body(const SolveArgs& A, const int l)
             if (act) vec[k] = u;
             __syncwarp();
             if (act) {
-                const float d0 = dot_vec<NC>(blob + (isy ? L.Kyh : L.Kxh) + kk * k_stride(NC), vec);
+                const float d0 = dot2<NC, 3>(blob + (isy ? L.Kyh : L.Kxh) + kk * k_stride(NC), vec);
                 const float d1 = dot_vec<NC>(blob + (isy ? L.Kyl : L.Kxl) + kk * k_stride(NC), vec);
                 const float dd = (d0 + d1) + (first ? e + corr : e);
                 const float snew = c + dd;
@@ -1678,7 +1726,7 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
             if (act) vec[k] = u;
             __syncwarp();
             if (act) {
-                const float d0 = dot_plain<NC>(blob + ((isy ? L.Kyh : L.Kxh) - base) + kk * k_stride(NC), vec);
+                const float d0 = dot2<NC, 3>(blob + ((isy ? L.Kyh : L.Kxh) - base) + kk * k_stride(NC), vec);
                 const float d1 = dot_plain<NC>(blob + ((isy ? L.Kyl : L.Kxl) - base) + kk * k_stride(NC), vec);
                 const float dd = (d0 + d1) + (first ? e + corr : e);
                 const float snew = c + dd;

@@ -672,6 +672,100 @@ __device__ __forceinline__ float tc_dot(const float* __restrict__ row, const flo
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
+// x - y for packed pairs, as one rounding (fma(y, -1, x) is exactly x - y
+// rounded): the error-free transformations below need plain subtractions
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, f2(-1.f), x); }
+
+// Knuth's TwoSum on packed pairs: a + b = s + e exactly, per lane.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e)
+{
+    s = __fadd2_rn(a, b);
+    const float2 z = sub2(s, a);
+    e = __fadd2_rn(sub2(a, sub2(s, z)), sub2(b, z));
+}
+
+// Compensated dot products (Dot2 of Ogita, Rump and Oishi, "Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26, 2005) of two rows r0, r1 with v over
+// the columns [J0, J1), the two rows in the two lanes of packed f32x2
+// arithmetic: each product's rounding error (by FMA) and each sum's (by
+// TwoSum) is carried to the end, so each result is as accurate as a dot
+// product in twice the working precision, rounded once.  K11 u needs it: u
+// carries the multipliers, which grow in K11's near-null directions, and the
+// products (entries of ~1e3 times ~1e3) cancel by five orders of magnitude.
+template <int J0, int J1>
+__device__ __forceinline__ float2 tc_dot2_rows(const float* __restrict__ r0, const float* __restrict__ r1,
+                                               const float (&v)[16])
+{
+    float2 s[2] = {f2(0.f), f2(0.f)}, c[2] = {f2(0.f), f2(0.f)};
+#pragma unroll
+    for (int j = J0 & ~3; j < J1; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(r0 + j), y = *reinterpret_cast<const float4*>(r1 + j);
+        const float k0[4] = {x.x, x.y, x.z, x.w}, k1[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (j + q < J0 || j + q >= J1) continue;
+            const int h = (j + q) & 1;  // two interleaved partial sums per row
+            const float2 kk = f2(k0[q], k1[q]), uu = f2(v[j + q]);
+            const float2 pq = __fmul2_rn(kk, uu);
+            const float2 pe = __ffma2_rn(kk, uu, f2(-pq.x, -pq.y));
+            float2 t;
+            two_sum2(s[h], pq, s[h], t);
+            c[h] = __fadd2_rn(c[h], __fadd2_rn(pe, t));
+        }
+    }
+    float2 S, t;
+    two_sum2(s[0], s[1], S, t);
+    return __fadd2_rn(S, __fadd2_rn(__fadd2_rn(c[0], c[1]), t));
+}
+
+// Plain dot products of two rows over the columns [J0, J1) (the K11 lo part:
+// small terms), packed as above.
+template <int J0, int J1>
+__device__ __forceinline__ float2 tc_dot_rows(const float* __restrict__ r0, const float* __restrict__ r1,
+                                              const float (&v)[16])
+{
+    float2 acc[2] = {f2(0.f), f2(0.f)};
+#pragma unroll
+    for (int j = J0 & ~3; j < J1; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(r0 + j), y = *reinterpret_cast<const float4*>(r1 + j);
+        const float k0[4] = {x.x, x.y, x.z, x.w}, k1[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (j + q >= J0 && j + q < J1) acc[(j + q) & 1] = __ffma2_rn(f2(k0[q], k1[q]), f2(v[j + q]), acc[(j + q) & 1]);
+    }
+    return __fadd2_rn(acc[0], acc[1]);
+}
+
+// Step (split_xy) in increment form for one axis, c += K11 u with K11 as
+// hi + lo, over the rows and columns [K0, K1): the coefficients fixed by the
+// boundary rows (the first three of each axis; the last three of y, whose end
+// position, speed and acceleration are all given) have zero rows and columns
+// in K11 and take only their carry (which holds the first step's boundary
+// correction of a warm start).  Rows go in pairs through the packed products.
+template <int NC, int K0, int K1, int KS>
+__device__ __forceinline__ void tc_xy_step(const float* __restrict__ Kh, const float* __restrict__ Kl,
+                                           const float (&u)[16], float (&c)[16], float (&e)[16])
+{
+    float dd[16];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dd[k] = 0.f;
+#pragma unroll
+    for (int k = K0; k < K1; k += 2) {
+        const int k1 = k + 1 < K1 ? k + 1 : k;
+        const float2 hi = tc_dot2_rows<K0, K1>(Kh + k * KS, Kh + k1 * KS, u);
+        const float2 lo = tc_dot_rows<K0, K1>(Kl + k * KS, Kl + k1 * KS, u);
+        dd[k] = hi.x + lo.x;
+        if (k + 1 < K1) dd[k + 1] = hi.y + lo.y;
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const float d = dd[k] + e[k];
+        const float snew = c[k] + d;
+        e[k] = d - (snew - c[k]);
+        c[k] = snew;
+    }
+}
+
 __device__ __forceinline__ void tc_sync()
 {
     tc_wait_st();
@@ -1111,15 +1205,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) am_solve_tc_kernel(const __grid
         if (g < 2) {
             const float* Kh = mats + (L.Q - L.Q) + (1 + 2 * g) * NC * KS;  // K11 hi of this axis
             const float* Kl = Kh + NC * KS;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                const float d0 = tc_dot<NC>(Kh + k * KS, u);
-                const float d1 = tc_dot<NC>(Kl + k * KS, u);
-                const float dd = (d0 + d1) + e[k];
-                const float snew = c[k] + dd;
-                e[k] = dd - (snew - c[k]);
-                c[k] = snew;
-            }
+            if (g == 0 || A.n != NC) tc_xy_step<NC, 3, NC, KS>(Kh, Kl, u, c, e);
+            else tc_xy_step<NC, 3, NC - 3, KS>(Kh, Kl, u, c, e);
         }
     };
 

@@ -330,17 +330,15 @@ def test_precision_workload_sampled(capsys):
     orc = U.oracle_solve(params, ego, obst, goals[sel])
     sens = U.sensitivity(params, ego, obst, goals[sel], orc["coef"], trials=1)
     gs = {k: v[sel] for k, v in gpu.items()}
-    # At N = 200, n = 16 the FP32 rounding of 100 iterations accumulates past
-    # 1e-3 m on a few trajectories that input perturbations rate as well
-    # conditioned (each FP32 effect alone -- basis rows, the heading QP,
-    # multiplier storage, reciprocal square root, atan2 -- moves them by at
-    # most 2e-4 m), so this workload states its error: 1e-3 m on 90 % of the
-    # parity set, 1e-2 m (the residual target) on all of it.
+    # The stated bars on the whole parity set.  (The step's K11 u is a
+    # compensated dot product: with plain FP32 sums the products, which
+    # cancel by five orders of magnitude once the multipliers have grown
+    # along K11's near-null directions, cost up to 3.5e-3 m here.)
     err = U.pos_err(params, gs["coef"], orc["coef"])
     good = sens < U.SENS_TOL
     assert good.mean() >= 0.3
-    assert np.mean(err[good] <= U.POS_TOL) >= 0.9, err[good]
-    assert np.all(err[good] <= U.CHAOS_TOL), err[good]
+    assert np.all(err[good] <= U.POS_TOL), err[good]
+    assert np.all(err <= U.CHAOS_TOL), err
     assert np.all(np.isfinite(gs["coef"]))
     meta = dict(sc.meta)
     c_gpu, am_gpu = U.gpu_score(params, obst.shape[0], gs["coef"], meta)
@@ -353,7 +351,9 @@ def test_precision_workload_sampled(capsys):
               f"share <= 1e-3 m {np.mean(err[good] <= U.POS_TOL):.3f}; "
               f"all: median {np.median(err):.2e}; meta cost rel error max {rel.max() if rel.size else 0:.2e}; "
               f"argmin gpu {am_gpu} oracle {am_orc}")
-    assert rel.size == 0 or rel.max() <= U.COST_RTOL * 10
+    assert rel.size == 0 or rel.max() <= U.COST_RTOL
+    # the same argmin over the sample, or an equally good one within the cost tolerance
+    assert am_gpu == am_orc or abs(c_orc[am_gpu] - c_orc[am_orc]) <= U.COST_RTOL * abs(c_orc[am_orc])
 
 
 @pytest.mark.parametrize("variant", [1, 2])
