@@ -722,11 +722,10 @@ def run_warm(args):
             e2e_conv = int((h_out[1][:, :3].max(dim=1).values <= TOL).sum())
     e2e_ms = (time.perf_counter() - te) * 1e3 / Ke
 
-    # the library's launches per step: features; per inference chunk of SMs x
-    # 512 rows one rounding and four layer GEMMs; decode; the batch run (reset,
+    # the library's launches per step: features; the network's forward (one
+    # launch of the single-kernel network); decode; the batch run (reset,
     # order, solve, fallback compaction, fallback solve, score, finish)
-    chunks = -(-S * B // (SM_COUNT * 512))
-    launches_per_step = 1 + 5 * chunks + 1 + 7
+    launches_per_step = 1 + ws.net.forward_launches(S * B) + 1 + 7
     agg = combine_ranks(dict(units=converged, ms=ms, e2e_units=e2e_conv, e2e_ms=e2e_ms), world, dist)
     tagg = combine_ranks(dict(units=S * B, ms=ms, e2e_units=S * B, e2e_ms=e2e_ms), world, dist)
     if rank != 0:

@@ -164,6 +164,12 @@ int mmpc_mlp_set_tensor_cores(mmpc_mlp* net, int on);
  * unchanged.  Other values of on: MMPC_ERR_INVALID_ARG. */
 int mmpc_mlp_set_train_tensor_cores(mmpc_mlp* net, int on);
 
+/* Number of kernel launches mmpc_mlp_forward enqueues for M rows in the
+ * current mode (one for the single-kernel network of mode 1; per inference
+ * chunk one per layer, plus the rounding of the features in mode 1 where the
+ * single kernel does not take the shape); -1 for a NULL network or M < 0. */
+int mmpc_mlp_forward_launches(mmpc_mlp* net, int M);
+
 /* Synchronises the device and reports MMPC_ERR_TIMEOUT if a bounded wait of
  * a tensor-core kernel expired since the network was created. */
 int mmpc_mlp_status(mmpc_mlp* net);

@@ -2169,6 +2169,16 @@ int mmpc_mlp_write(mmpc_mlp* n, int what, int layer, const float* host, size_t c
     return e == cudaSuccess ? MMPC_OK : cuda_fail(e, "mmpc_mlp_write");
 }
 
+int mmpc_mlp_forward_launches(mmpc_mlp* n, int M)
+{
+    if (!n || M < 0) return -1;
+    if (M == 0) return 0;
+    if (n->tensor == 1 && n->fused_ok) return 1;
+    const int chunks = (M + n->inf_rows - 1) / n->inf_rows;
+    const int per_chunk = n->L + ((n->tensor == 1 && n->tma_widths) ? 1 : 0);
+    return chunks * per_chunk;
+}
+
 int mmpc_mlp_set_tensor_cores(mmpc_mlp* n, int on)
 {
     if (!n) return fail(MMPC_ERR_NOT_SETUP, "NULL network");

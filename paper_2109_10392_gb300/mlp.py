@@ -19,7 +19,7 @@ EXPORTED = ("mmpc_features", "mmpc_warm_decode", "mmpc_warm_encode", "mmpc_colum
             "mmpc_standardize",
             "mmpc_mlp_create", "mmpc_mlp_forward", "mmpc_mlp_loss_grad", "mmpc_mlp_adamw", "mmpc_mlp_read",
             "mmpc_mlp_write", "mmpc_mlp_destroy", "mmpc_mlp_last_error", "mmpc_mlp_set_tensor_cores",
-            "mmpc_mlp_set_train_tensor_cores", "mmpc_mlp_status")
+            "mmpc_mlp_set_train_tensor_cores", "mmpc_mlp_forward_launches", "mmpc_mlp_status")
 READ_W, READ_B, READ_DW, READ_DB, READ_MW, READ_VW, READ_MB, READ_VB = range(8)
 
 
@@ -73,6 +73,7 @@ def lib():
     L.mmpc_mlp_write.argtypes = [vp, ip, ip, vp, ctypes.c_size_t]
     L.mmpc_mlp_set_tensor_cores.argtypes = [vp, ip]
     L.mmpc_mlp_set_train_tensor_cores.argtypes = [vp, ip]
+    L.mmpc_mlp_forward_launches.argtypes = [vp, ip]
     L.mmpc_mlp_status.argtypes = [vp]
     L.mmpc_mlp_destroy.argtypes = [vp]
     L.mmpc_mlp_destroy.restype = None
@@ -231,6 +232,13 @@ class Mlp:
         """False/0: training on the FP32 SIMT kernels; True/1: its three
         products per layer on the tcgen05 pipeline (bfloat16 operands)."""
         _check(lib().mmpc_mlp_set_train_tensor_cores(self.handle, int(on)))
+
+    def forward_launches(self, rows):
+        """Kernel launches a forward pass over `rows` rows enqueues."""
+        k = lib().mmpc_mlp_forward_launches(self.handle, int(rows))
+        if k < 0:
+            raise RuntimeError("mmpc_mlp_forward_launches: bad arguments")
+        return k
 
     def status(self):
         _check(lib().mmpc_mlp_status(self.handle))

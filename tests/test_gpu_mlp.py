@@ -433,3 +433,25 @@ def test_tensor_core_training_mode_checked():
         with pytest.raises(RuntimeError):
             net.set_train_tensor_cores(bad)
     net.close()
+
+
+def test_forward_launch_count():
+    """mmpc_mlp_forward_launches: one launch for the single-kernel network of
+    mode 1; layer by layer otherwise (per inference chunk one per layer, plus
+    the features' rounding in mode 1)."""
+    import torch
+    widths = (64, 256, 256, 256, 36)
+    Ws, bs = scenes.mlp_init(3, widths)
+    net = mlp.Mlp(widths, Ws, bs, max_batch=64)
+    net.set_tensor_cores(1)
+    assert net.forward_launches(0) == 0
+    assert net.forward_launches(1_000_000) == 1
+    net.set_tensor_cores(0)
+    chunk = max(65536, torch.cuda.get_device_properties(0).multi_processor_count * 512)
+    assert net.forward_launches(chunk) == 4 and net.forward_launches(chunk + 1) == 8
+    net.close()
+    Ws, bs = scenes.mlp_init(3, (64, 320, 40))   # a hidden layer wider than 256: layer by layer
+    net = mlp.Mlp((64, 320, 40), Ws, bs, max_batch=64)
+    net.set_tensor_cores(1)
+    assert net.forward_launches(10) == 3
+    net.close()
