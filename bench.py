@@ -620,11 +620,13 @@ def run_warm(args):
     keep = ev.pop("_keep")
     plain = dense["plain"]
     for e_ in (ev, ev32, evbf):
-        for k in ("cold", "warm", "warm_fallback", "warm_fallback_budget"):
+        for k in ("cold", "warm", "warm_fallback", "warm_fallback_budget", "warm_fallback_near"):
             e_[f"{k}_vs_plain"] = e_[k]["trajectories_per_s"] / plain["trajectories_per_s"]
             e_[f"{k}_converged_vs_plain"] = e_[k]["converged_per_s"] / plain["converged_per_s"]
             e_[f"{k}_converged_vs_batched_cold"] = e_[k]["converged_per_s"] / dense["cold"]["converged_per_s"]
             e_[f"{k}_converged_vs_batched_cold_stall"] = e_[k]["converged_per_s"] / ev32["cold"]["converged_per_s"]
+            # against the batched cold start on the same kernel, with the stall stop
+            e_[f"{k}_converged_vs_same_kernel_cold"] = e_[k]["converged_per_s"] / e_["cold"]["converged_per_s"]
     warm, stream = keep["warm"], keep["stream"]
     graph = keep["graphs"][HEADLINE]
     converged = ev[HEADLINE]["converged"]

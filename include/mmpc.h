@@ -286,10 +286,18 @@ int mmpc_batch_run(mmpc_batch* b, void* stream);
  * misses that ran the whole iteration budget -- a miss that the opt-in stall
  * rule (mmpc_params.stall_tol / stall_ratio) stopped earlier is kept as it
  * is, because its residual trace showed it far from the target and no longer
- * closing in (mode 2 is not in the paper; without the stall rule it equals
- * mode 1).  Needs resid_out (and, for mode 2, iters_out) of the warm-started
- * scenes.  Other modes -> MMPC_ERR_INVALID_ARG. */
+ * closing in (without the stall rule mode 2 equals mode 1) -- and 3 only the
+ * near misses among those of mode 2: convergence residual at most near x
+ * tol (mmpc_batch_set_fallback_near, default 5), re-solved on the FP32
+ * pair kernel also in a tensor-core batch (one CTA per trajectory suits a
+ * few misses per scene).  A NaN residual always falls back.  Modes 2 and 3 are not in the paper.  Needs resid_out (and,
+ * for modes 2 and 3, iters_out) of the warm-started scenes.  Other modes ->
+ * MMPC_ERR_INVALID_ARG. */
 int mmpc_batch_set_fallback(mmpc_batch* b, int on);
+
+/* The near-miss factor of fallback mode 3 (finite, >= 1; default 5):
+ * MMPC_ERR_INVALID_ARG otherwise. */
+int mmpc_batch_set_fallback_near(mmpc_batch* b, float near);
 
 /* Optional timing of the solve launches inside mmpc_batch_run: events[0..3]
  * (cudaEvent_t, created by the caller with timing enabled) are recorded on

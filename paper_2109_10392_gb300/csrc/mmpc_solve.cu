@@ -1776,6 +1776,21 @@ __global__ void __launch_bounds__(MAXT, MinBlocks1<MAXT>::value) am_solve_kernel
     if (lane == 0 && A.work) atomicAdd(A.work, work);
 }
 
+// Which misses go (mode, see mmpc_batch_set_fallback): 1 every miss; 2 not a
+// miss that the stall rule stopped before the iteration budget (iters_out <
+// iters), whose residual trace already showed it far from the target and no
+// longer closing in; 3 as 2, and only near misses, whose residual is at most
+// near x tol.  A NaN residual always goes.
+__device__ __forceinline__ bool fallback_takes(int mode, float near, bool nan, float conv, float tol, int iters_run,
+                                               int budget)
+{
+    if (nan) return true;
+    if (conv <= tol) return false;
+    if (mode >= 2 && iters_run < budget) return false;
+    if (mode == 3 && !(conv <= near * tol)) return false;
+    return true;
+}
+
 #include "mmpc_tc.cuh"
 
 // ---------------------------------------------------------------------------
@@ -1927,15 +1942,13 @@ __global__ void batch_reset_kernel(unsigned long long* scratch, int S, int G, in
 // Fallback of warm-started trajectories: every item of a scene with a warm
 // start whose convergence residual (the largest of the obstacle,
 // acceleration and non-holonomic residuals) missed the scene's tol > 0, or is
-// NaN, goes to the fallback list, to be solved again from the cold start.
-// The list order depends on timing; each trajectory's solve does not.  Also
-// rewinds the work queue for the next persistent launch.
-// With budget_only set, a miss that the stall rule stopped before the
-// iteration budget (iters_out < iters) is not solved again: its residual
-// trace already showed it far from the target and no longer closing in.
+// NaN, and that fallback_takes selects, goes to the fallback list, to be
+// solved again from the cold start.  The list order depends on timing; each
+// trajectory's solve does not.  Also rewinds the work queue for the next
+// persistent launch.
 __global__ void fallback_compact_kernel(const SolveArgs* __restrict__ warm, const int2* __restrict__ items, int total,
                                         int2* __restrict__ fb_items, int* __restrict__ fb_count,
-                                        unsigned long long* scratch, int budget_only)
+                                        unsigned long long* scratch, int mode, float near)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) scratch[0] = 0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -1945,8 +1958,8 @@ __global__ void fallback_compact_kernel(const SolveArgs* __restrict__ warm, cons
         const float* r = A.resid_out + (size_t)sl.y * 4;
         const float conv = fmaxf(fmaxf(r[0], r[1]), r[2]);
         const bool nan = isnan(r[0]) || isnan(r[1]) || isnan(r[2]);
-        if (!nan && conv <= A.tol) continue;
-        if (budget_only && !nan && A.iters_out && A.iters_out[sl.y] < A.iters) continue;
+        const int run = A.iters_out ? A.iters_out[sl.y] : A.iters;
+        if (!fallback_takes(mode, near, nan, conv, A.tol, run, A.iters)) continue;
         fb_items[atomicAdd(fb_count, 1)] = sl;
     }
 }
@@ -2712,7 +2725,8 @@ struct mmpc_batch {
     int2* d_items = nullptr;
     int2* d_fb_items = nullptr;               // fallback list
     int* d_counts = nullptr;                  // [0] items, [1] fallback items, [2 + g] items of group g
-    int fallback = 0;  // 0 off, 1 every miss, 2 misses that ran the whole budget
+    int fallback = 0;  // 0 off, 1 every miss, 2 misses that ran the whole budget, 3 of those the near misses
+    float near = 5.f;  // mode 3: a near miss has residual <= near x tol
     // one context of variant 3 for every scene: the solve runs on the
     // tensor-core kernel over items of 32 goals (the fallback stays FP32)
     bool tc = false;     // the batch can run on the tensor-core kernel
@@ -3115,12 +3129,16 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
                                                                                 b->d_scratch, b->d_scratch);
         }
         if (b->timing[1]) cudaEventRecord(b->timing[1], st);
-        if (b->fallback && b->any_warm && b->use_tc) {
+        if (b->fallback && b->any_warm && b->use_tc && b->fallback != 3) {
             // the misses of each scene, in its slot order, solved again from
-            // the cold start on the tensor-core kernel (one item per scene)
+            // the cold start on the tensor-core kernel (one item per scene).
+            // The near misses of mode 3 (a few per scene) go to the pair
+            // kernel below instead: one CTA per trajectory, where a
+            // tensor-core item of a few goals would leave most of its
+            // sub-partition's 32 lanes idle.
             const mmpc_ctx* c = b->scenes[0].ctx;
             cudaMemsetAsync(b->d_tc_fb, 0, sizeof(int) * 4, st);
-            tc_fallback_compact<<<b->S, 256, 0, st>>>(b->d_args, b->d_tc_off, b->d_tc_order + 4, b->fallback == 2,
+            tc_fallback_compact<<<b->S, 256, 0, st>>>(b->d_args, b->d_tc_off, b->d_tc_order + 4, b->fallback, b->near,
                                                      b->d_tc_fb + 4, b->d_tc_fb_items, b->d_counts + 1);
             if (b->timing[2]) cudaEventRecord(b->timing[2], st);
             TcArgs T{};
@@ -3146,7 +3164,7 @@ extern "C" int mmpc_batch_run(mmpc_batch* b, void* stream)
             if (b->timing[3]) cudaEventRecord(b->timing[3], st);
         } else if (b->fallback && b->any_warm) {
             fallback_compact_kernel<<<std::min(1024, (b->total + 255) / 256), 256, 0, st>>>(
-                b->d_args, b->d_items, b->total, b->d_fb_items, b->d_counts + 1, b->d_scratch, b->fallback == 2);
+                b->d_args, b->d_items, b->total, b->d_fb_items, b->d_counts + 1, b->d_scratch, b->fallback, b->near);
             if (b->timing[2]) cudaEventRecord(b->timing[2], st);
             reinterpret_cast<KernT>(b->kern)<<<b->grid, b->threads, b->smem, st>>>(b->d_args_cold, b->d_fb_items,
                                                                                 b->d_counts + 1, b->d_scratch,
@@ -3235,8 +3253,17 @@ extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
 extern "C" int mmpc_batch_set_fallback(mmpc_batch* b, int on)
 {
     if (!b) return batch_fail("mmpc_batch_set_fallback: NULL batch", MMPC_ERR_NOT_SETUP);
-    if (on < 0 || on > 2) return batch_fail("mmpc_batch_set_fallback: mode must be 0, 1 or 2", MMPC_ERR_INVALID_ARG);
+    if (on < 0 || on > 3) return batch_fail("mmpc_batch_set_fallback: mode must be 0, 1, 2 or 3", MMPC_ERR_INVALID_ARG);
     b->fallback = on;
+    return MMPC_OK;
+}
+
+extern "C" int mmpc_batch_set_fallback_near(mmpc_batch* b, float near)
+{
+    if (!b) return batch_fail("mmpc_batch_set_fallback_near: NULL batch", MMPC_ERR_NOT_SETUP);
+    if (!(near >= 1.f) || !std::isfinite(near))
+        return batch_fail("mmpc_batch_set_fallback_near: the factor must be finite and >= 1", MMPC_ERR_INVALID_ARG);
+    b->near = near;
     return MMPC_OK;
 }
 

@@ -167,12 +167,12 @@ __global__ void tc_order_scatter(const float* __restrict__ goals, int B, int* __
 
 // Misses of a warm-started scene for the cold fallback on the tensor cores
 // (one CTA per scene): the trajectories whose convergence residual missed
-// tol (or is NaN) -- with budget_only, those that also ran the whole budget
-// -- written in the scene's slot order to its segment of `list`, and the
+// tol (or is NaN), as selected by the fallback mode (fallback_takes) --
+// written in the scene's slot order to its segment of `list`, and the
 // scene's item (scene, 0, count, segment offset); counts added to *total.
 __global__ void __launch_bounds__(256) tc_fallback_compact(const SolveArgs* __restrict__ sc,
                                                            const int* __restrict__ scene_off,
-                                                           const int* __restrict__ order, int budget_only,
+                                                           const int* __restrict__ order, int mode, float near,
                                                            int* __restrict__ list, int4* __restrict__ items,
                                                            int* __restrict__ total)
 {
@@ -192,8 +192,7 @@ __global__ void __launch_bounds__(256) tc_fallback_compact(const SolveArgs* __re
             const float* r = A.resid_out + (size_t)i * 4;
             const bool nan = isnan(r[0]) || isnan(r[1]) || isnan(r[2]);
             const float conv = fmaxf(fmaxf(r[0], r[1]), r[2]);
-            miss = nan || !(conv <= A.tol);
-            if (miss && budget_only && !nan && A.iters_out && A.iters_out[i] < A.iters) miss = false;
+            miss = fallback_takes(mode, near, nan, conv, A.tol, A.iters_out ? A.iters_out[i] : A.iters, A.iters);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, miss);
         if (lane == 0) warp_cnt[w] = __popc(bal);

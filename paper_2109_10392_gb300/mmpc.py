@@ -31,7 +31,7 @@ MMPC_META_ABS = 2
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
             "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
             "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
-            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_set_timing", "mmpc_batch_fallbacks", "mmpc_step_host",
+            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_set_fallback_near", "mmpc_batch_set_timing", "mmpc_batch_fallbacks", "mmpc_step_host",
             "mmpc_measure_peaks", "mmpc_status", "mmpc_batch_status", "mmpc_debug_expire_wait")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
@@ -152,6 +152,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_step_host.restype = ctypes.c_int
     L.mmpc_batch_set_fallback.argtypes = [vp, ctypes.c_int]
     L.mmpc_batch_set_fallback.restype = ctypes.c_int
+    L.mmpc_batch_set_fallback_near.argtypes = [vp, ctypes.c_float]
+    L.mmpc_batch_set_fallback_near.restype = ctypes.c_int
     L.mmpc_batch_set_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
     L.mmpc_batch_set_timing.restype = ctypes.c_int
     L.mmpc_batch_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
@@ -576,11 +578,15 @@ class Batch:
         out.S = S
         return out
 
-    def set_fallback(self, on) -> None:
+    def set_fallback(self, on, near=None) -> None:
         """False / 0: off; True / 1: every warm-started miss; 2: only the misses
-        that ran the whole iteration budget (not stopped by the stall rule)."""
+        that ran the whole iteration budget (not stopped by the stall rule);
+        3: of those only the near misses, residual <= near x tol (near: the
+        factor, kept when None; default 5)."""
         mode = int(on) if not isinstance(on, bool) else (1 if on else 0)
         rc = lib().mmpc_batch_set_fallback(self.handle, mode)
+        if rc == MMPC_OK and near is not None:
+            rc = lib().mmpc_batch_set_fallback_near(self.handle, float(near))
         if rc != MMPC_OK:
             _err(None, rc)
 

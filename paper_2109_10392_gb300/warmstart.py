@@ -241,12 +241,14 @@ def validation_loss(ws: WarmStart, X, T):
 
 def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256, seed: int = 10**6,
              reps: int = 3, tol: float = 1e-2, obstacles=None, x_range=None, plain: bool = False,
-             stall: tuple | None = None, keep: bool = False, precision: int = 0):
+             stall: tuple | None = None, keep: bool = False, precision: int = 0, near: float = 5.0):
     """Cold start against warm start (+ cold fallback) on S fresh scenes x B
     goals, each timed as one CUDA graph replay (warm: features, network,
     decode, solve, fallback solve, score).  Returns a dict of results.  With
     the stall stop, a fourth variant falls back only the misses that ran the
-    whole budget (`warm_fallback_budget`, mmpc_batch_set_fallback mode 2).
+    whole budget (`warm_fallback_budget`, mmpc_batch_set_fallback mode 2), and a
+    fifth only the near misses among those, residual <= near x tol
+    (`warm_fallback_near`, mode 3).
     With precision (an MMPC_PREC_* other than FP32), the batched solves run on
     the tensor-core kernel (variant 3); the plain method and the cold fallback
     stay FP32.  With keep, out["_keep"] holds the warm-started batch, its step function,
@@ -336,7 +338,8 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
     warm.set_fallback(False)
     g_w, ms = timed(warm_step)
     stats(warm, ms, "warm")
-    warm_conv = (warm.flat["resid"].view(-1, 4)[:, :3].max(dim=1).values <= tol)
+    warm_resid = warm.flat["resid"].view(-1, 4)[:, :3].max(dim=1).values.clone()
+    warm_conv = warm_resid <= tol
     warm_iters = warm.flat["iters"].clone()
     out["warm"]["misses"] = int((~warm_conv).sum().item())
     del g_w
@@ -351,6 +354,17 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
         out["warm_fallback_budget"]["budget_misses"] = int(budget_miss.sum().item())
         out["warm_fallback_budget"]["passes"] = int((warm_iters.to(torch.int64) + 1).sum().item() +
                                                     (cold.flat["iters"].to(torch.int64) + 1)[budget_miss].sum().item())
+    g_fb3 = None
+    if stall is not None:
+        # only the near misses (residual <= near x tol) that ran the whole budget
+        warm.set_fallback(3, near=near)
+        g_fb3, ms = timed(warm_step)
+        stats(warm, ms, "warm_fallback_near")
+        out["warm_fallback_near"]["fallbacks"] = warm.fallbacks()
+        out["warm_fallback_near"]["near"] = near
+        near_miss = (~warm_conv) & (warm_iters == int(pb["iters"])) & (warm_resid <= near * tol)
+        out["warm_fallback_near"]["passes"] = int((warm_iters.to(torch.int64) + 1).sum().item() +
+                                                  (cold.flat["iters"].to(torch.int64) + 1)[near_miss].sum().item())
     warm.set_fallback(True)
     g_f, ms = timed(warm_step)
     stats(warm, ms, "warm_fallback")
@@ -385,10 +399,11 @@ def evaluate(ws: WarmStart, cfg: WarmConfig, device, S: int = 4096, B: int = 256
         out["speedup_converged_per_s"] = out["warm_fallback"]["converged_per_s"] / out["cold"]["converged_per_s"]
     if keep:
         out["_keep"] = dict(warm=warm, cold=cold, step=warm_step, stream=stream, table=table, buf=buf,
-                            graphs=dict(cold=g_cold, warm_fallback=g_f, warm_fallback_budget=g_fb2),
+                            graphs=dict(cold=g_cold, warm_fallback=g_f, warm_fallback_budget=g_fb2,
+                                        warm_fallback_near=g_fb3),
                             inputs=dict(ego=ego, obst=obst, goals=goals))
         return out
-    del g_cold, g_f, g_fb2
+    del g_cold, g_f, g_fb2, g_fb3
     cold.close()
     warm.close()
     return out
