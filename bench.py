@@ -532,6 +532,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"highway_batch_S{S}_B16-512_m5-40_N{'-'.join(map(str, Ns))}_n12_K100_tol{TOL:g}",
                    "scenes_per_gpu": S, "trajectories_per_gpu": Btot, "schedule": schedule,
+                   "launch_shapes": bt.describe()["launches"],
                    "stall_stop": list(STALL) if args.stall else None,
                    "graph": "one CUDA graph replay per step", "start": "cold",
                    "l2": "flushed between timed steps (256 MiB memset outside the event brackets)"},

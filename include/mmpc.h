@@ -273,6 +273,24 @@ int mmpc_batch_set_schedule(mmpc_batch* b, int schedule);
  * of the same signature takes it without timing.  Synchronous. */
 int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen);
 
+/* One persistent solve launch of a batch's current schedule (what
+ * mmpc_batch_autotune chose, or mmpc_batch_set_schedule set). */
+typedef struct {
+    int kernel;        /* 0 the FP32 pair kernel (one CTA per trajectory), 1 the tensor-core kernel */
+    int threads;       /* threads per CTA */
+    int grid;          /* persistent CTAs */
+    int smem_bytes;    /* dynamic shared memory per CTA */
+    int trajectories;  /* goals the launch solves */
+} mmpc_launch_shape;
+
+/* The solve launches mmpc_batch_run enqueues in the current schedule: one
+ * for schedules 1-3 and 5, one per horizon group for schedule 4 (CTA size
+ * ceil(N / 2) rounded up to whole warps).  *schedule receives the schedule
+ * and *launches the count (either may be NULL); the first min(count, max)
+ * shapes go to out (may be NULL when max is 0).  Host-side, no device call
+ * except a device attribute query. */
+int mmpc_batch_describe(mmpc_batch* b, int* schedule, int* launches, mmpc_launch_shape* out, int max);
+
 /* Solves and scores every scene of the batch on `stream` (asynchronous).
  * With the fallback on, the trajectories of warm-started scenes whose
  * convergence residual (largest of resid_out[0..2]) missed the scene's

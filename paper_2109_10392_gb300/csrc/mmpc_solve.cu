@@ -3250,6 +3250,32 @@ extern "C" int mmpc_batch_autotune(mmpc_batch* b, void* stream, int* chosen)
     return rc;
 }
 
+extern "C" int mmpc_batch_describe(mmpc_batch* b, int* schedule, int* launches, mmpc_launch_shape* out, int max)
+{
+    if (!b) return batch_fail("mmpc_batch_describe: NULL batch", MMPC_ERR_NOT_SETUP);
+    if (max < 0 || (max > 0 && !out)) return batch_fail("mmpc_batch_describe: bad output array", MMPC_ERR_INVALID_ARG);
+    std::vector<mmpc_launch_shape> v;
+    if (b->use_tc) {
+        int sms = b->scenes[0].ctx->sm_count;
+        if (sms < 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaGetLastError();
+        }
+        v.push_back({1, mmpc::TC_THREADS, std::max(1, std::min(sms, (b->tc_items + 3) / 4)), (int)b->tc_smem_bytes,
+                     b->total});
+    } else if (b->schedule == 4) {
+        for (const auto& g : b->groups) v.push_back({0, g.threads, g.grid, (int)g.smem, g.total});
+    } else {
+        v.push_back({0, b->threads, b->grid, (int)b->smem, b->total});
+    }
+    if (schedule) *schedule = b->schedule;
+    if (launches) *launches = (int)v.size();
+    for (int i = 0; i < std::min(max, (int)v.size()); ++i) out[i] = v[i];
+    return MMPC_OK;
+}
+
 extern "C" int mmpc_batch_set_fallback(mmpc_batch* b, int on)
 {
     if (!b) return batch_fail("mmpc_batch_set_fallback: NULL batch", MMPC_ERR_NOT_SETUP);

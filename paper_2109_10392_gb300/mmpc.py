@@ -31,7 +31,7 @@ MMPC_META_ABS = 2
 EXPORTED = ("mmpc_problem_size", "mmpc_build", "mmpc_setup", "mmpc_solve", "mmpc_score", "mmpc_destroy",
             "mmpc_last_error", "mmpc_version", "mmpc_score_static", "mmpc_take_work_count", "mmpc_batch_create",
             "mmpc_batch_set_schedule", "mmpc_batch_autotune", "mmpc_batch_run", "mmpc_batch_times",
-            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_set_fallback_near", "mmpc_batch_set_timing", "mmpc_batch_fallbacks", "mmpc_step_host",
+            "mmpc_batch_destroy", "mmpc_batch_set_fallback", "mmpc_batch_set_fallback_near", "mmpc_batch_describe", "mmpc_batch_set_timing", "mmpc_batch_fallbacks", "mmpc_step_host",
             "mmpc_measure_peaks", "mmpc_status", "mmpc_batch_status", "mmpc_debug_expire_wait")
 MMPC_STATIC_SCORE_MAX_B = 65536
 
@@ -67,6 +67,11 @@ class MmpcMeta(ctypes.Structure):
         ("y_ref", ctypes.c_float),
         ("psi_max", ctypes.c_float),
     ]
+
+
+class MmpcLaunchShape(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("threads", ctypes.c_int), ("grid", ctypes.c_int),
+                ("smem_bytes", ctypes.c_int), ("trajectories", ctypes.c_int)]
 
 
 class MmpcScene(ctypes.Structure):
@@ -154,6 +159,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.mmpc_batch_set_fallback.restype = ctypes.c_int
     L.mmpc_batch_set_fallback_near.argtypes = [vp, ctypes.c_float]
     L.mmpc_batch_set_fallback_near.restype = ctypes.c_int
+    L.mmpc_batch_describe.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(MmpcLaunchShape), ctypes.c_int]
+    L.mmpc_batch_describe.restype = ctypes.c_int
     L.mmpc_batch_set_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
     L.mmpc_batch_set_timing.restype = ctypes.c_int
     L.mmpc_batch_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
@@ -631,6 +639,21 @@ class Batch:
         if rc != MMPC_OK:
             _err(None, rc)
         return int(chosen.value)
+
+    def describe(self) -> dict:
+        """The current schedule and its solve launches: a list of dicts with
+        kernel ("fp32 pair" or "tensor cores"), threads, grid, smem_bytes and
+        trajectories (one per horizon group in schedule 4)."""
+        sch, n = ctypes.c_int(0), ctypes.c_int(0)
+        rc = lib().mmpc_batch_describe(self.handle, ctypes.byref(sch), ctypes.byref(n), None, 0)
+        if rc == MMPC_OK and n.value > 0:
+            arr = (MmpcLaunchShape * n.value)()
+            rc = lib().mmpc_batch_describe(self.handle, None, None, arr, n.value)
+        if rc != MMPC_OK:
+            _err(None, rc)
+        return dict(schedule=int(sch.value), launches=[
+            dict(kernel="tensor cores" if a.kernel == 1 else "fp32 pair", threads=a.threads, grid=a.grid,
+                 smem_bytes=a.smem_bytes, trajectories=a.trajectories) for a in (arr if n.value > 0 else [])])
 
     def run(self, stream=None) -> None:
         rc = lib().mmpc_batch_run(self.handle, _stream(stream))

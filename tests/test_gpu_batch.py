@@ -111,6 +111,17 @@ def test_autotune_and_graph_replay(mixed):
     with torch.cuda.stream(stream):
         chosen = bt.autotune()
     assert chosen in (1, 2, 3, 4)
+    # the launch shapes of the choice: one per horizon group in schedule 4
+    # (whole warps, one CTA per trajectory, every trajectory once), else one
+    for sch in (1, 4, chosen):
+        bt.set_schedule(sch)
+        d = bt.describe()
+        assert d["schedule"] == sch
+        warps = {-(-((sc["params"]["N"] + 1) // 2) // 32) for sc in sds}  # CTA size in warps per scene
+        assert len(d["launches"]) == (len(warps) if sch == 4 else 1), (sch, d)
+        assert sum(x["trajectories"] for x in d["launches"]) == sum(int(sc["goals"].shape[0]) for sc in sds)
+        for x in d["launches"]:
+            assert x["kernel"] == "fp32 pair" and x["threads"] % 32 == 0 and x["grid"] >= 1 and x["smem_bytes"] > 0
     with torch.cuda.stream(stream):
         bt.run()
     torch.cuda.synchronize()

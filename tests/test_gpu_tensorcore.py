@@ -256,6 +256,11 @@ def test_batch_schedules_and_autotune():
     assert np.array_equal(bt.flat["coef"].view(-1, 3 * n)[:B].double().cpu().numpy(), one["coef"])
     with pytest.raises(mmpc.MmpcError):
         ref.set_schedule(5)
+    bt.set_schedule(5)
+    d = bt.describe()
+    assert d["schedule"] == 5 and len(d["launches"]) == 1
+    x = d["launches"][0]
+    assert x["kernel"] == "tensor cores" and x["threads"] == 384 and x["trajectories"] == S * B and x["grid"] >= 1
     chosen = bt.autotune()
     assert chosen in (1, 2, 3, 4, 5)
     again = _batch(p3, ego, obst, goals)
